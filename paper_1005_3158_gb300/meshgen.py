@@ -1,0 +1,331 @@
+"""Seeded synthetic inputs: linear-tet casting/mold meshes and their problem data.
+
+This module only *builds inputs* (coordinates, connectivity, material ids,
+boundary faces, initial temperatures, permutations).  It holds none of the
+method's arithmetic: no element matrices, no capacities, no enthalpy relation.
+Both the CUDA path and the FP64 oracle consume what it produces.
+
+The paper's own meshes (six casting+mold cases, Section 5, Table 2) are not
+available, so every workload is a jittered structured hex grid, each hex split
+into the 6 Kuhn (Freudenthal) tetrahedra along its main diagonal, with
+materials tagged by tet centroid.  All randomness comes from
+``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+
+import numpy as np
+
+# Material table rows: (rho, c, k, latent, T_solidus, T_liquidus).
+# The alloy is the Al-like casting alloy of the unit-cube and casting
+# workloads; steel is the mold / core material (no phase change).
+ALLOY = (2700.0, 900.0, 150.0, 3.9e5, 821.0, 913.0)
+STEEL = (7800.0, 460.0, 30.0, 0.0, 0.0, 0.0)
+
+T_POUR = 973.0     # alloy pouring temperature, Eq. 2
+T_MOLD = 300.0     # mold initial temperature
+T_AMB = 300.0      # ambient of the Robin faces, Eq. 4
+H_AMB = 1000.0     # heat-transfer coefficient of the Robin faces, Eq. 4
+
+
+@dataclasses.dataclass
+class Problem:
+    """A complete heat-conduction problem on a linear-tet mesh (Section 3)."""
+    xyz: np.ndarray          # [N,3] float64, metres
+    tets: np.ndarray         # [E,4] int32, 0-based node ids (either orientation)
+    mat: np.ndarray          # [E] int32 material id
+    materials: np.ndarray    # [M,6] float64 rows (rho, c, k, latent, Ts, Tl)
+    faces: np.ndarray        # [F,3] int32 Robin faces (node ids)
+    h: np.ndarray            # [F] float64 W/m^2K
+    t_inf: np.ndarray        # [F] float64 K
+    q: np.ndarray            # [F] float64 W/m^2 (prescribed outward flux)
+    T0: np.ndarray           # [N] float64 initial temperature, Eq. 2
+    dir_nodes: np.ndarray = dataclasses.field(
+        default_factory=lambda: np.zeros(0, np.int32))   # Dirichlet nodes, Eq. 3
+    dir_T: np.ndarray = dataclasses.field(
+        default_factory=lambda: np.zeros(0, np.float64))
+    name: str = ""
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def n_tets(self) -> int:
+        return int(self.tets.shape[0])
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.faces.shape[0])
+
+
+def rng_of(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# --------------------------------------------------------------------------
+# Structured grid -> Kuhn tetrahedra
+# --------------------------------------------------------------------------
+
+# The six Kuhn tets of the unit cube along the diagonal (0,0,0)-(1,1,1): one
+# per ordering of the three axes; each walks 000 -> +e_p0 -> +e_p1 -> 111.
+def _kuhn_corner_offsets() -> np.ndarray:
+    out = []
+    for perm in itertools.permutations(range(3)):
+        p = [0, 0, 0]
+        path = [tuple(p)]
+        for ax in perm:
+            p[ax] = 1
+            path.append(tuple(p))
+        out.append(path)
+    return np.asarray(out, dtype=np.int64)  # [6,4,3]
+
+
+_KUHN = _kuhn_corner_offsets()
+
+
+def box_grid(nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 1.0,
+             lz: float = 1.0, jitter: float = 0.0, seed: int | None = None):
+    """Nodes and Kuhn tets of an nx x ny x nz hex grid on [0,lx]x[0,ly]x[0,lz].
+
+    ``jitter`` moves every interior node by an independent uniform offset in
+    [-jitter, +jitter] x spacing along each axis (boundary nodes stay on the
+    box so the Robin faces stay planar).  Returns (xyz, tets, hex_index,
+    node_flags) where node_flags has bit 2*a (low) / 2*a+1 (high) set for a
+    node on the low / high boundary plane of axis a.
+    """
+    ii, jj, kk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1),
+                             np.arange(nz + 1), indexing="ij")
+    # node id = i + (nx+1)*(j + (ny+1)*k)
+    ii = ii.transpose(2, 1, 0).ravel()
+    jj = jj.transpose(2, 1, 0).ravel()
+    kk = kk.transpose(2, 1, 0).ravel()
+    h = np.array([lx / nx, ly / ny, lz / nz])
+    xyz = np.stack([ii * h[0], jj * h[1], kk * h[2]], axis=1).astype(np.float64)
+    flags = ((ii == 0) * 1 | (ii == nx) * 2 | (jj == 0) * 4 | (jj == ny) * 8
+             | (kk == 0) * 16 | (kk == nz) * 32).astype(np.int32)
+    if jitter > 0.0:
+        rng = rng_of(0 if seed is None else seed)
+        interior = flags == 0
+        d = rng.uniform(-jitter, jitter, size=(int(interior.sum()), 3)) * h
+        xyz[interior] += d
+    hi, hj, hk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz),
+                             indexing="ij")
+    hi = hi.transpose(2, 1, 0).ravel()
+    hj = hj.transpose(2, 1, 0).ravel()
+    hk = hk.transpose(2, 1, 0).ravel()
+    nh = hi.size
+    tets = np.empty((nh, 6, 4), dtype=np.int64)
+    sx, sy = nx + 1, (nx + 1) * (ny + 1)
+    for t in range(6):
+        for c in range(4):
+            o = _KUHN[t, c]
+            tets[:, t, c] = (hi + o[0]) + sx * (hj + o[1]) + sy * (hk + o[2])
+    hex_index = np.repeat(np.arange(nh), 6)
+    return xyz, tets.reshape(-1, 4).astype(np.int32), hex_index, flags
+
+
+_FACE_OMIT = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+
+
+def box_boundary_faces(tets: np.ndarray, node_flags: np.ndarray,
+                       plane_mask: int = 63) -> np.ndarray:
+    """Tet faces lying on the box boundary planes selected by ``plane_mask``.
+
+    A face is on the boundary exactly when its three nodes share one boundary
+    plane (no interior face of a box grid lies in a boundary plane).
+    """
+    out = []
+    for omit in _FACE_OMIT:
+        f = tets[:, omit]
+        common = (node_flags[f[:, 0]] & node_flags[f[:, 1]]
+                  & node_flags[f[:, 2]] & plane_mask)
+        out.append(f[common != 0])
+    return np.concatenate(out, axis=0).astype(np.int32)
+
+
+def centroids(xyz: np.ndarray, tets: np.ndarray) -> np.ndarray:
+    c = np.zeros((tets.shape[0], 3))
+    for k in range(4):
+        c += xyz[tets[:, k]]
+    return c * 0.25
+
+
+def _node_touches(n_nodes: int, tets: np.ndarray, elem_mask: np.ndarray) -> np.ndarray:
+    touch = np.zeros(n_nodes, dtype=bool)
+    touch[tets[elem_mask].ravel()] = True
+    return touch
+
+
+def _robin(faces: np.ndarray, h: float = H_AMB, t_inf: float = T_AMB):
+    nf = faces.shape[0]
+    return (np.full(nf, h), np.full(nf, t_inf), np.zeros(nf))
+
+
+# --------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------
+
+def unit_cube(n: int = 20, h: float = H_AMB, jitter: float = 0.0,
+              seed: int = 1000) -> Problem:
+    """Unit cube, n^3 hexes x 6 Kuhn tets, one alloy, T0 = 973 K, Robin h to
+    300 K on every boundary triangle.  n = 20 gives 9,261 nodes, 48,000 tets
+    and 4,800 boundary triangles."""
+    xyz, tets, _, flags = box_grid(n, n, n, jitter=jitter, seed=seed)
+    faces = box_boundary_faces(tets, flags)
+    hh, ti, q = _robin(faces, h=h)
+    return Problem(xyz=xyz, tets=tets, mat=np.zeros(tets.shape[0], np.int32),
+                   materials=np.array([ALLOY]), faces=faces, h=hh, t_inf=ti,
+                   q=q, T0=np.full(xyz.shape[0], T_POUR), name=f"unit_cube_{n}")
+
+
+def flanged_casting(nx: int = 70, ny: int = 70, nz: int = 68,
+                    seed: int = 1005, flange_r: float = 0.15,
+                    flange_t: float = 0.03, body_r: float = 0.10,
+                    body_h: float = 0.30, dims=(0.40, 0.40, 0.50)) -> Problem:
+    """Flanged-cylinder alloy casting inside a steel box mold.
+
+    Box mold dims[0] x dims[1] x dims[2] m; the cavity is a cylinder of radius
+    body_r and height body_h, axis along z through the box centre, centred in
+    z, with a flange disc (radius flange_r, thickness flange_t) at its bottom.
+    Tets whose centroid lies in the cavity are alloy (material 0), the rest
+    steel (material 1).  Interior nodes are jittered by +-5% of the spacing.
+    Alloy-touching nodes start at 973 K, the others at 300 K.  The outer mold
+    faces are Robin faces (h = 1000 W/m^2K to 300 K).  The default grid
+    70 x 70 x 68 gives 1,999,200 tets.
+    """
+    lx, ly, lz = dims
+    xyz, tets, _, flags = box_grid(nx, ny, nz, lx, ly, lz, jitter=0.05, seed=seed)
+    c = centroids(xyz, tets)
+    r = np.hypot(c[:, 0] - lx / 2, c[:, 1] - ly / 2)
+    z0 = (lz - body_h) / 2
+    body = (r <= body_r) & (c[:, 2] >= z0) & (c[:, 2] <= z0 + body_h)
+    flange = (r <= flange_r) & (c[:, 2] >= z0) & (c[:, 2] <= z0 + flange_t)
+    alloy = body | flange
+    mat = np.where(alloy, 0, 1).astype(np.int32)
+    faces = box_boundary_faces(tets, flags)
+    hh, ti, q = _robin(faces)
+    T0 = np.where(_node_touches(xyz.shape[0], tets, alloy), T_POUR, T_MOLD)
+    return Problem(xyz=xyz, tets=tets, mat=mat, materials=np.array([ALLOY, STEEL]),
+                   faces=faces, h=hh, t_inf=ti, q=q, T0=T0.astype(np.float64),
+                   name=f"flanged_casting_{nx}x{ny}x{nz}")
+
+
+def block_with_cores(n: int = 220, n_cores: int = 32, seed: int = 1007,
+                     side: float = 1.0) -> Problem:
+    """Alloy block (side^3 m, n^3 hexes, 5% jitter) with seeded spherical
+    steel cores.
+
+    Core centres are uniform in the box shrunk by the largest radius, radii
+    uniform in [3%, 8%] of the side.  A tet whose centroid falls in any sphere
+    is steel (material 1), otherwise alloy (material 0).  Alloy-touching nodes
+    start at 973 K, core-only nodes at 300 K.  Robin h = 1000 W/m^2K to 300 K
+    on all outer faces.  n = 220 gives 63,888,000 tets and 10,793,861 nodes.
+    """
+    xyz, tets, _, flags = box_grid(n, n, n, side, side, side, jitter=0.05, seed=seed)
+    rng = rng_of(seed + 1)
+    radii = rng.uniform(0.03, 0.08, size=n_cores) * side
+    centres = rng.uniform(0.08 * side, 0.92 * side, size=(n_cores, 3))
+    steel = np.zeros(tets.shape[0], dtype=bool)
+    chunk = 1 << 22
+    for s in range(0, tets.shape[0], chunk):
+        c = centroids(xyz, tets[s:s + chunk])
+        m = np.zeros(c.shape[0], dtype=bool)
+        for cc, rr in zip(centres, radii):
+            m |= ((c - cc) ** 2).sum(axis=1) <= rr * rr
+        steel[s:s + chunk] = m
+    mat = steel.astype(np.int32)
+    faces = box_boundary_faces(tets, flags)
+    hh, ti, q = _robin(faces)
+    T0 = np.where(_node_touches(xyz.shape[0], tets, ~steel), T_POUR, T_MOLD)
+    return Problem(xyz=xyz, tets=tets, mat=mat, materials=np.array([ALLOY, STEEL]),
+                   faces=faces, h=hh, t_inf=ti, q=q, T0=T0.astype(np.float64),
+                   name=f"block_with_cores_{n}")
+
+
+def random_small(seed: int, nx: int = 5, ny: int = 4, nz: int = 3,
+                 n_mat: int = 2, permute: bool = True,
+                 robin_fraction: float = 0.7) -> Problem:
+    """A small randomised problem for parity tests.
+
+    Jittered box (interior jitter 15% of spacing), random material per hex
+    (alloy-like phase-change materials with random ranges, plus steel-like
+    materials), random T0 in [300, 1000] K, a random subset of the boundary
+    triangles as Robin faces with random h, T_inf and q, and (optionally)
+    random node and element permutations.  Nodes shared by phase-change
+    materials with different ranges cannot occur: all phase-change materials
+    share one (Ts, Tl).
+    """
+    rng = rng_of(seed)
+    lx, ly, lz = rng.uniform(0.05, 0.2, size=3)
+    xyz, tets, hexi, flags = box_grid(nx, ny, nz, lx, ly, lz, jitter=0.15, seed=seed)
+    ts = rng.uniform(700.0, 850.0)
+    tl = ts + rng.uniform(5.0, 120.0)
+    mats = []
+    for m in range(n_mat):
+        if m % 2 == 0:
+            mats.append((rng.uniform(2000, 3000), rng.uniform(700, 1000),
+                         rng.uniform(50, 200), rng.uniform(1e5, 4e5), ts, tl))
+        else:
+            mats.append((rng.uniform(7000, 8000), rng.uniform(400, 600),
+                         rng.uniform(10, 50), 0.0, 0.0, 0.0))
+    hex_mat = rng.integers(0, n_mat, size=nx * ny * nz)
+    mat = hex_mat[hexi].astype(np.int32)
+    faces = box_boundary_faces(tets, flags)
+    keep = rng.random(faces.shape[0]) < robin_fraction
+    faces = faces[keep]
+    nf = faces.shape[0]
+    h = rng.uniform(100.0, 3000.0, size=nf)
+    t_inf = rng.uniform(280.0, 400.0, size=nf)
+    q = rng.uniform(-2e4, 2e4, size=nf)
+    T0 = rng.uniform(300.0, 1000.0, size=xyz.shape[0])
+    p = Problem(xyz=xyz, tets=tets, mat=mat, materials=np.array(mats), faces=faces,
+                h=h, t_inf=t_inf, q=q, T0=T0, name=f"random_small_{seed}")
+    if permute:
+        p = permute_nodes(p, rng_of(seed + 17))
+        p = permute_elements(p, rng_of(seed + 23))
+    return p
+
+
+# --------------------------------------------------------------------------
+# Orderings (inputs to the reordering experiments, Section 5.2)
+# --------------------------------------------------------------------------
+
+def permute_nodes(p: Problem, rng: np.random.Generator) -> Problem:
+    """Renumber nodes by a random permutation: old node i becomes new[i]."""
+    n = p.n_nodes
+    new = rng.permutation(n).astype(np.int64)
+    inv = np.empty(n, np.int64)
+    inv[new] = np.arange(n)
+    q = dataclasses.replace(p)
+    q.xyz = p.xyz[inv]
+    q.tets = new[p.tets].astype(np.int32)
+    q.faces = new[p.faces].astype(np.int32)
+    q.T0 = p.T0[inv]
+    q.dir_nodes = new[p.dir_nodes].astype(np.int32)
+    return q
+
+
+def permute_elements(p: Problem, rng: np.random.Generator) -> Problem:
+    perm = rng.permutation(p.n_tets)
+    q = dataclasses.replace(p)
+    q.tets = p.tets[perm]
+    q.mat = p.mat[perm]
+    # rotate each tet's corner list so corner order is not always the grid's
+    rot = rng.integers(0, 4, size=p.n_tets)
+    idx = (np.arange(4)[None, :] + rot[:, None]) % 4
+    q.tets = np.take_along_axis(q.tets, idx, axis=1).astype(np.int32)
+    return q
+
+
+def bar(n: int, length: float = 0.5, material=ALLOY, latent: float | None = None):
+    """A 1-hex-thick bar of n cubic hexes along x (cross-section
+    length/n x length/n); boundary flags returned for choosing BC faces."""
+    hsz = length / n
+    xyz, tets, _, flags = box_grid(n, 1, 1, length, hsz, hsz)
+    mats = np.array([material], dtype=np.float64)
+    if latent is not None:
+        mats[0, 3] = latent
+    return xyz, tets, flags, mats
