@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit EBE enthalpy step (tet-element updates/s).
+
+Default workload: ``block_with_cores_220`` -- a 1 m alloy block with 32
+seeded spherical steel cores, 220^3 hexes x 6 Kuhn tets = 63,888,000 tets,
+10,793,861 nodes, 5% nodal jitter, Robin on the outer faces, FP32 stepping
+with FP64 energy bookkeeping, block-partitioned atomic-free scatter.  One
+benchmark step is one explicit time step over the whole mesh (all kernels of
+the step).  Inputs (~2.7 GB of per-step traffic) are larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host instead (bounded sample of the same workload recipe).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="block_with_cores_220")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--variant", default="block", choices=["block", "atomic", "colored"])
+    ap.add_argument("--reorder", type=int, default=1)
+    ap.add_argument("--block-elems", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def make_problem(name: str):
+    from paper_1005_3158_gb300 import meshgen as mg
+    if name.startswith("block_with_cores_"):
+        return mg.block_with_cores(int(name.rsplit("_", 1)[1]))
+    if name.startswith("unit_cube_"):
+        return mg.unit_cube(int(name.rsplit("_", 1)[1]))
+    if name == "flanged_casting":
+        return mg.flanged_casting()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def make_problem_size(name: str) -> int:
+    """Number of tets of a named workload (without building it)."""
+    if name.startswith("block_with_cores_") or name.startswith("unit_cube_"):
+        return 6 * int(name.rsplit("_", 1)[1]) ** 3
+    if name == "flanged_casting":
+        return 6 * 70 * 70 * 68
+    raise SystemExit(f"unknown workload {name}")
+
+
+def sample_recipe(name: str, target_tets: float):
+    """A smaller problem with the same recipe (for the host-side oracle)."""
+    from paper_1005_3158_gb300 import meshgen as mg
+    n = max(4, int(round((target_tets / 6.0) ** (1.0 / 3.0))))
+    if name.startswith("block_with_cores_"):
+        return mg.block_with_cores(n), f"block_with_cores_{n}"
+    if name.startswith("unit_cube_"):
+        return mg.unit_cube(n), f"unit_cube_{n}"
+    return mg.flanged_casting(n, n, n), f"flanged_casting_{n}x{n}x{n}"
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload: str, seconds: float):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of
+    the same recipe; returns tet-updates/s."""
+    import oracle
+    p, name = sample_recipe(workload, 1.5e6)
+    o = oracle.OracleProblem(p)
+    o.set_temperature(p.T0)
+    dt = 0.9 * o.stable_dt()
+    o.step(1, dt)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 1000:
+            break
+    return {"value": p.n_tets * steps / el, "unit": "tet-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{name} ({p.n_tets} tets), {steps} FP64 steps, {el:.1f} s single-thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    # each step: one oracle time step on a sample sized so that the whole
+    # run stays within about two minutes
+    rate_guess = 3.0e7
+    full = make_problem_size(args.workload)
+    target = min(full, 8.0e6, max(5e4, 120.0 * rate_guess / max(1, args.steps + args.warmup)))
+    p, name = sample_recipe(args.workload, target)
+    o = oracle.OracleProblem(p)
+    o.set_temperature(p.T0)
+    dt = 0.9 * o.stable_dt()
+    o.step(args.warmup, dt)
+    t0 = time.perf_counter()
+    o.step(args.steps, dt)
+    el = time.perf_counter() - t0
+    val = p.n_tets * args.steps / el
+    line = {
+        "impl": "reference", "metric": "tet-element updates/s", "value": val,
+        "unit": "tet-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sample": name, "sample_tets": p.n_tets,
+                   "oracle": "plain FP64 C EBE solver, single thread"},
+        "cpu_baseline": {"value": val, "unit": "tet-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{name} ({p.n_tets} tets), {args.steps} steps"},
+        "e2e": {"value": val, "unit": "tet-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1005_3158_gb300 import fem
+
+    p = make_problem(args.workload)
+    t_setup = time.perf_counter()
+    mesh = fem.Mesh(p, args.precision, reorder=args.reorder, variant=args.variant,
+                    block_elems=args.block_elems, threads=args.threads)
+    dt = 0.9 * mesh.stable_dt()
+    stream = torch.cuda.Stream()
+    mesh.set_stream(stream.cuda_stream)
+    mesh.step(1, dt)
+    info = mesh.info()
+    t_setup = time.perf_counter() - t_setup
+    E, N = p.n_tets, p.n_nodes
+
+    # warm-up, then K timed steps between barriers, CUDA events on the stream
+    mesh.step(args.warmup, dt)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    mesh.step(args.steps, dt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = E * args.steps * world / (ms / 1e3)
+    kernels_per_step = 2 if info["n_shared_nodes"] > 0 or args.variant != "block" else 1
+    if args.variant != "block":
+        kernels_per_step = 3
+    n_launch_per_step = kernels_per_step
+    if args.variant == "colored":
+        n_launch_per_step = 2 + info["n_colors"]
+
+    # per-kernel device times (separate pass with events around each kernel)
+    kms = mesh.step_profile(args.profile_steps, dt) / max(1, args.profile_steps)
+    s = 4 if args.precision == "fp32" else 8
+    peak, peak_kind = hbm_peak()
+    if args.variant == "block":
+        n_int = info["n_interior_nodes"]
+        # algorithmic bytes: int32 connectivity + six stored conductances per
+        # tet, E read+write and C, Lc per node (stored-K^e EBE)
+        alg = [E * (16 + 6 * s) + n_int * 4 * s, (N - n_int) * 4 * s]
+        names = ["k_block_step", "k_shared_update"]
+    else:
+        alg = [N * 2 * s + N * 4 * s, E * (16 + 6 * s), N * 4 * s]
+        names = ["k_flat_temperature", "k_flat_elements", "k_flat_update"]
+    k_dom = int(np.argmax(kms))
+    achieved = alg[k_dom] / (kms[k_dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": names[k_dom], "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_source": peak_kind,
+                "alg_bytes_per_launch": int(alg[k_dom]),
+                "kernel_ms": {n: round(float(v), 4) for n, v in zip(names, kms)},
+                "step_alg_bytes_per_tet": round((E * (16 + 6 * s) + N * 4 * s) / E, 2)}
+
+    # end to end through the C ABI with pinned host buffers: every step
+    # uploads the state, steps once and reads the temperatures back
+    e2e = None
+    if not args.no_e2e:
+        ke = args.e2e_steps or args.steps
+        E_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        T_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        mesh.state(E_host.numpy())
+        mesh.set_state(E_host, 0, 0.0)
+        mesh.step(1, dt)
+        mesh.temperature(T_host)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            mesh.set_state(E_host, 0, 0.0)
+            mesh.step(1, dt)
+            mesh.temperature(T_host)
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": E * ke * world / el, "unit": "tet-updates/s",
+               "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline(args.workload, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "tet-element updates/s", "value": value, "unit": "tet-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_tets": E, "n_nodes": N,
+                       "n_faces": p.n_faces, "variant": args.variant,
+                       "precision": args.precision, "reorder": args.reorder,
+                       "n_blocks": info["n_blocks"], "threads": info["threads"],
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "dt_s": dt, "setup_s": round(t_setup, 1)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": n_launch_per_step * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,252 @@
+/*
+ * fem.h -- C ABI of libfem: the explicit element-by-element (EBE) enthalpy
+ * time step for transient heat conduction with phase change on linear
+ * tetrahedra, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: R. Tavakoli, "Improvement cache efficiency of explicit finite
+ * element procedure and its application to parallel casting solidification
+ * simulation" (arXiv 1005.3158): heat equation Eq. 1 with initial condition
+ * Eq. 2, Dirichlet Eq. 3 and flux/convective boundaries Eq. 4, in the
+ * enthalpy form Eq. 5 (H = integral of C dT, Eq. 11), Galerkin linear tets
+ * Eq. 9 with row-sum lumped capacity, explicit update Eq. 14 (theta = 0 of
+ * Eq. 10) evaluated as sums of element contributions, Eqs. 15-22.
+ *
+ * Conventions for every call
+ *   - All array arguments are HOST pointers unless stated otherwise.  The
+ *     library copies what it needs during the call; the caller keeps
+ *     ownership of its arrays and may free them when the call returns.
+ *     Output arrays are caller-allocated host arrays of the stated size.
+ *   - Node and element ids are 0-based.  All node-indexed inputs and outputs
+ *     use the CALLER's node order; any internal reordering is invisible.
+ *   - Units: SI (m, kg, s, K, J, W).
+ *   - Every call returns a fem_status and never aborts the process.  On an
+ *     error the object is left unchanged and fem_last_error() returns a
+ *     message for the calling thread.
+ *   - A fem_mesh is not thread-safe; use one mesh from one thread at a time.
+ *   - Device memory belongs to the library, allocated on the current CUDA
+ *     device the first time the mesh needs it and released by
+ *     fem_mesh_destroy.  Work is enqueued on the mesh's stream (the legacy
+ *     default stream unless fem_set_stream was called); the fem_get_* calls
+ *     synchronise that stream.
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fem_mesh fem_mesh; /* opaque; owned by the library until fem_mesh_destroy */
+
+typedef enum {
+    FEM_OK = 0,
+    FEM_EINVAL = 1,    /* invalid argument or mesh (message says which) */
+    FEM_ENOMEM = 2,    /* host or device allocation failed (nothing leaked) */
+    FEM_ECUDA = 3,     /* a CUDA runtime call failed, or no usable GPU */
+    FEM_ESTATE = 4,    /* call out of order (e.g. fem_step before materials) */
+    FEM_EUNSTABLE = 5, /* non-finite temperatures/energy: dt above the stable limit */
+    FEM_ETIMEOUT = 6   /* reserved: a bounded device wait gave up */
+} fem_status;
+
+typedef enum { FEM_FP64 = 0, FEM_FP32 = 1 } fem_precision;
+
+/* Scatter-add strategy of the element results into nodes (Eqs. 19-22).
+ *   FEM_VARIANT_BLOCK   -- default.  Elements are partitioned into blocks
+ *                          staged in shared memory; each node sums its
+ *                          element-corner results in a fixed order (no
+ *                          atomics, bit-reproducible); nodes shared between
+ *                          blocks exchange partial sums through a second
+ *                          kernel (the paper's exchange of calculated
+ *                          values between partitions, Eq. 22).
+ *   FEM_VARIANT_ATOMIC  -- every element adds its four results into a global
+ *                          nodal array with atomic adds (order-dependent
+ *                          rounding; for comparison).
+ *   FEM_VARIANT_COLORED -- elements are greedily coloured so that no two
+ *                          elements of one colour share a node; one launch
+ *                          per colour adds with plain read-modify-write
+ *                          (deterministic; for comparison). */
+typedef enum { FEM_VARIANT_BLOCK = 0, FEM_VARIANT_ATOMIC = 1, FEM_VARIANT_COLORED = 2 } fem_variant;
+
+/* One material (Section 2): density rho (kg/m^3), specific heat c (J/kgK),
+ * conductivity k (W/mK), latent heat (J/kg) released linearly between
+ * T_solidus and T_liquidus (K).  latent == 0 means no phase change (the
+ * two temperatures are then ignored); T_solidus == T_liquidus is an
+ * isothermal phase change. */
+typedef struct {
+    double rho, c, k, latent, T_solidus, T_liquidus;
+} fem_material;
+
+/* Options of fem_mesh_create_ex.  Zero-initialise and set what you need;
+ * zero fields take the defaults. */
+typedef struct {
+    int32_t variant;     /* fem_variant, default FEM_VARIANT_BLOCK */
+    int32_t block_elems; /* target elements per shared-memory block, 0 = auto
+                            (chosen from the precision and the GPU's shared
+                            memory); clamped to [64, 12288] */
+    int32_t threads;     /* threads per CTA of the block kernel, 0 = auto;
+                            one of 128, 256, 512 */
+    int32_t reserved[5];
+} fem_options;
+
+/* Statistics of the execution plan (fem_mesh_info). */
+typedef struct {
+    int64_t n_nodes, n_tets, n_faces;
+    int64_t n_blocks;          /* element blocks (block variant) */
+    int64_t n_interior_nodes;  /* nodes owned by exactly one block */
+    int64_t n_shared_nodes;    /* nodes touched by two or more blocks */
+    int64_t n_shared_copies;   /* (shared node, block) pairs */
+    int64_t n_sched_rounds;    /* 32-lane rounds of the node schedules */
+    int64_t n_colors;          /* colours (coloured variant), else 0 */
+    int64_t bandwidth_input;   /* max |i - j| over element node pairs, caller order */
+    int64_t bandwidth_internal;/* the same in the library's internal order */
+    int64_t max_block_elems;
+    int64_t device_bytes;      /* device memory held by the mesh */
+    int32_t precision, variant, threads, reorder;
+} fem_info;
+
+/* Create a mesh (Section 3: unstructured four-node tetrahedra).
+ *   xyz     [n_nodes][3] coordinates, m.
+ *   tets    [n_tets][4] node ids; either orientation is accepted (inverted
+ *           tets are re-oriented silently).
+ *   mat_id  [n_tets] material index into the table of fem_set_materials.
+ *   prec    arithmetic of the step: FEM_FP64, or FEM_FP32 (bulk arithmetic
+ *           in FP32; energy bookkeeping always FP64).
+ *   reorder 0 keep the caller's node order, 1 reverse Cuthill-McKee
+ *           (Section 5.2).
+ * Errors: FEM_EINVAL for n_nodes <= 0, n_tets <= 0, NULL arrays, an id out
+ * of range, a repeated node in a tet, a negative mat_id, or a degenerate
+ * tet (|V| < 1e-12 l^3, l the tet's mean edge length); FEM_ENOMEM.
+ * No device memory is touched by this call. */
+fem_status fem_mesh_create(const double *xyz, int64_t n_nodes, const int32_t *tets,
+                           int64_t n_tets, const int32_t *mat_id, fem_precision prec,
+                           int reorder, fem_mesh **out);
+
+/* As fem_mesh_create, with options (opts may be NULL for defaults). */
+fem_status fem_mesh_create_ex(const double *xyz, int64_t n_nodes, const int32_t *tets,
+                              int64_t n_tets, const int32_t *mat_id, fem_precision prec,
+                              int reorder, const fem_options *opts, fem_mesh **out);
+
+/* Material table [n_mat].  Builds the stored element conductances
+ * K^e = k V grad N_i . grad N_j (only K^e is stored, Eq. 18 and the text
+ * after it) and the row-sum lumped nodal capacities C_i = sum rho c V / 4,
+ * latent capacities Lc_i = sum rho L V / 4 (Section 3).
+ * Errors: FEM_EINVAL for n_mat <= 0, rho/c/k <= 0 or non-finite, latent < 0,
+ * T_liquidus < T_solidus with latent > 0, a mat_id >= n_mat, or a node
+ * touched by two phase-change materials with different (T_solidus,
+ * T_liquidus). */
+fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_mat);
+
+/* Flux/convective boundary Gamma_q, Eq. 4: -k dT/dn = q + h (T - T_inf) on
+ * each face.  faces [n_faces][3] node ids; h, T_inf [n_faces]; q [n_faces]
+ * or NULL for zero flux.  Each face must be a face of exactly one tet (a
+ * boundary face).  Replaces any previous boundary; n_faces == 0 makes every
+ * wall adiabatic.  Faces use the consistent Galerkin face matrix
+ * h A / 12 (1 + delta_ij) and load A/3 (h T_inf - q), evaluated at step n.
+ * Errors: FEM_EINVAL for an id out of range, a face that is not the face of
+ * exactly one tet, h < 0, or a non-finite value. */
+fem_status fem_set_boundary(fem_mesh *m, const int32_t *faces, int64_t n_faces,
+                            const double *h, const double *T_inf, const double *q);
+
+/* Dirichlet boundary Gamma_T, Eq. 3: nodes [n] held at temperatures T [n]
+ * (their enthalpy is never updated).  Replaces any previous set; n == 0
+ * clears it.  Errors: FEM_EINVAL for an id out of range or a non-finite T. */
+fem_status fem_set_dirichlet(fem_mesh *m, const int32_t *nodes, int64_t n, const double *T);
+
+/* Initial condition, Eq. 2: T0 [n_nodes].  Sets the nodal enthalpy
+ * E_i = C_i T0_i + Lc_i f_l(T0_i), resets the step count, time and the
+ * energy account (U0 = sum E_i).  Requires fem_set_materials (FEM_ESTATE).
+ * Errors: FEM_EINVAL for a non-finite T0. */
+fem_status fem_set_temperature(fem_mesh *m, const double *T0);
+
+/* Stable explicit step (reading of Eq. 13): 2 / max_i sum_j |(K + H)_ij| / C_i
+ * over non-Dirichlet nodes, K the assembled conductance, H the assembled
+ * Robin face matrix, C the sensible lumped capacity.  Host computation.
+ * Requires fem_set_materials (FEM_ESTATE). */
+fem_status fem_stable_dt(fem_mesh *m, double *dt_out);
+
+/* Advance n_steps explicit steps of size dt (Eq. 14 in enthalpy form):
+ * T_i = T(E_i); R = F - K T; E_i += dt R_i.  Asynchronous on the mesh's
+ * stream.  n_steps == 0 is a no-op.  Errors: FEM_EINVAL for n_steps < 0 or
+ * dt <= 0 / non-finite; FEM_ESTATE before fem_set_materials and
+ * fem_set_temperature (or fem_set_state); FEM_ECUDA. */
+fem_status fem_step(fem_mesh *m, int64_t n_steps, double dt);
+
+/* As fem_step, timing every kernel of the step with CUDA events on the
+ * mesh's stream (one synchronisation per step, so use it for measurement
+ * only).  ms_out [capacity] receives the summed device milliseconds of each
+ * kernel over the n_steps steps, *n_used the number of kernels per step:
+ * block variant {0: block step (passes 1-3), 1: shared-node update}; atomic
+ * and coloured variants {0: temperatures, 1: element pass (all colours),
+ * 2: node update}.  Errors as fem_step; FEM_EINVAL if capacity is too small. */
+fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_out,
+                            int32_t capacity, int32_t *n_used);
+
+/* Nodal temperatures T(E) [n_nodes] in the caller's order.  Synchronises.
+ * FEM_EUNSTABLE if any value is non-finite (the output is still written). */
+fem_status fem_get_temperature(fem_mesh *m, double *T_out);
+
+/* Specific nodal enthalpy E_i / m_i (J/kg) [n_nodes], caller's order. */
+fem_status fem_get_enthalpy(fem_mesh *m, double *h_out);
+
+/* FP64 energy account (device reduction): out[0] = U = sum_i E_i (J),
+ * out[1] = U0 at the initial condition, out[2] = cumulative heat that
+ * entered through the Robin faces, out[3] = latent heat not yet released
+ * sum_i Lc_i f_l(T_i).  Without Dirichlet nodes U - U0 - out[2] is zero up to
+ * rounding.  Synchronises.  FEM_EUNSTABLE if U is non-finite. */
+fem_status fem_get_energy(fem_mesh *m, double out[4]);
+
+/* Use the given cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later work of this mesh; NULL selects the legacy default stream. */
+fem_status fem_set_stream(fem_mesh *m, void *cuda_stream);
+
+/* Checkpoint: nodal enthalpy content E_i (J) [n_nodes] in the caller's
+ * order, with the step count and simulated time.  Synchronises. */
+fem_status fem_get_state(fem_mesh *m, double *E_out, int64_t *step, double *t);
+
+/* Restore a checkpoint written by fem_get_state (E [n_nodes], J).
+ * Asynchronous: E is staged through a device buffer on the mesh's stream;
+ * the call returns after the host-to-device copy has been enqueued, so the
+ * caller must keep E unchanged until the stream reaches it (any fem_get_*
+ * call guarantees that).  Errors: FEM_EINVAL for non-finite E. */
+fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t);
+
+/* Plan statistics (host computation; builds the plan if needed). */
+fem_status fem_mesh_info(fem_mesh *m, fem_info *out);
+
+/* Reverse Cuthill-McKee order of a tet mesh's node graph (Section 5.2),
+ * host only.  perm_out [n_nodes]: perm_out[old] = new.  bw_before /
+ * bw_after (may be NULL): max |i - j| over element node pairs before and
+ * after.  Errors: FEM_EINVAL for bad sizes or ids. */
+fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                         int32_t *perm_out, int64_t *bw_before, int64_t *bw_after);
+
+/* Host copies of the plan arrays, for inspection and tests.  which:
+ *   0 node_new   int32 [n_nodes]      caller node -> internal node
+ *   1 blocks     int32 [n_blocks][12] per block: e0, ne, f0, nf, n0, nint,
+ *                                     c0, nsh, g0, ngrp, ne_pad, nf_pad
+ *   2 elem_order int32 [E_pad]        padded element position -> caller
+ *                                     element (-1 for padding)
+ *   3 face_order int32 [F_pad]        padded face position -> caller face
+ *   4 copy_node  int32 [n_copies]     shared copy -> internal node
+ *   5 sh_ptr     int32 [n_shared+1]   shared node -> range in sh_copy
+ *   6 sh_copy    int32 [n_copies]     copy indices of each shared node
+ *   7 grp        int32 [..]           32-lane group -> first schedule round
+ *   8 sched      uint16 [rounds*32]   slot written/read by each lane/round
+ *   9 elem_nodes int32 [E_pad][4]     corner nodes (internal ids) per position
+ *  10 face_nodes int32 [F_pad][3]     corner nodes (internal ids) per position
+ * *data points into the mesh (valid until the next fem_set_* or destroy);
+ * *count is the number of scalar entries.  Builds the plan if needed. */
+fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t *count);
+
+/* Message of the last error on this thread ("" if none). */
+const char *fem_last_error(void);
+
+/* Release the mesh and its device memory (NULL is a no-op). */
+void fem_mesh_destroy(fem_mesh *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_H */

@@ -1,0 +1,1148 @@
+// C ABI of libfem (include/fem.h): argument validation, set-up of the
+// stored element conductances and lumped capacities (Section 3), plan and
+// device-memory management, and the step driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fem.h"
+#include "fem_internal.h"
+#include "fem_plan.h"
+
+using namespace fem;
+
+namespace {
+
+thread_local std::string g_err;
+
+fem_status fail(fem_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+fem_status ok()
+{
+    g_err.clear();
+    return FEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device allocations (with an allocation-failure injection hook for tests:
+// FEM_FAULT_ALLOC_AFTER=k makes every device allocation after the k-th fail)
+// ---------------------------------------------------------------------------
+long g_alloc_count = 0;
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    const char *env = getenv("FEM_FAULT_ALLOC_AFTER");
+    if (env && *env) {
+        long k = atol(env);
+        if (g_alloc_count >= k) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    }
+    g_alloc_count++;
+    return cudaMalloc(p, bytes == 0 ? 16 : bytes);
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct fem_mesh {
+    // ---- caller-order host data
+    int64_t N = 0, E = 0, F = 0;
+    std::vector<double> xyz;
+    std::vector<int32_t> tets, mat;
+    std::vector<double> vol;          // |V|
+    NodeElems adj;
+    std::vector<int32_t> rank;        // node priority (RCM position or identity)
+    int64_t bw_input = 0, bw_rank = 0;
+    fem_precision prec = FEM_FP64;
+    int reorder = 0;
+    fem_options opt{};
+    // materials
+    bool have_mat = false;
+    std::vector<double> w;            // [E][6] conductances
+    std::vector<double> Cn, mn, Lcn;  // lumped per node
+    std::vector<uint8_t> rng_id;      // phase-range index per node
+    std::vector<double> ranges;       // [nr][2]
+    // boundary
+    std::vector<int32_t> faces;
+    std::vector<double> fa, fg;       // h A / 12, A/3 (h T_inf - q)
+    // Dirichlet
+    std::vector<uint8_t> is_dir;
+    std::vector<double> dir_T;        // caller order (valid where is_dir)
+    // ---- plan
+    bool plan_ok = false;
+    BlockPlan bp;
+    FlatPlan fp;
+    std::vector<int32_t> nf_ptr, nf_idx;  // flat: node -> faces (internal ids)
+    std::vector<int32_t> blocks_flat;     // fem_plan_array view of bp.blocks
+    // ---- device
+    bool dev_ok = false;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    std::vector<DevBuf> bufs;
+    size_t dev_bytes = 0;
+    size_t smem_bytes = 0;
+    int threads = 256;
+    int n_sh_ctas = 0, n_node_ctas = 0;
+    // device pointers
+    void *dE = nullptr, *dC = nullptr, *dLc = nullptr, *dRanges = nullptr, *dW = nullptr,
+         *dFa = nullptr, *dFg = nullptr, *dP = nullptr, *dT = nullptr, *dR = nullptr;
+    uint8_t *dPh = nullptr;
+    BlockInfo *dBlocks = nullptr;
+    int32_t *dGrp = nullptr, *dCopy = nullptr, *dShPtr = nullptr, *dShCopy = nullptr,
+            *dNodeOld = nullptr, *dConn = nullptr, *dFconn = nullptr, *dNfPtr = nullptr,
+            *dNfIdx = nullptr;
+    uint16_t *dSched = nullptr;
+    double *dEpart = nullptr, *dQcum = nullptr, *dEpart2 = nullptr, *dIo = nullptr,
+           *dDirT = nullptr, *dOut = nullptr;
+    // ---- state
+    enum { ST_NONE, ST_PENDING_T, ST_PENDING_E, ST_DEVICE } state = ST_NONE;
+    std::vector<double> pending;      // T0 or E (caller order)
+    int64_t step = 0;
+    double time = 0.0;
+    double U0 = 0.0;
+    double q_carry = 0.0;             // boundary heat of device buffers already released
+    int64_t steps_since_account = 0;  // steps since the per-step partials were valid
+};
+
+namespace {
+
+bool finite_all(const double *p, int64_t n)
+{
+    for (int64_t i = 0; i < n; i++)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+void release_device(fem_mesh *m)
+{
+    if (m->device >= 0) cudaSetDevice(m->device);
+    for (auto &b : m->bufs) cudaFree(b.p);
+    m->bufs.clear();
+    m->dev_bytes = 0;
+    m->dev_ok = false;
+    m->dE = m->dC = m->dLc = m->dRanges = m->dW = m->dFa = m->dFg = m->dP = m->dT = m->dR = nullptr;
+    m->dPh = nullptr;
+    m->dBlocks = nullptr;
+    m->dGrp = m->dCopy = m->dShPtr = m->dShCopy = m->dNodeOld = m->dConn = m->dFconn = nullptr;
+    m->dNfPtr = m->dNfIdx = nullptr;
+    m->dSched = nullptr;
+    m->dEpart = m->dQcum = m->dEpart2 = m->dIo = m->dDirT = m->dOut = nullptr;
+}
+
+int default_block_elems(const fem_mesh *m)
+{
+    int be = m->opt.block_elems;
+    if (be <= 0) be = m->prec == FEM_FP32 ? 4096 : 2048;
+    return std::min(std::max(be, 64), 12288);
+}
+
+bool is_block(const fem_mesh *m) { return m->opt.variant == FEM_VARIANT_BLOCK; }
+
+// number of per-CTA cumulative boundary-heat entries
+int64_t n_qcum(const fem_mesh *m)
+{
+    return is_block(m) ? (int64_t)m->bp.blocks.size() : (int64_t)m->n_node_ctas;
+}
+
+// Build the plan (host) if needed.
+fem_status ensure_plan(fem_mesh *m)
+{
+    if (m->plan_ok) return FEM_OK;
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    std::vector<int32_t> owner;
+    if (m->F > 0) {
+        std::string err = face_owners(m->F, m->faces.data(), m->tets.data(), m->adj, owner);
+        if (!err.empty()) return fail(FEM_EINVAL, "%s", err.c_str());
+    }
+    std::string err;
+    try {
+        if (is_block(m)) {
+            err = build_block_plan(m->N, m->E, m->xyz.data(), m->tets.data(), m->rank, m->F,
+                                   m->faces.data(), owner, default_block_elems(m), m->bp);
+            if (err.empty()) {
+                m->blocks_flat.resize(m->bp.blocks.size() * 12);
+                std::memcpy(m->blocks_flat.data(), m->bp.blocks.data(),
+                            m->bp.blocks.size() * sizeof(BlockInfo));
+            }
+        } else {
+            err = build_flat_plan(m->N, m->E, m->tets.data(), m->rank, m->F,
+                                  m->opt.variant == FEM_VARIANT_COLORED, m->fp);
+            if (err.empty()) {
+                // node -> faces, internal node ids, face positions = caller ids
+                m->nf_ptr.assign((size_t)m->N + 1, 0);
+                for (int64_t i = 0; i < 3 * m->F; i++) m->nf_ptr[(size_t)m->fp.node_new[m->faces[i]] + 1]++;
+                for (int64_t n = 0; n < m->N; n++) m->nf_ptr[n + 1] += m->nf_ptr[n];
+                m->nf_idx.assign((size_t)(3 * m->F), 0);
+                std::vector<int32_t> fill(m->nf_ptr.begin(), m->nf_ptr.end() - 1);
+                for (int64_t f = 0; f < m->F; f++)
+                    for (int c = 0; c < 3; c++)
+                        m->nf_idx[fill[m->fp.node_new[m->faces[3 * f + c]]]++] = (int32_t)f;
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed while building the plan");
+    }
+    if (!err.empty()) return fail(FEM_EINVAL, "%s", err.c_str());
+    m->plan_ok = true;
+    return FEM_OK;
+}
+
+const std::vector<int32_t> &node_old_of(const fem_mesh *m)
+{
+    return is_block(m) ? m->bp.node_old : m->fp.node_old;
+}
+const std::vector<int32_t> &node_new_of(const fem_mesh *m)
+{
+    return is_block(m) ? m->bp.node_new : m->fp.node_new;
+}
+
+#define CU(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            fem_status s_ = e_ == cudaErrorMemoryAllocation ? FEM_ENOMEM : FEM_ECUDA;       \
+            return fail(s_, "%s failed: %s", #call, cudaGetErrorString(e_));                \
+        }                                                                                   \
+    } while (0)
+
+#define KERNEL(expr, what)                                                                  \
+    do {                                                                                    \
+        int e_ = (expr);                                                                    \
+        if (e_) return fail(FEM_ECUDA, "%s failed: %s", what, cudaGetErrorString((cudaError_t)e_)); \
+    } while (0)
+
+template <typename T>
+fem_status upload(fem_mesh *m, T **dst, const T *src, size_t count)
+{
+    void *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = dev_alloc(&p, bytes);
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? FEM_ENOMEM : FEM_ECUDA,
+                    "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    m->bufs.push_back({p, bytes});
+    m->dev_bytes += bytes;
+    if (src && count) CU(cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    else CU(cudaMemset(p, 0, bytes));
+    *dst = (T *)p;
+    return FEM_OK;
+}
+
+// Per-node arrays in internal order.
+template <typename real>
+fem_status upload_nodes(fem_mesh *m)
+{
+    const auto &old = node_old_of(m);
+    std::vector<real> C((size_t)m->N), Lc((size_t)m->N);
+    std::vector<uint8_t> ph((size_t)m->N);
+    for (int64_t i = 0; i < m->N; i++) {
+        int32_t o = old[i];
+        C[i] = (real)m->Cn[o];
+        Lc[i] = (real)m->Lcn[o];
+        ph[i] = (uint8_t)(m->rng_id[o] | (m->is_dir.empty() || !m->is_dir[o] ? 0 : kDirichletBit));
+    }
+    fem_status st;
+    real *p = nullptr;
+    if ((st = upload<real>(m, &p, nullptr, (size_t)m->N))) return st;
+    m->dE = p;
+    if ((st = upload<real>(m, &p, C.data(), C.size()))) return st;
+    m->dC = p;
+    if ((st = upload<real>(m, &p, Lc.data(), Lc.size()))) return st;
+    m->dLc = p;
+    if ((st = upload<uint8_t>(m, &m->dPh, ph.data(), ph.size()))) return st;
+    std::vector<real> rg(m->ranges.begin(), m->ranges.end());
+    if ((st = upload<real>(m, &p, rg.data(), rg.size()))) return st;
+    m->dRanges = p;
+    if ((st = upload<int32_t>(m, &m->dNodeOld, old.data(), old.size()))) return st;
+    if ((st = upload<double>(m, &m->dIo, nullptr, (size_t)m->N))) return st;
+    if ((st = upload<double>(m, &m->dOut, nullptr, 4))) return st;
+    if (!m->is_dir.empty()) {
+        std::vector<double> dT((size_t)m->N, 0.0);
+        for (int64_t i = 0; i < m->N; i++)
+            if (m->is_dir[old[i]]) dT[i] = m->dir_T[old[i]];
+        if ((st = upload<double>(m, &m->dDirT, dT.data(), dT.size()))) return st;
+    }
+    return FEM_OK;
+}
+
+template <typename real>
+fem_status upload_block(fem_mesh *m)
+{
+    const BlockPlan &bp = m->bp;
+    fem_status st;
+    if ((st = upload_nodes<real>(m))) return st;
+    // element conductances in block order, SoA [6][E_pad]
+    real *p = nullptr;
+    {
+        std::vector<real> w((size_t)bp.E_pad * 6, real(0));
+        for (int64_t q = 0; q < bp.E_pad; q++) {
+            int32_t e = bp.elem_order[q];
+            if (e < 0) continue;
+            for (int k = 0; k < 6; k++) w[(size_t)k * bp.E_pad + q] = (real)m->w[6 * (size_t)e + k];
+        }
+        if ((st = upload<real>(m, &p, w.data(), w.size()))) return st;
+        m->dW = p;
+    }
+    std::vector<real> fa((size_t)bp.F_pad, real(0)), fg((size_t)bp.F_pad, real(0));
+    for (int64_t q = 0; q < bp.F_pad; q++) {
+        int32_t f = bp.face_order[q];
+        if (f < 0) continue;
+        fa[q] = (real)m->fa[f];
+        fg[q] = (real)m->fg[f];
+    }
+    if ((st = upload<real>(m, &p, fa.data(), fa.size()))) return st;
+    m->dFa = p;
+    if ((st = upload<real>(m, &p, fg.data(), fg.size()))) return st;
+    m->dFg = p;
+    if ((st = upload<BlockInfo>(m, &m->dBlocks, bp.blocks.data(), bp.blocks.size()))) return st;
+    if ((st = upload<int32_t>(m, &m->dGrp, bp.grp.data(), bp.grp.size()))) return st;
+    if ((st = upload<uint16_t>(m, &m->dSched, bp.sched.data(), bp.sched.size()))) return st;
+    if ((st = upload<int32_t>(m, &m->dCopy, bp.copy_node.data(), bp.copy_node.size()))) return st;
+    if ((st = upload<real>(m, &p, nullptr, (size_t)bp.n_copies))) return st;
+    m->dP = p;
+    if ((st = upload<int32_t>(m, &m->dShPtr, bp.sh_ptr.data(), bp.sh_ptr.size()))) return st;
+    if ((st = upload<int32_t>(m, &m->dShCopy, bp.sh_copy.data(), bp.sh_copy.size()))) return st;
+    if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * bp.blocks.size()))) return st;
+    if ((st = upload<double>(m, &m->dQcum, nullptr, bp.blocks.size()))) return st;
+    m->n_sh_ctas = (int)std::max<int64_t>(1, (bp.n_sh + 255) / 256);
+    if ((st = upload<double>(m, &m->dEpart2, nullptr, 2 * (size_t)m->n_sh_ctas))) return st;
+    // kernel configuration
+    m->threads = m->opt.threads > 0 ? m->opt.threads : 256;
+    m->smem_bytes = (bp.max_slots + bp.max_nloc) * sizeof(real);
+    int dev = 0, optin = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if ((size_t)optin < m->smem_bytes + 1024)
+        return fail(FEM_EINVAL, "a block needs %zu bytes of shared memory (device limit %d); lower block_elems",
+                    m->smem_bytes, optin);
+    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes), "configuring the block kernel");
+    return FEM_OK;
+}
+
+template <typename real>
+fem_status upload_flat(fem_mesh *m)
+{
+    const FlatPlan &fp = m->fp;
+    fem_status st;
+    if ((st = upload_nodes<real>(m))) return st;
+    real *p = nullptr;
+    {
+        std::vector<real> w((size_t)fp.E_pad * 6, real(0));
+        std::vector<int32_t> conn((size_t)fp.E_pad * 4, -1);
+        for (int64_t q = 0; q < fp.E_pad; q++) {
+            int32_t e = fp.elem_order[q];
+            if (e < 0) continue;
+            for (int k = 0; k < 6; k++) w[(size_t)k * fp.E_pad + q] = (real)m->w[6 * (size_t)e + k];
+            for (int c = 0; c < 4; c++)
+                conn[(size_t)c * fp.E_pad + q] = fp.node_new[m->tets[4 * (size_t)e + c]];
+        }
+        if ((st = upload<real>(m, &p, w.data(), w.size()))) return st;
+        m->dW = p;
+        if ((st = upload<int32_t>(m, &m->dConn, conn.data(), conn.size()))) return st;
+    }
+    std::vector<real> fa((size_t)fp.F_pad, real(0)), fg((size_t)fp.F_pad, real(0));
+    std::vector<int32_t> fconn((size_t)fp.F_pad * 3, 0);
+    for (int64_t q = 0; q < fp.F_pad; q++) {
+        int32_t f = fp.face_order[q];
+        if (f < 0) continue;
+        fa[q] = (real)m->fa[f];
+        fg[q] = (real)m->fg[f];
+        for (int c = 0; c < 3; c++)
+            fconn[(size_t)c * fp.F_pad + q] = fp.node_new[m->faces[3 * (size_t)f + c]];
+    }
+    if ((st = upload<real>(m, &p, fa.data(), fa.size()))) return st;
+    m->dFa = p;
+    if ((st = upload<real>(m, &p, fg.data(), fg.size()))) return st;
+    m->dFg = p;
+    if ((st = upload<int32_t>(m, &m->dFconn, fconn.data(), fconn.size()))) return st;
+    if ((st = upload<int32_t>(m, &m->dNfPtr, m->nf_ptr.data(), m->nf_ptr.size()))) return st;
+    if ((st = upload<int32_t>(m, &m->dNfIdx, m->nf_idx.data(), m->nf_idx.size()))) return st;
+    if ((st = upload<real>(m, &p, nullptr, (size_t)m->N))) return st;
+    m->dT = p;
+    if ((st = upload<real>(m, &p, nullptr, (size_t)m->N))) return st;
+    m->dR = p;
+    m->n_node_ctas = (int)std::max<int64_t>(1, (m->N + 255) / 256);
+    if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * (size_t)m->n_node_ctas))) return st;
+    if ((st = upload<double>(m, &m->dQcum, nullptr, (size_t)m->n_node_ctas))) return st;
+    return FEM_OK;
+}
+
+template <typename real>
+BlockArgs<real> block_args(const fem_mesh *m)
+{
+    BlockArgs<real> a{};
+    a.blocks = m->dBlocks;
+    a.n_blocks = (int32_t)m->bp.blocks.size();
+    a.E = (real *)m->dE;
+    a.C = (const real *)m->dC;
+    a.Lc = (const real *)m->dLc;
+    a.ph = m->dPh;
+    a.ranges = (const real *)m->dRanges;
+    a.n_int = m->bp.n_int;
+    a.n_nodes = m->N;
+    a.w = (const real *)m->dW;
+    a.e_stride = m->bp.E_pad;
+    a.fa = (const real *)m->dFa;
+    a.fg = (const real *)m->dFg;
+    a.grp = m->dGrp;
+    a.sched = m->dSched;
+    a.copy_node = m->dCopy;
+    a.P = (real *)m->dP;
+    a.sh_ptr = m->dShPtr;
+    a.sh_copy = m->dShCopy;
+    a.epart = m->dEpart;
+    a.qcum = m->dQcum;
+    a.epart2 = m->dEpart2;
+    return a;
+}
+
+template <typename real>
+FlatArgs<real> flat_args(const fem_mesh *m)
+{
+    FlatArgs<real> a{};
+    a.E = (real *)m->dE;
+    a.C = (const real *)m->dC;
+    a.Lc = (const real *)m->dLc;
+    a.ph = m->dPh;
+    a.ranges = (const real *)m->dRanges;
+    a.n_nodes = m->N;
+    a.T = (real *)m->dT;
+    a.R = (real *)m->dR;
+    a.conn = m->dConn;
+    a.w = (const real *)m->dW;
+    a.n_elems = m->E;
+    a.e_stride = m->fp.E_pad;
+    a.fconn = m->dFconn;
+    a.fa = (const real *)m->dFa;
+    a.fg = (const real *)m->dFg;
+    a.n_faces = m->F;
+    a.f_stride = m->fp.F_pad;
+    a.epart = m->dEpart;
+    a.qcum = m->dQcum;
+    return a;
+}
+
+// Number of CTAs (and FP64 partial pairs) of the whole-state energy
+// snapshot; bounded by the size of the per-step partial array it reuses.
+int snapshot_ctas(const fem_mesh *m)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(n_qcum(m), 152 * 4));
+}
+
+// FP64 sums of the current state into m->dOut: {sum E, latent, sum qcum}.
+template <typename real>
+int energy_snapshot(fem_mesh *m)
+{
+    const int nct = snapshot_ctas(m);
+    int e = launch_energy_snapshot<real>((const real *)m->dE, (const real *)m->dC,
+                                         (const real *)m->dLc, m->dPh, (const real *)m->dRanges,
+                                         m->N, m->dEpart, nct, m->stream);
+    if (!e) e = launch_energy_reduce(m->dEpart, nct, nullptr, 0, m->dQcum, n_qcum(m), m->dOut, m->stream);
+    return e;
+}
+
+// Apply a pending initial condition or checkpoint on the device.
+template <typename real>
+fem_status apply_pending(fem_mesh *m)
+{
+    if (m->state != fem_mesh::ST_PENDING_T && m->state != fem_mesh::ST_PENDING_E) return FEM_OK;
+    CU(cudaMemcpyAsync(m->dIo, m->pending.data(), (size_t)m->N * sizeof(double),
+                       cudaMemcpyHostToDevice, m->stream));
+    const bool initial = m->state == fem_mesh::ST_PENDING_T;
+    if (initial)
+        KERNEL(launch_set_temperature<real>((real *)m->dE, (const real *)m->dC, (const real *)m->dLc,
+                                            m->dPh, (const real *)m->dRanges, m->dIo, m->dNodeOld,
+                                            m->dDirT, m->N, m->stream),
+               "initial-state kernel");
+    else
+        KERNEL(launch_set_state<real>((real *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+               "state kernel");
+    CU(cudaMemsetAsync(m->dQcum, 0, (size_t)n_qcum(m) * sizeof(double), m->stream));
+    if (initial) {
+        // a new energy account: U0 = sum E of the initial state, no boundary heat
+        KERNEL(energy_snapshot<real>(m), "energy kernel");
+        double out[3];
+        CU(cudaMemcpyAsync(out, m->dOut, 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+        CU(cudaStreamSynchronize(m->stream));
+        m->U0 = out[0];
+        m->q_carry = 0.0;
+    } else {
+        CU(cudaStreamSynchronize(m->stream));
+    }
+    m->state = fem_mesh::ST_DEVICE;
+    m->steps_since_account = 0;
+    std::vector<double>().swap(m->pending);
+    return FEM_OK;
+}
+
+fem_status ensure_device(fem_mesh *m)
+{
+    fem_status st = ensure_plan(m);
+    if (st) return st;
+    if (m->dev_ok) return FEM_OK;
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0)
+        return fail(FEM_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(ce));
+    CU(cudaGetDevice(&m->device));
+    if (is_block(m))
+        st = m->prec == FEM_FP32 ? upload_block<float>(m) : upload_block<double>(m);
+    else
+        st = m->prec == FEM_FP32 ? upload_flat<float>(m) : upload_flat<double>(m);
+    if (st) {
+        std::string keep = g_err;
+        release_device(m);
+        g_err = keep;
+        return st;
+    }
+    m->dev_ok = true;
+    return FEM_OK;
+}
+
+// Copy the device state back to a host checkpoint (before a plan rebuild),
+// so set_* calls after stepping keep the current state and energy account.
+fem_status stash_state(fem_mesh *m)
+{
+    if (!m->dev_ok || m->state != fem_mesh::ST_DEVICE) return FEM_OK;
+    cudaSetDevice(m->device);
+    std::vector<double> E((size_t)m->N);
+    KERNEL(m->prec == FEM_FP32
+               ? launch_get_state<float>((const float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
+               : launch_get_state<double>((const double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+           "state read-back");
+    CU(cudaMemcpyAsync(E.data(), m->dIo, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost,
+                       m->stream));
+    KERNEL(launch_energy_reduce(m->dEpart, 0, nullptr, 0, m->dQcum, n_qcum(m), m->dOut, m->stream),
+           "energy kernel");
+    double r[3];
+    CU(cudaMemcpyAsync(r, m->dOut, 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    m->q_carry += r[2];
+    m->pending.swap(E);
+    m->state = fem_mesh::ST_PENDING_E;
+    return FEM_OK;
+}
+
+fem_status invalidate_plan(fem_mesh *m)
+{
+    fem_status st = stash_state(m);
+    if (st) return st;
+    release_device(m);
+    m->plan_ok = false;
+    m->bp = BlockPlan();
+    m->fp = FlatPlan();
+    return FEM_OK;
+}
+
+// Kernels of one step, in launch order: block variant {block step, shared
+// update}; flat variants {temperatures, element pass, node update}.
+int step_kernel_count(const fem_mesh *m) { return is_block(m) ? 2 : 3; }
+
+template <typename real>
+fem_status launch_step_kernel(fem_mesh *m, int k, double dt)
+{
+    if (is_block(m)) {
+        const BlockArgs<real> a = block_args<real>(m);
+        if (k == 0)
+            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream), "block kernel");
+        else
+            KERNEL(launch_shared_update<real>(a, m->bp.n_sh, m->n_sh_ctas, dt, m->stream),
+                   "shared-node kernel");
+    } else {
+        const FlatArgs<real> a = flat_args<real>(m);
+        if (k == 0)
+            KERNEL(launch_flat_temperature<real>(a, m->stream), "temperature kernel");
+        else if (k == 1)
+            KERNEL(launch_flat_elements<real>(a, m->opt.variant == FEM_VARIANT_ATOMIC,
+                                              m->fp.color_start.data(), m->fp.n_colors, m->stream),
+                   "element kernel");
+        else
+            KERNEL(launch_flat_update<real>(a, m->dNfPtr, m->dNfIdx, m->n_node_ctas, dt, m->stream),
+                   "update kernel");
+    }
+    return FEM_OK;
+}
+
+template <typename real>
+fem_status step_impl(fem_mesh *m, int64_t n, double dt)
+{
+    const int nk = step_kernel_count(m);
+    for (int64_t s = 0; s < n; s++)
+        for (int k = 0; k < nk; k++) {
+            fem_status st = launch_step_kernel<real>(m, k, dt);
+            if (st) return st;
+        }
+    m->step += n;
+    m->time += dt * (double)n;
+    m->steps_since_account += n;
+    return FEM_OK;
+}
+
+// As step_impl, with CUDA events around every kernel; ms[k] accumulates
+// the device time of kernel k.
+template <typename real>
+fem_status step_profile_impl(fem_mesh *m, int64_t n, double dt, double *ms)
+{
+    const int nk = step_kernel_count(m);
+    cudaEvent_t ev[4];
+    for (int k = 0; k <= nk; k++) CU(cudaEventCreate(&ev[k]));
+    fem_status st = FEM_OK;
+    for (int64_t s = 0; s < n && st == FEM_OK; s++) {
+        for (int k = 0; k < nk && st == FEM_OK; k++) {
+            cudaEventRecord(ev[k], m->stream);
+            st = launch_step_kernel<real>(m, k, dt);
+        }
+        if (st) break;
+        cudaEventRecord(ev[nk], m->stream);
+        if (cudaEventSynchronize(ev[nk]) != cudaSuccess) {
+            st = fail(FEM_ECUDA, "event synchronisation failed");
+            break;
+        }
+        for (int k = 0; k < nk; k++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            ms[k] += t;
+        }
+        m->step += 1;
+        m->time += dt;
+        m->steps_since_account += 1;
+    }
+    for (int k = 0; k <= nk; k++) cudaEventDestroy(ev[k]);
+    return st;
+}
+
+fem_status ready_for_io(fem_mesh *m)
+{
+    if (m->state == fem_mesh::ST_NONE) return fail(FEM_ESTATE, "no initial state (call fem_set_temperature)");
+    fem_status st = ensure_device(m);
+    if (st) return st;
+    cudaSetDevice(m->device);
+    return m->prec == FEM_FP32 ? apply_pending<float>(m) : apply_pending<double>(m);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *fem_last_error(void) { return g_err.c_str(); }
+
+fem_status fem_mesh_create_ex(const double *xyz, int64_t n_nodes, const int32_t *tets,
+                              int64_t n_tets, const int32_t *mat_id, fem_precision prec,
+                              int reorder, const fem_options *opts, fem_mesh **out)
+{
+    if (!out) return fail(FEM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_nodes <= 0 || n_tets <= 0) return fail(FEM_EINVAL, "n_nodes and n_tets must be positive");
+    if (n_nodes > INT32_MAX - 1 || n_tets > INT32_MAX / 8)
+        return fail(FEM_EINVAL, "mesh too large for 32-bit ids");
+    if (!xyz || !tets || !mat_id) return fail(FEM_EINVAL, "NULL array argument");
+    if (prec != FEM_FP64 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision %d", (int)prec);
+    if (reorder != 0 && reorder != 1) return fail(FEM_EINVAL, "reorder must be 0 or 1");
+    fem_options opt{};
+    if (opts) opt = *opts;
+    if (opt.variant < 0 || opt.variant > 2) return fail(FEM_EINVAL, "unknown variant %d", opt.variant);
+    if (opt.threads != 0 && opt.threads != 128 && opt.threads != 256 && opt.threads != 512)
+        return fail(FEM_EINVAL, "threads must be 0, 128, 256 or 512");
+    std::unique_ptr<fem_mesh> m;
+    try {
+        if (!finite_all(xyz, 3 * n_nodes)) return fail(FEM_EINVAL, "non-finite coordinate");
+        m.reset(new fem_mesh());
+        m->N = n_nodes;
+        m->E = n_tets;
+        m->prec = prec;
+        m->reorder = reorder;
+        m->opt = opt;
+        m->xyz.assign(xyz, xyz + 3 * n_nodes);
+        m->tets.assign(tets, tets + 4 * n_tets);
+        m->mat.assign(mat_id, mat_id + n_tets);
+        m->vol.resize((size_t)n_tets);
+        for (int64_t e = 0; e < n_tets; e++) {
+            const int32_t *t = tets + 4 * e;
+            for (int c = 0; c < 4; c++)
+                if (t[c] < 0 || t[c] >= n_nodes)
+                    return fail(FEM_EINVAL, "tet %lld corner %d: node id %d out of range",
+                                (long long)e, c, t[c]);
+            for (int c = 0; c < 4; c++)
+                for (int d = c + 1; d < 4; d++)
+                    if (t[c] == t[d]) return fail(FEM_EINVAL, "tet %lld repeats node %d", (long long)e, t[c]);
+            if (mat_id[e] < 0) return fail(FEM_EINVAL, "tet %lld has negative material id", (long long)e);
+            const double *x[4];
+            for (int c = 0; c < 4; c++) x[c] = xyz + 3 * (size_t)t[c];
+            double V = tet_signed_volume(x[0], x[1], x[2], x[3]);
+            double l = 0.0;
+            for (int c = 0; c < 4; c++)
+                for (int d = c + 1; d < 4; d++) {
+                    double dx = x[c][0] - x[d][0], dy = x[c][1] - x[d][1], dz = x[c][2] - x[d][2];
+                    l += std::sqrt(dx * dx + dy * dy + dz * dz);
+                }
+            l /= 6.0;
+            if (std::fabs(V) < 1e-12 * l * l * l)
+                return fail(FEM_EINVAL, "tet %lld is degenerate (volume %g)", (long long)e, V);
+            m->vol[e] = std::fabs(V);
+        }
+        build_node_elems(n_nodes, n_tets, tets, m->adj);
+        for (int64_t n = 0; n < n_nodes; n++)
+            if (m->adj.ptr[n + 1] == m->adj.ptr[n])
+                return fail(FEM_EINVAL, "node %lld belongs to no tet", (long long)n);
+        m->bw_input = mesh_bandwidth(n_tets, tets, nullptr);
+        if (reorder) {
+            rcm_order(n_nodes, n_tets, tets, m->adj, m->rank);
+            m->bw_rank = mesh_bandwidth(n_tets, tets, m->rank.data());
+        } else {
+            m->rank.resize((size_t)n_nodes);
+            for (int64_t n = 0; n < n_nodes; n++) m->rank[n] = (int32_t)n;
+            m->bw_rank = m->bw_input;
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed");
+    }
+    *out = m.release();
+    return ok();
+}
+
+fem_status fem_mesh_create(const double *xyz, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                           const int32_t *mat_id, fem_precision prec, int reorder, fem_mesh **out)
+{
+    return fem_mesh_create_ex(xyz, n_nodes, tets, n_tets, mat_id, prec, reorder, nullptr, out);
+}
+
+void fem_mesh_destroy(fem_mesh *m)
+{
+    if (!m) return;
+    release_device(m);
+    delete m;
+}
+
+fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_mat)
+{
+    if (!m || !mats) return fail(FEM_EINVAL, "NULL argument");
+    if (n_mat <= 0) return fail(FEM_EINVAL, "n_mat must be positive");
+    for (int32_t i = 0; i < n_mat; i++) {
+        const fem_material &q = mats[i];
+        double v[6] = {q.rho, q.c, q.k, q.latent, q.T_solidus, q.T_liquidus};
+        if (!finite_all(v, 6)) return fail(FEM_EINVAL, "material %d has a non-finite value", i);
+        if (q.rho <= 0 || q.c <= 0 || q.k <= 0)
+            return fail(FEM_EINVAL, "material %d: rho, c and k must be positive", i);
+        if (q.latent < 0) return fail(FEM_EINVAL, "material %d: negative latent heat", i);
+        if (q.latent > 0 && q.T_liquidus < q.T_solidus)
+            return fail(FEM_EINVAL, "material %d: T_liquidus < T_solidus", i);
+    }
+    for (int64_t e = 0; e < m->E; e++)
+        if (m->mat[e] >= n_mat)
+            return fail(FEM_EINVAL, "tet %lld has material id %d >= n_mat", (long long)e, m->mat[e]);
+    try {
+        std::vector<double> w((size_t)m->E * 6), C((size_t)m->N, 0.0), mn((size_t)m->N, 0.0),
+            Lc((size_t)m->N, 0.0);
+        std::vector<uint8_t> rid((size_t)m->N, 0), has((size_t)m->N, 0);
+        // distinct (Ts, Tl) ranges of the phase-change materials
+        std::vector<double> ranges;
+        std::vector<int> mat_range((size_t)n_mat, -1);
+        for (int32_t i = 0; i < n_mat; i++) {
+            if (mats[i].latent <= 0) continue;
+            int found = -1;
+            for (size_t r = 0; r < ranges.size() / 2; r++)
+                if (ranges[2 * r] == mats[i].T_solidus && ranges[2 * r + 1] == mats[i].T_liquidus)
+                    found = (int)r;
+            if (found < 0) {
+                if ((int)(ranges.size() / 2) >= kMaxRanges)
+                    return fail(FEM_EINVAL, "more than %d distinct phase-change ranges", kMaxRanges);
+                found = (int)(ranges.size() / 2);
+                ranges.push_back(mats[i].T_solidus);
+                ranges.push_back(mats[i].T_liquidus);
+            }
+            mat_range[i] = found;
+        }
+        if (ranges.empty()) { ranges.push_back(0.0); ranges.push_back(0.0); }
+        for (int64_t e = 0; e < m->E; e++) {
+            const fem_material &q = mats[m->mat[e]];
+            const int32_t *t = &m->tets[4 * (size_t)e];
+            double V;
+            tet_conductances(&m->xyz[3 * (size_t)t[0]], &m->xyz[3 * (size_t)t[1]],
+                             &m->xyz[3 * (size_t)t[2]], &m->xyz[3 * (size_t)t[3]], q.k, &w[6 * e], &V);
+            // row-sum lumping: each corner gets a quarter of rho c V
+            for (int c = 0; c < 4; c++) {
+                int32_t n = t[c];
+                C[n] += q.rho * q.c * V / 4.0;
+                mn[n] += q.rho * V / 4.0;
+                if (q.latent > 0) {
+                    int r = mat_range[m->mat[e]];
+                    if (has[n] && rid[n] != r)
+                        return fail(FEM_EINVAL,
+                                    "node %d touches phase-change materials with different ranges", n);
+                    rid[n] = (uint8_t)r;
+                    has[n] = 1;
+                    Lc[n] += q.rho * q.latent * V / 4.0;
+                }
+            }
+        }
+        fem_status st = invalidate_plan(m);
+        if (st) return st;
+        m->w.swap(w);
+        m->Cn.swap(C);
+        m->mn.swap(mn);
+        m->Lcn.swap(Lc);
+        m->rng_id.swap(rid);
+        m->ranges.swap(ranges);
+        m->have_mat = true;
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed");
+    }
+    return ok();
+}
+
+fem_status fem_set_boundary(fem_mesh *m, const int32_t *faces, int64_t n_faces, const double *h,
+                            const double *T_inf, const double *q)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (n_faces < 0) return fail(FEM_EINVAL, "n_faces must be >= 0");
+    if (n_faces > 0 && (!faces || !h || !T_inf)) return fail(FEM_EINVAL, "NULL array argument");
+    if (n_faces > INT32_MAX / 3) return fail(FEM_EINVAL, "too many faces");
+    std::vector<int32_t> fc;
+    std::vector<double> fa, fg;
+    try {
+        if (n_faces > 0) fc.assign(faces, faces + 3 * n_faces);
+        fa.resize((size_t)n_faces);
+        fg.resize((size_t)n_faces);
+        for (int64_t f = 0; f < n_faces; f++) {
+            for (int c = 0; c < 3; c++)
+                if (fc[3 * f + c] < 0 || fc[3 * f + c] >= m->N)
+                    return fail(FEM_EINVAL, "face %lld: node id out of range", (long long)f);
+            double qq = q ? q[f] : 0.0;
+            if (!std::isfinite(h[f]) || !std::isfinite(T_inf[f]) || !std::isfinite(qq))
+                return fail(FEM_EINVAL, "face %lld: non-finite h, T_inf or q", (long long)f);
+            if (h[f] < 0) return fail(FEM_EINVAL, "face %lld: negative h", (long long)f);
+            const double *xa = &m->xyz[3 * (size_t)fc[3 * f]], *xb = &m->xyz[3 * (size_t)fc[3 * f + 1]],
+                         *xc = &m->xyz[3 * (size_t)fc[3 * f + 2]];
+            double u[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+            double v[3] = {xc[0] - xa[0], xc[1] - xa[1], xc[2] - xa[2]};
+            double nx = u[1] * v[2] - u[2] * v[1], ny = u[2] * v[0] - u[0] * v[2],
+                   nz = u[0] * v[1] - u[1] * v[0];
+            double A = 0.5 * std::sqrt(nx * nx + ny * ny + nz * nz);
+            fa[f] = h[f] * A / 12.0;
+            fg[f] = A / 3.0 * (h[f] * T_inf[f] - qq);
+        }
+        std::vector<int32_t> owner;
+        std::string err = face_owners(n_faces, fc.data(), m->tets.data(), m->adj, owner);
+        if (!err.empty()) return fail(FEM_EINVAL, "%s", err.c_str());
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed");
+    }
+    fem_status st = invalidate_plan(m);
+    if (st) return st;
+    m->faces.swap(fc);
+    m->fa.swap(fa);
+    m->fg.swap(fg);
+    m->F = n_faces;
+    return ok();
+}
+
+fem_status fem_set_dirichlet(fem_mesh *m, const int32_t *nodes, int64_t n, const double *T)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (n < 0 || (n > 0 && (!nodes || !T))) return fail(FEM_EINVAL, "bad Dirichlet arguments");
+    std::vector<uint8_t> is((size_t)m->N, 0);
+    std::vector<double> val((size_t)m->N, 0.0);
+    for (int64_t i = 0; i < n; i++) {
+        if (nodes[i] < 0 || nodes[i] >= m->N) return fail(FEM_EINVAL, "Dirichlet node id out of range");
+        if (!std::isfinite(T[i])) return fail(FEM_EINVAL, "non-finite Dirichlet temperature");
+        is[nodes[i]] = 1;
+        val[nodes[i]] = T[i];
+    }
+    fem_status st = invalidate_plan(m);
+    if (st) return st;
+    if (n == 0) {
+        m->is_dir.clear();
+        m->dir_T.clear();
+    } else {
+        m->is_dir.swap(is);
+        m->dir_T.swap(val);
+    }
+    return ok();
+}
+
+fem_status fem_set_temperature(fem_mesh *m, const double *T0)
+{
+    if (!m || !T0) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    if (!finite_all(T0, m->N)) return fail(FEM_EINVAL, "non-finite initial temperature");
+    m->pending.assign(T0, T0 + m->N);
+    m->state = fem_mesh::ST_PENDING_T;
+    m->step = 0;
+    m->time = 0.0;
+    m->q_carry = 0.0;
+    if (m->dev_ok) {
+        cudaSetDevice(m->device);
+        fem_status st = m->prec == FEM_FP32 ? apply_pending<float>(m) : apply_pending<double>(m);
+        if (st) return st;
+    }
+    return ok();
+}
+
+fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
+{
+    if (!m || !E) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    if (!finite_all(E, m->N)) return fail(FEM_EINVAL, "non-finite enthalpy");
+    if (m->dev_ok && m->state == fem_mesh::ST_DEVICE) {
+        // stage through the device buffer on the mesh's stream, no synchronisation
+        cudaSetDevice(m->device);
+        CU(cudaMemcpyAsync(m->dIo, E, (size_t)m->N * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+        KERNEL(m->prec == FEM_FP32
+                   ? launch_set_state<float>((float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
+                   : launch_set_state<double>((double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+               "state kernel");
+        m->steps_since_account = 0;
+    } else {
+        m->pending.assign(E, E + m->N);
+        m->state = fem_mesh::ST_PENDING_E;
+        if (m->dev_ok) {
+            cudaSetDevice(m->device);
+            fem_status st = m->prec == FEM_FP32 ? apply_pending<float>(m) : apply_pending<double>(m);
+            if (st) return st;
+        }
+    }
+    m->step = step;
+    m->time = t;
+    return ok();
+}
+
+fem_status fem_set_stream(fem_mesh *m, void *cuda_stream)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    m->stream = (cudaStream_t)cuda_stream;
+    return ok();
+}
+
+fem_status fem_stable_dt(fem_mesh *m, double *dt_out)
+{
+    if (!m || !dt_out) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    try {
+        *dt_out = gershgorin_dt(m->N, m->E, m->tets.data(), m->w.data(), m->adj, m->F,
+                                m->faces.data(), m->fa.data(), m->Cn.data(),
+                                m->is_dir.empty() ? nullptr : m->is_dir.data());
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed");
+    }
+    return ok();
+}
+
+fem_status fem_step(fem_mesh *m, int64_t n_steps, double dt)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (n_steps < 0) return fail(FEM_EINVAL, "n_steps must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(FEM_EINVAL, "dt must be positive and finite");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    if (m->state == fem_mesh::ST_NONE) return fail(FEM_ESTATE, "no initial state (call fem_set_temperature)");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    if (n_steps == 0) return ok();
+    st = m->prec == FEM_FP32 ? step_impl<float>(m, n_steps, dt) : step_impl<double>(m, n_steps, dt);
+    return st ? st : ok();
+}
+
+fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_out,
+                            int32_t capacity, int32_t *n_used)
+{
+    if (!m || !ms_out || !n_used) return fail(FEM_EINVAL, "NULL argument");
+    if (n_steps < 0) return fail(FEM_EINVAL, "n_steps must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(FEM_EINVAL, "dt must be positive and finite");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    if (m->state == fem_mesh::ST_NONE) return fail(FEM_ESTATE, "no initial state (call fem_set_temperature)");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    const int nk = step_kernel_count(m);
+    if (capacity < nk) return fail(FEM_EINVAL, "capacity %d < %d kernels per step", capacity, nk);
+    for (int k = 0; k < nk; k++) ms_out[k] = 0.0;
+    *n_used = nk;
+    st = m->prec == FEM_FP32 ? step_profile_impl<float>(m, n_steps, dt, ms_out)
+                             : step_profile_impl<double>(m, n_steps, dt, ms_out);
+    return st ? st : ok();
+}
+
+fem_status fem_get_temperature(fem_mesh *m, double *T_out)
+{
+    if (!m || !T_out) return fail(FEM_EINVAL, "NULL argument");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    KERNEL(m->prec == FEM_FP32
+               ? launch_get_temperature<float>((const float *)m->dE, (const float *)m->dC,
+                                               (const float *)m->dLc, m->dPh,
+                                               (const float *)m->dRanges, m->dIo, m->dNodeOld, m->N,
+                                               m->stream)
+               : launch_get_temperature<double>((const double *)m->dE, (const double *)m->dC,
+                                                (const double *)m->dLc, m->dPh,
+                                                (const double *)m->dRanges, m->dIo, m->dNodeOld,
+                                                m->N, m->stream),
+           "read-back kernel");
+    CU(cudaMemcpyAsync(T_out, m->dIo, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    if (!finite_all(T_out, m->N))
+        return fail(FEM_EUNSTABLE, "non-finite temperature: dt above the stable limit?");
+    return ok();
+}
+
+fem_status fem_get_state(fem_mesh *m, double *E_out, int64_t *step, double *t)
+{
+    if (!m || !E_out) return fail(FEM_EINVAL, "NULL argument");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    KERNEL(m->prec == FEM_FP32
+               ? launch_get_state<float>((const float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
+               : launch_get_state<double>((const double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+           "read-back kernel");
+    CU(cudaMemcpyAsync(E_out, m->dIo, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    if (step) *step = m->step;
+    if (t) *t = m->time;
+    return ok();
+}
+
+fem_status fem_get_enthalpy(fem_mesh *m, double *h_out)
+{
+    fem_status st = fem_get_state(m, h_out, nullptr, nullptr);
+    if (st) return st;
+    for (int64_t i = 0; i < m->N; i++) h_out[i] /= m->mn[i];
+    return ok();
+}
+
+fem_status fem_get_energy(fem_mesh *m, double out[4])
+{
+    if (!m || !out) return fail(FEM_EINVAL, "NULL argument");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    if (m->steps_since_account > 0) {
+        // the per-CTA FP64 partials written by the last step
+        if (is_block(m))
+            KERNEL(launch_energy_reduce(m->dEpart, (int64_t)m->bp.blocks.size(), m->dEpart2,
+                                        m->n_sh_ctas, m->dQcum, n_qcum(m), m->dOut, m->stream),
+                   "energy kernel");
+        else
+            KERNEL(launch_energy_reduce(m->dEpart, m->n_node_ctas, nullptr, 0, m->dQcum, n_qcum(m),
+                                        m->dOut, m->stream),
+                   "energy kernel");
+    } else {
+        // no step since the state was set: snapshot of the current state
+        KERNEL(m->prec == FEM_FP32 ? energy_snapshot<float>(m) : energy_snapshot<double>(m),
+               "energy kernel");
+    }
+    double r[3];
+    CU(cudaMemcpyAsync(r, m->dOut, 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    out[0] = r[0];
+    out[1] = m->U0;
+    out[2] = r[2] + m->q_carry;
+    out[3] = r[1];
+    if (!std::isfinite(r[0]))
+        return fail(FEM_EUNSTABLE, "non-finite total enthalpy: dt above the stable limit?");
+    return ok();
+}
+
+fem_status fem_mesh_info(fem_mesh *m, fem_info *out)
+{
+    if (!m || !out) return fail(FEM_EINVAL, "NULL argument");
+    fem_status st = ensure_plan(m);
+    if (st) return st;
+    std::memset(out, 0, sizeof(*out));
+    out->n_nodes = m->N;
+    out->n_tets = m->E;
+    out->n_faces = m->F;
+    out->bandwidth_input = m->bw_input;
+    out->bandwidth_internal = mesh_bandwidth(m->E, m->tets.data(), node_new_of(m).data());
+    if (is_block(m)) {
+        out->n_blocks = (int64_t)m->bp.blocks.size();
+        out->n_interior_nodes = m->bp.n_int;
+        out->n_shared_nodes = m->bp.n_sh;
+        out->n_shared_copies = m->bp.n_copies;
+        out->n_sched_rounds = m->bp.n_rounds;
+        out->max_block_elems = m->bp.max_ne;
+    } else {
+        out->n_colors = m->fp.n_colors;
+    }
+    out->device_bytes = (int64_t)m->dev_bytes;
+    out->precision = m->prec;
+    out->variant = m->opt.variant;
+    out->threads = m->opt.threads > 0 ? m->opt.threads : 256;
+    out->reorder = m->reorder;
+    return ok();
+}
+
+fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets, int32_t *perm_out,
+                         int64_t *bw_before, int64_t *bw_after)
+{
+    if (n_nodes <= 0 || n_tets <= 0 || !tets || !perm_out) return fail(FEM_EINVAL, "bad arguments");
+    for (int64_t i = 0; i < 4 * n_tets; i++)
+        if (tets[i] < 0 || tets[i] >= n_nodes) return fail(FEM_EINVAL, "node id out of range");
+    try {
+        NodeElems adj;
+        build_node_elems(n_nodes, n_tets, tets, adj);
+        std::vector<int32_t> perm;
+        rcm_order(n_nodes, n_tets, tets, adj, perm);
+        std::memcpy(perm_out, perm.data(), (size_t)n_nodes * sizeof(int32_t));
+        if (bw_before) *bw_before = mesh_bandwidth(n_tets, tets, nullptr);
+        if (bw_after) *bw_after = mesh_bandwidth(n_tets, tets, perm.data());
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed");
+    }
+    return ok();
+}
+
+fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t *count)
+{
+    if (!m || !data || !count) return fail(FEM_EINVAL, "NULL argument");
+    fem_status st = ensure_plan(m);
+    if (st) return st;
+    const bool block = is_block(m);
+    auto give = [&](const void *p, size_t n) {
+        *data = p;
+        *count = (int64_t)n;
+        return ok();
+    };
+    switch (which) {
+    case 0: return block ? give(m->bp.node_new.data(), m->bp.node_new.size())
+                         : give(m->fp.node_new.data(), m->fp.node_new.size());
+    case 2: return block ? give(m->bp.elem_order.data(), m->bp.elem_order.size())
+                         : give(m->fp.elem_order.data(), m->fp.elem_order.size());
+    case 3: return block ? give(m->bp.face_order.data(), m->bp.face_order.size())
+                         : give(m->fp.face_order.data(), m->fp.face_order.size());
+    default: break;
+    }
+    if (!block) return fail(FEM_EINVAL, "plan array %d exists only for the block variant", which);
+    switch (which) {
+    case 1: return give(m->blocks_flat.data(), m->blocks_flat.size());
+    case 4: return give(m->bp.copy_node.data(), m->bp.copy_node.size());
+    case 5: return give(m->bp.sh_ptr.data(), m->bp.sh_ptr.size());
+    case 6: return give(m->bp.sh_copy.data(), m->bp.sh_copy.size());
+    case 7: return give(m->bp.grp.data(), m->bp.grp.size());
+    case 8: return give(m->bp.sched.data(), m->bp.sched.size());
+    case 9: return give(m->bp.elem_nodes.data(), m->bp.elem_nodes.size());
+    case 10: return give(m->bp.face_nodes.data(), m->bp.face_nodes.size());
+    default: return fail(FEM_EINVAL, "unknown plan array %d", which);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the host side of libfem (fem_plan.cpp,
+// fem_api.cpp) and its CUDA kernels (fem_kernels.cu).  Not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace fem {
+
+// Per-block header of the block-partitioned step (one CTA per block).
+//   elements  [e0, e0+ne) of the block-sorted element arrays (e0 % 8 == 0)
+//   faces     [f0, f0+nf) of the block-sorted face arrays   (f0 % 8 == 0)
+//   interior  nodes [n0, n0+nint) of the internal numbering (owned here)
+//   shared    copies [c0, c0+nsh); copy_node[c] is the internal node id
+//   schedule  32-lane groups [g0, g0+ngrp]: grp[g0+g] .. grp[g0+g+1] are the
+//             rounds of group g; local node l = 32 g + lane (interior first,
+//             then shared copies in order)
+//   slot layout in shared memory: element corner c of local element e at
+//             c*ne_pad + e; face corner c of local face f at
+//             4*ne_pad + c*nf_pad + f
+struct BlockInfo {
+    int32_t e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad;
+};
+static_assert(sizeof(BlockInfo) == 48, "BlockInfo layout");
+
+constexpr uint16_t kNoSlot = 0xFFFF;
+constexpr uint8_t kDirichletBit = 0x80;  // in the per-node phase byte
+constexpr int kMaxRanges = 127;          // distinct (Ts, Tl) pairs
+
+// Arguments of the block-variant kernels (device pointers).
+template <typename real>
+struct BlockArgs {
+    const BlockInfo *blocks;
+    int32_t n_blocks;
+    // nodes, internal order: [0, n_int) interior, [n_int, n_nodes) shared
+    real *E;                  // enthalpy content, J (state, updated in place)
+    const real *C;            // sensible capacity, J/K
+    const real *Lc;           // latent capacity, J
+    const uint8_t *ph;        // phase-range index | kDirichletBit
+    const real *ranges;       // [n_ranges][2] (Ts, Tl)
+    int64_t n_int, n_nodes;
+    // elements: w[k * e_stride + p], k = 0..5 for corner pairs
+    // (0,1) (0,2) (0,3) (1,2) (1,3) (2,3): w_ab = -K^e_ab
+    const real *w;
+    int64_t e_stride;
+    // faces: fa[p] = h A / 12, fg[p] = A/3 (h T_inf - q)
+    const real *fa;
+    const real *fg;
+    // schedule
+    const int32_t *grp;
+    const uint16_t *sched;
+    // shared-node exchange
+    const int32_t *copy_node; // [n_copies]
+    real *P;                  // [n_copies] partial sums
+    const int32_t *sh_ptr;    // [n_sh + 1]
+    const int32_t *sh_copy;   // [n_copies]
+    // FP64 energy bookkeeping
+    double *epart;            // [n_blocks][2]: sum E, latent (interior nodes)
+    double *qcum;             // [n_blocks] cumulative boundary heat
+    double *epart2;           // [n_sh_ctas][2]: sum E, latent (shared nodes)
+};
+
+// Arguments of the atomic / coloured variants (device pointers).
+template <typename real>
+struct FlatArgs {
+    real *E;
+    const real *C;
+    const real *Lc;
+    const uint8_t *ph;
+    const real *ranges;
+    int64_t n_nodes;
+    real *T;                  // [n_nodes] temperatures of step n
+    real *R;                  // [n_nodes] residual accumulator
+    const int32_t *conn;      // [4][e_stride] internal node ids (SoA)
+    const real *w;            // [6][e_stride]
+    int64_t n_elems, e_stride;
+    const int32_t *fconn;     // [3][f_stride]
+    const real *fa, *fg;
+    int64_t n_faces, f_stride;
+    double *epart;            // [n_node_ctas][2]
+    double *qcum;             // [n_node_ctas] cumulative boundary heat
+};
+
+// Launchers (fem_kernels.cu).  All return a cudaError_t as int.
+// Block variant, one step = launch_block_kernel + launch_shared_update.
+template <typename real>
+int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
+                        void *stream);
+template <typename real>
+int launch_shared_update(const BlockArgs<real> &a, int64_t n_sh, int n_sh_ctas, double dt,
+                         void *stream);
+template <typename real>
+int configure_block_kernel(int threads, size_t smem_bytes);
+
+// Flat variants, one step = temperatures, element pass (atomic adds, or one
+// launch per colour with plain adds), node update with the Robin faces
+// gathered through the node -> faces CSR (nf_ptr, nf_idx).
+template <typename real>
+int launch_flat_temperature(const FlatArgs<real> &a, void *stream);
+template <typename real>
+int launch_flat_elements(const FlatArgs<real> &a, bool atomic, const int64_t *color_start,
+                         int n_colors, void *stream);
+template <typename real>
+int launch_flat_update(const FlatArgs<real> &a, const int32_t *nf_ptr, const int32_t *nf_idx,
+                       int n_node_ctas, double dt, void *stream);
+
+// Initial state / read-back kernels.
+template <typename real>
+int launch_set_temperature(real *E, const real *C, const real *Lc, const uint8_t *ph,
+                           const real *ranges, const double *T_in, const int32_t *node_old,
+                           const double *dirT_int, int64_t n, void *stream);
+template <typename real>
+int launch_set_state(real *E, const double *E_in, const int32_t *node_old, int64_t n,
+                     void *stream);
+template <typename real>
+int launch_get_temperature(const real *E, const real *C, const real *Lc, const uint8_t *ph,
+                           const real *ranges, double *T_out, const int32_t *node_old,
+                           int64_t n, void *stream);
+template <typename real>
+int launch_get_state(const real *E, double *E_out, const int32_t *node_old, int64_t n,
+                     void *stream);
+template <typename real>
+int launch_energy_snapshot(const real *E, const real *C, const real *Lc, const uint8_t *ph,
+                           const real *ranges, int64_t n, double *part, int n_ctas,
+                           void *stream);
+// Sums n_a pairs of part_a, n_b pairs of part_b and n_q entries of q into
+// out[0] (sum E), out[1] (latent), out[2] (boundary heat).
+int launch_energy_reduce(const double *part_a, int64_t n_a, const double *part_b, int64_t n_b,
+                         const double *q, int64_t n_q, double *out, void *stream);
+
+}  // namespace fem

@@ -1,0 +1,637 @@
+// Host-side preprocessing of libfem.  See fem_plan.h.
+#include "fem_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <thread>
+
+namespace fem {
+
+namespace {
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+inline void sub3(const double *a, const double *b, double *o)
+{
+    o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
+}
+inline void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// corner pair index used by the six stored conductances
+constexpr int kPair[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
+
+}  // namespace
+
+void build_node_elems(int64_t N, int64_t E, const int32_t *tets, NodeElems &out)
+{
+    out.ptr.assign((size_t)N + 1, 0);
+    for (int64_t i = 0; i < 4 * E; i++) out.ptr[(size_t)tets[i] + 1]++;
+    for (int64_t n = 0; n < N; n++) out.ptr[n + 1] += out.ptr[n];
+    out.elem.resize((size_t)(4 * E));
+    std::vector<int64_t> fill(out.ptr.begin(), out.ptr.end() - 1);
+    for (int64_t e = 0; e < E; e++)
+        for (int c = 0; c < 4; c++) out.elem[fill[tets[4 * e + c]]++] = (int32_t)e;
+}
+
+double tet_signed_volume(const double *x0, const double *x1, const double *x2, const double *x3)
+{
+    double a[3], b[3], c[3], bc[3];
+    sub3(x1, x0, a); sub3(x2, x0, b); sub3(x3, x0, c);
+    cross3(b, c, bc);
+    return dot3(a, bc) / 6.0;
+}
+
+void tet_conductances(const double *x0, const double *x1, const double *x2, const double *x3,
+                      double k, double w[6], double *abs_vol)
+{
+    const double *x[4] = {x0, x1, x2, x3};
+    double V = std::fabs(tet_signed_volume(x0, x1, x2, x3));
+    double g[4][3];
+    for (int a = 0; a < 4; a++) {
+        // the face opposite corner a: corners j, k, l
+        int j = (a + 1) & 3, kk = (a + 2) & 3, l = (a + 3) & 3;
+        double u[3], v[3], n[3], d[3];
+        sub3(x[kk], x[j], u);
+        sub3(x[l], x[j], v);
+        cross3(u, v, n);          // |n| = 2 * face area
+        sub3(x[a], x[j], d);
+        double s = dot3(n, d) > 0.0 ? 1.0 : -1.0;  // make n point towards a
+        // grad N_a points into the tet towards a, |grad N_a| = area / (3V)
+        for (int q = 0; q < 3; q++) g[a][q] = s * n[q] / (6.0 * V);
+    }
+    for (int a = 0; a < 4; a++)
+        for (int b = a + 1; b < 4; b++) w[kPair[a][b]] = -k * V * dot3(g[a], g[b]);
+    *abs_vol = V;
+}
+
+int64_t mesh_bandwidth(int64_t E, const int32_t *tets, const int32_t *perm)
+{
+    int64_t bw = 0;
+    for (int64_t e = 0; e < E; e++) {
+        int64_t lo = INT64_MAX, hi = INT64_MIN;
+        for (int c = 0; c < 4; c++) {
+            int64_t v = perm ? perm[tets[4 * e + c]] : tets[4 * e + c];
+            lo = std::min(lo, v);
+            hi = std::max(hi, v);
+        }
+        bw = std::max(bw, hi - lo);
+    }
+    return bw;
+}
+
+namespace {
+
+// node graph (unique neighbours) as CSR
+void node_graph(int64_t N, const int32_t *tets, const NodeElems &adj, std::vector<int64_t> &ptr,
+                std::vector<int32_t> &nbr)
+{
+    std::vector<int32_t> mark((size_t)N, -1);
+    ptr.assign((size_t)N + 1, 0);
+    for (int64_t n = 0; n < N; n++) {
+        int64_t d = 0;
+        mark[n] = (int32_t)n;
+        for (int64_t p = adj.ptr[n]; p < adj.ptr[n + 1]; p++) {
+            int64_t e = adj.elem[p];
+            for (int c = 0; c < 4; c++) {
+                int32_t m = tets[4 * e + c];
+                if (mark[m] != n) { mark[m] = (int32_t)n; d++; }
+            }
+        }
+        ptr[n + 1] = ptr[n] + d;
+    }
+    nbr.resize((size_t)ptr[N]);
+    std::fill(mark.begin(), mark.end(), -1);
+    for (int64_t n = 0; n < N; n++) {
+        int64_t q = ptr[n];
+        mark[n] = (int32_t)n;
+        for (int64_t p = adj.ptr[n]; p < adj.ptr[n + 1]; p++) {
+            int64_t e = adj.elem[p];
+            for (int c = 0; c < 4; c++) {
+                int32_t m = tets[4 * e + c];
+                if (mark[m] != n) { mark[m] = (int32_t)n; nbr[q++] = m; }
+            }
+        }
+    }
+}
+
+// BFS from root over nodes with done[] == 0; returns the number of levels
+// and the nodes of the last level.
+int bfs_levels(int32_t root, const std::vector<int64_t> &ptr, const std::vector<int32_t> &nbr,
+               const std::vector<uint8_t> &done, std::vector<int32_t> &stamp, int32_t tag,
+               std::vector<int32_t> &queue, std::vector<int32_t> &last)
+{
+    queue.clear();
+    queue.push_back(root);
+    stamp[root] = tag;
+    size_t head = 0;
+    int levels = 0;
+    while (head < queue.size()) {
+        size_t end = queue.size();
+        last.assign(queue.begin() + (int64_t)head, queue.begin() + (int64_t)end);
+        levels++;
+        for (; head < end; head++) {
+            int32_t u = queue[head];
+            for (int64_t p = ptr[u]; p < ptr[u + 1]; p++) {
+                int32_t v = nbr[p];
+                if (!done[v] && stamp[v] != tag) { stamp[v] = tag; queue.push_back(v); }
+            }
+        }
+    }
+    return levels;
+}
+
+}  // namespace
+
+void rcm_order(int64_t N, int64_t E, const int32_t *tets, const NodeElems &adj,
+               std::vector<int32_t> &perm)
+{
+    (void)E;
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> nbr;
+    node_graph(N, tets, adj, ptr, nbr);
+    auto deg = [&](int32_t v) { return ptr[v + 1] - ptr[v]; };
+    std::vector<uint8_t> done((size_t)N, 0);
+    std::vector<int32_t> stamp((size_t)N, -1), queue, last, order, cand;
+    order.reserve((size_t)N);
+    int32_t tag = 0;
+    for (int64_t seed = 0; seed < N; seed++) {
+        if (done[seed]) continue;
+        // pseudo-peripheral node of this component (George & Liu)
+        int32_t r = (int32_t)seed;
+        bfs_levels(r, ptr, nbr, done, stamp, ++tag, queue, last);
+        // start from a minimum-degree node of the component
+        for (int32_t v : queue)
+            if (deg(v) < deg(r) || (deg(v) == deg(r) && v < r)) r = v;
+        int ecc = bfs_levels(r, ptr, nbr, done, stamp, ++tag, queue, last);
+        for (int it = 0; it < 8; it++) {
+            int32_t c = last[0];
+            for (int32_t v : last)
+                if (deg(v) < deg(c) || (deg(v) == deg(c) && v < c)) c = v;
+            int ecc_c = bfs_levels(c, ptr, nbr, done, stamp, ++tag, queue, last);
+            if (ecc_c > ecc) { r = c; ecc = ecc_c; } else break;
+        }
+        // Cuthill-McKee from r: neighbours in ascending degree
+        size_t head = order.size();
+        order.push_back(r);
+        done[r] = 1;
+        while (head < order.size()) {
+            int32_t u = order[head++];
+            cand.clear();
+            for (int64_t p = ptr[u]; p < ptr[u + 1]; p++) {
+                int32_t v = nbr[p];
+                if (!done[v]) { done[v] = 1; cand.push_back(v); }
+            }
+            std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+                return deg(a) != deg(b) ? deg(a) < deg(b) : a < b;
+            });
+            for (int32_t v : cand) order.push_back(v);
+        }
+    }
+    perm.resize((size_t)N);
+    for (int64_t i = 0; i < N; i++) perm[order[i]] = (int32_t)(N - 1 - i);
+}
+
+std::string face_owners(int64_t F, const int32_t *faces, const int32_t *tets,
+                        const NodeElems &adj, std::vector<int32_t> &owner)
+{
+    owner.assign((size_t)F, -1);
+    for (int64_t f = 0; f < F; f++) {
+        int32_t a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+        if (a == b || b == c || a == c)
+            return "face " + std::to_string(f) + " repeats a node";
+        int count = 0;
+        for (int64_t p = adj.ptr[a]; p < adj.ptr[a + 1]; p++) {
+            int64_t e = adj.elem[p];
+            bool hb = false, hc = false;
+            for (int q = 0; q < 4; q++) {
+                hb |= tets[4 * e + q] == b;
+                hc |= tets[4 * e + q] == c;
+            }
+            if (hb && hc) { count++; owner[f] = (int32_t)e; }
+        }
+        if (count != 1)
+            return "face " + std::to_string(f) + " is a face of " + std::to_string(count) +
+                   " tets (a boundary face belongs to exactly one)";
+    }
+    return "";
+}
+
+int greedy_color(int64_t N, int64_t E, const int32_t *tets, const int32_t *order,
+                 std::vector<int32_t> &color)
+{
+    constexpr int W = 4;  // up to 256 colours
+    std::vector<uint64_t> used((size_t)N * W, 0);
+    color.assign((size_t)E, -1);
+    int ncol = 0;
+    for (int64_t i = 0; i < E; i++) {
+        int64_t e = order ? order[i] : i;
+        uint64_t m[W] = {0, 0, 0, 0};
+        for (int c = 0; c < 4; c++)
+            for (int w = 0; w < W; w++) m[w] |= used[(size_t)tets[4 * e + c] * W + w];
+        int col = -1;
+        for (int w = 0; w < W && col < 0; w++)
+            if (~m[w]) col = 64 * w + __builtin_ctzll(~m[w]);
+        if (col < 0) return -1;
+        color[e] = col;
+        for (int c = 0; c < 4; c++)
+            used[(size_t)tets[4 * e + c] * W + col / 64] |= 1ull << (col % 64);
+        ncol = std::max(ncol, col + 1);
+    }
+    return ncol;
+}
+
+// ---------------------------------------------------------------------------
+// Recursive coordinate bisection of element centroids
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Cen {
+    float x[3];
+    int32_t id;
+};
+
+// Splits a[0, n) into `parts` parts of balanced size: the first parts/2
+// parts take the n*(parts/2)/parts items with the smallest coordinate along
+// the longest axis of the bounding box, recursively.
+void rcb(Cen *a, int64_t n, int64_t parts, int depth)
+{
+    if (parts <= 1) return;
+    float lo[3] = {a[0].x[0], a[0].x[1], a[0].x[2]}, hi[3] = {lo[0], lo[1], lo[2]};
+    for (int64_t i = 1; i < n; i++)
+        for (int d = 0; d < 3; d++) {
+            lo[d] = std::min(lo[d], a[i].x[d]);
+            hi[d] = std::max(hi[d], a[i].x[d]);
+        }
+    int ax = 0;
+    for (int d = 1; d < 3; d++)
+        if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+    int64_t p1 = parts / 2, p2 = parts - p1;
+    int64_t mid = n * p1 / parts;
+    std::nth_element(a, a + mid, a + n, [ax](const Cen &u, const Cen &v) {
+        return u.x[ax] != v.x[ax] ? u.x[ax] < v.x[ax] : u.id < v.id;
+    });
+    if (depth < 3 && n > (1 << 20)) {
+        std::thread t([=] { rcb(a, mid, p1, depth + 1); });
+        rcb(a + mid, n - mid, p2, depth + 1);
+        t.join();
+    } else {
+        rcb(a, mid, p1, depth + 1);
+        rcb(a + mid, n - mid, p2, depth + 1);
+    }
+}
+
+}  // namespace
+
+std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int32_t *tets,
+                             const std::vector<int32_t> &rank, int64_t F,
+                             const int32_t *faces, const std::vector<int32_t> &face_owner,
+                             int block_elems, BlockPlan &out)
+{
+    out = BlockPlan();
+    out.N = N; out.E = E; out.F = F;
+    int64_t nparts = std::max<int64_t>(1, (E + block_elems - 1) / block_elems);
+    // --- partition: element order and part starts
+    std::vector<Cen> cen((size_t)E);
+    for (int64_t e = 0; e < E; e++) {
+        double s[3] = {0, 0, 0};
+        for (int c = 0; c < 4; c++)
+            for (int d = 0; d < 3; d++) s[d] += xyz[3 * (size_t)tets[4 * e + c] + d];
+        for (int d = 0; d < 3; d++) cen[e].x[d] = (float)(0.25 * s[d]);
+        cen[e].id = (int32_t)e;
+    }
+    // part p covers [pstart[p], pstart[p+1]) of the bisected order; the
+    // starts follow from the same size recursion that rcb applies.
+    rcb(cen.data(), E, nparts, 0);
+    std::vector<int64_t> pstart((size_t)nparts + 1, 0);
+    {
+        std::function<void(int64_t, int64_t, int64_t, int64_t)> sizes =
+            [&](int64_t off, int64_t n, int64_t parts, int64_t first) {
+                if (parts <= 1) { pstart[(size_t)first] = off; return; }
+                int64_t p1 = parts / 2;
+                int64_t mid = n * p1 / parts;
+                sizes(off, mid, p1, first);
+                sizes(off + mid, n - mid, parts - p1, first + p1);
+            };
+        sizes(0, E, nparts, 0);
+        pstart[(size_t)nparts] = E;
+    }
+    std::vector<int32_t> eorder((size_t)E);
+    for (int64_t i = 0; i < E; i++) eorder[i] = cen[i].id;
+    std::vector<Cen>().swap(cen);
+    std::vector<int32_t> eblock((size_t)E);
+    for (int64_t p = 0; p < nparts; p++)
+        for (int64_t i = pstart[p]; i < pstart[p + 1]; i++) eblock[eorder[i]] = (int32_t)p;
+    // --- faces grouped by the block of their owner element
+    std::vector<int64_t> fcount((size_t)nparts + 1, 0);
+    for (int64_t f = 0; f < F; f++) fcount[eblock[face_owner[f]] + 1]++;
+    for (int64_t p = 0; p < nparts; p++) fcount[p + 1] += fcount[p];
+    std::vector<int32_t> forder((size_t)F);
+    {
+        std::vector<int64_t> fill(fcount.begin(), fcount.end() - 1);
+        for (int64_t f = 0; f < F; f++) forder[fill[eblock[face_owner[f]]]++] = (int32_t)f;
+    }
+    // --- node classification: number of distinct blocks touching each node
+    std::vector<int32_t> nblk((size_t)N, 0), lastb((size_t)N, -1);
+    for (int64_t p = 0; p < nparts; p++)
+        for (int64_t i = pstart[p]; i < pstart[p + 1]; i++)
+            for (int c = 0; c < 4; c++) {
+                int32_t n = tets[4 * (size_t)eorder[i] + c];
+                if (lastb[n] != p) { lastb[n] = (int32_t)p; nblk[n]++; }
+            }
+    for (int64_t n = 0; n < N; n++)
+        if (nblk[n] == 0) return "node " + std::to_string(n) + " belongs to no tet";
+    // signatures (sorted block lists) of shared nodes
+    std::vector<int64_t> sig_ptr((size_t)N + 1, 0);
+    for (int64_t n = 0; n < N; n++) sig_ptr[n + 1] = sig_ptr[n] + (nblk[n] > 1 ? nblk[n] : 0);
+    std::vector<int32_t> sig((size_t)sig_ptr[N]);
+    {
+        std::vector<int64_t> fill(sig_ptr.begin(), sig_ptr.end() - 1);
+        std::fill(lastb.begin(), lastb.end(), -1);
+        for (int64_t p = 0; p < nparts; p++)
+            for (int64_t i = pstart[p]; i < pstart[p + 1]; i++)
+                for (int c = 0; c < 4; c++) {
+                    int32_t n = tets[4 * (size_t)eorder[i] + c];
+                    if (nblk[n] > 1 && lastb[n] != p) { lastb[n] = (int32_t)p; sig[fill[n]++] = (int32_t)p; }
+                }
+    }
+    std::vector<int32_t> shared;
+    for (int64_t n = 0; n < N; n++)
+        if (nblk[n] > 1) shared.push_back((int32_t)n);
+    std::sort(shared.begin(), shared.end(), [&](int32_t a, int32_t b) {
+        int64_t la = sig_ptr[a + 1] - sig_ptr[a], lb = sig_ptr[b + 1] - sig_ptr[b];
+        const int32_t *sa = &sig[sig_ptr[a]], *sb = &sig[sig_ptr[b]];
+        for (int64_t k = 0; k < std::min(la, lb); k++)
+            if (sa[k] != sb[k]) return sa[k] < sb[k];
+        if (la != lb) return la < lb;
+        return rank[a] < rank[b];
+    });
+    const int64_t n_sh = (int64_t)shared.size();
+    const int64_t n_int = N - n_sh;
+    std::vector<int32_t> sid((size_t)N, -1);
+    for (int64_t s = 0; s < n_sh; s++) sid[shared[s]] = (int32_t)s;
+    out.n_int = n_int; out.n_sh = n_sh;
+    out.node_new.assign((size_t)N, -1);
+    out.node_old.assign((size_t)N, -1);
+    for (int64_t s = 0; s < n_sh; s++) {
+        out.node_new[shared[s]] = (int32_t)(n_int + s);
+        out.node_old[n_int + s] = shared[s];
+    }
+    // shared-node copy lists
+    out.sh_ptr.assign((size_t)n_sh + 1, 0);
+    for (int64_t s = 0; s < n_sh; s++) out.sh_ptr[s + 1] = out.sh_ptr[s] + nblk[shared[s]];
+    out.n_copies = out.sh_ptr[n_sh];
+    out.sh_copy.assign((size_t)out.n_copies, -1);
+    out.copy_node.assign((size_t)out.n_copies, -1);
+    std::vector<int32_t> sh_fill(out.sh_ptr.begin(), out.sh_ptr.end() - 1);
+
+    // --- per-block layout
+    int64_t epos = 0, fpos = 0, cpos = 0, ipos = 0, rounds = 0;
+    out.blocks.resize((size_t)nparts);
+    std::vector<int32_t> loc((size_t)N, -1), cnt((size_t)N, 0);
+    std::vector<int32_t> nodes_int, nodes_sh, row_ptr, rows, fillr;
+    // elem_order / face_order / elem_nodes are sized at the end
+    std::vector<int32_t> elem_order, face_order;
+    elem_order.reserve((size_t)(E + 8 * nparts));
+    face_order.reserve((size_t)(F + 8 * nparts));
+    out.grp.reserve((size_t)(nparts * 40));
+    for (int64_t p = 0; p < nparts; p++) {
+        BlockInfo bi{};
+        epos = round_up(epos, 8);
+        fpos = round_up(fpos, 8);
+        elem_order.resize((size_t)epos, -1);
+        face_order.resize((size_t)fpos, -1);
+        bi.e0 = (int32_t)epos;
+        bi.ne = (int32_t)(pstart[p + 1] - pstart[p]);
+        bi.f0 = (int32_t)fpos;
+        bi.nf = (int32_t)(fcount[p + 1] - fcount[p]);
+        bi.ne_pad = (int32_t)round_up(bi.ne, 32);
+        bi.nf_pad = bi.nf ? (int32_t)round_up(bi.nf, 32) : 0;
+        int64_t nslot = 4 * (int64_t)bi.ne_pad + 3 * (int64_t)bi.nf_pad;
+        if (nslot > 65535)
+            return "block " + std::to_string(p) + " needs " + std::to_string(nslot) +
+                   " slots (> 65535); lower block_elems";
+        const int32_t *pe = &eorder[(size_t)pstart[p]];
+        const int32_t *pf = &forder[(size_t)fcount[p]];
+        // local nodes and their slot counts
+        nodes_int.clear();
+        nodes_sh.clear();
+        for (int32_t i = 0; i < bi.ne; i++)
+            for (int c = 0; c < 4; c++) {
+                int32_t n = tets[4 * (size_t)pe[i] + c];
+                if (cnt[n]++ == 0) (nblk[n] == 1 ? nodes_int : nodes_sh).push_back(n);
+            }
+        for (int32_t i = 0; i < bi.nf; i++)
+            for (int c = 0; c < 3; c++) cnt[faces[3 * (size_t)pf[i] + c]]++;
+        std::sort(nodes_int.begin(), nodes_int.end(), [&](int32_t a, int32_t b) {
+            return cnt[a] != cnt[b] ? cnt[a] > cnt[b] : rank[a] < rank[b];
+        });
+        std::sort(nodes_sh.begin(), nodes_sh.end(),
+                  [&](int32_t a, int32_t b) { return sid[a] < sid[b]; });
+        bi.n0 = (int32_t)ipos;
+        bi.nint = (int32_t)nodes_int.size();
+        bi.c0 = (int32_t)cpos;
+        bi.nsh = (int32_t)nodes_sh.size();
+        for (int32_t k = 0; k < bi.nint; k++) {
+            int32_t n = nodes_int[k];
+            out.node_new[n] = (int32_t)(ipos + k);
+            out.node_old[ipos + k] = n;
+            loc[n] = k;
+        }
+        for (int32_t k = 0; k < bi.nsh; k++) {
+            int32_t n = nodes_sh[k];
+            loc[n] = bi.nint + k;
+            out.copy_node[cpos + k] = (int32_t)(n_int + sid[n]);
+            out.sh_copy[sh_fill[sid[n]]++] = (int32_t)(cpos + k);
+        }
+        const int32_t nloc = bi.nint + bi.nsh;
+        // rows: local node -> slots, elements first (block order), then faces
+        row_ptr.assign((size_t)nloc + 1, 0);
+        for (int32_t l = 0; l < nloc; l++) {
+            int32_t n = l < bi.nint ? nodes_int[l] : nodes_sh[l - bi.nint];
+            row_ptr[l + 1] = row_ptr[l] + cnt[n];
+        }
+        rows.assign((size_t)row_ptr[nloc], 0);
+        fillr.assign(row_ptr.begin(), row_ptr.end() - 1);
+        for (int32_t i = 0; i < bi.ne; i++)
+            for (int c = 0; c < 4; c++) {
+                int32_t l = loc[tets[4 * (size_t)pe[i] + c]];
+                rows[fillr[l]++] = c * bi.ne_pad + i;
+            }
+        for (int32_t i = 0; i < bi.nf; i++)
+            for (int c = 0; c < 3; c++) {
+                int32_t l = loc[faces[3 * (size_t)pf[i] + c]];
+                if (l < 0) return "face owner bookkeeping failed";
+                rows[fillr[l]++] = 4 * bi.ne_pad + c * bi.nf_pad + i;
+            }
+        // 32-lane groups
+        bi.g0 = (int32_t)out.grp.size();
+        bi.ngrp = (nloc + 31) / 32;
+        for (int32_t g = 0; g < bi.ngrp; g++) {
+            out.grp.push_back((int32_t)rounds);
+            int32_t J = 0;
+            for (int32_t lane = 0; lane < 32; lane++) {
+                int32_t l = 32 * g + lane;
+                if (l < nloc) J = std::max(J, row_ptr[l + 1] - row_ptr[l]);
+            }
+            for (int32_t j = 0; j < J; j++)
+                for (int32_t lane = 0; lane < 32; lane++) {
+                    int32_t l = 32 * g + lane;
+                    uint16_t s = kNoSlot;
+                    if (l < nloc && j < row_ptr[l + 1] - row_ptr[l])
+                        s = (uint16_t)rows[row_ptr[l] + j];
+                    out.sched.push_back(s);
+                }
+            rounds += J;
+        }
+        out.grp.push_back((int32_t)rounds);
+        // element / face positions
+        for (int32_t i = 0; i < bi.ne; i++) elem_order.push_back(pe[i]);
+        for (int32_t i = 0; i < bi.nf; i++) face_order.push_back(pf[i]);
+        epos += bi.ne;
+        fpos += bi.nf;
+        ipos += bi.nint;
+        cpos += bi.nsh;
+        out.max_ne = std::max(out.max_ne, bi.ne);
+        out.max_slots = std::max(out.max_slots, (size_t)nslot);
+        out.max_nloc = std::max(out.max_nloc, (size_t)nloc);
+        // reset scratch
+        for (int32_t n : nodes_int) { cnt[n] = 0; loc[n] = -1; }
+        for (int32_t n : nodes_sh) { cnt[n] = 0; loc[n] = -1; }
+        out.blocks[(size_t)p] = bi;
+    }
+    if (ipos != n_int || cpos != out.n_copies) return "node classification bookkeeping failed";
+    out.E_pad = round_up(std::max<int64_t>(epos, 1), 8);
+    out.F_pad = round_up(std::max<int64_t>(fpos, 1), 8);
+    elem_order.resize((size_t)out.E_pad, -1);
+    face_order.resize((size_t)out.F_pad, -1);
+    out.elem_order.swap(elem_order);
+    out.face_order.swap(face_order);
+    out.n_rounds = rounds;
+    out.elem_nodes.assign((size_t)out.E_pad * 4, -1);
+    for (int64_t i = 0; i < out.E_pad; i++) {
+        int32_t e = out.elem_order[i];
+        if (e >= 0)
+            for (int c = 0; c < 4; c++) out.elem_nodes[4 * i + c] = out.node_new[tets[4 * (size_t)e + c]];
+    }
+    out.face_nodes.assign((size_t)out.F_pad * 3, -1);
+    for (int64_t i = 0; i < out.F_pad; i++) {
+        int32_t f = out.face_order[i];
+        if (f >= 0)
+            for (int c = 0; c < 3; c++) out.face_nodes[3 * i + c] = out.node_new[faces[3 * (size_t)f + c]];
+    }
+    return "";
+}
+
+std::string build_flat_plan(int64_t N, int64_t E, const int32_t *tets,
+                            const std::vector<int32_t> &rank, int64_t F, bool colored,
+                            FlatPlan &out)
+{
+    out = FlatPlan();
+    out.N = N; out.E = E; out.F = F;
+    out.node_new = rank;
+    out.node_old.assign((size_t)N, -1);
+    for (int64_t n = 0; n < N; n++) out.node_old[rank[n]] = (int32_t)n;
+    std::vector<int32_t> minnode((size_t)E);
+    for (int64_t e = 0; e < E; e++) {
+        int32_t m = INT32_MAX;
+        for (int c = 0; c < 4; c++) m = std::min(m, rank[tets[4 * e + c]]);
+        minnode[e] = m;
+    }
+    std::vector<int32_t> order((size_t)E);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return minnode[a] < minnode[b]; });
+    if (colored) {
+        std::vector<int32_t> color;
+        int nc = greedy_color(N, E, tets, order.data(), color);
+        if (nc < 0) return "greedy colouring needs more than 256 colours";
+        out.n_colors = nc;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return color[a] < color[b]; });
+        // colour classes start on 8-element boundaries
+        out.color_start.assign((size_t)nc + 1, 0);
+        std::vector<int32_t> padded;
+        int64_t i = 0;
+        for (int c = 0; c < nc; c++) {
+            while (padded.size() % 8) padded.push_back(-1);
+            out.color_start[c] = (int64_t)padded.size();
+            while (i < E && color[order[i]] == c) padded.push_back(order[i++]);
+        }
+        while (padded.size() % 8 || padded.empty()) padded.push_back(-1);
+        out.color_start[nc] = (int64_t)padded.size();
+        out.elem_order.swap(padded);
+    } else {
+        out.elem_order = order;
+        while (out.elem_order.size() % 8 || out.elem_order.empty()) out.elem_order.push_back(-1);
+    }
+    out.E_pad = (int64_t)out.elem_order.size();
+    out.face_order.resize((size_t)F);
+    std::iota(out.face_order.begin(), out.face_order.end(), 0);
+    while (out.face_order.size() % 8 || out.face_order.empty()) out.face_order.push_back(-1);
+    out.F_pad = (int64_t)out.face_order.size();
+    return "";
+}
+
+double gershgorin_dt(int64_t N, int64_t E, const int32_t *tets, const double *w,
+                     const NodeElems &adj, int64_t F, const int32_t *faces, const double *fa,
+                     const double *C, const uint8_t *is_dir)
+{
+    (void)E;
+    // node -> faces
+    std::vector<int64_t> fptr((size_t)N + 1, 0);
+    for (int64_t i = 0; i < 3 * F; i++) fptr[(size_t)faces[i] + 1]++;
+    for (int64_t n = 0; n < N; n++) fptr[n + 1] += fptr[n];
+    std::vector<int32_t> fidx((size_t)(3 * F));
+    {
+        std::vector<int64_t> fill(fptr.begin(), fptr.end() - 1);
+        for (int64_t f = 0; f < F; f++)
+            for (int c = 0; c < 3; c++) fidx[fill[faces[3 * f + c]]++] = (int32_t)f;
+    }
+    double lam = 0.0;
+    std::vector<int32_t> col;
+    std::vector<double> val;
+    auto add = [&](int32_t j, double v) {
+        for (size_t q = 0; q < col.size(); q++)
+            if (col[q] == j) { val[q] += v; return; }
+        col.push_back(j);
+        val.push_back(v);
+    };
+    for (int64_t i = 0; i < N; i++) {
+        if (is_dir && is_dir[i]) continue;
+        col.clear();
+        val.clear();
+        for (int64_t p = adj.ptr[i]; p < adj.ptr[i + 1]; p++) {
+            int64_t e = adj.elem[p];
+            int a = 0;
+            while (tets[4 * e + a] != i) a++;
+            for (int b = 0; b < 4; b++) {
+                if (b == a) continue;
+                double wab = w[6 * e + kPair[a][b]];
+                add((int32_t)i, wab);                 // K_ii = sum_b w_ab
+                add(tets[4 * e + b], -wab);           // K_ij = -w_ab
+            }
+        }
+        for (int64_t p = fptr[i]; p < fptr[i + 1]; p++) {
+            int64_t f = fidx[p];
+            for (int c = 0; c < 3; c++) {
+                int32_t j = faces[3 * f + c];
+                add(j, j == i ? 2.0 * fa[f] : fa[f]);
+            }
+        }
+        double s = 0.0;
+        for (double v : val) s += std::fabs(v);
+        lam = std::max(lam, s / C[i]);
+    }
+    return lam > 0.0 ? 2.0 / lam : INFINITY;
+}
+
+}  // namespace fem

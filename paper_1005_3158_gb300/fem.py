@@ -1,0 +1,378 @@
+"""Thin ctypes binding of libfem (include/fem.h).
+
+Argument marshalling only: every computation of the step runs in the CUDA
+kernels of ``libfem.so``.  The module-level functions carry the C names; the
+``Mesh`` class wraps one handle.  Importing this module loads the library
+and raises if it has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfem.so")
+
+FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_ESTATE, FEM_EUNSTABLE, FEM_ETIMEOUT = range(7)
+FEM_FP64, FEM_FP32 = 0, 1
+FEM_VARIANT_BLOCK, FEM_VARIANT_ATOMIC, FEM_VARIANT_COLORED = 0, 1, 2
+STATUS_NAMES = {0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_ENOMEM", 3: "FEM_ECUDA", 4: "FEM_ESTATE",
+                5: "FEM_EUNSTABLE", 6: "FEM_ETIMEOUT"}
+VARIANTS = {"block": FEM_VARIANT_BLOCK, "atomic": FEM_VARIANT_ATOMIC,
+            "colored": FEM_VARIANT_COLORED}
+PRECISIONS = {"fp64": FEM_FP64, "f64": FEM_FP64, "fp32": FEM_FP32, "f32": FEM_FP32}
+
+# names declared in include/fem.h
+ABI_SYMBOLS = (
+    "fem_mesh_create", "fem_mesh_create_ex", "fem_set_materials", "fem_set_boundary",
+    "fem_set_dirichlet", "fem_set_temperature", "fem_stable_dt", "fem_step", "fem_step_profile",
+    "fem_get_temperature", "fem_get_enthalpy", "fem_get_energy", "fem_set_stream",
+    "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
+    "fem_last_error", "fem_mesh_destroy",
+)
+
+
+class FemMaterial(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("c", ctypes.c_double), ("k", ctypes.c_double),
+                ("latent", ctypes.c_double), ("T_solidus", ctypes.c_double),
+                ("T_liquidus", ctypes.c_double)]
+
+
+class FemOptions(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("block_elems", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class FemInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_nodes", "n_tets", "n_faces", "n_blocks", "n_interior_nodes", "n_shared_nodes",
+        "n_shared_copies", "n_sched_rounds", "n_colors", "bandwidth_input",
+        "bandwidth_internal", "max_block_elems", "device_bytes")] + [
+        (n, ctypes.c_int32) for n in ("precision", "variant", "threads", "reorder")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class FemError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+            f"g.build()\"` (the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    i64 = ctypes.c_int64
+    sig = {
+        "fem_mesh_create": [dp, i64, ip, i64, ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)],
+        "fem_mesh_create_ex": [dp, i64, ip, i64, ip, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(FemOptions), ctypes.POINTER(P)],
+        "fem_set_materials": [P, ctypes.POINTER(FemMaterial), ctypes.c_int32],
+        "fem_set_boundary": [P, ip, i64, dp, dp, dp],
+        "fem_set_dirichlet": [P, ip, i64, dp],
+        "fem_set_temperature": [P, dp],
+        "fem_stable_dt": [P, dp],
+        "fem_step": [P, i64, ctypes.c_double],
+        "fem_step_profile": [P, i64, ctypes.c_double, dp, ctypes.c_int32,
+                             ctypes.POINTER(ctypes.c_int32)],
+        "fem_get_temperature": [P, P],
+        "fem_get_enthalpy": [P, P],
+        "fem_get_energy": [P, dp],
+        "fem_set_stream": [P, P],
+        "fem_get_state": [P, P, ctypes.POINTER(i64), dp],
+        "fem_set_state": [P, P, i64, ctypes.c_double],
+        "fem_mesh_info": [P, ctypes.POINTER(FemInfo)],
+        "fem_rcm_order": [i64, ip, i64, ip, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "fem_plan_array": [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fem_last_error.restype = ctypes.c_char_p
+    lib.fem_last_error.argtypes = []
+    lib.fem_mesh_destroy.restype = None
+    lib.fem_mesh_destroy.argtypes = [P]
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(st):
+    if st != FEM_OK:
+        raise FemError(st, _lib.fem_last_error().decode())
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _pi(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _host_ptr(buf, n, writable):
+    """Pointer to a host buffer of n doubles: a numpy array or a (pinned)
+    torch CPU tensor.  Returns (pointer, keep-alive)."""
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.float64 or not buf.flags["C_CONTIGUOUS"] or buf.size < n:
+            raise ValueError("host buffer must be a C-contiguous float64 array of size >= n_nodes")
+        if writable and not buf.flags["WRITEABLE"]:
+            raise ValueError("output buffer is read-only")
+        return ctypes.c_void_p(buf.ctypes.data), buf
+    # torch tensor (duck-typed so the binding does not import torch)
+    if getattr(buf, "device", None) is not None and str(buf.device) != "cpu":
+        raise ValueError("host buffer expected (got a device tensor)")
+    if str(buf.dtype) != "torch.float64" or not buf.is_contiguous() or buf.numel() < n:
+        raise ValueError("host tensor must be contiguous float64 of size >= n_nodes")
+    return ctypes.c_void_p(buf.data_ptr()), buf
+
+
+# ---------------------------------------------------------------------------
+# Module-level functions with the C names
+# ---------------------------------------------------------------------------
+
+def fem_mesh_create(xyz, tets, mat_id, prec=FEM_FP64, reorder=0, options=None):
+    xyz, tets, mat_id = _d(xyz), _i(tets), _i(mat_id)
+    h = ctypes.c_void_p()
+    opt = None
+    if options is not None:
+        opt = FemOptions()
+        opt.variant = int(options.get("variant", 0))
+        opt.block_elems = int(options.get("block_elems", 0))
+        opt.threads = int(options.get("threads", 0))
+    if opt is None:
+        st = _lib.fem_mesh_create(_pd(xyz), xyz.shape[0], _pi(tets), tets.shape[0], _pi(mat_id),
+                                  prec, reorder, ctypes.byref(h))
+    else:
+        st = _lib.fem_mesh_create_ex(_pd(xyz), xyz.shape[0], _pi(tets), tets.shape[0],
+                                     _pi(mat_id), prec, reorder, ctypes.byref(opt),
+                                     ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def fem_set_materials(h, materials):
+    mats = np.asarray(materials, dtype=np.float64).reshape(-1, 6)
+    arr = (FemMaterial * len(mats))(*[FemMaterial(*row) for row in mats])
+    _check(_lib.fem_set_materials(h, arr, len(mats)))
+
+
+def fem_set_boundary(h, faces, hcoef, t_inf, q=None):
+    faces = _i(np.asarray(faces).reshape(-1, 3))
+    hcoef, t_inf = _d(hcoef), _d(t_inf)
+    qq = _d(q) if q is not None else None
+    _check(_lib.fem_set_boundary(h, _pi(faces), faces.shape[0], _pd(hcoef), _pd(t_inf),
+                                 _pd(qq) if qq is not None else None))
+
+
+def fem_set_dirichlet(h, nodes, T):
+    nodes, T = _i(nodes), _d(T)
+    _check(_lib.fem_set_dirichlet(h, _pi(nodes), nodes.shape[0], _pd(T)))
+
+
+def fem_set_temperature(h, T0):
+    T0 = _d(T0)
+    _check(_lib.fem_set_temperature(h, _pd(T0)))
+
+
+def fem_stable_dt(h):
+    dt = ctypes.c_double()
+    _check(_lib.fem_stable_dt(h, ctypes.byref(dt)))
+    return dt.value
+
+
+def fem_step(h, n_steps, dt):
+    _check(_lib.fem_step(h, int(n_steps), float(dt)))
+
+
+def fem_step_profile(h, n_steps, dt):
+    """Run n_steps timing each kernel; returns the summed ms per kernel."""
+    ms = np.zeros(8)
+    n = ctypes.c_int32()
+    _check(_lib.fem_step_profile(h, int(n_steps), float(dt), _pd(ms), 8, ctypes.byref(n)))
+    return ms[:n.value].copy()
+
+
+def fem_get_temperature(h, n_nodes, out=None):
+    out = np.empty(n_nodes) if out is None else out
+    p, _keep = _host_ptr(out, n_nodes, True)
+    _check(_lib.fem_get_temperature(h, p))
+    return out
+
+
+def fem_get_enthalpy(h, n_nodes, out=None):
+    out = np.empty(n_nodes) if out is None else out
+    p, _keep = _host_ptr(out, n_nodes, True)
+    _check(_lib.fem_get_enthalpy(h, p))
+    return out
+
+
+def fem_get_energy(h):
+    out = np.zeros(4)
+    _check(_lib.fem_get_energy(h, _pd(out)))
+    return out
+
+
+def fem_set_stream(h, stream):
+    _check(_lib.fem_set_stream(h, ctypes.c_void_p(int(stream) if stream else 0)))
+
+
+def fem_get_state(h, n_nodes, out=None):
+    out = np.empty(n_nodes) if out is None else out
+    p, _keep = _host_ptr(out, n_nodes, True)
+    step = ctypes.c_int64()
+    t = ctypes.c_double()
+    _check(_lib.fem_get_state(h, p, ctypes.byref(step), ctypes.byref(t)))
+    return out, step.value, t.value
+
+
+def fem_set_state(h, n_nodes, E, step=0, t=0.0):
+    p, _keep = _host_ptr(E, n_nodes, False)
+    _check(_lib.fem_set_state(h, p, int(step), float(t)))
+
+
+def fem_mesh_info(h):
+    info = FemInfo()
+    _check(_lib.fem_mesh_info(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def fem_rcm_order(n_nodes, tets):
+    tets = _i(tets)
+    perm = np.empty(n_nodes, np.int32)
+    b0, b1 = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.fem_rcm_order(n_nodes, _pi(tets), tets.shape[0], _pi(perm), ctypes.byref(b0),
+                              ctypes.byref(b1)))
+    return perm, b0.value, b1.value
+
+
+_PLAN_TYPES = {0: np.int32, 1: np.int32, 2: np.int32, 3: np.int32, 4: np.int32, 5: np.int32,
+               6: np.int32, 7: np.int32, 8: np.uint16, 9: np.int32, 10: np.int32}
+PLAN_ARRAYS = {"node_new": 0, "blocks": 1, "elem_order": 2, "face_order": 3, "copy_node": 4,
+               "sh_ptr": 5, "sh_copy": 6, "grp": 7, "sched": 8, "elem_nodes": 9,
+               "face_nodes": 10}
+
+
+def fem_plan_array(h, which):
+    w = PLAN_ARRAYS[which] if isinstance(which, str) else int(which)
+    p = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    _check(_lib.fem_plan_array(h, w, ctypes.byref(p), ctypes.byref(n)))
+    dt = np.dtype(_PLAN_TYPES[w])
+    if n.value == 0:
+        return np.zeros(0, dt)
+    buf = (ctypes.c_char * (n.value * dt.itemsize)).from_address(p.value)
+    return np.frombuffer(buf, dtype=dt).copy()
+
+
+def fem_last_error():
+    return _lib.fem_last_error().decode()
+
+
+def fem_mesh_destroy(h):
+    _lib.fem_mesh_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Mesh:
+    """One libfem mesh handle built from a ``meshgen.Problem``-like object."""
+
+    def __init__(self, prob, precision="fp64", reorder=1, variant="block", block_elems=0,
+                 threads=0, faces=True, dirichlet=True, set_temperature=True):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        self.n_nodes = int(prob.xyz.shape[0])
+        self.n_tets = int(prob.tets.shape[0])
+        self.h = fem_mesh_create(prob.xyz, prob.tets, prob.mat, prec, reorder,
+                                 {"variant": var, "block_elems": block_elems, "threads": threads})
+        try:
+            fem_set_materials(self.h, prob.materials)
+            if faces and prob.faces.shape[0] > 0:
+                fem_set_boundary(self.h, prob.faces, prob.h, prob.t_inf, prob.q)
+            if dirichlet and prob.dir_nodes.shape[0] > 0:
+                fem_set_dirichlet(self.h, prob.dir_nodes, prob.dir_T)
+            if set_temperature:
+                fem_set_temperature(self.h, prob.T0)
+        except Exception:
+            fem_mesh_destroy(self.h)
+            self.h = None
+            raise
+
+    def close(self):
+        if self.h:
+            fem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stable_dt(self):
+        return fem_stable_dt(self.h)
+
+    def step(self, n, dt):
+        fem_step(self.h, n, dt)
+
+    def step_profile(self, n, dt):
+        return fem_step_profile(self.h, n, dt)
+
+    def set_temperature(self, T0):
+        fem_set_temperature(self.h, T0)
+
+    def temperature(self, out=None):
+        return fem_get_temperature(self.h, self.n_nodes, out)
+
+    def enthalpy(self, out=None):
+        return fem_get_enthalpy(self.h, self.n_nodes, out)
+
+    def energy(self):
+        return fem_get_energy(self.h)
+
+    def state(self, out=None):
+        return fem_get_state(self.h, self.n_nodes, out)
+
+    def set_state(self, E, step=0, t=0.0):
+        fem_set_state(self.h, self.n_nodes, E, step, t)
+
+    def set_stream(self, stream):
+        fem_set_stream(self.h, stream)
+
+    def info(self):
+        return fem_mesh_info(self.h)
+
+    def plan(self, which):
+        return fem_plan_array(self.h, which)

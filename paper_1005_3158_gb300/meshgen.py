@@ -90,41 +90,45 @@ def box_grid(nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 1.0,
              lz: float = 1.0, jitter: float = 0.0, seed: int | None = None):
     """Nodes and Kuhn tets of an nx x ny x nz hex grid on [0,lx]x[0,ly]x[0,lz].
 
-    ``jitter`` moves every interior node by an independent uniform offset in
-    [-jitter, +jitter] x spacing along each axis (boundary nodes stay on the
-    box so the Robin faces stay planar).  Returns (xyz, tets, hex_index,
-    node_flags) where node_flags has bit 2*a (low) / 2*a+1 (high) set for a
-    node on the low / high boundary plane of axis a.
+    Node (i, j, k) has id i + (nx+1) (j + (ny+1) k); hex (i, j, k) has id
+    i + nx (j + ny k) and owns tets 6 id .. 6 id + 5.  ``jitter`` moves every
+    interior node by an independent uniform offset in [-jitter, +jitter] x
+    spacing along each axis (boundary nodes stay on the box so the Robin faces
+    stay planar).  Returns (xyz, tets, hex_index, node_flags) where node_flags
+    has bit 2*a (low) / 2*a+1 (high) set for a node on the low / high
+    boundary plane of axis a.
     """
-    ii, jj, kk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1),
-                             np.arange(nz + 1), indexing="ij")
-    # node id = i + (nx+1)*(j + (ny+1)*k)
-    ii = ii.transpose(2, 1, 0).ravel()
-    jj = jj.transpose(2, 1, 0).ravel()
-    kk = kk.transpose(2, 1, 0).ravel()
+    sx, sy = nx + 1, (nx + 1) * (ny + 1)
+    n_nodes = sy * (nz + 1)
+    node = np.arange(n_nodes, dtype=np.int64)
+    ii = node % sx
+    jj = (node // sx) % (ny + 1)
+    kk = node // sy
     h = np.array([lx / nx, ly / ny, lz / nz])
-    xyz = np.stack([ii * h[0], jj * h[1], kk * h[2]], axis=1).astype(np.float64)
+    xyz = np.empty((n_nodes, 3), dtype=np.float64)
+    xyz[:, 0] = ii * h[0]
+    xyz[:, 1] = jj * h[1]
+    xyz[:, 2] = kk * h[2]
     flags = ((ii == 0) * 1 | (ii == nx) * 2 | (jj == 0) * 4 | (jj == ny) * 8
              | (kk == 0) * 16 | (kk == nz) * 32).astype(np.int32)
+    del ii, jj, kk, node
     if jitter > 0.0:
         rng = rng_of(0 if seed is None else seed)
-        interior = flags == 0
-        d = rng.uniform(-jitter, jitter, size=(int(interior.sum()), 3)) * h
+        interior = np.nonzero(flags == 0)[0]
+        d = rng.uniform(-jitter, jitter, size=(interior.size, 3)) * h
         xyz[interior] += d
-    hi, hj, hk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz),
-                             indexing="ij")
-    hi = hi.transpose(2, 1, 0).ravel()
-    hj = hj.transpose(2, 1, 0).ravel()
-    hk = hk.transpose(2, 1, 0).ravel()
-    nh = hi.size
-    tets = np.empty((nh, 6, 4), dtype=np.int64)
-    sx, sy = nx + 1, (nx + 1) * (ny + 1)
+    nh = nx * ny * nz
+    hx = np.arange(nh, dtype=np.int64)
+    base = (hx % nx) + sx * ((hx // nx) % ny) + sy * (hx // (nx * ny))
+    base = base.astype(np.int32)
+    del hx
+    tets = np.empty((nh, 6, 4), dtype=np.int32)
     for t in range(6):
         for c in range(4):
             o = _KUHN[t, c]
-            tets[:, t, c] = (hi + o[0]) + sx * (hj + o[1]) + sy * (hk + o[2])
-    hex_index = np.repeat(np.arange(nh), 6)
-    return xyz, tets.reshape(-1, 4).astype(np.int32), hex_index, flags
+            tets[:, t, c] = base + int(o[0] + sx * o[1] + sy * o[2])
+    hex_index = np.repeat(np.arange(nh, dtype=np.int32), 6)
+    return xyz, tets.reshape(-1, 4), hex_index, flags
 
 
 _FACE_OMIT = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
@@ -135,11 +139,15 @@ def box_boundary_faces(tets: np.ndarray, node_flags: np.ndarray,
     """Tet faces lying on the box boundary planes selected by ``plane_mask``.
 
     A face is on the boundary exactly when its three nodes share one boundary
-    plane (no interior face of a box grid lies in a boundary plane).
+    plane (no interior face of a box grid lies in a boundary plane).  Faces
+    are listed by omitted corner (0..3), then by tet.
     """
+    # only tets with a boundary node can own a boundary face
+    cand = np.nonzero((node_flags[tets] & plane_mask).any(axis=1))[0]
+    sub = tets[cand]
     out = []
     for omit in _FACE_OMIT:
-        f = tets[:, omit]
+        f = sub[:, omit]
         common = (node_flags[f[:, 0]] & node_flags[f[:, 1]]
                   & node_flags[f[:, 2]] & plane_mask)
         out.append(f[common != 0])
@@ -229,13 +237,18 @@ def block_with_cores(n: int = 220, n_cores: int = 32, seed: int = 1007,
     radii = rng.uniform(0.03, 0.08, size=n_cores) * side
     centres = rng.uniform(0.08 * side, 0.92 * side, size=(n_cores, 3))
     steel = np.zeros(tets.shape[0], dtype=bool)
-    chunk = 1 << 22
-    for s in range(0, tets.shape[0], chunk):
-        c = centroids(xyz, tets[s:s + chunk])
-        m = np.zeros(c.shape[0], dtype=bool)
-        for cc, rr in zip(centres, radii):
-            m |= ((c - cc) ** 2).sum(axis=1) <= rr * rr
-        steel[s:s + chunk] = m
+    hsz = side / n
+    for cc, rr in zip(centres, radii):
+        # only the hexes of the sphere's bounding box (one hex of margin for
+        # the jitter) can hold a tet whose centroid is inside the sphere
+        lo = np.maximum(np.floor((cc - rr) / hsz).astype(int) - 1, 0)
+        hi = np.minimum(np.ceil((cc + rr) / hsz).astype(int) + 1, n - 1)
+        gi, gj, gk = np.meshgrid(np.arange(lo[0], hi[0] + 1), np.arange(lo[1], hi[1] + 1),
+                                 np.arange(lo[2], hi[2] + 1), indexing="ij")
+        hexes = (gi + n * (gj + n * gk)).ravel()
+        cand = (6 * hexes[:, None] + np.arange(6)[None, :]).ravel()
+        c = centroids(xyz, tets[cand])
+        steel[cand[((c - cc) ** 2).sum(axis=1) <= rr * rr]] = True
     mat = steel.astype(np.int32)
     faces = box_boundary_faces(tets, flags)
     hh, ti, q = _robin(faces)

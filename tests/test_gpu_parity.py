@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (max nodal temperature error): FP64 device path <= 1e-9 K, FP32
+bulk path <= 0.05 K, at every 100th of 1000 steps on the 9,261-node unit
+cube, and on small randomised meshes with several blocks and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1005_3158_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 0.05}
+
+
+@pytest.fixture(scope="module")
+def fem():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_3158_gb300 import fem as f
+    return f
+
+
+def _oracle_traj(p, dt, n, every):
+    o = oracle.OracleProblem(p)
+    o.set_temperature(p.T0)
+    out = []
+    for _ in range(n // every):
+        o.step(every, dt)
+        out.append((o.temperature(), o.energy()))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_unit_cube_1000_steps(fem, prec, reorder):
+    p = mg.unit_cube(20)
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    ref = _oracle_traj(p, dt, 1000, 100)
+    with fem.Mesh(p, prec, reorder=reorder) as m:
+        worst = 0.0
+        for k, (T_ref, e_ref) in enumerate(ref):
+            m.step(100, dt)
+            T = m.temperature()
+            err = np.abs(T - T_ref).max()
+            worst = max(worst, err)
+            assert err <= TOL[prec], f"step {100 * (k + 1)}: max error {err:.3e} K"
+        e = m.energy()
+        # the cube has solidified and approached the ambient
+        assert T.max() < mg.ALLOY[4]
+        U, U0, Qb, lat = e
+        rel = 1e-12 if prec == "fp64" else 1e-5
+        assert abs(U - U0 - Qb) <= rel * abs(U0)
+        assert U == pytest.approx(e_ref[0], rel=1e-12 if prec == "fp64" else 1e-6)
+        print(f"{prec} reorder={reorder}: max error over 1000 steps {worst:.3e} K")
+
+
+@pytest.mark.parametrize("variant", ["block", "atomic", "colored"])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_random_small_fp64(fem, variant, seed):
+    p = mg.random_small(seed, nx=7, ny=6, nz=5, n_mat=3)
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    o.set_temperature(p.T0)
+    o.step(200, dt)
+    with fem.Mesh(p, "fp64", reorder=seed % 2, variant=variant, block_elems=96) as m:
+        m.step(200, dt)
+        err = np.abs(m.temperature() - o.temperature()).max()
+        assert err <= 1e-9
+        e, eo = m.energy(), o.energy()
+        np.testing.assert_allclose(e, eo, rtol=1e-11, atol=1e-6)
+
+
+@pytest.mark.parametrize("block_elems", [64, 100, 333, 12288])
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_block_sizes_and_threads(fem, block_elems, threads):
+    p = mg.random_small(11, nx=9, ny=7, nz=6, n_mat=2)
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    o.set_temperature(p.T0)
+    o.step(50, dt)
+    with fem.Mesh(p, "fp64", reorder=1, block_elems=block_elems, threads=threads) as m:
+        m.step(50, dt)
+        assert np.abs(m.temperature() - o.temperature()).max() <= 1e-9
+
+
+def test_dirichlet_and_isothermal(fem):
+    # Stefan-type bar: isothermal phase change, Dirichlet wall
+    xyz, tets, flags, _ = mg.bar(40, 0.6)
+    mats = np.array([[2700.0, 900.0, 150.0, 3.9e5, 933.0, 933.0]])
+    d = np.nonzero(xyz[:, 0] < 1e-12)[0].astype(np.int32)
+    p = mg.Problem(xyz=xyz, tets=tets, mat=np.zeros(len(tets), np.int32), materials=mats,
+                   faces=np.zeros((0, 3), np.int32), h=np.zeros(0), t_inf=np.zeros(0),
+                   q=np.zeros(0), T0=np.full(len(xyz), 973.0), dir_nodes=d,
+                   dir_T=np.full(len(d), 300.0))
+    o = oracle.OracleProblem(p)
+    dt = 0.5 * o.stable_dt()
+    o.set_temperature(p.T0)
+    o.step(400, dt)
+    for prec in ("fp64", "fp32"):
+        with fem.Mesh(p, prec, reorder=1, block_elems=64) as m:
+            m.step(400, dt)
+            assert np.abs(m.temperature() - o.temperature()).max() <= TOL[prec]
+
+
+def test_single_tet_and_adiabatic(fem):
+    xyz = np.array([[0, 0, 0], [0.1, 0, 0], [0, 0.1, 0], [0, 0, 0.1]], float)
+    p = mg.Problem(xyz=xyz, tets=np.array([[0, 2, 1, 3]], np.int32), mat=np.zeros(1, np.int32),
+                   materials=np.array([mg.ALLOY]), faces=np.zeros((0, 3), np.int32),
+                   h=np.zeros(0), t_inf=np.zeros(0), q=np.zeros(0),
+                   T0=np.array([400.0, 900.0, 850.0, 1000.0]))
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    o.set_temperature(p.T0)
+    o.step(300, dt)
+    with fem.Mesh(p, "fp64", reorder=0) as m:
+        m.step(300, dt)
+        assert np.abs(m.temperature() - o.temperature()).max() <= 1e-9
+        U, U0, Qb, lat = m.energy()
+        assert Qb == 0.0 and abs(U - U0) <= 1e-12 * U0
+
+
+def test_block_variant_is_deterministic(fem):
+    p = mg.random_small(5, nx=10, ny=8, nz=6)
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    runs = []
+    for _ in range(3):
+        with fem.Mesh(p, "fp32", reorder=1, block_elems=128) as m:
+            m.step(300, dt)
+            runs.append(m.state()[0])
+    assert all(np.array_equal(runs[0], r) for r in runs[1:])
+
+
+def test_checkpoint_restart_bitwise(fem):
+    p = mg.unit_cube(12)
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    with fem.Mesh(p, "fp32", reorder=1) as a:
+        a.step(1000, dt)
+        E_full = a.state()[0]
+    with fem.Mesh(p, "fp32", reorder=1) as b:
+        b.step(500, dt)
+        E_half, step, t = b.state()
+        assert step == 500
+    with fem.Mesh(p, "fp32", reorder=1, set_temperature=False) as c:
+        c.set_state(E_half, step, t)
+        c.step(500, dt)
+        E2, step2, _ = c.state()
+        assert step2 == 1000
+    assert np.array_equal(E_full, E2)
+
+
+def test_get_enthalpy_units(fem):
+    p = mg.unit_cube(6)
+    with fem.Mesh(p, "fp64", reorder=1) as m:
+        hsp = m.enthalpy()
+        # liquid alloy at 973 K: c T + L per unit mass
+        np.testing.assert_allclose(hsp, mg.ALLOY[1] * 973.0 + mg.ALLOY[3], rtol=1e-12)
+
+
+def test_casting_fp64_and_fp32(fem):
+    """Flanged casting in a steel mold (~2M tets, two materials): a few steps
+    against the oracle in the launch configuration the library picks."""
+    p = mg.flanged_casting()
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    o.set_temperature(p.T0)
+    o.step(20, dt)
+    T_ref = o.temperature()
+    for prec in ("fp64", "fp32"):
+        with fem.Mesh(p, prec, reorder=1) as m:
+            m.step(20, dt)
+            err = np.abs(m.temperature() - T_ref).max()
+            print(f"casting {prec}: max error after 20 steps {err:.3e} K")
+            assert err <= TOL[prec]
