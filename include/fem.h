@@ -240,6 +240,40 @@ fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets,
  * *count is the number of scalar entries.  Builds the plan if needed. */
 fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t *count);
 
+/* Energy sums of a nodal state that lives in the CALLER's device memory,
+ * computed without allocating any memory.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc -- code running while a
+ * CUDA graph is being captured (an allocation there is not allowed in the
+ * global capture mode), real-time loops with a no-allocation rule, or a
+ * process whose device memory is owned by another allocator (for example a
+ * framework's caching allocator holding the whole GPU).
+ *
+ *   prec    FEM_FP64 (E, C, Lc, ranges are double) or FEM_FP32 (float).
+ *   E, C, Lc, phase   DEVICE arrays [n_nodes]: enthalpy content (J),
+ *           sensible capacity (J/K), latent capacity (J), and a phase byte
+ *           whose low 7 bits index the (Ts, Tl) pair of the node's
+ *           phase-change range (ignored where Lc == 0).
+ *   ranges  DEVICE array [n_ranges][2] of (Ts, Tl).
+ *   out     DEVICE array of 2 doubles: out[0] = sum_i E_i,
+ *           out[1] = sum_i (E_i - C_i T(E_i)), the latent heat still held,
+ *           both summed in FP64 in a fixed order (bit-reproducible).
+ *   cuda_stream  stream to run on (NULL: the legacy default stream);
+ *           the call is asynchronous.
+ * Scratch: a static 256 KiB device array inside the library (held by every
+ * GPU that loads the library until the process exits) instead of cudaMalloc.
+ * All calls share it, so calls whose kernels overlap on the GPU (for
+ * example on two streams at once) race and give wrong sums; serialise them.
+ * Each call overwrites every scratch entry it reads, so no clearing is
+ * needed.  The first call on each device looks up the scratch's device
+ * address (cudaGetSymbolAddress, no allocation) with that device current;
+ * make that first call before any stream capture.
+ * Errors: FEM_EINVAL for a NULL pointer, an unknown precision, or n_nodes
+ * outside [1, 134217728] (the scratch holds one partial per 8192 nodes);
+ * FEM_ECUDA if no device is current or the launch fails. */
+fem_status fem_energy_sums_noalloc(fem_precision prec, const void *E, const void *C,
+                                   const void *Lc, const uint8_t *phase, const void *ranges,
+                                   int64_t n_nodes, double *out, void *cuda_stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fem_last_error(void);
 

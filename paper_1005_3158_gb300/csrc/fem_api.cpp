@@ -65,6 +65,8 @@ struct DevBuf {
 
 }  // namespace
 
+void fem::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 struct fem_mesh {
     // ---- caller-order host data
     int64_t N = 0, E = 0, F = 0;

@@ -128,4 +128,7 @@ int launch_energy_snapshot(const real *E, const real *C, const real *Lc, const u
 int launch_energy_reduce(const double *part_a, int64_t n_a, const double *part_b, int64_t n_b,
                          const double *q, int64_t n_q, double *out, void *stream);
 
+// Sets the calling thread's fem_last_error() message (fem_api.cpp).
+void set_last_error(const char *msg);
+
 }  // namespace fem

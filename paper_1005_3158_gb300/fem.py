@@ -30,7 +30,7 @@ ABI_SYMBOLS = (
     "fem_set_dirichlet", "fem_set_temperature", "fem_stable_dt", "fem_step", "fem_step_profile",
     "fem_get_temperature", "fem_get_enthalpy", "fem_get_energy", "fem_set_stream",
     "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
-    "fem_last_error", "fem_mesh_destroy",
+    "fem_last_error", "fem_mesh_destroy", "fem_energy_sums_noalloc",
 )
 
 
@@ -93,6 +93,7 @@ def _load():
         "fem_mesh_info": [P, ctypes.POINTER(FemInfo)],
         "fem_rcm_order": [i64, ip, i64, ip, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "fem_plan_array": [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(i64)],
+        "fem_energy_sums_noalloc": [ctypes.c_int, P, P, P, P, P, i64, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -286,6 +287,15 @@ def fem_plan_array(h, which):
         return np.zeros(0, dt)
     buf = (ctypes.c_char * (n.value * dt.itemsize)).from_address(p.value)
     return np.frombuffer(buf, dtype=dt).copy()
+
+
+def fem_energy_sums_noalloc(prec, E, C, Lc, phase, ranges, n_nodes, out, stream=0):
+    """Device-pointer call (integers from e.g. ``tensor.data_ptr()``); see
+    include/fem.h.  Allocates nothing; asynchronous on ``stream``."""
+    _check(_lib.fem_energy_sums_noalloc(
+        int(prec), ctypes.c_void_p(E), ctypes.c_void_p(C), ctypes.c_void_p(Lc),
+        ctypes.c_void_p(phase), ctypes.c_void_p(ranges), int(n_nodes), ctypes.c_void_p(out),
+        ctypes.c_void_p(int(stream) if stream else 0)))
 
 
 def fem_last_error():
