@@ -47,7 +47,8 @@ typedef enum {
     FEM_ECUDA = 3,     /* a CUDA runtime call failed, or no usable GPU */
     FEM_ESTATE = 4,    /* call out of order (e.g. fem_step before materials) */
     FEM_EUNSTABLE = 5, /* non-finite temperatures/energy: dt above the stable limit */
-    FEM_ETIMEOUT = 6   /* reserved: a bounded device wait gave up */
+    FEM_ETIMEOUT = 6   /* a bounded device wait gave up (reported by the next
+                          fem_get_* call; the state is then not valid) */
 } fem_status;
 
 typedef enum { FEM_FP64 = 0, FEM_FP32 = 1 } fem_precision;
@@ -83,10 +84,11 @@ typedef struct {
 typedef struct {
     int32_t variant;     /* fem_variant, default FEM_VARIANT_BLOCK */
     int32_t block_elems; /* target elements per shared-memory block, 0 = auto
-                            (chosen from the precision and the GPU's shared
-                            memory); clamped to [64, 12288] */
-    int32_t threads;     /* threads per CTA of the block kernel, 0 = auto;
-                            one of 128, 256, 512 */
+                            (2048 for FP32, 1024 for FP64, so that two CTAs
+                            fit in one SM's shared memory); clamped to
+                            [64, 12288] */
+    int32_t threads;     /* threads per CTA of the block kernel, 0 = auto
+                            (512); one of 128, 256, 512 */
     int32_t reserved[5];
 } fem_options;
 
@@ -224,8 +226,9 @@ fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets,
 
 /* Host copies of the plan arrays, for inspection and tests.  which:
  *   0 node_new   int32 [n_nodes]      caller node -> internal node
- *   1 blocks     int32 [n_blocks][12] per block: e0, ne, f0, nf, n0, nint,
- *                                     c0, nsh, g0, ngrp, ne_pad, nf_pad
+ *   1 blocks     int32 [n_blocks][16] per block: e0, ne, f0, nf, n0, nint,
+ *                                     c0, nsh, g0, ngrp, ne_pad, nf_pad, nep,
+ *                                     r0, nrounds, 0
  *   2 elem_order int32 [E_pad]        padded element position -> caller
  *                                     element (-1 for padding)
  *   3 face_order int32 [F_pad]        padded face position -> caller face
@@ -233,9 +236,13 @@ fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets,
  *   5 sh_ptr     int32 [n_shared+1]   shared node -> range in sh_copy
  *   6 sh_copy    int32 [n_copies]     copy indices of each shared node
  *   7 grp        int32 [..]           32-lane group -> first schedule round
- *   8 sched      uint16 [rounds*32]   slot written/read by each lane/round
+ *   8 sched      uint16 [rounds*32]   slot written/read by each lane/round,
+ *                                     (round r, lane) at (r/2)*64 + 2*lane + r%2;
+ *                                     padding names slot 4*ne_pad + 3*nf_pad
  *   9 elem_nodes int32 [E_pad][4]     corner nodes (internal ids) per position
  *  10 face_nodes int32 [F_pad][3]     corner nodes (internal ids) per position
+ *  11 copy_pos   int32 [n_copies]     position of each copy's partial sum in
+ *                                     the node-ordered partial array
  * *data points into the mesh (valid until the next fem_set_* or destroy);
  * *count is the number of scalar entries.  Builds the plan if needed. */
 fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t *count);

@@ -111,12 +111,13 @@ struct fem_mesh {
          *dFa = nullptr, *dFg = nullptr, *dP = nullptr, *dT = nullptr, *dR = nullptr;
     uint8_t *dPh = nullptr;
     BlockInfo *dBlocks = nullptr;
-    int32_t *dGrp = nullptr, *dCopy = nullptr, *dShPtr = nullptr, *dShCopy = nullptr,
+    int32_t *dGrp = nullptr, *dCopy = nullptr, *dShPtr = nullptr, *dCopyPos = nullptr,
             *dNodeOld = nullptr, *dConn = nullptr, *dFconn = nullptr, *dNfPtr = nullptr,
             *dNfIdx = nullptr;
     uint16_t *dSched = nullptr;
-    double *dEpart = nullptr, *dQcum = nullptr, *dEpart2 = nullptr, *dIo = nullptr,
+    double *dEpart = nullptr, *dQcum = nullptr, *dIo = nullptr,
            *dDirT = nullptr, *dOut = nullptr;
+    int *dErr = nullptr;
     // ---- state
     enum { ST_NONE, ST_PENDING_T, ST_PENDING_E, ST_DEVICE } state = ST_NONE;
     std::vector<double> pending;      // T0 or E (caller order)
@@ -124,7 +125,6 @@ struct fem_mesh {
     double time = 0.0;
     double U0 = 0.0;
     double q_carry = 0.0;             // boundary heat of device buffers already released
-    int64_t steps_since_account = 0;  // steps since the per-step partials were valid
 };
 
 namespace {
@@ -146,16 +146,17 @@ void release_device(fem_mesh *m)
     m->dE = m->dC = m->dLc = m->dRanges = m->dW = m->dFa = m->dFg = m->dP = m->dT = m->dR = nullptr;
     m->dPh = nullptr;
     m->dBlocks = nullptr;
-    m->dGrp = m->dCopy = m->dShPtr = m->dShCopy = m->dNodeOld = m->dConn = m->dFconn = nullptr;
+    m->dGrp = m->dCopy = m->dShPtr = m->dCopyPos = m->dNodeOld = m->dConn = m->dFconn = nullptr;
     m->dNfPtr = m->dNfIdx = nullptr;
     m->dSched = nullptr;
-    m->dEpart = m->dQcum = m->dEpart2 = m->dIo = m->dDirT = m->dOut = nullptr;
+    m->dEpart = m->dQcum = m->dIo = m->dDirT = m->dOut = nullptr;
+    m->dErr = nullptr;
 }
 
 int default_block_elems(const fem_mesh *m)
 {
     int be = m->opt.block_elems;
-    if (be <= 0) be = m->prec == FEM_FP32 ? 4096 : 2048;
+    if (be <= 0) be = m->prec == FEM_FP32 ? 2048 : 1024;
     return std::min(std::max(be, 64), 12288);
 }
 
@@ -183,7 +184,7 @@ fem_status ensure_plan(fem_mesh *m)
             err = build_block_plan(m->N, m->E, m->xyz.data(), m->tets.data(), m->rank, m->F,
                                    m->faces.data(), owner, default_block_elems(m), m->bp);
             if (err.empty()) {
-                m->blocks_flat.resize(m->bp.blocks.size() * 12);
+                m->blocks_flat.resize(m->bp.blocks.size() * 16);
                 std::memcpy(m->blocks_flat.data(), m->bp.blocks.data(),
                             m->bp.blocks.size() * sizeof(BlockInfo));
             }
@@ -294,15 +295,17 @@ fem_status upload_block(fem_mesh *m)
     const BlockPlan &bp = m->bp;
     fem_status st;
     if ((st = upload_nodes<real>(m))) return st;
-    // element conductances in block order, SoA [6][E_pad]
+    // element conductances: per block one chunk of six rows,
+    // w[6*e0 + k*nep + i] for local element i (zero in the padding)
     real *p = nullptr;
     {
         std::vector<real> w((size_t)bp.E_pad * 6, real(0));
-        for (int64_t q = 0; q < bp.E_pad; q++) {
-            int32_t e = bp.elem_order[q];
-            if (e < 0) continue;
-            for (int k = 0; k < 6; k++) w[(size_t)k * bp.E_pad + q] = (real)m->w[6 * (size_t)e + k];
-        }
+        for (const BlockInfo &b : bp.blocks)
+            for (int32_t i = 0; i < b.ne; i++) {
+                int32_t e = bp.elem_order[(size_t)b.e0 + i];
+                for (int k = 0; k < 6; k++)
+                    w[6 * (size_t)b.e0 + (size_t)k * b.nep + i] = (real)m->w[6 * (size_t)e + k];
+            }
         if ((st = upload<real>(m, &p, w.data(), w.size()))) return st;
         m->dW = p;
     }
@@ -324,14 +327,19 @@ fem_status upload_block(fem_mesh *m)
     if ((st = upload<real>(m, &p, nullptr, (size_t)bp.n_copies))) return st;
     m->dP = p;
     if ((st = upload<int32_t>(m, &m->dShPtr, bp.sh_ptr.data(), bp.sh_ptr.size()))) return st;
-    if ((st = upload<int32_t>(m, &m->dShCopy, bp.sh_copy.data(), bp.sh_copy.size()))) return st;
+    if ((st = upload<int32_t>(m, &m->dCopyPos, bp.copy_pos.data(), bp.copy_pos.size()))) return st;
     if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * bp.blocks.size()))) return st;
     if ((st = upload<double>(m, &m->dQcum, nullptr, bp.blocks.size()))) return st;
     m->n_sh_ctas = (int)std::max<int64_t>(1, (bp.n_sh + 255) / 256);
-    if ((st = upload<double>(m, &m->dEpart2, nullptr, 2 * (size_t)m->n_sh_ctas))) return st;
+    if ((st = upload<int>(m, &m->dErr, nullptr, 1))) return st;
     // kernel configuration
-    m->threads = m->opt.threads > 0 ? m->opt.threads : 256;
-    m->smem_bytes = (bp.max_slots + bp.max_nloc) * sizeof(real);
+    m->threads = m->opt.threads > 0 ? m->opt.threads : 512;
+    m->smem_bytes = 0;
+    for (const BlockInfo &b : bp.blocks)
+        m->smem_bytes = std::max(m->smem_bytes, block_smem_bytes(b, sizeof(real)));
+    if (bp.max_nloc > (size_t)kMaxLocalNodes)
+        return fail(FEM_EINVAL, "a block has %zu local nodes (> %d); lower block_elems", bp.max_nloc,
+                    kMaxLocalNodes);
     int dev = 0, optin = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -412,10 +420,9 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.copy_node = m->dCopy;
     a.P = (real *)m->dP;
     a.sh_ptr = m->dShPtr;
-    a.sh_copy = m->dShCopy;
-    a.epart = m->dEpart;
+    a.copy_pos = m->dCopyPos;
     a.qcum = m->dQcum;
-    a.epart2 = m->dEpart2;
+    a.err = m->dErr;
     return a;
 }
 
@@ -440,7 +447,6 @@ FlatArgs<real> flat_args(const fem_mesh *m)
     a.fg = (const real *)m->dFg;
     a.n_faces = m->F;
     a.f_stride = m->fp.F_pad;
-    a.epart = m->dEpart;
     a.qcum = m->dQcum;
     return a;
 }
@@ -493,7 +499,6 @@ fem_status apply_pending(fem_mesh *m)
         CU(cudaStreamSynchronize(m->stream));
     }
     m->state = fem_mesh::ST_DEVICE;
-    m->steps_since_account = 0;
     std::vector<double>().swap(m->pending);
     return FEM_OK;
 }
@@ -597,7 +602,6 @@ fem_status step_impl(fem_mesh *m, int64_t n, double dt)
         }
     m->step += n;
     m->time += dt * (double)n;
-    m->steps_since_account += n;
     return FEM_OK;
 }
 
@@ -628,10 +632,23 @@ fem_status step_profile_impl(fem_mesh *m, int64_t n, double dt, double *ms)
         }
         m->step += 1;
         m->time += dt;
-        m->steps_since_account += 1;
     }
     for (int k = 0; k <= nk; k++) cudaEventDestroy(ev[k]);
     return st;
+}
+
+// Device error flag of the block kernel (a bounded wait that gave up).
+fem_status check_device_flag(fem_mesh *m)
+{
+    if (!m->dErr) return FEM_OK;
+    int flag = 0;
+    CU(cudaMemcpyAsync(&flag, m->dErr, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    if (flag) {
+        CU(cudaMemsetAsync(m->dErr, 0, sizeof(int), m->stream));
+        return fail(FEM_ETIMEOUT, "a bounded device wait gave up (flag %d); the state is not valid", flag);
+    }
+    return FEM_OK;
 }
 
 fem_status ready_for_io(fem_mesh *m)
@@ -917,7 +934,6 @@ fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
                    ? launch_set_state<float>((float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
                    : launch_set_state<double>((double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
                "state kernel");
-        m->steps_since_account = 0;
     } else {
         m->pending.assign(E, E + m->N);
         m->state = fem_mesh::ST_PENDING_E;
@@ -991,6 +1007,7 @@ fem_status fem_get_temperature(fem_mesh *m, double *T_out)
     if (!m || !T_out) return fail(FEM_EINVAL, "NULL argument");
     fem_status st = ready_for_io(m);
     if (st) return st;
+    if ((st = check_device_flag(m))) return st;
     KERNEL(m->prec == FEM_FP32
                ? launch_get_temperature<float>((const float *)m->dE, (const float *)m->dC,
                                                (const float *)m->dLc, m->dPh,
@@ -1013,6 +1030,7 @@ fem_status fem_get_state(fem_mesh *m, double *E_out, int64_t *step, double *t)
     if (!m || !E_out) return fail(FEM_EINVAL, "NULL argument");
     fem_status st = ready_for_io(m);
     if (st) return st;
+    if ((st = check_device_flag(m))) return st;
     KERNEL(m->prec == FEM_FP32
                ? launch_get_state<float>((const float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
                : launch_get_state<double>((const double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
@@ -1037,21 +1055,11 @@ fem_status fem_get_energy(fem_mesh *m, double out[4])
     if (!m || !out) return fail(FEM_EINVAL, "NULL argument");
     fem_status st = ready_for_io(m);
     if (st) return st;
-    if (m->steps_since_account > 0) {
-        // the per-CTA FP64 partials written by the last step
-        if (is_block(m))
-            KERNEL(launch_energy_reduce(m->dEpart, (int64_t)m->bp.blocks.size(), m->dEpart2,
-                                        m->n_sh_ctas, m->dQcum, n_qcum(m), m->dOut, m->stream),
-                   "energy kernel");
-        else
-            KERNEL(launch_energy_reduce(m->dEpart, m->n_node_ctas, nullptr, 0, m->dQcum, n_qcum(m),
-                                        m->dOut, m->stream),
-                   "energy kernel");
-    } else {
-        // no step since the state was set: snapshot of the current state
-        KERNEL(m->prec == FEM_FP32 ? energy_snapshot<float>(m) : energy_snapshot<double>(m),
-               "energy kernel");
-    }
+    if ((st = check_device_flag(m))) return st;
+    // FP64 reductions of the current state (sum E, latent) and of the
+    // per-CTA cumulative boundary heat
+    KERNEL(m->prec == FEM_FP32 ? energy_snapshot<float>(m) : energy_snapshot<double>(m),
+           "energy kernel");
     double r[3];
     CU(cudaMemcpyAsync(r, m->dOut, 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
@@ -1088,7 +1096,7 @@ fem_status fem_mesh_info(fem_mesh *m, fem_info *out)
     out->device_bytes = (int64_t)m->dev_bytes;
     out->precision = m->prec;
     out->variant = m->opt.variant;
-    out->threads = m->opt.threads > 0 ? m->opt.threads : 256;
+    out->threads = m->opt.threads > 0 ? m->opt.threads : (is_block(m) ? 512 : 256);
     out->reorder = m->reorder;
     return ok();
 }
@@ -1143,6 +1151,7 @@ fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t
     case 8: return give(m->bp.sched.data(), m->bp.sched.size());
     case 9: return give(m->bp.elem_nodes.data(), m->bp.elem_nodes.size());
     case 10: return give(m->bp.face_nodes.data(), m->bp.face_nodes.size());
+    case 11: return give(m->bp.copy_pos.data(), m->bp.copy_pos.size());
     default: return fail(FEM_EINVAL, "unknown plan array %d", which);
     }
 }

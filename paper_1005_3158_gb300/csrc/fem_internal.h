@@ -5,6 +5,12 @@
 #include <cstddef>
 #include <cstdint>
 
+#ifdef __CUDACC__
+#define FEM_HD __host__ __device__
+#else
+#define FEM_HD
+#endif
+
 namespace fem {
 
 // Per-block header of the block-partitioned step (one CTA per block).
@@ -18,12 +24,40 @@ namespace fem {
 //   slot layout in shared memory: element corner c of local element e at
 //             c*ne_pad + e; face corner c of local face f at
 //             4*ne_pad + c*nf_pad + f
+//   weights   the block's six conductance rows are one contiguous chunk
+//             w[6*e0 + k*nep + e] (nep = ne rounded up to 8), so one bulk
+//             copy brings them to shared memory
+//   rounds    [r0, r0+nrounds) of the schedule (64 bytes each), contiguous;
+//             each group has an even number of rounds, stored as one 32-bit
+//             word (two slot indices) per lane and pair of rounds; padding
+//             entries name the dummy slot 4*ne_pad + 3*nf_pad
 struct BlockInfo {
     int32_t e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad;
+    int32_t nep, r0, nrounds, pad;
 };
-static_assert(sizeof(BlockInfo) == 48, "BlockInfo layout");
+static_assert(sizeof(BlockInfo) == 64, "BlockInfo layout");
 
-constexpr uint16_t kNoSlot = 0xFFFF;
+// Dynamic shared memory of one block-kernel CTA (16-byte aligned parts):
+// [2 mbarriers][weights 6*nep][schedule nrounds*32 u16][slots]
+constexpr size_t kSmemBarBytes = 16;
+FEM_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+FEM_HD inline size_t block_smem_bytes(const BlockInfo &b, size_t real_size)
+{
+    const size_t nslot = 4 * (size_t)b.ne_pad + 3 * (size_t)b.nf_pad + 1;  // + dummy
+    const size_t nloc = (size_t)b.nint + (size_t)b.nsh;
+    (void)nloc;
+    return kSmemBarBytes + align16(6 * (size_t)b.nep * real_size) + align16((size_t)b.nrounds * 64) +
+           align16(nslot * real_size);
+}
+
+// Bounded waits: an mbarrier wait gives up after this many polls, sets the
+// error flag and the step returns FEM_ETIMEOUT at the next read-back.
+constexpr uint32_t kSpinLimit = 1u << 24;
+// Local nodes of one block are held in registers, kMaxLocalNodes / threads
+// per thread; the planner keeps every block at or below this.
+constexpr int kMaxLocalNodes = 1024;
+constexpr int kErrWaitTimeout = 1;
+
 constexpr uint8_t kDirichletBit = 0x80;  // in the per-node phase byte
 constexpr int kMaxRanges = 127;          // distinct (Ts, Tl) pairs
 
@@ -50,14 +84,13 @@ struct BlockArgs {
     const int32_t *grp;
     const uint16_t *sched;
     // shared-node exchange
-    const int32_t *copy_node; // [n_copies]
-    real *P;                  // [n_copies] partial sums
-    const int32_t *sh_ptr;    // [n_sh + 1]
-    const int32_t *sh_copy;   // [n_copies]
+    const int32_t *copy_node; // [n_copies] internal node of each block-ordered copy
+    const int32_t *copy_pos;  // [n_copies] where the copy's partial goes in P
+    real *P;                  // [n_copies] partial sums, grouped by shared node
+    const int32_t *sh_ptr;    // [n_sh + 1] node s owns P[sh_ptr[s] .. sh_ptr[s+1])
     // FP64 energy bookkeeping
-    double *epart;            // [n_blocks][2]: sum E, latent (interior nodes)
-    double *qcum;             // [n_blocks] cumulative boundary heat
-    double *epart2;           // [n_sh_ctas][2]: sum E, latent (shared nodes)
+    double *qcum;             // [n_blocks] cumulative heat through the Robin faces
+    int *err;                 // device error flag (kErrWaitTimeout)
 };
 
 // Arguments of the atomic / coloured variants (device pointers).
@@ -77,7 +110,6 @@ struct FlatArgs {
     const int32_t *fconn;     // [3][f_stride]
     const real *fa, *fg;
     int64_t n_faces, f_stride;
-    double *epart;            // [n_node_ctas][2]
     double *qcum;             // [n_node_ctas] cumulative boundary heat
 };
 

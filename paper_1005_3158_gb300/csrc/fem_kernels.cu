@@ -16,8 +16,9 @@
 //                     Eqs. 19-22).
 //   k_shared_update   sums the partials of every shared node in a fixed
 //                     order and updates it.
-// Both accumulate the FP64 energy account (sum E, latent heat still to be
-// released, heat through the Robin faces) per CTA.
+// The step accumulates, in FP64 per CTA, the heat that entered through the
+// Robin faces; the state functions sum E and latent heat still to release
+// are FP64 reductions of the state (k_energy_snapshot) taken on demand.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -102,103 +103,250 @@ __device__ __forceinline__ void block_sum(double (&v)[K])
 // ---------------------------------------------------------------------------
 // Block variant
 // ---------------------------------------------------------------------------
-template <typename real, int NT>
-__global__ void __launch_bounds__(NT) k_block_step(const BlockArgs<real> a, const real dt)
+
+// PTX wrappers: mbarrier + 1-D bulk copy (TMA) global -> shared.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real *const sv = reinterpret_cast<real *>(smem_raw);
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Waits for phase `parity` of the barrier; gives up after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Element product of one tet: r_a = sum_b w_ab (T_b - T_a), w_ab = -K^e_ab
+// (the row of -K^e T^e; K^e symmetric with zero row sums, Eq. 9).
+template <typename real>
+__device__ __forceinline__ void tet_products(real w01, real w02, real w03, real w12, real w13,
+                                             real w23, real T0, real T1, real T2, real T3,
+                                             real &r0, real &r1, real &r2, real &r3)
+{
+    const real p01 = w01 * (T1 - T0), p02 = w02 * (T2 - T0), p03 = w03 * (T3 - T0);
+    const real p12 = w12 * (T2 - T1), p13 = w13 * (T3 - T1), p23 = w23 * (T3 - T2);
+    r0 = p01 + p02 + p03;
+    r1 = (p12 + p13) - p01;
+    r2 = p23 - (p02 + p12);
+    r3 = -(p03 + p13 + p23);
+}
+
+template <typename real>
+struct Vec4Of;
+template <>
+struct Vec4Of<float> {
+    using type = float4;   // four elements per 16-byte access
+    static constexpr int n = 4;
+};
+template <>
+struct Vec4Of<double> {
+    using type = double2;  // two elements per 16-byte access
+    static constexpr int n = 2;
+};
+
+// 16-byte vector of `real` accessed by lane index
+__device__ __forceinline__ float &vat(float4 &v, int i) { return (&v.x)[i]; }
+__device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
+
+// One CTA per element block.  Thread t owns local nodes t, t+NT, ... in
+// every pass (32-lane group g = warp + j*NW covers nodes 32 g + lane), so
+// their T and E stay in registers.
+template <typename real, int NT>
+__global__ void __launch_bounds__(NT, 2) k_block_step(const BlockArgs<real> a, const real dt)
+{
+    constexpr int NW = NT / 32;
+    constexpr int MAXJ = kMaxLocalNodes / NT;   // local nodes per thread
+    using V = typename Vec4Of<real>::type;
+    constexpr int VN = Vec4Of<real>::n;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const BlockInfo bi = a.blocks[blockIdx.x];
     const int nloc = bi.nint + bi.nsh;
-    const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad;
-    const int fbase = 4 * ne_pad;
-    real *const Es = sv + fbase + 3 * nf_pad;   // enthalpy of each local node
+    const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad, nep = bi.nep;
+    const int dummy = 4 * ne_pad + 3 * nf_pad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NW = NT / 32;
 
-    // pass 1: T of every local node, written to the slots of its corners
-    for (int g = warp; g < bi.ngrp; g += NW) {
-        const int l = 32 * g + lane;
-        real T = real(0);
+    // shared memory: [barriers][weights][schedule][slots + dummy]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+    unsigned char *q = smem_raw + kSmemBarBytes;
+    real *sw = reinterpret_cast<real *>(q);
+    q += align16(6 * (size_t)nep * sizeof(real));
+    const uint32_t *ss = reinterpret_cast<const uint32_t *>(q);   // [pair][lane]
+    q += align16((size_t)bi.nrounds * 64);
+    real *sv = reinterpret_cast<real *>(q);
+    const uint32_t bar_s = smem_addr(&bars[0]), bar_w = smem_addr(&bars[1]);
+
+    // bulk copies: the block's schedule and its six conductance rows
+    if (threadIdx.x == 0) {
+        mbar_init(bar_s, 1);
+        mbar_init(bar_w, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t sbytes = (uint32_t)bi.nrounds * 64u;
+        mbar_arrive_expect_tx(bar_s, sbytes);
+        if (sbytes) bulk_load(smem_addr(ss), a.sched + (size_t)bi.r0 * 32, sbytes, bar_s);
+        const uint32_t wbytes = (uint32_t)(6 * (size_t)nep * sizeof(real));
+        mbar_arrive_expect_tx(bar_w, wbytes);
+        bulk_load(smem_addr(sw), a.w + 6 * (size_t)bi.e0, wbytes, bar_w);
+    }
+
+    // nodal enthalpy -> temperature (Eqs. 5, 11), overlapping the copies
+    real Tl[MAXJ], El[MAXJ];
+#pragma unroll
+    for (int j = 0; j < MAXJ; j++) {
+        const int l = threadIdx.x + j * NT;
+        Tl[j] = real(0);
+        El[j] = real(0);
         if (l < nloc) {
             const int64_t gid = l < bi.nint ? (int64_t)bi.n0 + l
                                             : (int64_t)__ldg(a.copy_node + bi.c0 + (l - bi.nint));
-            const real E = a.E[gid];
-            T = temperature_of(E, __ldg(a.C + gid), __ldg(a.Lc + gid), __ldg(a.ph + gid), a.ranges);
-            Es[l] = E;
-        }
-        const int r0 = __ldg(a.grp + bi.g0 + g), r1 = __ldg(a.grp + bi.g0 + g + 1);
-        const uint16_t *s = a.sched + (size_t)r0 * 32 + lane;
-        for (int r = r0; r < r1; ++r, s += 32) {
-            const uint16_t v = __ldg(s);
-            if (v != kNoSlot) sv[v] = T;
+            El[j] = a.E[gid];
+            Tl[j] = temperature_of(El[j], __ldg(a.C + gid), __ldg(a.Lc + gid), __ldg(a.ph + gid),
+                                   a.ranges);
         }
     }
-    __syncthreads();
 
-    // pass 2: element products r_a = sum_b w_ab (T_b - T_a), w_ab = -K^e_ab
-    {
-        const real *__restrict__ w = a.w + bi.e0;
-        const int64_t st = a.e_stride;
-        for (int e = threadIdx.x; e < bi.ne; e += NT) {
-            const real w01 = __ldg(w + e), w02 = __ldg(w + st + e), w03 = __ldg(w + 2 * st + e);
-            const real w12 = __ldg(w + 3 * st + e), w13 = __ldg(w + 4 * st + e),
-                       w23 = __ldg(w + 5 * st + e);
-            const real T0 = sv[e], T1 = sv[ne_pad + e], T2 = sv[2 * ne_pad + e],
-                       T3 = sv[3 * ne_pad + e];
-            const real p01 = w01 * (T1 - T0), p02 = w02 * (T2 - T0), p03 = w03 * (T3 - T0);
-            const real p12 = w12 * (T2 - T1), p13 = w13 * (T3 - T1), p23 = w23 * (T3 - T2);
-            sv[e] = p01 + p02 + p03;
-            sv[ne_pad + e] = (p12 + p13) - p01;
-            sv[2 * ne_pad + e] = p23 - (p02 + p12);
-            sv[3 * ne_pad + e] = -(p03 + p13 + p23);
-        }
-    }
-    // Robin faces (Eq. 4): r_c = A/3 (h T_inf - q) - h A/12 (T_c + T_0 + T_1 + T_2)
-    double qin = 0.0;
-    for (int f = threadIdx.x; f < bi.nf; f += NT) {
-        real *s0 = sv + fbase + f;
-        const real T0 = s0[0], T1 = s0[nf_pad], T2 = s0[2 * nf_pad];
-        const real ha = __ldg(a.fa + bi.f0 + f), hg = __ldg(a.fg + bi.f0 + f);
-        const real S = T0 + T1 + T2;
-        const real r0 = hg - ha * (T0 + S), r1 = hg - ha * (T1 + S), r2 = hg - ha * (T2 + S);
-        s0[0] = r0;
-        s0[nf_pad] = r1;
-        s0[2 * nf_pad] = r2;
-        qin += (double)r0 + (double)r1 + (double)r2;
-    }
-    __syncthreads();
+    // one thread polls (bounded), then every thread observes the phase
+    int failed = 0;
+    if (threadIdx.x == 0) failed = !mbar_wait(bar_s, 0);
+    if (__syncthreads_or(failed)) goto timeout;
+    mbar_try_wait(bar_s, 0);
 
-    // pass 3: fixed-order node sums; interior update or shared partial
-    double acc[3] = {0.0, 0.0, qin};
-    for (int g = warp; g < bi.ngrp; g += NW) {
-        const int l = 32 * g + lane;
-        const int r0 = __ldg(a.grp + bi.g0 + g), r1 = __ldg(a.grp + bi.g0 + g + 1);
-        const uint16_t *s = a.sched + (size_t)r0 * 32 + lane;
-        real R = real(0);
-        for (int r = r0; r < r1; ++r, s += 32) {
-            const uint16_t v = __ldg(s);
-            if (v != kNoSlot) R += sv[v];
-        }
-        if (l < bi.nint) {
-            const int64_t gid = (int64_t)bi.n0 + l;
-            const uint8_t ph = __ldg(a.ph + gid);
-            real E = Es[l];
-            if (!(ph & kDirichletBit)) {
-                E += dt * R;
-                a.E[gid] = E;
+    // pass 1: T of every local node into the slots of its element corners
+    // (padding entries all name the dummy slot)
+#pragma unroll
+    for (int j = 0; j < MAXJ; j++) {
+        const int g = warp + j * NW;
+        if (g < bi.ngrp) {
+            const int p0 = (__ldg(a.grp + bi.g0 + g) - bi.r0) >> 1;
+            const int p1 = (__ldg(a.grp + bi.g0 + g + 1) - bi.r0) >> 1;
+            const real T = Tl[j];
+            for (int pr = p0; pr < p1; ++pr) {
+                const uint32_t v = ss[pr * 32 + lane];
+                sv[v & 0xFFFFu] = T;
+                sv[v >> 16] = T;
             }
-            acc[0] += (double)E;
-            acc[1] += latent_of(E, __ldg(a.C + gid), __ldg(a.Lc + gid), ph, a.ranges);
-        } else if (l < nloc) {
-            a.P[bi.c0 + (l - bi.nint)] = R;
         }
     }
-    block_sum<NT, 3>(acc);
-    if (threadIdx.x == 0) {
-        a.epart[2 * blockIdx.x] = acc[0];
-        a.epart[2 * blockIdx.x + 1] = acc[1];
-        a.qcum[blockIdx.x] += (double)dt * acc[2];
+    if (threadIdx.x == 0) failed = !mbar_wait(bar_w, 0);
+    if (__syncthreads_or(failed)) goto timeout;
+    mbar_try_wait(bar_w, 0);
+
+    // pass 2: element products, VN elements per 16-byte access
+    for (int e = threadIdx.x * VN; e < bi.ne; e += NT * VN) {
+        const V w01 = *reinterpret_cast<const V *>(sw + e);
+        const V w02 = *reinterpret_cast<const V *>(sw + nep + e);
+        const V w03 = *reinterpret_cast<const V *>(sw + 2 * nep + e);
+        const V w12 = *reinterpret_cast<const V *>(sw + 3 * nep + e);
+        const V w13 = *reinterpret_cast<const V *>(sw + 4 * nep + e);
+        const V w23 = *reinterpret_cast<const V *>(sw + 5 * nep + e);
+        V T0 = *reinterpret_cast<const V *>(sv + e);
+        V T1 = *reinterpret_cast<const V *>(sv + ne_pad + e);
+        V T2 = *reinterpret_cast<const V *>(sv + 2 * ne_pad + e);
+        V T3 = *reinterpret_cast<const V *>(sv + 3 * ne_pad + e);
+#pragma unroll
+        for (int i = 0; i < VN; i++) {
+            V c01 = w01, c02 = w02, c03 = w03, c12 = w12, c13 = w13, c23 = w23;
+            tet_products(vat(c01, i), vat(c02, i), vat(c03, i), vat(c12, i), vat(c13, i),
+                         vat(c23, i), vat(T0, i), vat(T1, i), vat(T2, i), vat(T3, i), vat(T0, i),
+                         vat(T1, i), vat(T2, i), vat(T3, i));
+        }
+        *reinterpret_cast<V *>(sv + e) = T0;
+        *reinterpret_cast<V *>(sv + ne_pad + e) = T1;
+        *reinterpret_cast<V *>(sv + 2 * ne_pad + e) = T2;
+        *reinterpret_cast<V *>(sv + 3 * ne_pad + e) = T3;
     }
+    if (threadIdx.x == 0) sv[dummy] = real(0);   // padding adds nothing in pass 3
+    // Robin faces (Eq. 4): r_c = A/3 (h T_inf - q) - h A/12 (T_c + T_0 + T_1 + T_2)
+    {
+        double qin = 0.0;   // heat entering through the block's faces (FP64)
+        const int fbase = 4 * ne_pad;
+        for (int f = threadIdx.x; f < bi.nf; f += NT) {
+            real *s0 = sv + fbase + f;
+            const real T0 = s0[0], T1 = s0[nf_pad], T2 = s0[2 * nf_pad];
+            const real ha = __ldg(a.fa + bi.f0 + f), hg = __ldg(a.fg + bi.f0 + f);
+            const real S = T0 + T1 + T2;
+            const real r0 = hg - ha * (T0 + S), r1 = hg - ha * (T1 + S), r2 = hg - ha * (T2 + S);
+            s0[0] = r0;
+            s0[nf_pad] = r1;
+            s0[2 * nf_pad] = r2;
+            qin += (double)r0 + (double)r1 + (double)r2;
+        }
+        __syncthreads();
+
+        // pass 3: fixed-order node sums; interior update or shared partial
+#pragma unroll
+        for (int j = 0; j < MAXJ; j++) {
+            const int g = warp + j * NW;
+            if (g >= bi.ngrp) continue;
+            const int l = 32 * g + lane;
+            const int p0 = (__ldg(a.grp + bi.g0 + g) - bi.r0) >> 1;
+            const int p1 = (__ldg(a.grp + bi.g0 + g + 1) - bi.r0) >> 1;
+            real R = real(0);
+            for (int pr = p0; pr < p1; ++pr) {
+                const uint32_t v = ss[pr * 32 + lane];
+                R += sv[v & 0xFFFFu];
+                R += sv[v >> 16];
+            }
+            if (l < bi.nint) {
+                const int64_t gid = (int64_t)bi.n0 + l;
+                if (!(__ldg(a.ph + gid) & kDirichletBit)) a.E[gid] = El[j] + dt * R;
+            } else if (l < nloc) {
+                a.P[__ldg(a.copy_pos + bi.c0 + (l - bi.nint))] = R;
+            }
+        }
+        // cumulative boundary heat of the blocks that own Robin faces
+        if (bi.nf > 0) {
+            double acc[1] = {qin};
+            block_sum<NT, 1>(acc);
+            if (threadIdx.x == 0) a.qcum[blockIdx.x] += (double)dt * acc[0];
+        }
+    }
+    return;
+
+timeout:
+    // a copy did not complete in time: flag it, give the copies in flight a
+    // bounded second chance to land before the shared memory is released
+    if (threadIdx.x == 0) {
+        atomicExch(a.err, kErrWaitTimeout);
+        mbar_wait(bar_s, 0);
+        mbar_wait(bar_w, 0);
+    }
+    __syncthreads();
 }
 
 template <typename real, int NT>
@@ -206,26 +354,13 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
                                                       const real dt)
 {
     const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
-    double acc[2] = {0.0, 0.0};
-    if (s < n_sh) {
-        const int64_t gid = a.n_int + s;
-        real R = real(0);
-        const int k1 = __ldg(a.sh_ptr + s + 1);
-        for (int k = __ldg(a.sh_ptr + s); k < k1; ++k) R += a.P[__ldg(a.sh_copy + k)];
-        const uint8_t ph = __ldg(a.ph + gid);
-        real E = a.E[gid];
-        if (!(ph & kDirichletBit)) {
-            E += dt * R;
-            a.E[gid] = E;
-        }
-        acc[0] = (double)E;
-        acc[1] = latent_of(E, __ldg(a.C + gid), __ldg(a.Lc + gid), ph, a.ranges);
-    }
-    block_sum<NT, 2>(acc);
-    if (threadIdx.x == 0) {
-        a.epart2[2 * blockIdx.x] = acc[0];
-        a.epart2[2 * blockIdx.x + 1] = acc[1];
-    }
+    if (s >= n_sh) return;
+    const int64_t gid = a.n_int + s;
+    if (__ldg(a.ph + gid) & kDirichletBit) return;
+    real R = real(0);
+    const int k1 = __ldg(a.sh_ptr + s + 1);
+    for (int k = __ldg(a.sh_ptr + s); k < k1; ++k) R += a.P[k];   // block order
+    a.E[gid] += dt * R;
 }
 
 // ---------------------------------------------------------------------------
@@ -277,7 +412,7 @@ __global__ void __launch_bounds__(NT) k_flat_update(const FlatArgs<real> a, cons
                                                     const int32_t *nf_idx, const real dt)
 {
     const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double acc[1] = {0.0};
     if (i < a.n_nodes) {
         real R = a.R[i];
         const real Ti = a.T[i];
@@ -289,23 +424,12 @@ __global__ void __launch_bounds__(NT) k_flat_update(const FlatArgs<real> a, cons
                            __ldg(a.T + __ldg(a.fconn + 2 * fs + f));
             const real r = __ldg(a.fg + f) - __ldg(a.fa + f) * (Ti + S);
             R += r;
-            acc[2] += (double)r;
+            acc[0] += (double)r;
         }
-        const uint8_t ph = __ldg(a.ph + i);
-        real E = a.E[i];
-        if (!(ph & kDirichletBit)) {
-            E += dt * R;
-            a.E[i] = E;
-        }
-        acc[0] = (double)E;
-        acc[1] = latent_of(E, __ldg(a.C + i), __ldg(a.Lc + i), ph, a.ranges);
+        if (!(__ldg(a.ph + i) & kDirichletBit)) a.E[i] += dt * R;
     }
-    block_sum<NT, 3>(acc);
-    if (threadIdx.x == 0) {
-        a.epart[2 * blockIdx.x] = acc[0];
-        a.epart[2 * blockIdx.x + 1] = acc[1];
-        a.qcum[blockIdx.x] += (double)dt * acc[2];
-    }
+    block_sum<NT, 1>(acc);
+    if (threadIdx.x == 0) a.qcum[blockIdx.x] += (double)dt * acc[0];
 }
 
 // ---------------------------------------------------------------------------

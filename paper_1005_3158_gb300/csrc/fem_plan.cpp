@@ -390,6 +390,7 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
     for (int64_t s = 0; s < n_sh; s++) out.sh_ptr[s + 1] = out.sh_ptr[s] + nblk[shared[s]];
     out.n_copies = out.sh_ptr[n_sh];
     out.sh_copy.assign((size_t)out.n_copies, -1);
+    out.copy_pos.assign((size_t)out.n_copies, -1);
     out.copy_node.assign((size_t)out.n_copies, -1);
     std::vector<int32_t> sh_fill(out.sh_ptr.begin(), out.sh_ptr.end() - 1);
 
@@ -414,11 +415,14 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         bi.f0 = (int32_t)fpos;
         bi.nf = (int32_t)(fcount[p + 1] - fcount[p]);
         bi.ne_pad = (int32_t)round_up(bi.ne, 32);
+        bi.nep = (int32_t)round_up(bi.ne, 8);
         bi.nf_pad = bi.nf ? (int32_t)round_up(bi.nf, 32) : 0;
         int64_t nslot = 4 * (int64_t)bi.ne_pad + 3 * (int64_t)bi.nf_pad;
-        if (nslot > 65535)
+        // slot nslot is the dummy target of schedule padding
+        if (nslot + 1 > 65535)
             return "block " + std::to_string(p) + " needs " + std::to_string(nslot) +
-                   " slots (> 65535); lower block_elems";
+                   " slots (> 65534); lower block_elems";
+        const uint16_t dummy = (uint16_t)nslot;
         const int32_t *pe = &eorder[(size_t)pstart[p]];
         const int32_t *pf = &forder[(size_t)fcount[p]];
         // local nodes and their slot counts
@@ -434,8 +438,12 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         std::sort(nodes_int.begin(), nodes_int.end(), [&](int32_t a, int32_t b) {
             return cnt[a] != cnt[b] ? cnt[a] > cnt[b] : rank[a] < rank[b];
         });
-        std::sort(nodes_sh.begin(), nodes_sh.end(),
-                  [&](int32_t a, int32_t b) { return sid[a] < sid[b]; });
+        // shared copies by descending slot count too, so that the 32-lane
+        // groups of the schedule hold rows of similar length (little
+        // padding); ties keep the signature order
+        std::sort(nodes_sh.begin(), nodes_sh.end(), [&](int32_t a, int32_t b) {
+            return cnt[a] != cnt[b] ? cnt[a] > cnt[b] : sid[a] < sid[b];
+        });
         bi.n0 = (int32_t)ipos;
         bi.nint = (int32_t)nodes_int.size();
         bi.c0 = (int32_t)cpos;
@@ -450,6 +458,7 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
             int32_t n = nodes_sh[k];
             loc[n] = bi.nint + k;
             out.copy_node[cpos + k] = (int32_t)(n_int + sid[n]);
+            out.copy_pos[cpos + k] = sh_fill[sid[n]];
             out.sh_copy[sh_fill[sid[n]]++] = (int32_t)(cpos + k);
         }
         const int32_t nloc = bi.nint + bi.nsh;
@@ -474,6 +483,7 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
             }
         // 32-lane groups
         bi.g0 = (int32_t)out.grp.size();
+        bi.r0 = (int32_t)rounds;
         bi.ngrp = (nloc + 31) / 32;
         for (int32_t g = 0; g < bi.ngrp; g++) {
             out.grp.push_back((int32_t)rounds);
@@ -482,17 +492,20 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
                 int32_t l = 32 * g + lane;
                 if (l < nloc) J = std::max(J, row_ptr[l + 1] - row_ptr[l]);
             }
-            for (int32_t j = 0; j < J; j++)
-                for (int32_t lane = 0; lane < 32; lane++) {
-                    int32_t l = 32 * g + lane;
-                    uint16_t s = kNoSlot;
-                    if (l < nloc && j < row_ptr[l + 1] - row_ptr[l])
-                        s = (uint16_t)rows[row_ptr[l] + j];
-                    out.sched.push_back(s);
-                }
+            J = (J + 1) & ~1;   // rounds go in pairs (one 32-bit word per lane)
+            for (int32_t jp = 0; jp < J / 2; jp++)
+                for (int32_t lane = 0; lane < 32; lane++)
+                    for (int32_t h = 0; h < 2; h++) {
+                        int32_t l = 32 * g + lane, j = 2 * jp + h;
+                        uint16_t sl = dummy;
+                        if (l < nloc && j < row_ptr[l + 1] - row_ptr[l])
+                            sl = (uint16_t)rows[row_ptr[l] + j];
+                        out.sched.push_back(sl);
+                    }
             rounds += J;
         }
         out.grp.push_back((int32_t)rounds);
+        bi.nrounds = (int32_t)(rounds - bi.r0);
         // element / face positions
         for (int32_t i = 0; i < bi.ne; i++) elem_order.push_back(pe[i]);
         for (int32_t i = 0; i < bi.nf; i++) face_order.push_back(pf[i]);
@@ -501,7 +514,7 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         ipos += bi.nint;
         cpos += bi.nsh;
         out.max_ne = std::max(out.max_ne, bi.ne);
-        out.max_slots = std::max(out.max_slots, (size_t)nslot);
+        out.max_slots = std::max(out.max_slots, (size_t)nslot + 1);
         out.max_nloc = std::max(out.max_nloc, (size_t)nloc);
         // reset scratch
         for (int32_t n : nodes_int) { cnt[n] = 0; loc[n] = -1; }

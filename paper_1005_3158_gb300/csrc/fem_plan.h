@@ -59,9 +59,12 @@ struct BlockPlan {
     std::vector<int32_t> face_order;  // [F_pad] caller face or -1
     std::vector<int32_t> copy_node;   // [n_copies]
     std::vector<int32_t> sh_ptr;      // [n_sh+1]
-    std::vector<int32_t> sh_copy;     // [n_copies]
+    std::vector<int32_t> sh_copy;     // [n_copies] copy index of each (node, block)
+    std::vector<int32_t> copy_pos;    // [n_copies] position of a copy's partial in the
+                                      // node-ordered partial array (inverse of sh_copy)
     std::vector<int32_t> grp;         // group -> first round (per block ngrp+1)
-    std::vector<uint16_t> sched;      // [n_rounds * 32]
+    std::vector<uint16_t> sched;      // [n_rounds * 32], pairs of rounds per lane:
+                                      // (round r, lane) at (r/2)*64 + 2*lane + r%2
     std::vector<int32_t> elem_nodes;  // [E_pad][4] internal ids (-1 pad)
     std::vector<int32_t> face_nodes;  // [F_pad][3]
 };

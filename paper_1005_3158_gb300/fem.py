@@ -271,10 +271,10 @@ def fem_rcm_order(n_nodes, tets):
 
 
 _PLAN_TYPES = {0: np.int32, 1: np.int32, 2: np.int32, 3: np.int32, 4: np.int32, 5: np.int32,
-               6: np.int32, 7: np.int32, 8: np.uint16, 9: np.int32, 10: np.int32}
+               6: np.int32, 7: np.int32, 8: np.uint16, 9: np.int32, 10: np.int32, 11: np.int32}
 PLAN_ARRAYS = {"node_new": 0, "blocks": 1, "elem_order": 2, "face_order": 3, "copy_node": 4,
                "sh_ptr": 5, "sh_copy": 6, "grp": 7, "sched": 8, "elem_nodes": 9,
-               "face_nodes": 10}
+               "face_nodes": 10, "copy_pos": 11}
 
 
 def fem_plan_array(h, which):

@@ -91,13 +91,14 @@ def test_degenerate_tet_rejected():
 
 
 def _check_plan(p, m):
-    blocks = m.plan("blocks").reshape(-1, 12)
+    blocks = m.plan("blocks").reshape(-1, 16)
     sched = m.plan("sched").astype(np.int64)
     grp = m.plan("grp")
     elem_order = m.plan("elem_order")
     face_order = m.plan("face_order")
     copy_node = m.plan("copy_node")
     sh_ptr, sh_copy = m.plan("sh_ptr"), m.plan("sh_copy")
+    copy_pos = m.plan("copy_pos")
     node_new = m.plan("node_new")
     node_old = np.empty_like(node_new)
     node_old[node_new] = np.arange(p.n_nodes)
@@ -106,8 +107,12 @@ def _check_plan(p, m):
     seen_elem = np.zeros(p.n_tets, int)
     seen_face = np.zeros(p.n_faces, int)
     touched_by = [set() for _ in range(p.n_nodes)]
-    for b, (e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad) in enumerate(blocks):
+    for b, (e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad, nep, r0, nrounds, _) in enumerate(blocks):
         assert e0 % 8 == 0 and f0 % 8 == 0 and ne_pad >= ne and nf_pad >= nf
+        assert nep % 8 == 0 and ne <= nep <= ne + 7
+        assert grp[g0] == r0 and grp[g0 + ngrp] == r0 + nrounds
+        if b + 1 < len(blocks):
+            assert blocks[b + 1][0] >= e0 + nep and blocks[b + 1][13] == r0 + nrounds
         nslot = 4 * ne_pad + 3 * nf_pad
         assert nslot <= 65535
         nloc = nint + nsh
@@ -115,13 +120,17 @@ def _check_plan(p, m):
         local_nodes = np.concatenate([n0 + np.arange(nint), copy_node[c0:c0 + nsh]])
         assert (local_nodes[:nint] < n_int).all() and (copy_node[c0:c0 + nsh] >= n_int).all()
         slot_owner = np.full(nslot, -1)
+        dummy = nslot
         for g in range(ngrp):
-            r0, r1 = grp[g0 + g], grp[g0 + g + 1]
-            S = sched[32 * r0:32 * r1].reshape(-1, 32)
+            ra, rb = grp[g0 + g], grp[g0 + g + 1]
+            assert ra % 2 == 0 and rb % 2 == 0
+            # (round r, lane) at (r/2)*64 + 2*lane + r%2
+            S = sched[32 * ra:32 * rb].reshape(-1, 32, 2)
             for lane in range(32):
                 l = 32 * g + lane
-                col = S[:, lane]
-                col = col[col != 0xFFFF]
+                col = S[:, lane, :].ravel()
+                assert (col <= dummy).all()
+                col = col[col != dummy]
                 if l >= nloc:
                     assert col.size == 0
                     continue
@@ -159,6 +168,7 @@ def _check_plan(p, m):
             copies = sh_copy[sh_ptr[s]:sh_ptr[s + 1]]
             assert len(copies) == len(touched_by[n]) >= 2
             assert (copy_node[copies] == i).all()
+            assert (copy_pos[copies] == np.arange(sh_ptr[s], sh_ptr[s + 1])).all()
 
 
 @pytest.mark.parametrize("seed,block_elems", [(0, 64), (3, 100), (5, 333), (7, 5000)])
