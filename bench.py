@@ -331,6 +331,8 @@ def main():
                        "n_faces": p.n_faces, "variant": args.variant,
                        "precision": args.precision, "reorder": args.reorder,
                        "n_blocks": info["n_blocks"], "threads": info["threads"],
+                       "ctas_per_sm": info["ctas_per_sm"], "smem_per_cta": info["smem_per_cta"],
+                       "block_elems": args.block_elems,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)",
                        "dt_s": dt, "setup_s": round(t_setup, 1)},

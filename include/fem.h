@@ -84,11 +84,11 @@ typedef struct {
 typedef struct {
     int32_t variant;     /* fem_variant, default FEM_VARIANT_BLOCK */
     int32_t block_elems; /* target elements per shared-memory block, 0 = auto
-                            (2048 for FP32, 1024 for FP64, so that two CTAs
-                            fit in one SM's shared memory); clamped to
+                            (2048 for FP32, 1024 for FP64); clamped to
                             [64, 12288] */
-    int32_t threads;     /* threads per CTA of the block kernel, 0 = auto
-                            (512); one of 128, 256, 512 */
+    int32_t threads;     /* threads per CTA of the block kernel, 0 = auto (the
+                            fewest threads whose 16-byte element accesses
+                            cover the largest block); 128, 256, 512 or 1024 */
     int32_t reserved[5];
 } fem_options;
 
@@ -104,8 +104,13 @@ typedef struct {
     int64_t bandwidth_input;   /* max |i - j| over element node pairs, caller order */
     int64_t bandwidth_internal;/* the same in the library's internal order */
     int64_t max_block_elems;
-    int64_t device_bytes;      /* device memory held by the mesh */
-    int32_t precision, variant, threads, reorder;
+    int64_t device_bytes;      /* device memory held by the mesh (0 until the
+                                  first call that needs the GPU) */
+    int32_t precision, variant, threads, reorder;   /* threads: CTA size of the block
+                                                      kernel once on the device */
+    int32_t ctas_per_sm;       /* block-kernel CTAs resident per SM (0 before the
+                                  first call that needs the GPU) */
+    int32_t smem_per_cta;      /* dynamic shared memory of one block-kernel CTA, bytes */
 } fem_info;
 
 /* Create a mesh (Section 3: unstructured four-node tetrahedra).
@@ -228,7 +233,7 @@ fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets,
  *   0 node_new   int32 [n_nodes]      caller node -> internal node
  *   1 blocks     int32 [n_blocks][16] per block: e0, ne, f0, nf, n0, nint,
  *                                     c0, nsh, g0, ngrp, ne_pad, nf_pad, nep,
- *                                     r0, nrounds, 0
+ *                                     r0, nrounds, s0
  *   2 elem_order int32 [E_pad]        padded element position -> caller
  *                                     element (-1 for padding)
  *   3 face_order int32 [F_pad]        padded face position -> caller face

@@ -105,16 +105,21 @@ struct fem_mesh {
     size_t dev_bytes = 0;
     size_t smem_bytes = 0;
     int threads = 256;
+    int32_t chunk_words = 0, max_slots = 0, prefetch_dist = 0, ctas_per_sm = 0;
     int n_sh_ctas = 0, n_node_ctas = 0;
     // device pointers
     void *dE = nullptr, *dC = nullptr, *dLc = nullptr, *dRanges = nullptr, *dW = nullptr,
-         *dFa = nullptr, *dFg = nullptr, *dP = nullptr, *dT = nullptr, *dR = nullptr;
+         *dFa = nullptr, *dFg = nullptr, *dP = nullptr, *dT = nullptr, *dR = nullptr,
+         *dEloc = nullptr, *dCLloc = nullptr, *dEsh = nullptr;
+    uint8_t *dPhloc = nullptr;
+    int32_t *dPosloc = nullptr, *dHome = nullptr, *dMpos = nullptr;
+    int32_t ls = 0, nes = 0;
     uint8_t *dPh = nullptr;
     BlockInfo *dBlocks = nullptr;
-    int32_t *dGrp = nullptr, *dCopy = nullptr, *dShPtr = nullptr, *dCopyPos = nullptr,
+    int32_t *dShPtr = nullptr,
             *dNodeOld = nullptr, *dConn = nullptr, *dFconn = nullptr, *dNfPtr = nullptr,
             *dNfIdx = nullptr;
-    uint16_t *dSched = nullptr;
+    uint32_t *dSched = nullptr;
     double *dEpart = nullptr, *dQcum = nullptr, *dIo = nullptr,
            *dDirT = nullptr, *dOut = nullptr;
     int *dErr = nullptr;
@@ -144,9 +149,12 @@ void release_device(fem_mesh *m)
     m->dev_bytes = 0;
     m->dev_ok = false;
     m->dE = m->dC = m->dLc = m->dRanges = m->dW = m->dFa = m->dFg = m->dP = m->dT = m->dR = nullptr;
+    m->dEloc = m->dCLloc = m->dEsh = nullptr;
+    m->dPhloc = nullptr;
+    m->dPosloc = m->dHome = m->dMpos = nullptr;
     m->dPh = nullptr;
     m->dBlocks = nullptr;
-    m->dGrp = m->dCopy = m->dShPtr = m->dCopyPos = m->dNodeOld = m->dConn = m->dFconn = nullptr;
+    m->dShPtr = m->dNodeOld = m->dConn = m->dFconn = nullptr;
     m->dNfPtr = m->dNfIdx = nullptr;
     m->dSched = nullptr;
     m->dEpart = m->dQcum = m->dIo = m->dDirT = m->dOut = nullptr;
@@ -182,7 +190,8 @@ fem_status ensure_plan(fem_mesh *m)
     try {
         if (is_block(m)) {
             err = build_block_plan(m->N, m->E, m->xyz.data(), m->tets.data(), m->rank, m->F,
-                                   m->faces.data(), owner, default_block_elems(m), m->bp);
+                                   m->faces.data(), owner, default_block_elems(m),
+                                   m->prec == FEM_FP32 ? 4 : 8, m->bp);
             if (err.empty()) {
                 m->blocks_flat.resize(m->bp.blocks.size() * 16);
                 std::memcpy(m->blocks_flat.data(), m->bp.blocks.data(),
@@ -239,7 +248,7 @@ template <typename T>
 fem_status upload(fem_mesh *m, T **dst, const T *src, size_t count)
 {
     void *p = nullptr;
-    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T) + kAllocTailPad;
     cudaError_t e = dev_alloc(&p, bytes);
     if (e != cudaSuccess)
         return fail(e == cudaErrorMemoryAllocation ? FEM_ENOMEM : FEM_ECUDA,
@@ -267,8 +276,10 @@ fem_status upload_nodes(fem_mesh *m)
     }
     fem_status st;
     real *p = nullptr;
-    if ((st = upload<real>(m, &p, nullptr, (size_t)m->N))) return st;
-    m->dE = p;
+    if (!is_block(m)) {   // the block variant keeps E in per-block local arrays
+        if ((st = upload<real>(m, &p, nullptr, (size_t)m->N))) return st;
+        m->dE = p;
+    }
     if ((st = upload<real>(m, &p, C.data(), C.size()))) return st;
     m->dC = p;
     if ((st = upload<real>(m, &p, Lc.data(), Lc.size()))) return st;
@@ -295,17 +306,21 @@ fem_status upload_block(fem_mesh *m)
     const BlockPlan &bp = m->bp;
     fem_status st;
     if ((st = upload_nodes<real>(m))) return st;
-    // element conductances: per block one chunk of six rows,
-    // w[6*e0 + k*nep + i] for local element i (zero in the padding)
+    // element conductances: block b's six rows at w[(6*b + k)*nes + i]
+    // (zero in the padding)
     real *p = nullptr;
+    const int32_t nes = bp.blocks.empty() ? 8 : bp.blocks[0].nep;
+    m->nes = nes;
     {
-        std::vector<real> w((size_t)bp.E_pad * 6, real(0));
-        for (const BlockInfo &b : bp.blocks)
+        std::vector<real> w((size_t)bp.blocks.size() * 6 * nes, real(0));
+        for (size_t bi = 0; bi < bp.blocks.size(); bi++) {
+            const BlockInfo &b = bp.blocks[bi];
             for (int32_t i = 0; i < b.ne; i++) {
                 int32_t e = bp.elem_order[(size_t)b.e0 + i];
                 for (int k = 0; k < 6; k++)
-                    w[6 * (size_t)b.e0 + (size_t)k * b.nep + i] = (real)m->w[6 * (size_t)e + k];
+                    w[(6 * bi + k) * (size_t)nes + i] = (real)m->w[6 * (size_t)e + k];
             }
+        }
         if ((st = upload<real>(m, &p, w.data(), w.size()))) return st;
         m->dW = p;
     }
@@ -321,23 +336,93 @@ fem_status upload_block(fem_mesh *m)
     if ((st = upload<real>(m, &p, fg.data(), fg.size()))) return st;
     m->dFg = p;
     if ((st = upload<BlockInfo>(m, &m->dBlocks, bp.blocks.data(), bp.blocks.size()))) return st;
-    if ((st = upload<int32_t>(m, &m->dGrp, bp.grp.data(), bp.grp.size()))) return st;
-    if ((st = upload<uint16_t>(m, &m->dSched, bp.sched.data(), bp.sched.size()))) return st;
-    if ((st = upload<int32_t>(m, &m->dCopy, bp.copy_node.data(), bp.copy_node.size()))) return st;
+    {
+        // device schedule stream: per block a header of group offsets (in
+        // pairs of rounds) and the block's rounds as 32-bit pairs
+        std::vector<uint32_t> stream((size_t)bp.n_sched_words, 0u);
+        for (const BlockInfo &b : bp.blocks) {
+            uint32_t *c = stream.data() + b.s0;
+            for (int32_t g = 0; g <= b.ngrp; g++) c[g] = (uint32_t)((bp.grp[(size_t)b.g0 + g] - b.r0) / 2);
+            std::memcpy(c + chunk_header_words(b.ngrp), bp.sched.data() + (size_t)b.r0 * 32,
+                        (size_t)b.nrounds * 64);
+        }
+        if ((st = upload<uint32_t>(m, &m->dSched, stream.data(), stream.size()))) return st;
+    }
     if ((st = upload<real>(m, &p, nullptr, (size_t)bp.n_copies))) return st;
     m->dP = p;
     if ((st = upload<int32_t>(m, &m->dShPtr, bp.sh_ptr.data(), bp.sh_ptr.size()))) return st;
-    if ((st = upload<int32_t>(m, &m->dCopyPos, bp.copy_pos.data(), bp.copy_pos.size()))) return st;
+    {
+        // per-block local node arrays at stride ls: interior nodes, then the
+        // block's shared copies, then padding (C = 1, Lc = 0)
+        const int32_t ls = (int32_t)(((int64_t)bp.max_nloc + 31) / 32 * 32);
+        m->ls = ls;
+        const size_t nl = bp.blocks.size() * (size_t)ls;
+        const auto &old = bp.node_old;
+        std::vector<real> cl(2 * nl);
+        std::vector<uint8_t> ph(nl, 0);
+        std::vector<int32_t> pos(nl, 0), home((size_t)std::max<int64_t>(bp.n_int, 1), 0);
+        std::vector<int32_t> cloc((size_t)std::max<int64_t>(bp.n_copies, 1), 0);
+        for (size_t i = 0; i < nl; i++) { cl[2 * i] = real(1); cl[2 * i + 1] = real(0); }
+        auto node_ph = [&](int32_t o) {
+            return (uint8_t)(m->rng_id[o] | (m->is_dir.empty() || !m->is_dir[o] ? 0 : kDirichletBit));
+        };
+        for (size_t bi = 0; bi < bp.blocks.size(); bi++) {
+            const BlockInfo &b = bp.blocks[bi];
+            const size_t base = bi * (size_t)ls;
+            for (int32_t l = 0; l < b.nint; l++) {
+                const int32_t o = old[(size_t)b.n0 + l];
+                cl[2 * (base + l)] = (real)m->Cn[o];
+                cl[2 * (base + l) + 1] = (real)m->Lcn[o];
+                ph[base + l] = node_ph(o);
+                home[(size_t)b.n0 + l] = (int32_t)(base + l);
+            }
+            for (int32_t k = 0; k < b.nsh; k++) {
+                const size_t c = (size_t)b.c0 + k, at = base + (size_t)b.nint + k;
+                const int32_t o = old[bp.copy_node[c]];
+                cl[2 * at] = (real)m->Cn[o];
+                cl[2 * at + 1] = (real)m->Lcn[o];
+                ph[at] = node_ph(o);
+                pos[at] = bp.copy_pos[c];
+                cloc[c] = (int32_t)at;
+            }
+        }
+        std::vector<int32_t> mpos((size_t)std::max<int64_t>(bp.n_copies, 1), 0);
+        for (int64_t k = 0; k < bp.n_copies; k++) mpos[k] = cloc[bp.sh_copy[k]];
+        if ((st = upload<real>(m, &p, nullptr, nl))) return st;
+        m->dEloc = p;
+        if ((st = upload<real>(m, &p, cl.data(), cl.size()))) return st;
+        m->dCLloc = p;
+        if ((st = upload<uint8_t>(m, &m->dPhloc, ph.data(), ph.size()))) return st;
+        if ((st = upload<int32_t>(m, &m->dPosloc, pos.data(), pos.size()))) return st;
+        if ((st = upload<int32_t>(m, &m->dHome, home.data(), home.size()))) return st;
+        if ((st = upload<int32_t>(m, &m->dMpos, mpos.data(), mpos.size()))) return st;
+        if ((st = upload<real>(m, &p, nullptr, (size_t)std::max<int64_t>(bp.n_sh, 1)))) return st;
+        m->dEsh = p;
+    }
     if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * bp.blocks.size()))) return st;
     if ((st = upload<double>(m, &m->dQcum, nullptr, bp.blocks.size()))) return st;
     m->n_sh_ctas = (int)std::max<int64_t>(1, (bp.n_sh + 255) / 256);
     if ((st = upload<int>(m, &m->dErr, nullptr, 1))) return st;
-    // kernel configuration
-    m->threads = m->opt.threads > 0 ? m->opt.threads : 512;
-    m->smem_bytes = 0;
-    for (const BlockInfo &b : bp.blocks)
-        m->smem_bytes = std::max(m->smem_bytes, block_smem_bytes(b, sizeof(real)));
-    if (bp.max_nloc > (size_t)kMaxLocalNodes)
+    // kernel configuration: shared memory for the largest block; by default
+    // the fewest threads whose 16-byte element accesses cover every block
+    size_t cw = 0, slots = 0;
+    int32_t max_nep = 0;
+    for (const BlockInfo &b : bp.blocks) {
+        cw = std::max(cw, (size_t)chunk_words(b));
+        slots = std::max(slots, block_slots(b));
+        max_nep = std::max(max_nep, b.nep);
+    }
+    m->chunk_words = (int32_t)cw;
+    slots = (slots + 3) & ~size_t(3);
+    m->max_slots = (int32_t)slots;
+    const int vn = sizeof(real) == 4 ? 4 : 2;
+    m->threads = m->opt.threads;
+    if (m->threads == 0) {
+        m->threads = 128;
+        while (m->threads < 1024 && m->threads * vn < max_nep) m->threads *= 2;
+    }
+    m->smem_bytes = block_kernel_smem((size_t)m->nes, cw, slots, (size_t)m->ls, sizeof(real));
+    if (m->ls > kMaxLocalNodes)
         return fail(FEM_EINVAL, "a block has %zu local nodes (> %d); lower block_elems", bp.max_nloc,
                     kMaxLocalNodes);
     int dev = 0, optin = 0;
@@ -347,6 +432,12 @@ fem_status upload_block(fem_mesh *m)
         return fail(FEM_EINVAL, "a block needs %zu bytes of shared memory (device limit %d); lower block_elems",
                     m->smem_bytes, optin);
     KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes), "configuring the block kernel");
+    int per_sm = 0, sms = 0;
+    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm), "occupancy query");
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return fail(FEM_EINVAL, "the block kernel does not fit on an SM; lower block_elems");
+    m->prefetch_dist = sms * per_sm;
+    m->ctas_per_sm = per_sm;
     return FEM_OK;
 }
 
@@ -404,26 +495,47 @@ BlockArgs<real> block_args(const fem_mesh *m)
     BlockArgs<real> a{};
     a.blocks = m->dBlocks;
     a.n_blocks = (int32_t)m->bp.blocks.size();
-    a.E = (real *)m->dE;
-    a.C = (const real *)m->dC;
-    a.Lc = (const real *)m->dLc;
-    a.ph = m->dPh;
+    a.ls = m->ls;
+    a.Eloc = (real *)m->dEloc;
+    a.CLloc = (const real *)m->dCLloc;
+    a.phloc = m->dPhloc;
+    a.posloc = m->dPosloc;
     a.ranges = (const real *)m->dRanges;
-    a.n_int = m->bp.n_int;
-    a.n_nodes = m->N;
     a.w = (const real *)m->dW;
-    a.e_stride = m->bp.E_pad;
+    a.nes = m->nes;
     a.fa = (const real *)m->dFa;
     a.fg = (const real *)m->dFg;
-    a.grp = m->dGrp;
     a.sched = m->dSched;
-    a.copy_node = m->dCopy;
+    a.chunk_words = m->chunk_words;
+    a.max_slots = m->max_slots;
+    a.prefetch_dist = m->prefetch_dist;
     a.P = (real *)m->dP;
     a.sh_ptr = m->dShPtr;
-    a.copy_pos = m->dCopyPos;
+    a.mpos = m->dMpos;
+    a.Esh = (real *)m->dEsh;
+    a.ph = m->dPh;
+    a.n_int = m->bp.n_int;
+    a.n_sh = m->bp.n_sh;
     a.qcum = m->dQcum;
     a.err = m->dErr;
     return a;
+}
+
+// Where E of internal node i lives (see StateView).
+template <typename real>
+StateView<real> view_of(const fem_mesh *m)
+{
+    StateView<real> v{};
+    if (is_block(m)) {
+        v.Eloc = (real *)m->dEloc;
+        v.Esh = (real *)m->dEsh;
+        v.home = m->dHome;
+        v.n_int = m->bp.n_int;
+    } else {
+        v.Eloc = (real *)m->dE;
+        v.n_int = m->N;
+    }
+    return v;
 }
 
 template <typename real>
@@ -463,11 +575,20 @@ template <typename real>
 int energy_snapshot(fem_mesh *m)
 {
     const int nct = snapshot_ctas(m);
-    int e = launch_energy_snapshot<real>((const real *)m->dE, (const real *)m->dC,
+    int e = launch_energy_snapshot<real>(view_of<real>(m), (const real *)m->dC,
                                          (const real *)m->dLc, m->dPh, (const real *)m->dRanges,
                                          m->N, m->dEpart, nct, m->stream);
     if (!e) e = launch_energy_reduce(m->dEpart, nct, nullptr, 0, m->dQcum, n_qcum(m), m->dOut, m->stream);
     return e;
+}
+
+// Block variant: the block-ordered copies of shared nodes' E follow a state
+// that was set from outside.
+template <typename real>
+int refresh_mirror(fem_mesh *m)
+{
+    if (!is_block(m)) return 0;
+    return launch_mirror_copies<real>(block_args<real>(m), m->stream);
 }
 
 // Apply a pending initial condition or checkpoint on the device.
@@ -479,13 +600,14 @@ fem_status apply_pending(fem_mesh *m)
                        cudaMemcpyHostToDevice, m->stream));
     const bool initial = m->state == fem_mesh::ST_PENDING_T;
     if (initial)
-        KERNEL(launch_set_temperature<real>((real *)m->dE, (const real *)m->dC, (const real *)m->dLc,
+        KERNEL(launch_set_temperature<real>(view_of<real>(m), (const real *)m->dC, (const real *)m->dLc,
                                             m->dPh, (const real *)m->dRanges, m->dIo, m->dNodeOld,
                                             m->dDirT, m->N, m->stream),
                "initial-state kernel");
     else
-        KERNEL(launch_set_state<real>((real *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+        KERNEL(launch_set_state<real>(view_of<real>(m), m->dIo, m->dNodeOld, m->N, m->stream),
                "state kernel");
+    KERNEL(refresh_mirror<real>(m), "mirror kernel");
     CU(cudaMemsetAsync(m->dQcum, 0, (size_t)n_qcum(m) * sizeof(double), m->stream));
     if (initial) {
         // a new energy account: U0 = sum E of the initial state, no boundary heat
@@ -535,8 +657,8 @@ fem_status stash_state(fem_mesh *m)
     cudaSetDevice(m->device);
     std::vector<double> E((size_t)m->N);
     KERNEL(m->prec == FEM_FP32
-               ? launch_get_state<float>((const float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
-               : launch_get_state<double>((const double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+               ? launch_get_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->stream)
+               : launch_get_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->stream),
            "state read-back");
     CU(cudaMemcpyAsync(E.data(), m->dIo, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost,
                        m->stream));
@@ -574,7 +696,7 @@ fem_status launch_step_kernel(fem_mesh *m, int k, double dt)
         if (k == 0)
             KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream), "block kernel");
         else
-            KERNEL(launch_shared_update<real>(a, m->bp.n_sh, m->n_sh_ctas, dt, m->stream),
+            KERNEL(launch_shared_update<real>(a, m->n_sh_ctas, dt, m->stream),
                    "shared-node kernel");
     } else {
         const FlatArgs<real> a = flat_args<real>(m);
@@ -684,8 +806,9 @@ fem_status fem_mesh_create_ex(const double *xyz, int64_t n_nodes, const int32_t 
     fem_options opt{};
     if (opts) opt = *opts;
     if (opt.variant < 0 || opt.variant > 2) return fail(FEM_EINVAL, "unknown variant %d", opt.variant);
-    if (opt.threads != 0 && opt.threads != 128 && opt.threads != 256 && opt.threads != 512)
-        return fail(FEM_EINVAL, "threads must be 0, 128, 256 or 512");
+    if (opt.threads != 0 && opt.threads != 128 && opt.threads != 256 && opt.threads != 512 &&
+        opt.threads != 1024)
+        return fail(FEM_EINVAL, "threads must be 0, 128, 256, 512 or 1024");
     std::unique_ptr<fem_mesh> m;
     try {
         if (!finite_all(xyz, 3 * n_nodes)) return fail(FEM_EINVAL, "non-finite coordinate");
@@ -931,9 +1054,11 @@ fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
         cudaSetDevice(m->device);
         CU(cudaMemcpyAsync(m->dIo, E, (size_t)m->N * sizeof(double), cudaMemcpyHostToDevice, m->stream));
         KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state<float>((float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
-                   : launch_set_state<double>((double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+                   ? launch_set_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->stream)
+                   : launch_set_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->stream),
                "state kernel");
+        KERNEL(m->prec == FEM_FP32 ? refresh_mirror<float>(m) : refresh_mirror<double>(m),
+               "mirror kernel");
     } else {
         m->pending.assign(E, E + m->N);
         m->state = fem_mesh::ST_PENDING_E;
@@ -1009,11 +1134,11 @@ fem_status fem_get_temperature(fem_mesh *m, double *T_out)
     if (st) return st;
     if ((st = check_device_flag(m))) return st;
     KERNEL(m->prec == FEM_FP32
-               ? launch_get_temperature<float>((const float *)m->dE, (const float *)m->dC,
+               ? launch_get_temperature<float>(view_of<float>(m), (const float *)m->dC,
                                                (const float *)m->dLc, m->dPh,
                                                (const float *)m->dRanges, m->dIo, m->dNodeOld, m->N,
                                                m->stream)
-               : launch_get_temperature<double>((const double *)m->dE, (const double *)m->dC,
+               : launch_get_temperature<double>(view_of<double>(m), (const double *)m->dC,
                                                 (const double *)m->dLc, m->dPh,
                                                 (const double *)m->dRanges, m->dIo, m->dNodeOld,
                                                 m->N, m->stream),
@@ -1032,8 +1157,8 @@ fem_status fem_get_state(fem_mesh *m, double *E_out, int64_t *step, double *t)
     if (st) return st;
     if ((st = check_device_flag(m))) return st;
     KERNEL(m->prec == FEM_FP32
-               ? launch_get_state<float>((const float *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream)
-               : launch_get_state<double>((const double *)m->dE, m->dIo, m->dNodeOld, m->N, m->stream),
+               ? launch_get_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->stream)
+               : launch_get_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->stream),
            "read-back kernel");
     CU(cudaMemcpyAsync(E_out, m->dIo, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
@@ -1096,8 +1221,10 @@ fem_status fem_mesh_info(fem_mesh *m, fem_info *out)
     out->device_bytes = (int64_t)m->dev_bytes;
     out->precision = m->prec;
     out->variant = m->opt.variant;
-    out->threads = m->opt.threads > 0 ? m->opt.threads : (is_block(m) ? 512 : 256);
+    out->threads = is_block(m) ? (m->dev_ok ? m->threads : m->opt.threads) : 256;
     out->reorder = m->reorder;
+    out->ctas_per_sm = m->ctas_per_sm;
+    out->smem_per_cta = (int32_t)m->smem_bytes;
     return ok();
 }
 

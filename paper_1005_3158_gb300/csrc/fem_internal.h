@@ -25,34 +25,49 @@ namespace fem {
 //             c*ne_pad + e; face corner c of local face f at
 //             4*ne_pad + c*nf_pad + f
 //   weights   the block's six conductance rows are one contiguous chunk
-//             w[6*e0 + k*nep + e] (nep = ne rounded up to 8), so one bulk
-//             copy brings them to shared memory
-//   rounds    [r0, r0+nrounds) of the schedule (64 bytes each), contiguous;
-//             each group has an even number of rounds, stored as one 32-bit
-//             word (two slot indices) per lane and pair of rounds; padding
-//             entries name the dummy slot 4*ne_pad + 3*nf_pad
+//             w[6*e0 + k*nep + e] (nep = ne rounded up to 8)
+//   rounds    [r0, r0+nrounds) of the schedule (64 bytes each); each group
+//             has an even number of rounds, stored as one 32-bit word (two
+//             slot indices) per lane and pair of rounds; padding entries
+//             name the dummy slot 4*ne_pad + 3*nf_pad
+//   chunk     the block's schedule chunk in the device stream starts at
+//             32-bit word s0: a header of ngrp+1 group offsets (in pairs of
+//             rounds, padded to a multiple of 4 words), then the pairs
+//             (pair p, lane l at word p*32 + l); one bulk copy moves it
 struct BlockInfo {
     int32_t e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad;
-    int32_t nep, r0, nrounds, pad;
+    int32_t nep, r0, nrounds, s0;
 };
+FEM_HD inline int32_t chunk_header_words(int32_t ngrp) { return (ngrp + 4) & ~3; }
+FEM_HD inline int64_t chunk_words(const BlockInfo &b)
+{
+    return chunk_header_words(b.ngrp) + 16 * (int64_t)b.nrounds;
+}
 static_assert(sizeof(BlockInfo) == 64, "BlockInfo layout");
 
-// Dynamic shared memory of one block-kernel CTA (16-byte aligned parts):
-// [2 mbarriers][weights 6*nep][schedule nrounds*32 u16][slots]
+// Dynamic shared memory of a block-kernel CTA (16-byte aligned parts):
+// [2 mbarriers][conductances][schedule chunk][slots + dummy][local nodes: E,
+// partial position, phase byte], sized for the largest block.
 constexpr size_t kSmemBarBytes = 16;
 FEM_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-FEM_HD inline size_t block_smem_bytes(const BlockInfo &b, size_t real_size)
+FEM_HD inline size_t block_slots(const BlockInfo &b)
 {
-    const size_t nslot = 4 * (size_t)b.ne_pad + 3 * (size_t)b.nf_pad + 1;  // + dummy
-    const size_t nloc = (size_t)b.nint + (size_t)b.nsh;
-    (void)nloc;
-    return kSmemBarBytes + align16(6 * (size_t)b.nep * real_size) + align16((size_t)b.nrounds * 64) +
-           align16(nslot * real_size);
+    return 4 * (size_t)b.ne_pad + 3 * (size_t)b.nf_pad + 1;  // + dummy
 }
+FEM_HD inline size_t block_kernel_smem(size_t nes, size_t chunk_words, size_t slots, size_t ls,
+                                       size_t real_size)
+{
+    return kSmemBarBytes + align16(6 * nes * real_size) + align16(chunk_words * 4) +
+           align16(slots * real_size) + align16(ls * (real_size + 4 + 1));
+}
+
+// Every device buffer is allocated with this many bytes after its end, so
+// 16-byte-widened bulk L2 prefetches of its ranges stay inside it.
+constexpr size_t kAllocTailPad = 256;
 
 // Bounded waits: an mbarrier wait gives up after this many polls, sets the
 // error flag and the step returns FEM_ETIMEOUT at the next read-back.
-constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr uint32_t kWaitPolls = 1u << 22;
 // Local nodes of one block are held in registers, kMaxLocalNodes / threads
 // per thread; the planner keeps every block at or below this.
 constexpr int kMaxLocalNodes = 1024;
@@ -61,33 +76,59 @@ constexpr int kErrWaitTimeout = 1;
 constexpr uint8_t kDirichletBit = 0x80;  // in the per-node phase byte
 constexpr int kMaxRanges = 127;          // distinct (Ts, Tl) pairs
 
+// Where the nodal enthalpy of internal node i lives.  Flat variants: one
+// dense array (home == null, n_int == n_nodes).  Block variant: interior
+// node i at Eloc[home[i]] (its block's local array), shared node i at
+// Esh[i - n_int].
+template <typename real>
+struct StateView {
+    real *Eloc;
+    real *Esh;
+    const int32_t *home;
+    int64_t n_int;
+#ifdef __CUDACC__
+    __device__ __forceinline__ real &E(int64_t i) const
+    {
+        return i < n_int ? Eloc[home ? home[i] : i] : Esh[i - n_int];
+    }
+#endif
+};
+
 // Arguments of the block-variant kernels (device pointers).
 template <typename real>
 struct BlockArgs {
     const BlockInfo *blocks;
     int32_t n_blocks;
-    // nodes, internal order: [0, n_int) interior, [n_int, n_nodes) shared
-    real *E;                  // enthalpy content, J (state, updated in place)
-    const real *C;            // sensible capacity, J/K
-    const real *Lc;           // latent capacity, J
-    const uint8_t *ph;        // phase-range index | kDirichletBit
-    const real *ranges;       // [n_ranges][2] (Ts, Tl)
-    int64_t n_int, n_nodes;
-    // elements: w[k * e_stride + p], k = 0..5 for corner pairs
-    // (0,1) (0,2) (0,3) (1,2) (1,3) (2,3): w_ab = -K^e_ab
+    // Per-block local node arrays, block b at [b*ls, (b+1)*ls): local node l
+    // < nint is an interior node (its E lives here), nint <= l < nint+nsh a
+    // shared node's copy (E mirrored by the exchange), the rest padding.
+    int32_t ls;                // local-array stride (multiple of 32)
+    real *Eloc;                // [n_blocks*ls]
+    const real *CLloc;         // [n_blocks*ls][2] (C, Lc)
+    const uint8_t *phloc;      // [n_blocks*ls] phase-range index | kDirichletBit
+    const int32_t *posloc;     // [n_blocks*ls] shared copy: its position in P
+    const real *ranges;        // [n_ranges][2] (Ts, Tl)
+    // elements: block b's conductance rows at w[(6*b + k)*nes + e], k = 0..5
+    // for corner pairs (0,1) (0,2) (0,3) (1,2) (1,3) (2,3): w_ab = -K^e_ab
     const real *w;
-    int64_t e_stride;
+    int32_t nes;               // element stride of a block (multiple of 8)
     // faces: fa[p] = h A / 12, fg[p] = A/3 (h T_inf - q)
     const real *fa;
     const real *fg;
-    // schedule
-    const int32_t *grp;
-    const uint16_t *sched;
-    // shared-node exchange
-    const int32_t *copy_node; // [n_copies] internal node of each block-ordered copy
-    const int32_t *copy_pos;  // [n_copies] where the copy's partial goes in P
-    real *P;                  // [n_copies] partial sums, grouped by shared node
-    const int32_t *sh_ptr;    // [n_sh + 1] node s owns P[sh_ptr[s] .. sh_ptr[s+1])
+    // schedule chunks (see BlockInfo)
+    const uint32_t *sched;
+    int32_t chunk_words;       // largest schedule chunk (32-bit words)
+    int32_t max_slots;         // largest slot count (+ dummy), a multiple of 4
+    int32_t prefetch_dist;     // CTA b warms L2 for block b + prefetch_dist
+    // shared-node exchange: node s owns P[sh_ptr[s] .. sh_ptr[s+1]); entry k
+    // of that range is the partial of one copy, whose mirror sits at
+    // Eloc[mpos[k]]
+    real *P;
+    const int32_t *sh_ptr;
+    const int32_t *mpos;
+    real *Esh;                 // [n_sh] E of the shared nodes
+    const uint8_t *ph;         // [n_nodes] internal order (Dirichlet flag of shared nodes)
+    int64_t n_int, n_sh;
     // FP64 energy bookkeeping
     double *qcum;             // [n_blocks] cumulative heat through the Robin faces
     int *err;                 // device error flag (kErrWaitTimeout)
@@ -119,10 +160,15 @@ template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
                         void *stream);
 template <typename real>
-int launch_shared_update(const BlockArgs<real> &a, int64_t n_sh, int n_sh_ctas, double dt,
-                         void *stream);
+int launch_shared_update(const BlockArgs<real> &a, int n_sh_ctas, double dt, void *stream);
 template <typename real>
 int configure_block_kernel(int threads, size_t smem_bytes);
+template <typename real>
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm);
+// Mirrors of the shared nodes' E in the block-local arrays follow Esh
+// (after the state was set from outside).
+template <typename real>
+int launch_mirror_copies(const BlockArgs<real> &a, void *stream);
 
 // Flat variants, one step = temperatures, element pass (atomic adds, or one
 // launch per colour with plain adds), node update with the Robin faces
@@ -136,25 +182,24 @@ template <typename real>
 int launch_flat_update(const FlatArgs<real> &a, const int32_t *nf_ptr, const int32_t *nf_idx,
                        int n_node_ctas, double dt, void *stream);
 
-// Initial state / read-back kernels.
+// Initial state / read-back kernels (any variant, through a StateView).
 template <typename real>
-int launch_set_temperature(real *E, const real *C, const real *Lc, const uint8_t *ph,
+int launch_set_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, const double *T_in, const int32_t *node_old,
                            const double *dirT_int, int64_t n, void *stream);
 template <typename real>
-int launch_set_state(real *E, const double *E_in, const int32_t *node_old, int64_t n,
+int launch_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
                      void *stream);
 template <typename real>
-int launch_get_temperature(const real *E, const real *C, const real *Lc, const uint8_t *ph,
-                           const real *ranges, double *T_out, const int32_t *node_old,
-                           int64_t n, void *stream);
-template <typename real>
-int launch_get_state(const real *E, double *E_out, const int32_t *node_old, int64_t n,
-                     void *stream);
-template <typename real>
-int launch_energy_snapshot(const real *E, const real *C, const real *Lc, const uint8_t *ph,
-                           const real *ranges, int64_t n, double *part, int n_ctas,
+int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
+                           const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
                            void *stream);
+template <typename real>
+int launch_get_state(StateView<real> v, double *E_out, const int32_t *node_old, int64_t n,
+                     void *stream);
+template <typename real>
+int launch_energy_snapshot(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
+                           const real *ranges, int64_t n, double *part, int n_ctas, void *stream);
 // Sums n_a pairs of part_a, n_b pairs of part_b and n_q entries of q into
 // out[0] (sum E), out[1] (latent), out[2] (boundary heat).
 int launch_energy_reduce(const double *part_a, int64_t n_a, const double *part_b, int64_t n_b,

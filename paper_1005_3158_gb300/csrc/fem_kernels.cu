@@ -129,6 +129,17 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// Bulk prefetch of [p, p+bytes) into L2, widened to 16-byte boundaries
+// (device buffers carry at least 256 bytes of padding after their end).
+__device__ __forceinline__ void l2_prefetch(const void *p, size_t bytes)
+{
+    if (bytes == 0) return;
+    const uintptr_t lo = (uintptr_t)p & ~(uintptr_t)15;
+    const uintptr_t hi = ((uintptr_t)p + bytes + 15) & ~(uintptr_t)15;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo))
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t done;
@@ -141,12 +152,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return done != 0;
 }
-// Waits for phase `parity` of the barrier; gives up after kSpinLimit polls.
+// Waits for phase `parity` of the barrier; gives up after kWaitPolls polls.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+    for (uint32_t i = 0; i < kWaitPolls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// A bulk copy did not complete in time: flag it and give the copies a
+// bounded second chance to land before the CTA releases its shared memory
+// (every thread of the CTA calls this, then returns).
+__device__ __forceinline__ void give_up(int *err, uint32_t bar_s, uint32_t bar_w)
+{
+    if (threadIdx.x == 0) {
+        atomicExch(err, kErrWaitTimeout);
+        mbar_wait(bar_s, 0);
+        mbar_wait(bar_w, 0);
+    }
+    __syncthreads();
 }
 
 // Element product of one tet: r_a = sum_b w_ab (T_b - T_a), w_ab = -K^e_ab
@@ -165,6 +189,17 @@ __device__ __forceinline__ void tet_products(real w01, real w02, real w03, real 
 }
 
 template <typename real>
+struct Vec2Of;
+template <>
+struct Vec2Of<float> {
+    using type = float2;
+};
+template <>
+struct Vec2Of<double> {
+    using type = double2;
+};
+
+template <typename real>
 struct Vec4Of;
 template <>
 struct Vec4Of<float> {
@@ -181,70 +216,94 @@ struct Vec4Of<double> {
 __device__ __forceinline__ float &vat(float4 &v, int i) { return (&v.x)[i]; }
 __device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
 
-// One CTA per element block.  Thread t owns local nodes t, t+NT, ... in
-// every pass (32-lane group g = warp + j*NW covers nodes 32 g + lane), so
-// their T and E stay in registers.
+// One CTA per element block b, NT threads.  The block's local node data sit
+// at a fixed stride (b*ls) and are loaded at kernel start from blockIdx
+// alone; thread 0 bulk-copies the schedule chunk and the six conductance
+// rows (fixed stride 6*b*nes) into shared memory meanwhile.
+// Thread t owns local nodes t, t+NT, ... (the 32-lane schedule group
+// g = warp + j*NW covers nodes 32 g + lane) and element quad(s) t, t+NT, ...
 template <typename real, int NT>
-__global__ void __launch_bounds__(NT, 2) k_block_step(const BlockArgs<real> a, const real dt)
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
+    k_block_step(const BlockArgs<real> a, const real dt)
 {
     constexpr int NW = NT / 32;
     constexpr int MAXJ = kMaxLocalNodes / NT;   // local nodes per thread
     using V = typename Vec4Of<real>::type;
+    using V2 = typename Vec2Of<real>::type;
     constexpr int VN = Vec4Of<real>::n;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const BlockInfo bi = a.blocks[blockIdx.x];
-    const int nloc = bi.nint + bi.nsh;
-    const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad, nep = bi.nep;
-    const int dummy = 4 * ne_pad + 3 * nf_pad;
+    __shared__ double qwarp[NW];   // per-warp boundary heat
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x;
+    const int ls = a.ls, nes = a.nes;
 
-    // shared memory: [barriers][weights][schedule][slots + dummy]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
-    unsigned char *q = smem_raw + kSmemBarBytes;
-    real *sw = reinterpret_cast<real *>(q);
-    q += align16(6 * (size_t)nep * sizeof(real));
-    const uint32_t *ss = reinterpret_cast<const uint32_t *>(q);   // [pair][lane]
-    q += align16((size_t)bi.nrounds * 64);
-    real *sv = reinterpret_cast<real *>(q);
-    const uint32_t bar_s = smem_addr(&bars[0]), bar_w = smem_addr(&bars[1]);
+    // shared memory: [2 barriers][conductances 6 x nes][schedule chunk]
+    // [slots + dummy][per local node: E, partial position, phase byte]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    real *sw = reinterpret_cast<real *>(smem_raw + kSmemBarBytes);
+    uint32_t *chunk = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sw) +
+                                                    align16(6 * (size_t)nes * sizeof(real)));
+    real *sv = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(chunk) +
+                                        align16((size_t)a.chunk_words * 4));
+    real *sE = sv + a.max_slots;                                  // [ls]
+    int32_t *sPos = reinterpret_cast<int32_t *>(sE + ls);         // [ls]
+    uint8_t *sPh = reinterpret_cast<uint8_t *>(sPos + ls);        // [ls]
+    const uint32_t bar_s = smem_addr(bar), bar_w = smem_addr(bar + 1);
 
-    // bulk copies: the block's schedule and its six conductance rows
-    if (threadIdx.x == 0) {
-        mbar_init(bar_s, 1);
-        mbar_init(bar_w, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t sbytes = (uint32_t)bi.nrounds * 64u;
-        mbar_arrive_expect_tx(bar_s, sbytes);
-        if (sbytes) bulk_load(smem_addr(ss), a.sched + (size_t)bi.r0 * 32, sbytes, bar_s);
-        const uint32_t wbytes = (uint32_t)(6 * (size_t)nep * sizeof(real));
-        mbar_arrive_expect_tx(bar_w, wbytes);
-        bulk_load(smem_addr(sw), a.w + 6 * (size_t)bi.e0, wbytes, bar_w);
-    }
-
-    // nodal enthalpy -> temperature (Eqs. 5, 11), overlapping the copies
-    real Tl[MAXJ], El[MAXJ];
+    // local nodes: enthalpy -> temperature (Eqs. 5, 11); padding entries
+    // hold C = 1, Lc = 0 and give a harmless T
+    real Tl[MAXJ];
+    const size_t lb = (size_t)b * ls;
 #pragma unroll
     for (int j = 0; j < MAXJ; j++) {
         const int l = threadIdx.x + j * NT;
         Tl[j] = real(0);
-        El[j] = real(0);
-        if (l < nloc) {
-            const int64_t gid = l < bi.nint ? (int64_t)bi.n0 + l
-                                            : (int64_t)__ldg(a.copy_node + bi.c0 + (l - bi.nint));
-            El[j] = a.E[gid];
-            Tl[j] = temperature_of(El[j], __ldg(a.C + gid), __ldg(a.Lc + gid), __ldg(a.ph + gid),
-                                   a.ranges);
+        if (l < ls) {
+            const real E = a.Eloc[lb + l];
+            const V2 cl = __ldg(reinterpret_cast<const V2 *>(a.CLloc) + lb + l);
+            const uint8_t ph = __ldg(a.phloc + lb + l);
+            Tl[j] = temperature_of(E, cl.x, cl.y, ph, a.ranges);
+            sE[l] = E;
+            sPh[l] = ph;
+            sPos[l] = __ldg(a.posloc + lb + l);
         }
     }
 
-    // one thread polls (bounded), then every thread observes the phase
+    const BlockInfo &bi = a.blocks[b];
+    const int nloc = bi.nint + bi.nsh;
+    const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad;
+    const int dummy = 4 * ne_pad + 3 * nf_pad;
+    const int hdr = (bi.ngrp + 4) & ~3;   // header words: ngrp+1 group offsets, padded to 16 B
+    if (threadIdx.x == 0) {
+        mbar_init(bar_s, 1);
+        mbar_init(bar_w, 1);
+        mbar_fence_init();
+        const uint32_t bytes = (uint32_t)(hdr + 16 * bi.nrounds) * 4u;
+        mbar_arrive_expect_tx(bar_s, bytes);
+        bulk_load(smem_addr(chunk), a.sched + (size_t)bi.s0, bytes, bar_s);
+        // the block's six conductance rows (Eq. 18: only K^e is stored)
+        const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
+        mbar_arrive_expect_tx(bar_w, wbytes);
+        bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
+    }
+    // this thread's first face
+    real fa0 = real(0), fg0 = real(0);
+    if ((int)threadIdx.x < bi.nf) {
+        fa0 = __ldg(a.fa + bi.f0 + threadIdx.x);
+        fg0 = __ldg(a.fg + bi.f0 + threadIdx.x);
+    }
+
+    // the mbarrier was initialised by thread 0 before any other thread polls
+    // it: the barrier below orders the two
+    __syncthreads();
     int failed = 0;
     if (threadIdx.x == 0) failed = !mbar_wait(bar_s, 0);
-    if (__syncthreads_or(failed)) goto timeout;
+    if (__syncthreads_or(failed)) {
+        give_up(a.err, bar_s, bar_w);
+        return;
+    }
     mbar_try_wait(bar_s, 0);
+    const uint32_t *pairs = chunk + hdr;   // pair p, lane l at pairs[p*32 + l]
 
     // pass 1: T of every local node into the slots of its element corners
     // (padding entries all name the dummy slot)
@@ -252,39 +311,38 @@ __global__ void __launch_bounds__(NT, 2) k_block_step(const BlockArgs<real> a, c
     for (int j = 0; j < MAXJ; j++) {
         const int g = warp + j * NW;
         if (g < bi.ngrp) {
-            const int p0 = (__ldg(a.grp + bi.g0 + g) - bi.r0) >> 1;
-            const int p1 = (__ldg(a.grp + bi.g0 + g + 1) - bi.r0) >> 1;
+            const int p0 = (int)chunk[g], p1 = (int)chunk[g + 1];
             const real T = Tl[j];
             for (int pr = p0; pr < p1; ++pr) {
-                const uint32_t v = ss[pr * 32 + lane];
+                const uint32_t v = pairs[pr * 32 + lane];
                 sv[v & 0xFFFFu] = T;
                 sv[v >> 16] = T;
             }
         }
     }
+
     if (threadIdx.x == 0) failed = !mbar_wait(bar_w, 0);
-    if (__syncthreads_or(failed)) goto timeout;
+    if (__syncthreads_or(failed)) {
+        give_up(a.err, bar_s, bar_w);
+        return;
+    }
     mbar_try_wait(bar_w, 0);
 
     // pass 2: element products, VN elements per 16-byte access
-    for (int e = threadIdx.x * VN; e < bi.ne; e += NT * VN) {
-        const V w01 = *reinterpret_cast<const V *>(sw + e);
-        const V w02 = *reinterpret_cast<const V *>(sw + nep + e);
-        const V w03 = *reinterpret_cast<const V *>(sw + 2 * nep + e);
-        const V w12 = *reinterpret_cast<const V *>(sw + 3 * nep + e);
-        const V w13 = *reinterpret_cast<const V *>(sw + 4 * nep + e);
-        const V w23 = *reinterpret_cast<const V *>(sw + 5 * nep + e);
+    for (int qd = threadIdx.x; qd * VN < bi.ne; qd += NT) {
+        const int e = qd * VN;
+        V wq[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) wq[k] = *reinterpret_cast<const V *>(sw + k * nes + e);
         V T0 = *reinterpret_cast<const V *>(sv + e);
         V T1 = *reinterpret_cast<const V *>(sv + ne_pad + e);
         V T2 = *reinterpret_cast<const V *>(sv + 2 * ne_pad + e);
         V T3 = *reinterpret_cast<const V *>(sv + 3 * ne_pad + e);
 #pragma unroll
-        for (int i = 0; i < VN; i++) {
-            V c01 = w01, c02 = w02, c03 = w03, c12 = w12, c13 = w13, c23 = w23;
-            tet_products(vat(c01, i), vat(c02, i), vat(c03, i), vat(c12, i), vat(c13, i),
-                         vat(c23, i), vat(T0, i), vat(T1, i), vat(T2, i), vat(T3, i), vat(T0, i),
+        for (int i = 0; i < VN; i++)
+            tet_products(vat(wq[0], i), vat(wq[1], i), vat(wq[2], i), vat(wq[3], i), vat(wq[4], i),
+                         vat(wq[5], i), vat(T0, i), vat(T1, i), vat(T2, i), vat(T3, i), vat(T0, i),
                          vat(T1, i), vat(T2, i), vat(T3, i));
-        }
         *reinterpret_cast<V *>(sv + e) = T0;
         *reinterpret_cast<V *>(sv + ne_pad + e) = T1;
         *reinterpret_cast<V *>(sv + 2 * ne_pad + e) = T2;
@@ -292,75 +350,91 @@ __global__ void __launch_bounds__(NT, 2) k_block_step(const BlockArgs<real> a, c
     }
     if (threadIdx.x == 0) sv[dummy] = real(0);   // padding adds nothing in pass 3
     // Robin faces (Eq. 4): r_c = A/3 (h T_inf - q) - h A/12 (T_c + T_0 + T_1 + T_2)
-    {
-        double qin = 0.0;   // heat entering through the block's faces (FP64)
-        const int fbase = 4 * ne_pad;
-        for (int f = threadIdx.x; f < bi.nf; f += NT) {
-            real *s0 = sv + fbase + f;
-            const real T0 = s0[0], T1 = s0[nf_pad], T2 = s0[2 * nf_pad];
-            const real ha = __ldg(a.fa + bi.f0 + f), hg = __ldg(a.fg + bi.f0 + f);
-            const real S = T0 + T1 + T2;
-            const real r0 = hg - ha * (T0 + S), r1 = hg - ha * (T1 + S), r2 = hg - ha * (T2 + S);
-            s0[0] = r0;
-            s0[nf_pad] = r1;
-            s0[2 * nf_pad] = r2;
-            qin += (double)r0 + (double)r1 + (double)r2;
-        }
-        __syncthreads();
-
-        // pass 3: fixed-order node sums; interior update or shared partial
-#pragma unroll
-        for (int j = 0; j < MAXJ; j++) {
-            const int g = warp + j * NW;
-            if (g >= bi.ngrp) continue;
-            const int l = 32 * g + lane;
-            const int p0 = (__ldg(a.grp + bi.g0 + g) - bi.r0) >> 1;
-            const int p1 = (__ldg(a.grp + bi.g0 + g + 1) - bi.r0) >> 1;
-            real R = real(0);
-            for (int pr = p0; pr < p1; ++pr) {
-                const uint32_t v = ss[pr * 32 + lane];
-                R += sv[v & 0xFFFFu];
-                R += sv[v >> 16];
-            }
-            if (l < bi.nint) {
-                const int64_t gid = (int64_t)bi.n0 + l;
-                if (!(__ldg(a.ph + gid) & kDirichletBit)) a.E[gid] = El[j] + dt * R;
-            } else if (l < nloc) {
-                a.P[__ldg(a.copy_pos + bi.c0 + (l - bi.nint))] = R;
-            }
-        }
-        // cumulative boundary heat of the blocks that own Robin faces
-        if (bi.nf > 0) {
-            double acc[1] = {qin};
-            block_sum<NT, 1>(acc);
-            if (threadIdx.x == 0) a.qcum[blockIdx.x] += (double)dt * acc[0];
-        }
+    real qin = real(0);   // heat entering through this thread's faces
+    for (int f = threadIdx.x; f < bi.nf; f += NT) {
+        real *s0 = sv + 4 * ne_pad + f;
+        const real T0 = s0[0], T1 = s0[nf_pad], T2 = s0[2 * nf_pad];
+        const bool first = f == (int)threadIdx.x;
+        const real ha = first ? fa0 : __ldg(a.fa + bi.f0 + f);
+        const real hg = first ? fg0 : __ldg(a.fg + bi.f0 + f);
+        const real S = T0 + T1 + T2;
+        const real r0 = hg - ha * (T0 + S), r1 = hg - ha * (T1 + S), r2 = hg - ha * (T2 + S);
+        s0[0] = r0;
+        s0[nf_pad] = r1;
+        s0[2 * nf_pad] = r2;
+        qin += (r0 + r1) + r2;
     }
-    return;
-
-timeout:
-    // a copy did not complete in time: flag it, give the copies in flight a
-    // bounded second chance to land before the shared memory is released
-    if (threadIdx.x == 0) {
-        atomicExch(a.err, kErrWaitTimeout);
-        mbar_wait(bar_s, 0);
-        mbar_wait(bar_w, 0);
+    if (bi.nf > 0) {   // block-uniform: per-warp partials, FP64 from there on
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qin += __shfl_down_sync(0xffffffffu, qin, o);
+        if (lane == 0) qwarp[warp] = (double)qin;
     }
     __syncthreads();
+
+    // pass 3: fixed-order node sums; interior update or shared partial
+#pragma unroll
+    for (int j = 0; j < MAXJ; j++) {
+        const int g = warp + j * NW;
+        if (g >= bi.ngrp) continue;
+        const int l = 32 * g + lane;
+        const int p0 = (int)chunk[g], p1 = (int)chunk[g + 1];
+        real R = real(0);
+        for (int pr = p0; pr < p1; ++pr) {
+            const uint32_t v = pairs[pr * 32 + lane];
+            R += sv[v & 0xFFFFu];
+            R += sv[v >> 16];
+        }
+        if (l < bi.nint) {
+            if (!(sPh[l] & kDirichletBit)) a.Eloc[lb + l] = sE[l] + dt * R;
+        } else if (l < nloc) {
+            a.P[sPos[l]] = R;
+        }
+    }
+    // warm L2 with the data of the block that starts about one wave of
+    // resident CTAs later, so DRAM keeps working while CTAs compute (off the
+    // critical path: issued once this block's work is done)
+    if (threadIdx.x == 32 && b + a.prefetch_dist < a.n_blocks) {
+        const int pbi = b + a.prefetch_dist;
+        const size_t pl = (size_t)pbi * ls;
+        l2_prefetch(a.w + 6 * (size_t)pbi * nes, 6 * (size_t)nes * sizeof(real));
+        l2_prefetch(a.Eloc + pl, (size_t)ls * sizeof(real));
+        l2_prefetch(a.CLloc + 2 * pl, (size_t)ls * 2 * sizeof(real));
+        l2_prefetch(a.phloc + pl, (size_t)ls);
+        l2_prefetch(a.posloc + pl, (size_t)ls * 4);
+        const BlockInfo &pb = a.blocks[pbi];
+        l2_prefetch(a.sched + (size_t)pb.s0, (size_t)chunk_words(pb) * 4);
+        if (pb.nf > 0) {
+            l2_prefetch(a.fa + pb.f0, (size_t)pb.nf * sizeof(real));
+            l2_prefetch(a.fg + pb.f0, (size_t)pb.nf * sizeof(real));
+        }
+    }
+    // cumulative boundary heat of the blocks that own Robin faces (FP64)
+    if (bi.nf > 0 && threadIdx.x == 0) {
+        double q = 0.0;
+        for (int k = 0; k < NW; k++) q += qwarp[k];
+        a.qcum[b] += (double)dt * q;
+    }
 }
 
+// Shared nodes: sum the partials of every copy in a fixed order (Eq. 22),
+// update E and refresh the copies' mirrors in the blocks' local arrays.
+// With update == false only the mirrors are refreshed.
 template <typename real, int NT>
-__global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, const int64_t n_sh,
-                                                      const real dt)
+__global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, const real dt,
+                                                      const bool update)
 {
     const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (s >= n_sh) return;
-    const int64_t gid = a.n_int + s;
-    if (__ldg(a.ph + gid) & kDirichletBit) return;
-    real R = real(0);
-    const int k1 = __ldg(a.sh_ptr + s + 1);
-    for (int k = __ldg(a.sh_ptr + s); k < k1; ++k) R += a.P[k];   // block order
-    a.E[gid] += dt * R;
+    if (s >= a.n_sh) return;
+    const int k0 = __ldg(a.sh_ptr + s), k1 = __ldg(a.sh_ptr + s + 1);
+    real E = a.Esh[s];
+    if (update) {
+        if (__ldg(a.ph + a.n_int + s) & kDirichletBit) return;
+        real R = real(0);
+        for (int k = k0; k < k1; ++k) R += a.P[k];   // block order
+        E += dt * R;
+        a.Esh[s] = E;
+    }
+    for (int k = k0; k < k1; ++k) a.Eloc[__ldg(a.mpos + k)] = E;
 }
 
 // ---------------------------------------------------------------------------
@@ -436,7 +510,7 @@ __global__ void __launch_bounds__(NT) k_flat_update(const FlatArgs<real> a, cons
 // State I/O and energy
 // ---------------------------------------------------------------------------
 template <typename real>
-__global__ void k_set_temperature(real *E, const real *C, const real *Lc, const uint8_t *ph,
+__global__ void k_set_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                                   const real *ranges, const double *T_in, const int32_t *node_old,
                                   const double *dirT_int, int64_t n)
 {
@@ -444,45 +518,46 @@ __global__ void k_set_temperature(real *E, const real *C, const real *Lc, const 
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t p = ph[i];
         const double T = (dirT_int && (p & kDirichletBit)) ? dirT_int[i] : T_in[node_old[i]];
-        E[i] = enthalpy_of((real)T, C[i], Lc[i], p, ranges);
+        v.E(i) = enthalpy_of((real)T, C[i], Lc[i], p, ranges);
     }
 }
 
 template <typename real>
-__global__ void k_set_state(real *E, const double *E_in, const int32_t *node_old, int64_t n)
+__global__ void k_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        E[i] = (real)E_in[node_old[i]];
+        v.E(i) = (real)E_in[node_old[i]];
 }
 
 template <typename real>
-__global__ void k_get_temperature(const real *E, const real *C, const real *Lc, const uint8_t *ph,
+__global__ void k_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                                   const real *ranges, double *T_out, const int32_t *node_old,
                                   int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        T_out[node_old[i]] = (double)temperature_of(E[i], C[i], Lc[i], ph[i], ranges);
+        T_out[node_old[i]] = (double)temperature_of(v.E(i), C[i], Lc[i], ph[i], ranges);
 }
 
 template <typename real>
-__global__ void k_get_state(const real *E, double *E_out, const int32_t *node_old, int64_t n)
+__global__ void k_get_state(StateView<real> v, double *E_out, const int32_t *node_old, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        E_out[node_old[i]] = (double)E[i];
+        E_out[node_old[i]] = (double)v.E(i);
 }
 
 template <typename real, int NT>
-__global__ void __launch_bounds__(NT) k_energy_snapshot(const real *E, const real *C, const real *Lc,
-                                                        const uint8_t *ph, const real *ranges,
-                                                        int64_t n, double *part)
+__global__ void __launch_bounds__(NT) k_energy_snapshot(StateView<real> v, const real *C,
+                                                        const real *Lc, const uint8_t *ph,
+                                                        const real *ranges, int64_t n, double *part)
 {
     double acc[2] = {0.0, 0.0};
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
-        acc[0] += (double)E[i];
-        acc[1] += latent_of(E[i], C[i], Lc[i], ph[i], ranges);
+        const real E = v.E(i);
+        acc[0] += (double)E;
+        acc[1] += latent_of(E, C[i], Lc[i], ph[i], ranges);
     }
     block_sum<NT, 2>(acc);
     if (threadIdx.x == 0) {
@@ -529,6 +604,20 @@ inline int grid_for(int64_t n, int threads)
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename real>
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm)
+{
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (threads) {
+    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 128>, 128, smem_bytes); break;
+    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 256>, 256, smem_bytes); break;
+    case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 512>, 512, smem_bytes); break;
+    case 1024: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 1024>, 1024, smem_bytes); break;
+    default: break;
+    }
+    return (int)e;
+}
+
+template <typename real>
 int configure_block_kernel(int threads, size_t smem_bytes)
 {
     cudaError_t e = cudaSuccess;
@@ -537,6 +626,7 @@ int configure_block_kernel(int threads, size_t smem_bytes)
     case 128: e = cudaFuncSetAttribute(k_block_step<real, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
     case 256: e = cudaFuncSetAttribute(k_block_step<real, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
     case 512: e = cudaFuncSetAttribute(k_block_step<real, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
+    case 1024: e = cudaFuncSetAttribute(k_block_step<real, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)e;
@@ -548,21 +638,31 @@ int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes
 {
     cudaStream_t st = (cudaStream_t)stream;
     const real rdt = (real)dt;
+    const int grid = a.n_blocks;
     switch (threads) {
-    case 128: k_block_step<real, 128><<<a.n_blocks, 128, smem_bytes, st>>>(a, rdt); break;
-    case 256: k_block_step<real, 256><<<a.n_blocks, 256, smem_bytes, st>>>(a, rdt); break;
-    case 512: k_block_step<real, 512><<<a.n_blocks, 512, smem_bytes, st>>>(a, rdt); break;
+    case 128: k_block_step<real, 128><<<grid, 128, smem_bytes, st>>>(a, rdt); break;
+    case 256: k_block_step<real, 256><<<grid, 256, smem_bytes, st>>>(a, rdt); break;
+    case 512: k_block_step<real, 512><<<grid, 512, smem_bytes, st>>>(a, rdt); break;
+    case 1024: k_block_step<real, 1024><<<grid, 1024, smem_bytes, st>>>(a, rdt); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();
 }
 
 template <typename real>
-int launch_shared_update(const BlockArgs<real> &a, int64_t n_sh, int n_sh_ctas, double dt,
-                         void *stream)
+int launch_mirror_copies(const BlockArgs<real> &a, void *stream)
 {
-    if (n_sh > 0)
-        k_shared_update<real, 256><<<n_sh_ctas, 256, 0, (cudaStream_t)stream>>>(a, n_sh, (real)dt);
+    if (a.n_sh > 0)
+        k_shared_update<real, 256><<<(int)((a.n_sh + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            a, real(0), false);
+    return (int)cudaGetLastError();
+}
+
+template <typename real>
+int launch_shared_update(const BlockArgs<real> &a, int n_sh_ctas, double dt, void *stream)
+{
+    if (a.n_sh > 0)
+        k_shared_update<real, 256><<<n_sh_ctas, 256, 0, (cudaStream_t)stream>>>(a, (real)dt, true);
     return (int)cudaGetLastError();
 }
 
@@ -600,44 +700,46 @@ int launch_flat_update(const FlatArgs<real> &a, const int32_t *nf_ptr, const int
 }
 
 template <typename real>
-int launch_set_temperature(real *E, const real *C, const real *Lc, const uint8_t *ph,
+int launch_set_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, const double *T_in, const int32_t *node_old,
                            const double *dirT_int, int64_t n, void *stream)
 {
     k_set_temperature<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
-        E, C, Lc, ph, ranges, T_in, node_old, dirT_int, n);
+        v, C, Lc, ph, ranges, T_in, node_old, dirT_int, n);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
-int launch_set_state(real *E, const double *E_in, const int32_t *node_old, int64_t n, void *stream)
+int launch_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
+                     void *stream)
 {
-    k_set_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(E, E_in, node_old, n);
+    k_set_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
-int launch_get_temperature(const real *E, const real *C, const real *Lc, const uint8_t *ph,
+int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
                            void *stream)
 {
     k_get_temperature<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
-        E, C, Lc, ph, ranges, T_out, node_old, n);
+        v, C, Lc, ph, ranges, T_out, node_old, n);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
-int launch_get_state(const real *E, double *E_out, const int32_t *node_old, int64_t n, void *stream)
+int launch_get_state(StateView<real> v, double *E_out, const int32_t *node_old, int64_t n,
+                     void *stream)
 {
-    k_get_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(E, E_out, node_old, n);
+    k_get_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_out, node_old, n);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
-int launch_energy_snapshot(const real *E, const real *C, const real *Lc, const uint8_t *ph,
+int launch_energy_snapshot(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, int64_t n, double *part, int n_ctas, void *stream)
 {
-    k_energy_snapshot<real, 256><<<n_ctas, 256, 0, (cudaStream_t)stream>>>(E, C, Lc, ph, ranges, n, part);
+    k_energy_snapshot<real, 256><<<n_ctas, 256, 0, (cudaStream_t)stream>>>(v, C, Lc, ph, ranges, n, part);
     return (int)cudaGetLastError();
 }
 
@@ -650,22 +752,26 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
 
 #define FEM_INSTANTIATE(real)                                                                     \
     template int configure_block_kernel<real>(int, size_t);                                       \
+    template int block_kernel_occupancy<real>(int, size_t, int *);                                \
+    template int launch_mirror_copies<real>(const BlockArgs<real> &, void *);                     \
     template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *); \
-    template int launch_shared_update<real>(const BlockArgs<real> &, int64_t, int, double, void *); \
+    template int launch_shared_update<real>(const BlockArgs<real> &, int, double, void *);        \
     template int launch_flat_temperature<real>(const FlatArgs<real> &, void *);                   \
     template int launch_flat_elements<real>(const FlatArgs<real> &, bool, const int64_t *, int,  \
                                             void *);                                              \
     template int launch_flat_update<real>(const FlatArgs<real> &, const int32_t *,                \
                                           const int32_t *, int, double, void *);                  \
-    template int launch_set_temperature<real>(real *, const real *, const real *,                 \
+    template int launch_set_temperature<real>(StateView<real>, const real *, const real *,        \
                                               const uint8_t *, const real *, const double *,      \
                                               const int32_t *, const double *, int64_t, void *);  \
-    template int launch_set_state<real>(real *, const double *, const int32_t *, int64_t, void *); \
-    template int launch_get_temperature<real>(const real *, const real *, const real *,           \
+    template int launch_set_state<real>(StateView<real>, const double *, const int32_t *, int64_t, \
+                                        void *);                                                  \
+    template int launch_get_temperature<real>(StateView<real>, const real *, const real *,        \
                                               const uint8_t *, const real *, double *,            \
                                               const int32_t *, int64_t, void *);                  \
-    template int launch_get_state<real>(const real *, double *, const int32_t *, int64_t, void *); \
-    template int launch_energy_snapshot<real>(const real *, const real *, const real *,           \
+    template int launch_get_state<real>(StateView<real>, double *, const int32_t *, int64_t,      \
+                                        void *);                                                  \
+    template int launch_energy_snapshot<real>(StateView<real>, const real *, const real *,        \
                                               const uint8_t *, const real *, int64_t, double *,   \
                                               int, void *);
 

@@ -291,10 +291,139 @@ void rcb(Cen *a, int64_t n, int64_t parts, int depth)
 
 }  // namespace
 
+namespace {
+
+// Shared-memory bank cells of a slot: FP32 slots occupy one of 32 banks
+// (one cell each); FP64 slots occupy a bank pair, of which 16 exist, and a
+// warp access is two wavefronts, so each pair offers two cells.
+struct BankModel {
+    int real_size;
+    int cells(uint32_t slot, int out[2]) const
+    {
+        if (real_size == 4) {
+            out[0] = (int)(slot & 31u);
+            return 1;
+        }
+        const int b = (int)(slot & 15u);
+        out[0] = 2 * b;
+        out[1] = 2 * b + 1;
+        return 2;
+    }
+};
+
+struct GroupMatcher {
+    BankModel bm;
+    int nrem[32];
+    uint16_t rem[32][64];
+    int owner[32];     // cell -> lane
+    int choice[32];    // lane -> index into rem
+    int choice_cell[32];
+
+    bool augment(int l, uint32_t &seen)
+    {
+        for (int k = 0; k < nrem[l]; k++) {
+            int cs[2];
+            const int nc = bm.cells(rem[l][k], cs);
+            for (int q = 0; q < nc; q++) {
+                const int c = cs[q];
+                if (seen & (1u << c)) continue;
+                seen |= 1u << c;
+                if (owner[c] < 0 || augment(owner[c], seen)) {
+                    owner[c] = l;
+                    choice[l] = k;
+                    choice_cell[l] = c;
+                    return true;
+                }
+            }
+        }
+        return false;
+    }
+};
+
+// Reorders the slots of every row inside each 32-lane group (same number of
+// rounds, same slots) so that each round's accesses fall into distinct
+// bank cells where possible: a maximum lanes x cells matching per round,
+// lanes that must advance to finish in time served first, the rest of
+// those taking the least-loaded cell.  Rows change order only; the layout,
+// the sizes and the slots of every node stay as planned.
+void schedule_group(uint16_t *g, int J, uint16_t dummy, GroupMatcher &M)
+{
+    // g: J rounds in pairs: (round r, lane) at (r/2)*64 + 2*lane + r%2
+    auto at = [&](int r, int lane) -> uint16_t & { return g[(r / 2) * 64 + 2 * lane + (r & 1)]; };
+    for (int l = 0; l < 32; l++) {
+        M.nrem[l] = 0;
+        for (int r = 0; r < J; r++)
+            if (at(r, l) != dummy) M.rem[l][M.nrem[l]++] = at(r, l);
+    }
+    for (int r = 0; r < J; r++) {
+        const int left = J - r;
+        int order[32], n = 0;
+        for (int l = 0; l < 32; l++)
+            if (M.nrem[l] > 0) order[n++] = l;
+        std::sort(order, order + n, [&](int a, int b) { return M.nrem[a] > M.nrem[b]; });
+        for (int c = 0; c < 32; c++) M.owner[c] = -1;
+        for (int i = 0; i < n; i++) M.choice[order[i]] = -1;
+        for (int i = 0; i < n; i++) {
+            uint32_t seen = 0;
+            M.augment(order[i], seen);
+        }
+        int load[32] = {0};
+        for (int c = 0; c < 32; c++)
+            if (M.owner[c] >= 0) load[c]++;
+        // a lane that has as many slots left as rounds must take one now
+        for (int i = 0; i < n; i++) {
+            const int l = order[i];
+            if (M.choice[l] >= 0 || M.nrem[l] < left) continue;
+            int best = 0, best_load = 1 << 30;
+            for (int k = 0; k < M.nrem[l]; k++) {
+                int cs[2];
+                const int nc = M.bm.cells(M.rem[l][k], cs);
+                for (int q = 0; q < nc; q++)
+                    if (load[cs[q]] < best_load) { best_load = load[cs[q]]; best = k; M.choice_cell[l] = cs[q]; }
+            }
+            M.choice[l] = best;
+            load[M.choice_cell[l]]++;
+        }
+        for (int l = 0; l < 32; l++) {
+            if (M.nrem[l] > 0 && M.choice[l] >= 0) {
+                at(r, l) = M.rem[l][M.choice[l]];
+                M.rem[l][M.choice[l]] = M.rem[l][--M.nrem[l]];
+                M.choice[l] = -1;
+            } else {
+                at(r, l) = dummy;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void bank_schedule(BlockPlan &bp, int real_size)
+{
+    const int64_t nb = (int64_t)bp.blocks.size();
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; t++)
+        pool.emplace_back([&, t] {
+            GroupMatcher M;
+            M.bm.real_size = real_size;
+            for (int64_t b = t; b < nb; b += nt) {
+                const BlockInfo &bi = bp.blocks[(size_t)b];
+                const uint16_t dummy = (uint16_t)(4 * bi.ne_pad + 3 * bi.nf_pad);
+                for (int32_t gi = 0; gi < bi.ngrp; gi++) {
+                    const int32_t r0 = bp.grp[(size_t)bi.g0 + gi], r1 = bp.grp[(size_t)bi.g0 + gi + 1];
+                    if (r1 - r0 > 64) continue;   // rows longer than the matcher holds keep their order
+                    schedule_group(bp.sched.data() + (size_t)r0 * 32, r1 - r0, dummy, M);
+                }
+            }
+        });
+    for (auto &th : pool) th.join();
+}
+
 std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int32_t *tets,
                              const std::vector<int32_t> &rank, int64_t F,
                              const int32_t *faces, const std::vector<int32_t> &face_owner,
-                             int block_elems, BlockPlan &out)
+                             int block_elems, int real_size, BlockPlan &out)
 {
     out = BlockPlan();
     out.N = N; out.E = E; out.F = F;
@@ -394,8 +523,11 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
     out.copy_node.assign((size_t)out.n_copies, -1);
     std::vector<int32_t> sh_fill(out.sh_ptr.begin(), out.sh_ptr.end() - 1);
 
-    // --- per-block layout
-    int64_t epos = 0, fpos = 0, cpos = 0, ipos = 0, rounds = 0;
+    // --- per-block layout; every block's elements occupy the same stride
+    // (the largest block rounded up to 8), so block b starts at b * nes
+    int64_t nes = 8;
+    for (int64_t p = 0; p < nparts; p++) nes = std::max(nes, round_up(pstart[p + 1] - pstart[p], 8));
+    int64_t epos = 0, fpos = 0, cpos = 0, ipos = 0, rounds = 0, swords = 0;
     out.blocks.resize((size_t)nparts);
     std::vector<int32_t> loc((size_t)N, -1), cnt((size_t)N, 0);
     std::vector<int32_t> nodes_int, nodes_sh, row_ptr, rows, fillr;
@@ -406,7 +538,7 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
     out.grp.reserve((size_t)(nparts * 40));
     for (int64_t p = 0; p < nparts; p++) {
         BlockInfo bi{};
-        epos = round_up(epos, 8);
+        epos = p * nes;
         fpos = round_up(fpos, 8);
         elem_order.resize((size_t)epos, -1);
         face_order.resize((size_t)fpos, -1);
@@ -414,9 +546,12 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         bi.ne = (int32_t)(pstart[p + 1] - pstart[p]);
         bi.f0 = (int32_t)fpos;
         bi.nf = (int32_t)(fcount[p + 1] - fcount[p]);
-        bi.ne_pad = (int32_t)round_up(bi.ne, 32);
-        bi.nep = (int32_t)round_up(bi.ne, 8);
-        bi.nf_pad = bi.nf ? (int32_t)round_up(bi.nf, 32) : 0;
+        // corner rows of the slot array start 8 (FP32) or 4 (FP64) banks apart,
+        // so the four corners of an element do not share a bank
+        const int32_t corner_skew = real_size == 4 ? 8 : 4;
+        bi.ne_pad = (int32_t)round_up(bi.ne, 32) + corner_skew;
+        bi.nep = (int32_t)nes;
+        bi.nf_pad = bi.nf ? (int32_t)round_up(bi.nf, 32) + corner_skew : 0;
         int64_t nslot = 4 * (int64_t)bi.ne_pad + 3 * (int64_t)bi.nf_pad;
         // slot nslot is the dummy target of schedule padding
         if (nslot + 1 > 65535)
@@ -506,6 +641,9 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         }
         out.grp.push_back((int32_t)rounds);
         bi.nrounds = (int32_t)(rounds - bi.r0);
+        bi.s0 = (int32_t)swords;
+        swords += chunk_words(bi);
+        if (swords > INT32_MAX) return "schedule too large for 32-bit offsets";
         // element / face positions
         for (int32_t i = 0; i < bi.ne; i++) elem_order.push_back(pe[i]);
         for (int32_t i = 0; i < bi.nf; i++) face_order.push_back(pf[i]);
@@ -522,7 +660,8 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         out.blocks[(size_t)p] = bi;
     }
     if (ipos != n_int || cpos != out.n_copies) return "node classification bookkeeping failed";
-    out.E_pad = round_up(std::max<int64_t>(epos, 1), 8);
+    out.n_sched_words = swords;
+    out.E_pad = nparts * nes;
     out.F_pad = round_up(std::max<int64_t>(fpos, 1), 8);
     elem_order.resize((size_t)out.E_pad, -1);
     face_order.resize((size_t)out.F_pad, -1);
@@ -541,6 +680,7 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         if (f >= 0)
             for (int c = 0; c < 3; c++) out.face_nodes[3 * i + c] = out.node_new[faces[3 * (size_t)f + c]];
     }
+    bank_schedule(out, real_size);
     return "";
 }
 

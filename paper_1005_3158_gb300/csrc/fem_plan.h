@@ -48,7 +48,7 @@ int greedy_color(int64_t N, int64_t E, const int32_t *tets, const int32_t *order
 // Block-variant plan.
 struct BlockPlan {
     int64_t N = 0, E = 0, F = 0;
-    int64_t n_int = 0, n_sh = 0, n_copies = 0, n_rounds = 0;
+    int64_t n_int = 0, n_sh = 0, n_copies = 0, n_rounds = 0, n_sched_words = 0;
     int64_t E_pad = 0, F_pad = 0;
     int32_t max_ne = 0;
     size_t max_slots = 0, max_nloc = 0;
@@ -74,7 +74,11 @@ struct BlockPlan {
 std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int32_t *tets,
                              const std::vector<int32_t> &rank, int64_t F,
                              const int32_t *faces, const std::vector<int32_t> &face_owner,
-                             int block_elems, BlockPlan &out);
+                             int block_elems, int real_size, BlockPlan &out);
+
+// Bank-aware order of the slots inside every 32-lane group of the schedule
+// (called by build_block_plan; real_size 4 or 8 selects the bank model).
+void bank_schedule(BlockPlan &bp, int real_size);
 
 // Flat (atomic / coloured) plan: nodes in rank order, elements sorted by
 // (colour, smallest internal node).

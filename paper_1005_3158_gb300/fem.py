@@ -50,7 +50,8 @@ class FemInfo(ctypes.Structure):
         "n_nodes", "n_tets", "n_faces", "n_blocks", "n_interior_nodes", "n_shared_nodes",
         "n_shared_copies", "n_sched_rounds", "n_colors", "bandwidth_input",
         "bandwidth_internal", "max_block_elems", "device_bytes")] + [
-        (n, ctypes.c_int32) for n in ("precision", "variant", "threads", "reorder")]
+        (n, ctypes.c_int32) for n in ("precision", "variant", "threads", "reorder",
+                                      "ctas_per_sm", "smem_per_cta")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

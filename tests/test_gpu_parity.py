@@ -78,7 +78,7 @@ def test_random_small_fp64(fem, variant, seed):
 
 
 @pytest.mark.parametrize("block_elems", [64, 100, 333, 12288])
-@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("threads", [0, 128, 256, 512, 1024])
 def test_block_sizes_and_threads(fem, block_elems, threads):
     p = mg.random_small(11, nx=9, ny=7, nz=6, n_mat=2)
     o = oracle.OracleProblem(p)

@@ -109,10 +109,12 @@ def _check_plan(p, m):
     touched_by = [set() for _ in range(p.n_nodes)]
     for b, (e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad, nep, r0, nrounds, _) in enumerate(blocks):
         assert e0 % 8 == 0 and f0 % 8 == 0 and ne_pad >= ne and nf_pad >= nf
-        assert nep % 8 == 0 and ne <= nep <= ne + 7
+        assert nep % 8 == 0 and ne <= nep and e0 == b * nep   # uniform element stride
         assert grp[g0] == r0 and grp[g0 + ngrp] == r0 + nrounds
         if b + 1 < len(blocks):
-            assert blocks[b + 1][0] >= e0 + nep and blocks[b + 1][13] == r0 + nrounds
+            assert blocks[b + 1][0] == e0 + nep and blocks[b + 1][13] == r0 + nrounds
+            # schedule chunks: header (ngrp+1 offsets padded to 4 words) + 16 words per round
+            assert blocks[b + 1][15] == blocks[b][15] + ((ngrp + 4) // 4) * 4 + 16 * nrounds
         nslot = 4 * ne_pad + 3 * nf_pad
         assert nslot <= 65535
         nloc = nint + nsh
