@@ -413,6 +413,9 @@ fem_status upload_block(fem_mesh *m)
         max_nep = std::max(max_nep, b.nep);
     }
     m->chunk_words = (int32_t)cw;
+    // the slot area also receives the (C, Lc) pairs of the ls local nodes
+    // before pass 1
+    slots = std::max(slots, 2 * (size_t)m->ls);
     slots = (slots + 3) & ~size_t(3);
     m->max_slots = (int32_t)slots;
     const int vn = sizeof(real) == 4 ? 4 : 2;

@@ -46,9 +46,9 @@ FEM_HD inline int64_t chunk_words(const BlockInfo &b)
 static_assert(sizeof(BlockInfo) == 64, "BlockInfo layout");
 
 // Dynamic shared memory of a block-kernel CTA (16-byte aligned parts):
-// [2 mbarriers][conductances][schedule chunk][slots + dummy][local nodes: E,
+// [3 mbarriers][conductances][schedule chunk][slots + dummy][local nodes: E,
 // partial position, phase byte], sized for the largest block.
-constexpr size_t kSmemBarBytes = 16;
+constexpr size_t kSmemBarBytes = 32;
 FEM_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 FEM_HD inline size_t block_slots(const BlockInfo &b)
 {

@@ -163,10 +163,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 // A bulk copy did not complete in time: flag it and give the copies a
 // bounded second chance to land before the CTA releases its shared memory
 // (every thread of the CTA calls this, then returns).
-__device__ __forceinline__ void give_up(int *err, uint32_t bar_s, uint32_t bar_w)
+__device__ __forceinline__ void give_up(int *err, uint32_t bar_s, uint32_t bar_w, uint32_t bar_n)
 {
     if (threadIdx.x == 0) {
         atomicExch(err, kErrWaitTimeout);
+        mbar_wait(bar_n, 0);
         mbar_wait(bar_s, 0);
         mbar_wait(bar_w, 0);
     }
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     const int b = blockIdx.x;
     const int ls = a.ls, nes = a.nes;
 
-    // shared memory: [2 barriers][conductances 6 x nes][schedule chunk]
+    // shared memory: [3 barriers][conductances 6 x nes][schedule chunk]
     // [slots + dummy][per local node: E, partial position, phase byte]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     real *sw = reinterpret_cast<real *>(smem_raw + kSmemBarBytes);
@@ -248,40 +249,33 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     real *sE = sv + a.max_slots;                                  // [ls]
     int32_t *sPos = reinterpret_cast<int32_t *>(sE + ls);         // [ls]
     uint8_t *sPh = reinterpret_cast<uint8_t *>(sPos + ls);        // [ls]
-    const uint32_t bar_s = smem_addr(bar), bar_w = smem_addr(bar + 1);
-
-    // local nodes: enthalpy -> temperature (Eqs. 5, 11); padding entries
-    // hold C = 1, Lc = 0 and give a harmless T
-    real Tl[MAXJ];
+    const uint32_t bar_s = smem_addr(bar), bar_w = smem_addr(bar + 1), bar_n = smem_addr(bar + 2);
     const size_t lb = (size_t)b * ls;
-#pragma unroll
-    for (int j = 0; j < MAXJ; j++) {
-        const int l = threadIdx.x + j * NT;
-        Tl[j] = real(0);
-        if (l < ls) {
-            const real E = a.Eloc[lb + l];
-            const V2 cl = __ldg(reinterpret_cast<const V2 *>(a.CLloc) + lb + l);
-            const uint8_t ph = __ldg(a.phloc + lb + l);
-            Tl[j] = temperature_of(E, cl.x, cl.y, ph, a.ranges);
-            sE[l] = E;
-            sPh[l] = ph;
-            sPos[l] = __ldg(a.posloc + lb + l);
-        }
-    }
 
+    // bulk copies: the local node data first (fixed stride, needed first;
+    // (C, Lc) goes to the slot area, free until pass 1), then the schedule
+    // chunk and the six conductance rows named by the block header
+    if (threadIdx.x == 0) {
+        mbar_init(bar_s, 1);
+        mbar_init(bar_w, 1);
+        mbar_init(bar_n, 1);
+        mbar_fence_init();
+        const uint32_t eb = (uint32_t)(ls * sizeof(real));
+        mbar_arrive_expect_tx(bar_n, 3u * eb + 5u * (uint32_t)ls);   // E, (C, Lc), phase, position
+        bulk_load(smem_addr(sE), a.Eloc + lb, eb, bar_n);
+        bulk_load(smem_addr(sv), a.CLloc + 2 * lb, 2 * eb, bar_n);
+        bulk_load(smem_addr(sPh), a.phloc + lb, (uint32_t)ls, bar_n);
+        bulk_load(smem_addr(sPos), a.posloc + lb, (uint32_t)ls * 4u, bar_n);
+    }
     const BlockInfo &bi = a.blocks[b];
     const int nloc = bi.nint + bi.nsh;
     const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad;
     const int dummy = 4 * ne_pad + 3 * nf_pad;
     const int hdr = (bi.ngrp + 4) & ~3;   // header words: ngrp+1 group offsets, padded to 16 B
     if (threadIdx.x == 0) {
-        mbar_init(bar_s, 1);
-        mbar_init(bar_w, 1);
-        mbar_fence_init();
         const uint32_t bytes = (uint32_t)(hdr + 16 * bi.nrounds) * 4u;
         mbar_arrive_expect_tx(bar_s, bytes);
         bulk_load(smem_addr(chunk), a.sched + (size_t)bi.s0, bytes, bar_s);
-        // the block's six conductance rows (Eq. 18: only K^e is stored)
         const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
         mbar_arrive_expect_tx(bar_w, wbytes);
         bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
@@ -293,13 +287,33 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         fg0 = __ldg(a.fg + bi.f0 + threadIdx.x);
     }
 
-    // the mbarrier was initialised by thread 0 before any other thread polls
-    // it: the barrier below orders the two
+    // the mbarriers were initialised by thread 0 before any other thread
+    // polls them: the barrier below orders the two
     __syncthreads();
     int failed = 0;
+    if (threadIdx.x == 0) failed = !mbar_wait(bar_n, 0);
+    if (__syncthreads_or(failed)) {
+        give_up(a.err, bar_s, bar_w, bar_n);
+        return;
+    }
+    mbar_try_wait(bar_n, 0);
+    // local nodes: enthalpy -> temperature (Eqs. 5, 11); padding entries
+    // hold C = 1, Lc = 0 and give a harmless T
+    real Tl[MAXJ];
+#pragma unroll
+    for (int j = 0; j < MAXJ; j++) {
+        const int l = threadIdx.x + j * NT;
+        Tl[j] = real(0);
+        if (l < ls) {
+            const V2 cl = reinterpret_cast<const V2 *>(sv)[l];
+            Tl[j] = temperature_of(sE[l], cl.x, cl.y, sPh[l], a.ranges);
+        }
+    }
+    // the vote below is also the barrier that ends the reads of (C, Lc)
+    // from the slot area before pass 1 overwrites it
     if (threadIdx.x == 0) failed = !mbar_wait(bar_s, 0);
     if (__syncthreads_or(failed)) {
-        give_up(a.err, bar_s, bar_w);
+        give_up(a.err, bar_s, bar_w, bar_n);
         return;
     }
     mbar_try_wait(bar_s, 0);
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
 
     if (threadIdx.x == 0) failed = !mbar_wait(bar_w, 0);
     if (__syncthreads_or(failed)) {
-        give_up(a.err, bar_s, bar_w);
+        give_up(a.err, bar_s, bar_w, bar_n);
         return;
     }
     mbar_try_wait(bar_w, 0);
@@ -390,23 +404,16 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
             a.P[sPos[l]] = R;
         }
     }
-    // warm L2 with the data of the block that starts about one wave of
-    // resident CTAs later, so DRAM keeps working while CTAs compute (off the
-    // critical path: issued once this block's work is done)
+    // warm L2 with the fixed-stride data of the block that starts about one
+    // wave of resident CTAs later, so DRAM keeps working while CTAs compute
+    // (issued once this block's work is done, no dependent load)
     if (threadIdx.x == 32 && b + a.prefetch_dist < a.n_blocks) {
-        const int pbi = b + a.prefetch_dist;
-        const size_t pl = (size_t)pbi * ls;
-        l2_prefetch(a.w + 6 * (size_t)pbi * nes, 6 * (size_t)nes * sizeof(real));
+        const size_t pbi = (size_t)b + a.prefetch_dist, pl = pbi * ls;
+        l2_prefetch(a.w + 6 * pbi * nes, 6 * (size_t)nes * sizeof(real));
         l2_prefetch(a.Eloc + pl, (size_t)ls * sizeof(real));
         l2_prefetch(a.CLloc + 2 * pl, (size_t)ls * 2 * sizeof(real));
         l2_prefetch(a.phloc + pl, (size_t)ls);
         l2_prefetch(a.posloc + pl, (size_t)ls * 4);
-        const BlockInfo &pb = a.blocks[pbi];
-        l2_prefetch(a.sched + (size_t)pb.s0, (size_t)chunk_words(pb) * 4);
-        if (pb.nf > 0) {
-            l2_prefetch(a.fa + pb.f0, (size_t)pb.nf * sizeof(real));
-            l2_prefetch(a.fg + pb.f0, (size_t)pb.nf * sizeof(real));
-        }
     }
     // cumulative boundary heat of the blocks that own Robin faces (FP64)
     if (bi.nf > 0 && threadIdx.x == 0) {
