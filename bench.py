@@ -29,12 +29,61 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per unit of work of a kernel, from one ncu capture (see the
+# matching summary under profiles/); valid while the sources it was taken on
+# are unchanged
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+TRAFFIC_SOURCES = ("fem_kernels.cu", "fem_internal.h", "fem_plan.cpp", "fem_plan.h", "fem_api.cpp")
+
+
+def sources_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1005_3158_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, precision: str, variant: str, n_units: int):
+    """ncu DRAM bytes (read + write) per launch of `kernel`, scaled from the
+    captured workload to n_units by the units processed; None when no
+    capture matches or the sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            entries = json.load(fh)["entries"]
+    except (OSError, ValueError, KeyError):
+        return None
+    digest = sources_digest()
+    for e in entries:
+        if (e["kernel"], e["precision"], e["variant"]) == (kernel, precision, variant) \
+                and e["sources_sha256"] == digest:
+            per_unit = (e["dram_read_bytes"] + e["dram_write_bytes"]) / e["units"]
+            return int(round(per_unit * n_units))
+    return None
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """Max of x over the ranks of the default process group (x for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job units per second: every rank processes units_per_rank per
+    step (weak scaling), the job takes the slowest rank's time."""
+    return units_per_rank * steps * world / seconds
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="block_with_cores_220")
@@ -44,7 +93,7 @@ def parse():
     ap.add_argument("--block-elems", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=20)
-    ap.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
+    ap.add_argument("--e2e-steps", type=int, default=200, help="0 = same as --steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -59,6 +108,12 @@ def make_problem(name: str):
         return mg.unit_cube(int(name.rsplit("_", 1)[1]))
     if name == "flanged_casting":
         return mg.flanged_casting()
+    if name == "flanged_casting_random":
+        # the unordered mesh of the ordering comparison: nodes and elements
+        # randomly renumbered (seed 1006)
+        import numpy as np
+        rng = np.random.Generator(np.random.PCG64(1006))
+        return mg.permute_elements(mg.permute_nodes(mg.flanged_casting(), rng), rng)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -66,7 +121,7 @@ def make_problem_size(name: str) -> int:
     """Number of tets of a named workload (without building it)."""
     if name.startswith("block_with_cores_") or name.startswith("unit_cube_"):
         return 6 * int(name.rsplit("_", 1)[1]) ** 3
-    if name == "flanged_casting":
+    if name.startswith("flanged_casting"):
         return 6 * 70 * 70 * 68
     raise SystemExit(f"unknown workload {name}")
 
@@ -254,11 +309,8 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = E * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = job_throughput(E, args.steps, world, ms / 1e3)
     kernels_per_step = 2 if info["n_shared_nodes"] > 0 or args.variant != "block" else 1
     if args.variant != "block":
         kernels_per_step = 3
@@ -283,7 +335,9 @@ def main():
     achieved = alg[k_dom] / (kms[k_dom] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": names[k_dom], "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "peak_source": peak_kind,
+                "traffic": measured_traffic(names[k_dom], args.precision, args.variant,
+                                            E if names[k_dom] != "k_shared_update" else N),
+                "peak_source": peak_kind,
                 "alg_bytes_per_launch": int(alg[k_dom]),
                 "kernel_ms": {n: round(float(v), 4) for n, v in zip(names, kms)},
                 "step_alg_bytes_per_tet": round((E * (16 + 6 * s) + N * 4 * s) / E, 2)}
@@ -306,12 +360,8 @@ def main():
             mesh.set_state(E_host, 0, 0.0)
             mesh.step(1, dt)
             mesh.temperature(T_host)
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": E * ke * world / el, "unit": "tet-updates/s",
+        el = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": job_throughput(E, ke, world, el), "unit": "tet-updates/s",
                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "steps": ke}
 
     cpu = None

@@ -191,7 +191,9 @@ fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_
                             int32_t capacity, int32_t *n_used);
 
 /* Nodal temperatures T(E) [n_nodes] in the caller's order.  Synchronises.
- * FEM_EUNSTABLE if any value is non-finite (the output is still written). */
+ * FEM_EUNSTABLE if any value is non-finite (checked on the device; the
+ * output is still written); FEM_EINVAL / FEM_ETIMEOUT for an error an
+ * earlier asynchronous call left on the device. */
 fem_status fem_get_temperature(fem_mesh *m, double *T_out);
 
 /* Specific nodal enthalpy E_i / m_i (J/kg) [n_nodes], caller's order. */
@@ -213,10 +215,13 @@ fem_status fem_set_stream(fem_mesh *m, void *cuda_stream);
 fem_status fem_get_state(fem_mesh *m, double *E_out, int64_t *step, double *t);
 
 /* Restore a checkpoint written by fem_get_state (E [n_nodes], J).
- * Asynchronous: E is staged through a device buffer on the mesh's stream;
- * the call returns after the host-to-device copy has been enqueued, so the
- * caller must keep E unchanged until the stream reaches it (any fem_get_*
- * call guarantees that).  Errors: FEM_EINVAL for non-finite E. */
+ * Asynchronous once the mesh is on the device: E is staged through a device
+ * buffer on the mesh's stream; the call returns after the host-to-device
+ * copy has been enqueued, so the caller must keep E unchanged until the
+ * stream reaches it (any fem_get_* call guarantees that).  The energy
+ * account (U0, boundary heat) is not changed.  Errors: FEM_EINVAL for
+ * non-finite E -- detected on the device and returned by the next fem_get_*
+ * call (before the mesh is on the device: by this call). */
 fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t);
 
 /* Plan statistics (host computation; builds the plan if needed). */

@@ -43,7 +43,8 @@ fem_status ok()
 
 // ---------------------------------------------------------------------------
 // Device allocations (with an allocation-failure injection hook for tests:
-// FEM_FAULT_ALLOC_AFTER=k makes every device allocation after the k-th fail)
+// FEM_FAULT_ALLOC_AFTER=k makes every device allocation after the k-th of
+// one mesh upload fail; the count restarts with each upload)
 // ---------------------------------------------------------------------------
 long g_alloc_count = 0;
 
@@ -291,6 +292,7 @@ fem_status upload_nodes(fem_mesh *m)
     if ((st = upload<int32_t>(m, &m->dNodeOld, old.data(), old.size()))) return st;
     if ((st = upload<double>(m, &m->dIo, nullptr, (size_t)m->N))) return st;
     if ((st = upload<double>(m, &m->dOut, nullptr, 4))) return st;
+    if ((st = upload<int>(m, &m->dErr, nullptr, 1))) return st;
     if (!m->is_dir.empty()) {
         std::vector<double> dT((size_t)m->N, 0.0);
         for (int64_t i = 0; i < m->N; i++)
@@ -402,7 +404,6 @@ fem_status upload_block(fem_mesh *m)
     if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * bp.blocks.size()))) return st;
     if ((st = upload<double>(m, &m->dQcum, nullptr, bp.blocks.size()))) return st;
     m->n_sh_ctas = (int)std::max<int64_t>(1, (bp.n_sh + 255) / 256);
-    if ((st = upload<int>(m, &m->dErr, nullptr, 1))) return st;
     // kernel configuration: shared memory for the largest block; by default
     // the fewest threads whose 16-byte element accesses cover every block
     size_t cw = 0, slots = 0;
@@ -521,6 +522,9 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.n_sh = m->bp.n_sh;
     a.qcum = m->dQcum;
     a.err = m->dErr;
+    // test hook: a bounded wait that runs out (see BlockArgs)
+    const char *skip = getenv("FEM_FAULT_SKIP_WEIGHT_COPY");
+    a.fault_skip_weights = (skip && *skip && *skip != '0') ? 1 : 0;
     return a;
 }
 
@@ -608,7 +612,7 @@ fem_status apply_pending(fem_mesh *m)
                                             m->dDirT, m->N, m->stream),
                "initial-state kernel");
     else
-        KERNEL(launch_set_state<real>(view_of<real>(m), m->dIo, m->dNodeOld, m->N, m->stream),
+        KERNEL(launch_set_state<real>(view_of<real>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream),
                "state kernel");
     KERNEL(refresh_mirror<real>(m), "mirror kernel");
     CU(cudaMemsetAsync(m->dQcum, 0, (size_t)n_qcum(m) * sizeof(double), m->stream));
@@ -638,6 +642,7 @@ fem_status ensure_device(fem_mesh *m)
     if (ce != cudaSuccess || ndev == 0)
         return fail(FEM_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(ce));
     CU(cudaGetDevice(&m->device));
+    g_alloc_count = 0;
     if (is_block(m))
         st = m->prec == FEM_FP32 ? upload_block<float>(m) : upload_block<double>(m);
     else
@@ -762,18 +767,22 @@ fem_status step_profile_impl(fem_mesh *m, int64_t n, double dt, double *ms)
     return st;
 }
 
-// Device error flag of the block kernel (a bounded wait that gave up).
+// Device error flag (kErr* bits): a bounded wait that gave up, a non-finite
+// value given to fem_set_state, a non-finite temperature read back.  The
+// stream is synchronised; the flag is cleared once reported.
 fem_status check_device_flag(fem_mesh *m)
 {
     if (!m->dErr) return FEM_OK;
     int flag = 0;
     CU(cudaMemcpyAsync(&flag, m->dErr, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
-    if (flag) {
-        CU(cudaMemsetAsync(m->dErr, 0, sizeof(int), m->stream));
-        return fail(FEM_ETIMEOUT, "a bounded device wait gave up (flag %d); the state is not valid", flag);
-    }
-    return FEM_OK;
+    if (!flag) return FEM_OK;
+    CU(cudaMemsetAsync(m->dErr, 0, sizeof(int), m->stream));
+    if (flag & kErrWaitTimeout)
+        return fail(FEM_ETIMEOUT, "a bounded device wait gave up; the state is not valid");
+    if (flag & kErrBadInput)
+        return fail(FEM_EINVAL, "fem_set_state received a non-finite enthalpy");
+    return fail(FEM_EUNSTABLE, "non-finite temperature: dt above the stable limit?");
 }
 
 fem_status ready_for_io(fem_mesh *m)
@@ -1051,18 +1060,20 @@ fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
 {
     if (!m || !E) return fail(FEM_EINVAL, "NULL argument");
     if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
-    if (!finite_all(E, m->N)) return fail(FEM_EINVAL, "non-finite enthalpy");
     if (m->dev_ok && m->state == fem_mesh::ST_DEVICE) {
+        // non-finite values are detected on the device and reported by the
+        // next fem_get_* call
         // stage through the device buffer on the mesh's stream, no synchronisation
         cudaSetDevice(m->device);
         CU(cudaMemcpyAsync(m->dIo, E, (size_t)m->N * sizeof(double), cudaMemcpyHostToDevice, m->stream));
         KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->stream)
-                   : launch_set_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->stream),
+                   ? launch_set_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream)
+                   : launch_set_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream),
                "state kernel");
         KERNEL(m->prec == FEM_FP32 ? refresh_mirror<float>(m) : refresh_mirror<double>(m),
                "mirror kernel");
     } else {
+        if (!finite_all(E, m->N)) return fail(FEM_EINVAL, "non-finite enthalpy");
         m->pending.assign(E, E + m->N);
         m->state = fem_mesh::ST_PENDING_E;
         if (m->dev_ok) {
@@ -1135,21 +1146,20 @@ fem_status fem_get_temperature(fem_mesh *m, double *T_out)
     if (!m || !T_out) return fail(FEM_EINVAL, "NULL argument");
     fem_status st = ready_for_io(m);
     if (st) return st;
-    if ((st = check_device_flag(m))) return st;
+    // one synchronisation: the flag read after the copy also reports what
+    // earlier asynchronous calls left on the device
     KERNEL(m->prec == FEM_FP32
                ? launch_get_temperature<float>(view_of<float>(m), (const float *)m->dC,
                                                (const float *)m->dLc, m->dPh,
                                                (const float *)m->dRanges, m->dIo, m->dNodeOld, m->N,
-                                               m->stream)
+                                               m->dErr, m->stream)
                : launch_get_temperature<double>(view_of<double>(m), (const double *)m->dC,
                                                 (const double *)m->dLc, m->dPh,
                                                 (const double *)m->dRanges, m->dIo, m->dNodeOld,
-                                                m->N, m->stream),
+                                                m->N, m->dErr, m->stream),
            "read-back kernel");
     CU(cudaMemcpyAsync(T_out, m->dIo, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-    CU(cudaStreamSynchronize(m->stream));
-    if (!finite_all(T_out, m->N))
-        return fail(FEM_EUNSTABLE, "non-finite temperature: dt above the stable limit?");
+    if ((st = check_device_flag(m))) return st;   // synchronises
     return ok();
 }
 

@@ -65,13 +65,18 @@ FEM_HD inline size_t block_kernel_smem(size_t nes, size_t chunk_words, size_t sl
 // 16-byte-widened bulk L2 prefetches of its ranges stay inside it.
 constexpr size_t kAllocTailPad = 256;
 
-// Bounded waits: an mbarrier wait gives up after this many polls, sets the
-// error flag and the step returns FEM_ETIMEOUT at the next read-back.
-constexpr uint32_t kWaitPolls = 1u << 22;
+// Bounded waits: an mbarrier wait gives up after kWaitNs nanoseconds of
+// device time (or kWaitPolls polls, whichever comes first), sets the error
+// flag and the step returns FEM_ETIMEOUT at the next read-back.
+constexpr uint32_t kWaitPolls = 1u << 24;
+constexpr unsigned long long kWaitNs = 500000000ull;
 // Local nodes of one block are held in registers, kMaxLocalNodes / threads
 // per thread; the planner keeps every block at or below this.
 constexpr int kMaxLocalNodes = 1024;
-constexpr int kErrWaitTimeout = 1;
+// Bits of the device error flag (read and cleared by the fem_get_* calls).
+constexpr int kErrWaitTimeout = 1;   // a bounded wait gave up
+constexpr int kErrBadInput = 2;      // fem_set_state received a non-finite value
+constexpr int kErrNonFinite = 4;     // a read-back temperature was non-finite
 
 constexpr uint8_t kDirichletBit = 0x80;  // in the per-node phase byte
 constexpr int kMaxRanges = 127;          // distinct (Ts, Tl) pairs
@@ -132,6 +137,9 @@ struct BlockArgs {
     // FP64 energy bookkeeping
     double *qcum;             // [n_blocks] cumulative heat through the Robin faces
     int *err;                 // device error flag (kErrWaitTimeout)
+    // test hook (FEM_FAULT_SKIP_WEIGHT_COPY): announce the conductance copy
+    // but never issue it, so that the wait for it runs out
+    int32_t fault_skip_weights;
 };
 
 // Arguments of the atomic / coloured variants (device pointers).
@@ -187,13 +195,15 @@ template <typename real>
 int launch_set_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, const double *T_in, const int32_t *node_old,
                            const double *dirT_int, int64_t n, void *stream);
+// launch_set_state / launch_get_temperature set kErrBadInput / kErrNonFinite
+// in *err for non-finite values (err may be null).
 template <typename real>
 int launch_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
-                     void *stream);
+                     int *err, void *stream);
 template <typename real>
 int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
-                           void *stream);
+                           int *err, void *stream);
 template <typename real>
 int launch_get_state(StateView<real> v, double *E_out, const int32_t *node_old, int64_t n,
                      void *stream);

@@ -152,11 +152,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return done != 0;
 }
-// Waits for phase `parity` of the barrier; gives up after kWaitPolls polls.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for phase `parity` of the barrier; gives up after kWaitNs of device
+// time or kWaitPolls polls.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < kWaitPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t i = 1; i < kWaitPolls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         bulk_load(smem_addr(chunk), a.sched + (size_t)bi.s0, bytes, bar_s);
         const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
         mbar_arrive_expect_tx(bar_w, wbytes);
-        bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
+        if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
     }
     // this thread's first face
     real fa0 = real(0), fg0 = real(0);
@@ -530,21 +541,32 @@ __global__ void k_set_temperature(StateView<real> v, const real *C, const real *
 }
 
 template <typename real>
-__global__ void k_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n)
+__global__ void k_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
+                            int *err)
 {
+    bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        v.E(i) = (real)E_in[node_old[i]];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double E = E_in[node_old[i]];
+        bad |= !isfinite(E);
+        v.E(i) = (real)E;
+    }
+    if (bad && err) atomicOr(err, kErrBadInput);
 }
 
 template <typename real>
 __global__ void k_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                                   const real *ranges, double *T_out, const int32_t *node_old,
-                                  int64_t n)
+                                  int64_t n, int *err)
 {
+    bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        T_out[node_old[i]] = (double)temperature_of(v.E(i), C[i], Lc[i], ph[i], ranges);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double T = (double)temperature_of(v.E(i), C[i], Lc[i], ph[i], ranges);
+        bad |= !isfinite(T);
+        T_out[node_old[i]] = T;
+    }
+    if (bad && err) atomicOr(err, kErrNonFinite);
 }
 
 template <typename real>
@@ -718,19 +740,19 @@ int launch_set_temperature(StateView<real> v, const real *C, const real *Lc, con
 
 template <typename real>
 int launch_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
-                     void *stream)
+                     int *err, void *stream)
 {
-    k_set_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n);
+    k_set_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n, err);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
 int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
-                           void *stream)
+                           int *err, void *stream)
 {
     k_get_temperature<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
-        v, C, Lc, ph, ranges, T_out, node_old, n);
+        v, C, Lc, ph, ranges, T_out, node_old, n, err);
     return (int)cudaGetLastError();
 }
 
@@ -772,10 +794,10 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
                                               const uint8_t *, const real *, const double *,      \
                                               const int32_t *, const double *, int64_t, void *);  \
     template int launch_set_state<real>(StateView<real>, const double *, const int32_t *, int64_t, \
-                                        void *);                                                  \
+                                        int *, void *);                                           \
     template int launch_get_temperature<real>(StateView<real>, const real *, const real *,        \
                                               const uint8_t *, const real *, double *,            \
-                                              const int32_t *, int64_t, void *);                  \
+                                              const int32_t *, int64_t, int *, void *);           \
     template int launch_get_state<real>(StateView<real>, double *, const int32_t *, int64_t,      \
                                         void *);                                                  \
     template int launch_energy_snapshot<real>(StateView<real>, const real *, const real *,        \

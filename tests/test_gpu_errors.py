@@ -1,0 +1,142 @@
+"""GPU error paths of the C ABI, all raised without faulting the GPU.
+
+* A non-finite enthalpy given to fem_set_state is detected on the device and
+  reported (FEM_EINVAL) by the next synchronising call; the flag is then
+  cleared and a valid state steps normally again.
+* A step far above the stable limit blows the state up; fem_get_temperature
+  reports FEM_EUNSTABLE (the output is still written).
+* Device allocation failure, injected on the host (FEM_FAULT_ALLOC_AFTER=k
+  fails every device allocation after the k-th of a mesh upload), returns
+  FEM_ENOMEM from the first call that needs the device, releases the partial
+  upload, and leaves the library usable.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1005_3158_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fem():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_3158_gb300 import fem as f
+    return f
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("variant", ["block", "atomic"])
+def test_non_finite_state_reported_by_next_get(fem, prec, variant):
+    p = mg.unit_cube(6)
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    with fem.Mesh(p, prec, reorder=1, variant=variant, block_elems=128) as m:
+        m.step(3, dt)
+        E, step, t = m.state()
+        bad = E.copy()
+        bad[len(bad) // 2] = np.nan
+        m.set_state(bad, step, t)          # asynchronous: no error yet
+        with pytest.raises(fem.FemError) as ei:
+            m.temperature()
+        assert ei.value.status == fem.FEM_EINVAL
+        # the flag was cleared; a valid state steps on normally
+        m.set_state(E, step, t)
+        m.step(5, dt)
+        o.set_temperature(p.T0)
+        o.step(8, dt)
+        tol = 1e-9 if prec == "fp64" else 0.05
+        assert np.abs(m.temperature() - o.temperature()).max() <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_unstable_step_reported(fem, prec):
+    p = mg.unit_cube(6)
+    o = oracle.OracleProblem(p)
+    dt = 50.0 * o.stable_dt()
+    with fem.Mesh(p, prec, reorder=1, block_elems=128) as m:
+        m.step(400, dt)
+        with pytest.raises(fem.FemError) as ei:
+            m.temperature()
+        assert ei.value.status == fem.FEM_EUNSTABLE
+        # reported once; the next read reports it again because the state
+        # is still non-finite
+        with pytest.raises(fem.FemError):
+            m.temperature()
+
+
+_CHILD = r"""
+import os, sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+from paper_1005_3158_gb300 import fem, meshgen as mg
+p = mg.unit_cube(8)
+
+def run():
+    with fem.Mesh(p, {prec!r}, reorder=1, variant={variant!r}, block_elems=128) as m:
+        try:
+            m.step(1, 1e-3)
+            return 0, m.temperature()
+        except fem.FemError as e:
+            return e.status, None
+
+status0, T0 = run()                   # loads the kernels; no injection yet
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+os.environ["FEM_FAULT_ALLOC_AFTER"] = "{k}"
+status, _ = run()
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+del os.environ["FEM_FAULT_ALLOC_AFTER"]
+status2, T2 = run()
+print("RESULT", status0, status, free0 - free1, status2, int(np.array_equal(T0, T2)))
+"""
+
+
+@pytest.mark.parametrize("variant", ["block", "atomic"])
+@pytest.mark.parametrize("k", [0, 1, 3, 7, 12])
+def test_injected_allocation_failure(fem, variant, k):
+    code = _CHILD.format(root=ROOT, prec="fp32", variant=variant, k=k)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("RESULT")][-1]
+    status0, status, leaked, status2, same = map(int, line.split()[1:])
+    assert status0 == 0 and status2 == 0 and same == 1
+    # every upload makes more than 12 device allocations
+    assert status == fem.FEM_ENOMEM
+    # everything the failed upload allocated was released
+    assert leaked <= 0
+
+
+def test_bounded_wait_gives_up(fem, monkeypatch):
+    """The block kernel's waits on its bulk copies are bounded: with the
+    conductance copy announced but never issued (test hook), every CTA gives
+    up after its time limit, sets the device flag and exits; the next read
+    reports FEM_ETIMEOUT and the CUDA context stays usable."""
+    p = mg.unit_cube(6)
+    o = oracle.OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    monkeypatch.setenv("FEM_FAULT_SKIP_WEIGHT_COPY", "1")
+    with fem.Mesh(p, "fp32", reorder=1, block_elems=128) as m:
+        m.step(1, dt)
+        with pytest.raises(fem.FemError) as ei:
+            m.temperature()
+        assert ei.value.status == fem.FEM_ETIMEOUT
+    monkeypatch.delenv("FEM_FAULT_SKIP_WEIGHT_COPY")
+    with fem.Mesh(p, "fp32", reorder=1, block_elems=128) as m:
+        m.step(10, dt)
+        o.set_temperature(p.T0)
+        o.step(10, dt)
+        assert np.abs(m.temperature() - o.temperature()).max() <= 0.05
