@@ -106,7 +106,7 @@ struct fem_mesh {
     size_t dev_bytes = 0;
     size_t smem_bytes = 0;
     int threads = 256;
-    int32_t chunk_words = 0, max_slots = 0, prefetch_dist = 0, ctas_per_sm = 0;
+    int32_t chunk_words = 0, max_slots = 0, ctas_per_sm = 0;
     int n_sh_ctas = 0, n_node_ctas = 0;
     // device pointers
     void *dE = nullptr, *dC = nullptr, *dLc = nullptr, *dRanges = nullptr, *dW = nullptr,
@@ -436,11 +436,9 @@ fem_status upload_block(fem_mesh *m)
         return fail(FEM_EINVAL, "a block needs %zu bytes of shared memory (device limit %d); lower block_elems",
                     m->smem_bytes, optin);
     KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes), "configuring the block kernel");
-    int per_sm = 0, sms = 0;
+    int per_sm = 0;
     KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm), "occupancy query");
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (per_sm < 1) return fail(FEM_EINVAL, "the block kernel does not fit on an SM; lower block_elems");
-    m->prefetch_dist = sms * per_sm;
     m->ctas_per_sm = per_sm;
     return FEM_OK;
 }
@@ -512,7 +510,6 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.sched = m->dSched;
     a.chunk_words = m->chunk_words;
     a.max_slots = m->max_slots;
-    a.prefetch_dist = m->prefetch_dist;
     a.P = (real *)m->dP;
     a.sh_ptr = m->dShPtr;
     a.mpos = m->dMpos;

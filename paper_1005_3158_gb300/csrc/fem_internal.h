@@ -61,8 +61,8 @@ FEM_HD inline size_t block_kernel_smem(size_t nes, size_t chunk_words, size_t sl
            align16(slots * real_size) + align16(ls * (real_size + 4 + 1));
 }
 
-// Every device buffer is allocated with this many bytes after its end, so
-// 16-byte-widened bulk L2 prefetches of its ranges stay inside it.
+// Every device buffer is allocated with this many bytes after its end
+// (room for 16-byte-granular bulk accesses at the end of a range).
 constexpr size_t kAllocTailPad = 256;
 
 // Bounded waits: an mbarrier wait gives up after kWaitNs nanoseconds of
@@ -124,7 +124,6 @@ struct BlockArgs {
     const uint32_t *sched;
     int32_t chunk_words;       // largest schedule chunk (32-bit words)
     int32_t max_slots;         // largest slot count (+ dummy), a multiple of 4
-    int32_t prefetch_dist;     // CTA b warms L2 for block b + prefetch_dist
     // shared-node exchange: node s owns P[sh_ptr[s] .. sh_ptr[s+1]); entry k
     // of that range is the partial of one copy, whose mirror sits at
     // Eloc[mpos[k]]

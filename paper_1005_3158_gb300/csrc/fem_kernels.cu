@@ -129,17 +129,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
-// Bulk prefetch of [p, p+bytes) into L2, widened to 16-byte boundaries
-// (device buffers carry at least 256 bytes of padding after their end).
-__device__ __forceinline__ void l2_prefetch(const void *p, size_t bytes)
-{
-    if (bytes == 0) return;
-    const uintptr_t lo = (uintptr_t)p & ~(uintptr_t)15;
-    const uintptr_t hi = ((uintptr_t)p + bytes + 15) & ~(uintptr_t)15;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo))
-                 : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t done;
@@ -414,17 +403,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         } else if (l < nloc) {
             a.P[sPos[l]] = R;
         }
-    }
-    // warm L2 with the fixed-stride data of the block that starts about one
-    // wave of resident CTAs later, so DRAM keeps working while CTAs compute
-    // (issued once this block's work is done, no dependent load)
-    if (threadIdx.x == 32 && b + a.prefetch_dist < a.n_blocks) {
-        const size_t pbi = (size_t)b + a.prefetch_dist, pl = pbi * ls;
-        l2_prefetch(a.w + 6 * pbi * nes, 6 * (size_t)nes * sizeof(real));
-        l2_prefetch(a.Eloc + pl, (size_t)ls * sizeof(real));
-        l2_prefetch(a.CLloc + 2 * pl, (size_t)ls * 2 * sizeof(real));
-        l2_prefetch(a.phloc + pl, (size_t)ls);
-        l2_prefetch(a.posloc + pl, (size_t)ls * 4);
     }
     // cumulative boundary heat of the blocks that own Robin faces (FP64)
     if (bi.nf > 0 && threadIdx.x == 0) {
