@@ -111,6 +111,8 @@ typedef struct {
     int32_t ctas_per_sm;       /* block-kernel CTAs resident per SM (0 before the
                                   first call that needs the GPU) */
     int32_t smem_per_cta;      /* dynamic shared memory of one block-kernel CTA, bytes */
+    int32_t n_instances;       /* parts of a batch (fem_batch_create), else 0 */
+    int32_t reserved_info;
 } fem_info;
 
 /* Create a mesh (Section 3: unstructured four-node tetrahedra).
@@ -253,6 +255,10 @@ fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets,
  *  10 face_nodes int32 [F_pad][3]     corner nodes (internal ids) per position
  *  11 copy_pos   int32 [n_copies]     position of each copy's partial sum in
  *                                     the node-ordered partial array
+ *  12 block_inst int32 [n_blocks]     instance of each block (0 unless a batch)
+ *  13 inst_block_start int32 [n_inst+1] first block of each instance, in plan
+ *                                     order
+ *  14 inst_order int32 [n_inst]       plan position -> instance
  * *data points into the mesh (valid until the next fem_set_* or destroy);
  * *count is the number of scalar entries.  Builds the plan if needed. */
 fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t *count);
@@ -290,6 +296,55 @@ fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t
 fem_status fem_energy_sums_noalloc(fem_precision prec, const void *E, const void *C,
                                    const void *Lc, const uint8_t *phase, const void *ranges,
                                    int64_t n_nodes, double *out, void *cuda_stream);
+
+/* ---- Batches: many independent meshes advanced together ------------------
+ * The paper solves one casting at a time; a batch runs many castings of
+ * uneven size (each with its own stable time step) on one GPU at once.  A
+ * batch is an ordinary fem_mesh: every call above works on it (node, tet
+ * and face ids are the concatenation of the parts': part k's node i is
+ * batch node inst_node[k] + i, in part order), with these differences:
+ * fem_set_materials, fem_set_boundary and fem_set_dirichlet are refused
+ * (FEM_ESTATE: the parts supply them); fem_step advances every instance by
+ * the same n steps of dt; fem_advance steps each instance with its own dt.
+ * Element blocks never mix instances.
+ */
+
+/* Build a batch from parts (block variant, one precision; every part has
+ * materials, optional boundary / Dirichlet data and an initial temperature,
+ * and has not been stepped).  The parts' data are copied: the parts stay the
+ * caller's and may be destroyed afterwards.  Every instance's time step
+ * starts at 0.9 x its stable step (fem_instance_stable_dt).
+ * Errors: FEM_EINVAL (NULL, mixed precision or variant, a part that is a
+ * batch, too many distinct phase-change ranges, > 2^31 ids), FEM_ESTATE (a
+ * part without materials or initial temperature, or already stepped). */
+fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **out);
+
+/* Per-instance stable steps [n_parts] (the fem_stable_dt of each part). */
+fem_status fem_instance_stable_dt(fem_mesh *m, double *dt_out);
+
+/* Per-instance largest time steps [n_parts], s (positive, finite). */
+fem_status fem_set_instance_dt(fem_mesh *m, const double *dt);
+
+/* Advance every instance from its own current time to t_end: instance i
+ * takes n_i = ceil((t_end - t_i) / dt_i) equal steps of (t_end - t_i) / n_i
+ * (none if t_i >= t_end).  Each step launches the block and shared-node
+ * kernels for the instances still stepping; the whole advance is captured
+ * into one CUDA graph, reused while the per-instance step counts repeat.
+ * Asynchronous on the mesh's stream (when that is the legacy default
+ * stream, the graph runs on a library stream and the call waits for it).
+ * Errors: FEM_ESTATE (not a batch, no initial state), FEM_EINVAL (t_end not
+ * finite), FEM_ECUDA. */
+fem_status fem_advance(fem_mesh *m, double t_end);
+
+/* Per-instance times [n_parts] (s) and step counts [n_parts]; either
+ * pointer may be NULL. */
+fem_status fem_get_instance_times(fem_mesh *m, double *t_out, int64_t *steps_out);
+
+/* Energy account of one instance, as fem_get_energy: out[0] = U (sum of
+ * its nodes' E, J), out[1] = U0 (at its initial temperature), out[2] =
+ * heat that entered through its Robin faces, out[3] = latent heat it still
+ * holds; FP64.  Synchronises (reads the state back to the host). */
+fem_status fem_get_instance_energy(fem_mesh *m, int32_t inst, double out[4]);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fem_last_error(void);

@@ -107,7 +107,7 @@ struct fem_mesh {
     size_t smem_bytes = 0;
     int threads = 256;
     int32_t chunk_words = 0, max_slots = 0, ctas_per_sm = 0;
-    int n_sh_ctas = 0, n_node_ctas = 0;
+    int n_node_ctas = 0;
     // device pointers
     void *dE = nullptr, *dC = nullptr, *dLc = nullptr, *dRanges = nullptr, *dW = nullptr,
          *dFa = nullptr, *dFg = nullptr, *dP = nullptr, *dT = nullptr, *dR = nullptr,
@@ -131,6 +131,19 @@ struct fem_mesh {
     double time = 0.0;
     double U0 = 0.0;
     double q_carry = 0.0;             // boundary heat of device buffers already released
+    // ---- batch of independent instances (fem_batch_create); n_inst == 0
+    // for a plain mesh.  Ranges are in caller order, [n_inst + 1] each.
+    int32_t n_inst = 0;
+    std::vector<int64_t> inst_node, inst_elem, inst_face;
+    std::vector<int32_t> inst_plan_order;      // plan position -> caller instance
+    std::vector<double> inst_stable, inst_dt;  // stable and chosen time steps
+    std::vector<double> inst_t, inst_U0, inst_q; // time, initial energy, boundary heat
+    std::vector<int64_t> inst_steps;
+    void *dBlkDt = nullptr, *dShDt = nullptr;  // per block / per shared node dt (real)
+    std::vector<double> dt_uploaded;           // per-instance dt the two arrays hold
+    cudaStream_t own_stream = nullptr;         // graph launches when stream is NULL
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int64_t> graph_key;            // per-plan-position step counts of graph
 };
 
 namespace {
@@ -160,6 +173,13 @@ void release_device(fem_mesh *m)
     m->dSched = nullptr;
     m->dEpart = m->dQcum = m->dIo = m->dDirT = m->dOut = nullptr;
     m->dErr = nullptr;
+    m->dBlkDt = m->dShDt = nullptr;
+    m->dt_uploaded.clear();
+    if (m->graph) cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_key.clear();
+    if (m->own_stream) cudaStreamDestroy(m->own_stream);
+    m->own_stream = nullptr;
 }
 
 int default_block_elems(const fem_mesh *m)
@@ -192,7 +212,8 @@ fem_status ensure_plan(fem_mesh *m)
         if (is_block(m)) {
             err = build_block_plan(m->N, m->E, m->xyz.data(), m->tets.data(), m->rank, m->F,
                                    m->faces.data(), owner, default_block_elems(m),
-                                   m->prec == FEM_FP32 ? 4 : 8, m->bp);
+                                   m->prec == FEM_FP32 ? 4 : 8, m->bp, m->inst_elem,
+                                   m->inst_plan_order);
             if (err.empty()) {
                 m->blocks_flat.resize(m->bp.blocks.size() * 16);
                 std::memcpy(m->blocks_flat.data(), m->bp.blocks.data(),
@@ -403,7 +424,13 @@ fem_status upload_block(fem_mesh *m)
     }
     if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * bp.blocks.size()))) return st;
     if ((st = upload<double>(m, &m->dQcum, nullptr, bp.blocks.size()))) return st;
-    m->n_sh_ctas = (int)std::max<int64_t>(1, (bp.n_sh + 255) / 256);
+    if (m->n_inst > 0) {   // per-instance time steps of fem_advance
+        real *p2 = nullptr;
+        if ((st = upload<real>(m, &p2, nullptr, bp.blocks.size()))) return st;
+        m->dBlkDt = p2;
+        if ((st = upload<real>(m, &p2, nullptr, (size_t)std::max<int64_t>(bp.n_sh, 1)))) return st;
+        m->dShDt = p2;
+    }
     // kernel configuration: shared memory for the largest block; by default
     // the fewest threads whose 16-byte element accesses cover every block
     size_t cw = 0, slots = 0;
@@ -519,6 +546,12 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.n_sh = m->bp.n_sh;
     a.qcum = m->dQcum;
     a.err = m->dErr;
+    a.b_first = 0;
+    a.b_count = (int32_t)m->bp.blocks.size();
+    a.s_first = 0;
+    a.s_end = m->bp.n_sh;
+    a.blk_dt = nullptr;
+    a.sh_dt = nullptr;
     // test hook: a bounded wait that runs out (see BlockArgs)
     const char *skip = getenv("FEM_FAULT_SKIP_WEIGHT_COPY");
     a.fault_skip_weights = (skip && *skip && *skip != '0') ? 1 : 0;
@@ -595,6 +628,24 @@ int refresh_mirror(fem_mesh *m)
     return launch_mirror_copies<real>(block_args<real>(m), m->stream);
 }
 
+// Sum of E over every instance's nodes (FP64, ascending caller node order),
+// from the device state.  Synchronises.
+template <typename real>
+fem_status instance_sums(fem_mesh *m, std::vector<double> &U)
+{
+    std::vector<double> E((size_t)m->N);
+    KERNEL(launch_get_state<real>(view_of<real>(m), m->dIo, m->dNodeOld, m->N, m->stream),
+           "read-back kernel");
+    CU(cudaMemcpyAsync(E.data(), m->dIo, (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost,
+                       m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    U.assign((size_t)m->n_inst, 0.0);
+    for (int32_t i = 0; i < m->n_inst; i++)
+        for (int64_t n = m->inst_node[(size_t)i]; n < m->inst_node[(size_t)i + 1]; n++)
+            U[(size_t)i] += E[(size_t)n];
+    return FEM_OK;
+}
+
 // Apply a pending initial condition or checkpoint on the device.
 template <typename real>
 fem_status apply_pending(fem_mesh *m)
@@ -621,6 +672,11 @@ fem_status apply_pending(fem_mesh *m)
         CU(cudaStreamSynchronize(m->stream));
         m->U0 = out[0];
         m->q_carry = 0.0;
+        if (m->n_inst > 0) {   // per-instance energy accounts
+            fem_status st = instance_sums<real>(m, m->inst_U0);
+            if (st) return st;
+            m->inst_q.assign((size_t)m->n_inst, 0.0);
+        }
     } else {
         CU(cudaStreamSynchronize(m->stream));
     }
@@ -701,8 +757,7 @@ fem_status launch_step_kernel(fem_mesh *m, int k, double dt)
         if (k == 0)
             KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream), "block kernel");
         else
-            KERNEL(launch_shared_update<real>(a, m->n_sh_ctas, dt, m->stream),
-                   "shared-node kernel");
+            KERNEL(launch_shared_update<real>(a, dt, m->stream), "shared-node kernel");
     } else {
         const FlatArgs<real> a = flat_args<real>(m);
         if (k == 0)
@@ -892,6 +947,7 @@ fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_ma
 {
     if (!m || !mats) return fail(FEM_EINVAL, "NULL argument");
     if (n_mat <= 0) return fail(FEM_EINVAL, "n_mat must be positive");
+    if (m->n_inst > 0) return fail(FEM_ESTATE, "a batch takes its materials and boundaries from its parts");
     for (int32_t i = 0; i < n_mat; i++) {
         const fem_material &q = mats[i];
         double v[6] = {q.rho, q.c, q.k, q.latent, q.T_solidus, q.T_liquidus};
@@ -970,6 +1026,7 @@ fem_status fem_set_boundary(fem_mesh *m, const int32_t *faces, int64_t n_faces, 
 {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
     if (n_faces < 0) return fail(FEM_EINVAL, "n_faces must be >= 0");
+    if (m->n_inst > 0) return fail(FEM_ESTATE, "a batch takes its materials and boundaries from its parts");
     if (n_faces > 0 && (!faces || !h || !T_inf)) return fail(FEM_EINVAL, "NULL array argument");
     if (n_faces > INT32_MAX / 3) return fail(FEM_EINVAL, "too many faces");
     std::vector<int32_t> fc;
@@ -1015,6 +1072,7 @@ fem_status fem_set_dirichlet(fem_mesh *m, const int32_t *nodes, int64_t n, const
 {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
     if (n < 0 || (n > 0 && (!nodes || !T))) return fail(FEM_EINVAL, "bad Dirichlet arguments");
+    if (m->n_inst > 0) return fail(FEM_ESTATE, "a batch takes its materials and boundaries from its parts");
     std::vector<uint8_t> is((size_t)m->N, 0);
     std::vector<double> val((size_t)m->N, 0.0);
     for (int64_t i = 0; i < n; i++) {
@@ -1045,6 +1103,10 @@ fem_status fem_set_temperature(fem_mesh *m, const double *T0)
     m->step = 0;
     m->time = 0.0;
     m->q_carry = 0.0;
+    if (m->n_inst > 0) {
+        m->inst_t.assign((size_t)m->n_inst, 0.0);
+        m->inst_steps.assign((size_t)m->n_inst, 0);
+    }
     if (m->dev_ok) {
         cudaSetDevice(m->device);
         fem_status st = m->prec == FEM_FP32 ? apply_pending<float>(m) : apply_pending<double>(m);
@@ -1116,7 +1178,12 @@ fem_status fem_step(fem_mesh *m, int64_t n_steps, double dt)
     if (st) return st;
     if (n_steps == 0) return ok();
     st = m->prec == FEM_FP32 ? step_impl<float>(m, n_steps, dt) : step_impl<double>(m, n_steps, dt);
-    return st ? st : ok();
+    if (st) return st;
+    for (int32_t i = 0; i < m->n_inst; i++) {
+        m->inst_t[(size_t)i] += dt * (double)n_steps;
+        m->inst_steps[(size_t)i] += n_steps;
+    }
+    return ok();
 }
 
 fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_out,
@@ -1235,6 +1302,7 @@ fem_status fem_mesh_info(fem_mesh *m, fem_info *out)
     out->reorder = m->reorder;
     out->ctas_per_sm = m->ctas_per_sm;
     out->smem_per_cta = (int32_t)m->smem_bytes;
+    out->n_instances = m->n_inst;
     return ok();
 }
 
@@ -1289,8 +1357,335 @@ fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t
     case 9: return give(m->bp.elem_nodes.data(), m->bp.elem_nodes.size());
     case 10: return give(m->bp.face_nodes.data(), m->bp.face_nodes.size());
     case 11: return give(m->bp.copy_pos.data(), m->bp.copy_pos.size());
+    case 12: return give(m->bp.block_inst.data(), m->bp.block_inst.size());
+    case 13: return give(m->bp.inst_block_start.data(), m->bp.inst_block_start.size());
+    case 14: return give(m->bp.inst_order.data(), m->bp.inst_order.size());
     default: return fail(FEM_EINVAL, "unknown plan array %d", which);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent instances
+// ---------------------------------------------------------------------------
+
+fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **out)
+{
+    if (!out) return fail(FEM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!parts || n_parts <= 0) return fail(FEM_EINVAL, "need at least one part");
+    const fem_mesh *p0 = parts[0];
+    for (int32_t i = 0; i < n_parts; i++) {
+        const fem_mesh *p = parts[i];
+        if (!p) return fail(FEM_EINVAL, "part %d is NULL", i);
+        if (p->n_inst > 0) return fail(FEM_EINVAL, "part %d is itself a batch", i);
+        if (!p->have_mat) return fail(FEM_ESTATE, "part %d: fem_set_materials has not been called", i);
+        if (p->state != fem_mesh::ST_PENDING_T)
+            return fail(FEM_ESTATE, "part %d: set an initial temperature and do not step it", i);
+        if (p->prec != p0->prec) return fail(FEM_EINVAL, "part %d: precision differs from part 0", i);
+        if (p->opt.variant != FEM_VARIANT_BLOCK)
+            return fail(FEM_EINVAL, "part %d: batches use the block variant", i);
+    }
+    std::unique_ptr<fem_mesh> m;
+    try {
+        m.reset(new fem_mesh());
+        m->prec = p0->prec;
+        m->reorder = p0->reorder;
+        m->opt = p0->opt;
+        m->n_inst = n_parts;
+        m->inst_node.assign(1, 0);
+        m->inst_elem.assign(1, 0);
+        m->inst_face.assign(1, 0);
+        for (int32_t i = 0; i < n_parts; i++) {
+            m->inst_node.push_back(m->inst_node.back() + parts[i]->N);
+            m->inst_elem.push_back(m->inst_elem.back() + parts[i]->E);
+            m->inst_face.push_back(m->inst_face.back() + parts[i]->F);
+        }
+        m->N = m->inst_node.back();
+        m->E = m->inst_elem.back();
+        m->F = m->inst_face.back();
+        if (m->N > INT32_MAX - 1 || m->E > INT32_MAX / 8 || m->F > INT32_MAX / 3)
+            return fail(FEM_EINVAL, "batch too large for 32-bit ids");
+        // distinct phase-change ranges over all parts
+        std::vector<std::vector<uint8_t>> rmap((size_t)n_parts);
+        for (int32_t i = 0; i < n_parts; i++) {
+            const fem_mesh *p = parts[i];
+            for (size_t r = 0; r < p->ranges.size() / 2; r++) {
+                int found = -1;
+                for (size_t q = 0; q < m->ranges.size() / 2; q++)
+                    if (m->ranges[2 * q] == p->ranges[2 * r] && m->ranges[2 * q + 1] == p->ranges[2 * r + 1])
+                        found = (int)q;
+                if (found < 0) {
+                    if ((int)(m->ranges.size() / 2) >= kMaxRanges)
+                        return fail(FEM_EINVAL, "more than %d distinct phase-change ranges", kMaxRanges);
+                    found = (int)(m->ranges.size() / 2);
+                    m->ranges.push_back(p->ranges[2 * r]);
+                    m->ranges.push_back(p->ranges[2 * r + 1]);
+                }
+                rmap[(size_t)i].push_back((uint8_t)found);
+            }
+        }
+        bool any_dir = false;
+        for (int32_t i = 0; i < n_parts; i++) any_dir |= !parts[i]->is_dir.empty();
+        for (int32_t i = 0; i < n_parts; i++) {
+            const fem_mesh *p = parts[i];
+            const int32_t no = (int32_t)m->inst_node[(size_t)i];
+            m->xyz.insert(m->xyz.end(), p->xyz.begin(), p->xyz.end());
+            for (int32_t v : p->tets) m->tets.push_back(v + no);
+            m->mat.insert(m->mat.end(), p->mat.begin(), p->mat.end());
+            m->vol.insert(m->vol.end(), p->vol.begin(), p->vol.end());
+            for (int32_t r : p->rank) m->rank.push_back(r + no);
+            m->w.insert(m->w.end(), p->w.begin(), p->w.end());
+            m->Cn.insert(m->Cn.end(), p->Cn.begin(), p->Cn.end());
+            m->mn.insert(m->mn.end(), p->mn.begin(), p->mn.end());
+            m->Lcn.insert(m->Lcn.end(), p->Lcn.begin(), p->Lcn.end());
+            for (uint8_t r : p->rng_id) m->rng_id.push_back(rmap[(size_t)i].empty() ? 0 : rmap[(size_t)i][r]);
+            for (int32_t v : p->faces) m->faces.push_back(v + no);
+            m->fa.insert(m->fa.end(), p->fa.begin(), p->fa.end());
+            m->fg.insert(m->fg.end(), p->fg.begin(), p->fg.end());
+            if (any_dir) {
+                if (p->is_dir.empty()) {
+                    m->is_dir.insert(m->is_dir.end(), (size_t)p->N, 0);
+                    m->dir_T.insert(m->dir_T.end(), (size_t)p->N, 0.0);
+                } else {
+                    m->is_dir.insert(m->is_dir.end(), p->is_dir.begin(), p->is_dir.end());
+                    m->dir_T.insert(m->dir_T.end(), p->dir_T.begin(), p->dir_T.end());
+                }
+            }
+            m->pending.insert(m->pending.end(), p->pending.begin(), p->pending.end());
+            m->bw_input = std::max(m->bw_input, p->bw_input);
+            m->bw_rank = std::max(m->bw_rank, p->bw_rank);
+            double dt = 0.0;
+            dt = gershgorin_dt(p->N, p->E, p->tets.data(), p->w.data(), p->adj, p->F,
+                               p->faces.data(), p->fa.data(), p->Cn.data(),
+                               p->is_dir.empty() ? nullptr : p->is_dir.data());
+            m->inst_stable.push_back(dt);
+        }
+        if (m->ranges.empty()) { m->ranges.push_back(0.0); m->ranges.push_back(0.0); }
+        build_node_elems(m->N, m->E, m->tets.data(), m->adj);
+        m->have_mat = true;
+        m->state = fem_mesh::ST_PENDING_T;
+        m->inst_dt.resize((size_t)n_parts);
+        for (int32_t i = 0; i < n_parts; i++) m->inst_dt[(size_t)i] = 0.9 * m->inst_stable[(size_t)i];
+        m->inst_t.assign((size_t)n_parts, 0.0);
+        m->inst_steps.assign((size_t)n_parts, 0);
+        m->inst_q.assign((size_t)n_parts, 0.0);
+        // plan order: the instances that need the most steps first (smallest
+        // stable step), so that with step sizes proportional to the stable
+        // ones the instances still stepping are always a prefix of the plan
+        m->inst_plan_order.resize((size_t)n_parts);
+        for (int32_t i = 0; i < n_parts; i++) m->inst_plan_order[(size_t)i] = i;
+        std::stable_sort(m->inst_plan_order.begin(), m->inst_plan_order.end(), [&](int32_t a, int32_t b) {
+            return m->inst_stable[(size_t)a] < m->inst_stable[(size_t)b];
+        });
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed");
+    }
+    *out = m.release();
+    return ok();
+}
+
+fem_status fem_instance_stable_dt(fem_mesh *m, double *dt_out)
+{
+    if (!m || !dt_out) return fail(FEM_EINVAL, "NULL argument");
+    if (m->n_inst == 0) return fail(FEM_ESTATE, "not a batch");
+    std::copy(m->inst_stable.begin(), m->inst_stable.end(), dt_out);
+    return ok();
+}
+
+fem_status fem_set_instance_dt(fem_mesh *m, const double *dt)
+{
+    if (!m || !dt) return fail(FEM_EINVAL, "NULL argument");
+    if (m->n_inst == 0) return fail(FEM_ESTATE, "not a batch");
+    for (int32_t i = 0; i < m->n_inst; i++)
+        if (!(dt[i] > 0.0) || !std::isfinite(dt[i]))
+            return fail(FEM_EINVAL, "instance %d: dt must be positive and finite", i);
+    m->inst_dt.assign(dt, dt + m->n_inst);
+    return ok();
+}
+
+fem_status fem_get_instance_times(fem_mesh *m, double *t_out, int64_t *steps_out)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (m->n_inst == 0) return fail(FEM_ESTATE, "not a batch");
+    if (t_out) std::copy(m->inst_t.begin(), m->inst_t.end(), t_out);
+    if (steps_out) std::copy(m->inst_steps.begin(), m->inst_steps.end(), steps_out);
+    return ok();
+}
+
+}  // extern "C"
+
+namespace {
+
+// One fem_advance: per plan position k the number of steps; every step
+// launches the block and exchange kernels once per run of consecutive plan
+// positions still stepping (a single run when the counts do not increase
+// along the plan).
+template <typename real>
+fem_status advance_launches(fem_mesh *m, const std::vector<int64_t> &nk, cudaStream_t st)
+{
+    const BlockPlan &bp = m->bp;
+    BlockArgs<real> a = block_args<real>(m);
+    a.blk_dt = (const real *)m->dBlkDt;
+    a.sh_dt = (const real *)m->dShDt;
+    const int64_t K = (int64_t)nk.size();
+    int64_t max_n = 0;
+    for (int64_t v : nk) max_n = std::max(max_n, v);
+    for (int64_t step = 0; step < max_n; step++) {
+        for (int64_t k0 = 0; k0 < K;) {
+            if (nk[(size_t)k0] <= step) { k0++; continue; }
+            int64_t k1 = k0;
+            while (k1 < K && nk[(size_t)k1] > step) k1++;
+            a.b_first = bp.inst_block_start[(size_t)k0];
+            a.b_count = bp.inst_block_start[(size_t)k1] - a.b_first;
+            a.s_first = bp.inst_sh_start[(size_t)k0];
+            a.s_end = bp.inst_sh_start[(size_t)k1];
+            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, 0.0, st), "block kernel");
+            KERNEL(launch_shared_update<real>(a, 0.0, st), "shared-node kernel");
+            k0 = k1;
+        }
+    }
+    return FEM_OK;
+}
+
+template <typename real>
+fem_status advance_impl(fem_mesh *m, double t_end)
+{
+    const BlockPlan &bp = m->bp;
+    const int32_t ni = m->n_inst;
+    // steps and step sizes per instance: n_i equal steps of at most dt_i
+    std::vector<int64_t> n((size_t)ni, 0);
+    std::vector<double> dtp((size_t)ni, 0.0);
+    for (int32_t i = 0; i < ni; i++) {
+        const double span = t_end - m->inst_t[(size_t)i];
+        if (!(span > 0.0)) continue;
+        const double r = span / m->inst_dt[(size_t)i];
+        int64_t c = (int64_t)std::ceil(r * (1.0 - 1e-12));
+        if (c < 1) c = 1;
+        n[(size_t)i] = c;
+        dtp[(size_t)i] = span / (double)c;
+    }
+    // per-block and per-shared-node step sizes (only when they change)
+    if (dtp != m->dt_uploaded) {
+        std::vector<real> bdt(bp.blocks.size()), sdt((size_t)std::max<int64_t>(bp.n_sh, 1), real(0));
+        for (size_t b = 0; b < bp.blocks.size(); b++) bdt[b] = (real)dtp[(size_t)bp.block_inst[b]];
+        for (size_t k = 0; k < bp.inst_order.size(); k++) {
+            const real d = (real)dtp[(size_t)bp.inst_order[k]];
+            for (int64_t sidx = bp.inst_sh_start[k]; sidx < bp.inst_sh_start[k + 1]; sidx++)
+                sdt[(size_t)sidx] = d;
+        }
+        CU(cudaMemcpyAsync(m->dBlkDt, bdt.data(), bdt.size() * sizeof(real), cudaMemcpyHostToDevice,
+                           m->stream));
+        CU(cudaMemcpyAsync(m->dShDt, sdt.data(), sdt.size() * sizeof(real), cudaMemcpyHostToDevice,
+                           m->stream));
+        CU(cudaStreamSynchronize(m->stream));
+        m->dt_uploaded = dtp;
+    }
+    std::vector<int64_t> nk(bp.inst_order.size());
+    for (size_t k = 0; k < nk.size(); k++) nk[k] = n[(size_t)bp.inst_order[k]];
+    // the whole advance is one CUDA graph, rebuilt when the step pattern
+    // changes; launched on the mesh's stream (or a stream of the library's
+    // own when that is the legacy default stream, which cannot be captured)
+    cudaStream_t st = m->stream;
+    if (!st) {
+        if (!m->own_stream) CU(cudaStreamCreate(&m->own_stream));
+        st = m->own_stream;
+    }
+    if (!m->graph || nk != m->graph_key) {
+        if (m->graph) cudaGraphExecDestroy(m->graph);
+        m->graph = nullptr;
+        m->graph_key.clear();
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        fem_status fs = advance_launches<real>(m, nk, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (fs) {
+            if (g) cudaGraphDestroy(g);
+            return fs;
+        }
+        if (ce != cudaSuccess) return fail(FEM_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&m->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            m->graph = nullptr;
+            return fail(FEM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+        }
+        m->graph_key = nk;
+    }
+    CU(cudaGraphLaunch(m->graph, st));
+    if (st != m->stream) CU(cudaStreamSynchronize(st));
+    int64_t max_n = 0;
+    for (int32_t i = 0; i < ni; i++) {
+        if (n[(size_t)i] == 0) continue;
+        m->inst_t[(size_t)i] = t_end;
+        m->inst_steps[(size_t)i] += n[(size_t)i];
+        max_n = std::max(max_n, n[(size_t)i]);
+    }
+    m->step += max_n;
+    m->time = std::max(m->time, t_end);
+    return FEM_OK;
+}
+
+// T(E) of one node on the host (Eqs. 5, 11; the same piecewise-linear
+// inverse the kernels use), for per-instance latent-heat sums.
+double host_temperature(double E, double C, double Lc, double Ts, double Tl)
+{
+    if (Lc <= 0.0) return E / C;
+    const double Es = C * Ts;
+    if (E <= Es) return E / C;
+    if (E >= C * Tl + Lc) return (E - Lc) / C;
+    if (Tl <= Ts) return Ts;
+    return Ts + (E - Es) * (Tl - Ts) / (C * (Tl - Ts) + Lc);
+}
+
+}  // namespace
+
+extern "C" {
+
+fem_status fem_advance(fem_mesh *m, double t_end)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (m->n_inst == 0) return fail(FEM_ESTATE, "not a batch");
+    if (!std::isfinite(t_end)) return fail(FEM_EINVAL, "t_end must be finite");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    st = m->prec == FEM_FP32 ? advance_impl<float>(m, t_end) : advance_impl<double>(m, t_end);
+    return st ? st : ok();
+}
+
+fem_status fem_get_instance_energy(fem_mesh *m, int32_t inst, double out[4])
+{
+    if (!m || !out) return fail(FEM_EINVAL, "NULL argument");
+    if (m->n_inst == 0) return fail(FEM_ESTATE, "not a batch");
+    if (inst < 0 || inst >= m->n_inst) return fail(FEM_EINVAL, "instance %d out of range", inst);
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    if ((st = check_device_flag(m))) return st;
+    std::vector<double> E((size_t)m->N), q(m->bp.blocks.size());
+    KERNEL(m->prec == FEM_FP32
+               ? launch_get_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->stream)
+               : launch_get_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->stream),
+           "read-back kernel");
+    CU(cudaMemcpyAsync(E.data(), m->dIo, E.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaMemcpyAsync(q.data(), m->dQcum, q.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    double U = 0.0, lat = 0.0, Qb = m->inst_q[(size_t)inst];
+    for (int64_t nn = m->inst_node[(size_t)inst]; nn < m->inst_node[(size_t)inst + 1]; nn++) {
+        const double e = E[(size_t)nn];
+        U += e;
+        if (m->Lcn[(size_t)nn] > 0.0) {
+            const int r = m->rng_id[(size_t)nn];
+            lat += e - m->Cn[(size_t)nn] * host_temperature(e, m->Cn[(size_t)nn], m->Lcn[(size_t)nn],
+                                                              m->ranges[2 * (size_t)r],
+                                                              m->ranges[2 * (size_t)r + 1]);
+        }
+    }
+    for (size_t b = 0; b < q.size(); b++)
+        if (m->bp.block_inst[b] == inst) Qb += q[b];
+    out[0] = U;
+    out[1] = m->inst_U0[(size_t)inst];
+    out[2] = Qb;
+    out[3] = lat;
+    return ok();
 }
 
 }  // extern "C"

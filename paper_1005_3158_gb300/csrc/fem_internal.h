@@ -136,6 +136,13 @@ struct BlockArgs {
     // FP64 energy bookkeeping
     double *qcum;             // [n_blocks] cumulative heat through the Robin faces
     int *err;                 // device error flag (kErrWaitTimeout)
+    // the blocks [b_first, b_first + b_count) and shared nodes [s_first,
+    // s_end) one launch processes (a batch steps only its active instances);
+    // per-block / per-shared-node time steps (null: the launch's dt)
+    int32_t b_first, b_count;
+    int64_t s_first, s_end;
+    const real *blk_dt;
+    const real *sh_dt;
     // test hook (FEM_FAULT_SKIP_WEIGHT_COPY): announce the conductance copy
     // but never issue it, so that the wait for it runs out
     int32_t fault_skip_weights;
@@ -167,7 +174,7 @@ template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
                         void *stream);
 template <typename real>
-int launch_shared_update(const BlockArgs<real> &a, int n_sh_ctas, double dt, void *stream);
+int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream);
 template <typename real>
 int configure_block_kernel(int threads, size_t smem_bytes);
 template <typename real>

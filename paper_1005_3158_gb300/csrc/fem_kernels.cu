@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double qwarp[NW];   // per-warp boundary heat
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x;
+    const int b = a.b_first + (int)blockIdx.x;
     const int ls = a.ls, nes = a.nes;
 
     // shared memory: [3 barriers][conductances 6 x nes][schedule chunk]
@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         mbar_arrive_expect_tx(bar_w, wbytes);
         if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
     }
+    // this block's time step (a batch gives every instance its own; the
+    // load's latency is hidden behind the passes)
+    const real dtb = a.blk_dt ? a.blk_dt[b] : dt;
     // this thread's first face
     real fa0 = real(0), fg0 = real(0);
     if ((int)threadIdx.x < bi.nf) {
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
             R += sv[v >> 16];
         }
         if (l < bi.nint) {
-            if (!(sPh[l] & kDirichletBit)) a.Eloc[lb + l] = sE[l] + dt * R;
+            if (!(sPh[l] & kDirichletBit)) a.Eloc[lb + l] = sE[l] + dtb * R;
         } else if (l < nloc) {
             a.P[sPos[l]] = R;
         }
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     if (bi.nf > 0 && threadIdx.x == 0) {
         double q = 0.0;
         for (int k = 0; k < NW; k++) q += qwarp[k];
-        a.qcum[b] += (double)dt * q;
+        a.qcum[b] += (double)dtb * q;
     }
 }
 
@@ -419,15 +422,16 @@ template <typename real, int NT>
 __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, const real dt,
                                                       const bool update)
 {
-    const int64_t s = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (s >= a.n_sh) return;
+    const int64_t s = a.s_first + (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (s >= a.s_end) return;
     const int k0 = __ldg(a.sh_ptr + s), k1 = __ldg(a.sh_ptr + s + 1);
     real E = a.Esh[s];
     if (update) {
         if (__ldg(a.ph + a.n_int + s) & kDirichletBit) return;
+        const real dts = a.sh_dt ? a.sh_dt[s] : dt;
         real R = real(0);
         for (int k = k0; k < k1; ++k) R += a.P[k];   // block order
-        E += dt * R;
+        E += dts * R;
         a.Esh[s] = E;
     }
     for (int k = k0; k < k1; ++k) a.Eloc[__ldg(a.mpos + k)] = E;
@@ -645,7 +649,8 @@ int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes
 {
     cudaStream_t st = (cudaStream_t)stream;
     const real rdt = (real)dt;
-    const int grid = a.n_blocks;
+    const int grid = a.b_count;
+    if (grid <= 0) return 0;
     switch (threads) {
     case 128: k_block_step<real, 128><<<grid, 128, smem_bytes, st>>>(a, rdt); break;
     case 256: k_block_step<real, 256><<<grid, 256, smem_bytes, st>>>(a, rdt); break;
@@ -659,17 +664,20 @@ int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes
 template <typename real>
 int launch_mirror_copies(const BlockArgs<real> &a, void *stream)
 {
-    if (a.n_sh > 0)
-        k_shared_update<real, 256><<<(int)((a.n_sh + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+    const int64_t n = a.s_end - a.s_first;
+    if (n > 0)
+        k_shared_update<real, 256><<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
             a, real(0), false);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
-int launch_shared_update(const BlockArgs<real> &a, int n_sh_ctas, double dt, void *stream)
+int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream)
 {
-    if (a.n_sh > 0)
-        k_shared_update<real, 256><<<n_sh_ctas, 256, 0, (cudaStream_t)stream>>>(a, (real)dt, true);
+    const int64_t n = a.s_end - a.s_first;
+    if (n > 0)
+        k_shared_update<real, 256><<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            a, (real)dt, true);
     return (int)cudaGetLastError();
 }
 
@@ -762,7 +770,7 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
     template int block_kernel_occupancy<real>(int, size_t, int *);                                \
     template int launch_mirror_copies<real>(const BlockArgs<real> &, void *);                     \
     template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *); \
-    template int launch_shared_update<real>(const BlockArgs<real> &, int, double, void *);        \
+    template int launch_shared_update<real>(const BlockArgs<real> &, double, void *);             \
     template int launch_flat_temperature<real>(const FlatArgs<real> &, void *);                   \
     template int launch_flat_elements<real>(const FlatArgs<real> &, bool, const int64_t *, int,  \
                                             void *);                                              \

@@ -423,36 +423,60 @@ void bank_schedule(BlockPlan &bp, int real_size)
 std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int32_t *tets,
                              const std::vector<int32_t> &rank, int64_t F,
                              const int32_t *faces, const std::vector<int32_t> &face_owner,
-                             int block_elems, int real_size, BlockPlan &out)
+                             int block_elems, int real_size, BlockPlan &out,
+                             const std::vector<int64_t> &inst_elem_start,
+                             const std::vector<int32_t> &inst_order)
 {
     out = BlockPlan();
     out.N = N; out.E = E; out.F = F;
-    int64_t nparts = std::max<int64_t>(1, (E + block_elems - 1) / block_elems);
-    // --- partition: element order and part starts
+    // instances in plan order: element ranges [es[i], es[i+1]) of the caller
+    std::vector<int64_t> es = inst_elem_start;
+    std::vector<int32_t> order = inst_order;
+    if (es.empty()) es = {0, E};
+    const int64_t n_inst = (int64_t)es.size() - 1;
+    if (order.empty())
+        for (int64_t i = 0; i < n_inst; i++) order.push_back((int32_t)i);
+    if ((int64_t)order.size() != n_inst || es[0] != 0 || es[(size_t)n_inst] != E)
+        return "inconsistent instance ranges";
+    // --- partition: element order and part starts; every instance is cut
+    // into its own blocks (recursive coordinate bisection of the centroids),
+    // instances one after another in plan order
     std::vector<Cen> cen((size_t)E);
-    for (int64_t e = 0; e < E; e++) {
-        double s[3] = {0, 0, 0};
-        for (int c = 0; c < 4; c++)
-            for (int d = 0; d < 3; d++) s[d] += xyz[3 * (size_t)tets[4 * e + c] + d];
-        for (int d = 0; d < 3; d++) cen[e].x[d] = (float)(0.25 * s[d]);
-        cen[e].id = (int32_t)e;
-    }
-    // part p covers [pstart[p], pstart[p+1]) of the bisected order; the
-    // starts follow from the same size recursion that rcb applies.
-    rcb(cen.data(), E, nparts, 0);
-    std::vector<int64_t> pstart((size_t)nparts + 1, 0);
+    std::vector<int64_t> pstart;
+    out.inst_order = order;
+    out.inst_block_start.assign(1, 0);
     {
-        std::function<void(int64_t, int64_t, int64_t, int64_t)> sizes =
-            [&](int64_t off, int64_t n, int64_t parts, int64_t first) {
-                if (parts <= 1) { pstart[(size_t)first] = off; return; }
-                int64_t p1 = parts / 2;
-                int64_t mid = n * p1 / parts;
-                sizes(off, mid, p1, first);
-                sizes(off + mid, n - mid, parts - p1, first + p1);
-            };
-        sizes(0, E, nparts, 0);
-        pstart[(size_t)nparts] = E;
+        int64_t off = 0;
+        for (int64_t k = 0; k < n_inst; k++) {
+            const int32_t i = order[(size_t)k];
+            const int64_t e_lo = es[(size_t)i], n = es[(size_t)i + 1] - e_lo;
+            if (n <= 0) return "instance " + std::to_string(i) + " has no elements";
+            for (int64_t j = 0; j < n; j++) {
+                const int64_t e = e_lo + j;
+                double sc[3] = {0, 0, 0};
+                for (int c = 0; c < 4; c++)
+                    for (int d = 0; d < 3; d++) sc[d] += xyz[3 * (size_t)tets[4 * e + c] + d];
+                for (int d = 0; d < 3; d++) cen[(size_t)(off + j)].x[d] = (float)(0.25 * sc[d]);
+                cen[(size_t)(off + j)].id = (int32_t)e;
+            }
+            const int64_t parts = (n + block_elems - 1) / block_elems;
+            rcb(cen.data() + off, n, parts, 0);
+            // part starts follow from the same size recursion that rcb applies
+            std::function<void(int64_t, int64_t, int64_t)> sizes =
+                [&](int64_t o, int64_t m, int64_t pp) {
+                    if (pp <= 1) { pstart.push_back(o); return; }
+                    const int64_t p1 = pp / 2, mid = m * p1 / pp;
+                    sizes(o, mid, p1);
+                    sizes(o + mid, m - mid, pp - p1);
+                };
+            sizes(off, n, parts);
+            for (int64_t q = 0; q < parts; q++) out.block_inst.push_back(i);
+            out.inst_block_start.push_back((int32_t)pstart.size());
+            off += n;
+        }
     }
+    const int64_t nparts = (int64_t)pstart.size();
+    pstart.push_back(E);
     std::vector<int32_t> eorder((size_t)E);
     for (int64_t i = 0; i < E; i++) eorder[i] = cen[i].id;
     std::vector<Cen>().swap(cen);
@@ -505,6 +529,24 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
     });
     const int64_t n_sh = (int64_t)shared.size();
     const int64_t n_int = N - n_sh;
+    // instances are independent: no node may be shared across two of them;
+    // shared nodes sort by their first block, hence by plan position
+    {
+        std::vector<int32_t> bpos((size_t)nparts);
+        for (int64_t k = 0; k < n_inst; k++)
+            for (int32_t b = out.inst_block_start[(size_t)k]; b < out.inst_block_start[(size_t)k + 1]; b++)
+                bpos[(size_t)b] = (int32_t)k;
+        out.inst_sh_start.assign((size_t)n_inst + 1, n_sh);
+        for (int64_t sidx = n_sh - 1; sidx >= 0; sidx--) {
+            const int32_t n = shared[(size_t)sidx];
+            const int32_t k = bpos[(size_t)sig[(size_t)sig_ptr[n]]];
+            if (bpos[(size_t)sig[(size_t)sig_ptr[n + 1] - 1]] != k)
+                return "node " + std::to_string(n) + " belongs to two instances";
+            out.inst_sh_start[(size_t)k] = sidx;
+        }
+        for (int64_t k = n_inst - 1; k >= 0; k--)
+            out.inst_sh_start[(size_t)k] = std::min(out.inst_sh_start[(size_t)k], out.inst_sh_start[(size_t)k + 1]);
+    }
     std::vector<int32_t> sid((size_t)N, -1);
     for (int64_t s = 0; s < n_sh; s++) sid[shared[s]] = (int32_t)s;
     out.n_int = n_int; out.n_sh = n_sh;
@@ -680,6 +722,9 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         if (f >= 0)
             for (int c = 0; c < 3; c++) out.face_nodes[3 * i + c] = out.node_new[faces[3 * (size_t)f + c]];
     }
+    out.inst_int_start.assign((size_t)n_inst + 1, n_int);
+    for (int64_t k = 0; k < n_inst; k++)
+        out.inst_int_start[(size_t)k] = out.blocks[(size_t)out.inst_block_start[(size_t)k]].n0;
     bank_schedule(out, real_size);
     return "";
 }

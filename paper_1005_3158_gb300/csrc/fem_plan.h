@@ -67,14 +67,27 @@ struct BlockPlan {
                                       // (round r, lane) at (r/2)*64 + 2*lane + r%2
     std::vector<int32_t> elem_nodes;  // [E_pad][4] internal ids (-1 pad)
     std::vector<int32_t> face_nodes;  // [F_pad][3]
+    // independent instances (a batch): blocks never mix instances; plan
+    // position k holds caller instance inst_order[k], whose blocks are
+    // [inst_block_start[k], inst_block_start[k+1]); its interior nodes and
+    // its shared nodes are contiguous too (inst_int_start, inst_sh_start)
+    std::vector<int32_t> inst_order;
+    std::vector<int32_t> inst_block_start;
+    std::vector<int64_t> inst_int_start, inst_sh_start;
+    std::vector<int32_t> block_inst;  // [n_blocks] caller instance of each block
 };
 
 // rank[n]: priority of node n (its position in the chosen node order);
 // used to order nodes inside blocks.  face_owner[f]: owning element.
+// inst_elem_start: element ranges of independent instances ([n_inst+1],
+// empty = one instance); inst_order: plan order of the instances (empty =
+// caller order).  Instances must not share nodes.
 std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int32_t *tets,
                              const std::vector<int32_t> &rank, int64_t F,
                              const int32_t *faces, const std::vector<int32_t> &face_owner,
-                             int block_elems, int real_size, BlockPlan &out);
+                             int block_elems, int real_size, BlockPlan &out,
+                             const std::vector<int64_t> &inst_elem_start = {},
+                             const std::vector<int32_t> &inst_order = {});
 
 // Bank-aware order of the slots inside every 32-lane group of the schedule
 // (called by build_block_plan; real_size 4 or 8 selects the bank model).

@@ -30,7 +30,9 @@ ABI_SYMBOLS = (
     "fem_set_dirichlet", "fem_set_temperature", "fem_stable_dt", "fem_step", "fem_step_profile",
     "fem_get_temperature", "fem_get_enthalpy", "fem_get_energy", "fem_set_stream",
     "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
-    "fem_last_error", "fem_mesh_destroy", "fem_energy_sums_noalloc",
+    "fem_last_error", "fem_mesh_destroy", "fem_energy_sums_noalloc", "fem_batch_create",
+    "fem_instance_stable_dt", "fem_set_instance_dt", "fem_advance", "fem_get_instance_times",
+    "fem_get_instance_energy",
 )
 
 
@@ -51,7 +53,8 @@ class FemInfo(ctypes.Structure):
         "n_shared_copies", "n_sched_rounds", "n_colors", "bandwidth_input",
         "bandwidth_internal", "max_block_elems", "device_bytes")] + [
         (n, ctypes.c_int32) for n in ("precision", "variant", "threads", "reorder",
-                                      "ctas_per_sm", "smem_per_cta")]
+                                      "ctas_per_sm", "smem_per_cta", "n_instances",
+                                      "reserved_info")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -95,6 +98,12 @@ def _load():
         "fem_rcm_order": [i64, ip, i64, ip, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "fem_plan_array": [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(i64)],
         "fem_energy_sums_noalloc": [ctypes.c_int, P, P, P, P, P, i64, P, P],
+        "fem_batch_create": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(P)],
+        "fem_instance_stable_dt": [P, dp],
+        "fem_set_instance_dt": [P, dp],
+        "fem_advance": [P, ctypes.c_double],
+        "fem_get_instance_times": [P, dp, ctypes.POINTER(i64)],
+        "fem_get_instance_energy": [P, ctypes.c_int32, dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -272,10 +281,12 @@ def fem_rcm_order(n_nodes, tets):
 
 
 _PLAN_TYPES = {0: np.int32, 1: np.int32, 2: np.int32, 3: np.int32, 4: np.int32, 5: np.int32,
-               6: np.int32, 7: np.int32, 8: np.uint16, 9: np.int32, 10: np.int32, 11: np.int32}
+               6: np.int32, 7: np.int32, 8: np.uint16, 9: np.int32, 10: np.int32, 11: np.int32,
+               12: np.int32, 13: np.int32, 14: np.int32}
 PLAN_ARRAYS = {"node_new": 0, "blocks": 1, "elem_order": 2, "face_order": 3, "copy_node": 4,
                "sh_ptr": 5, "sh_copy": 6, "grp": 7, "sched": 8, "elem_nodes": 9,
-               "face_nodes": 10, "copy_pos": 11}
+               "face_nodes": 10, "copy_pos": 11, "block_inst": 12, "inst_block_start": 13,
+               "inst_order": 14}
 
 
 def fem_plan_array(h, which):
@@ -297,6 +308,41 @@ def fem_energy_sums_noalloc(prec, E, C, Lc, phase, ranges, n_nodes, out, stream=
         int(prec), ctypes.c_void_p(E), ctypes.c_void_p(C), ctypes.c_void_p(Lc),
         ctypes.c_void_p(phase), ctypes.c_void_p(ranges), int(n_nodes), ctypes.c_void_p(out),
         ctypes.c_void_p(int(stream) if stream else 0)))
+
+
+def fem_batch_create(parts):
+    arr = (ctypes.c_void_p * len(parts))(*[p for p in parts])
+    out = ctypes.c_void_p()
+    _check(_lib.fem_batch_create(arr, len(parts), ctypes.byref(out)))
+    return out
+
+
+def fem_instance_stable_dt(h, n_inst):
+    out = np.zeros(n_inst)
+    _check(_lib.fem_instance_stable_dt(h, _pd(out)))
+    return out
+
+
+def fem_set_instance_dt(h, dt):
+    dt = _d(dt)
+    _check(_lib.fem_set_instance_dt(h, _pd(dt)))
+
+
+def fem_advance(h, t_end):
+    _check(_lib.fem_advance(h, float(t_end)))
+
+
+def fem_get_instance_times(h, n_inst):
+    t = np.zeros(n_inst)
+    n = np.zeros(n_inst, np.int64)
+    _check(_lib.fem_get_instance_times(h, _pd(t), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return t, n
+
+
+def fem_get_instance_energy(h, inst):
+    out = np.zeros(4)
+    _check(_lib.fem_get_instance_energy(h, int(inst), _pd(out)))
+    return out
 
 
 def fem_last_error():
@@ -387,3 +433,42 @@ class Mesh:
 
     def plan(self, which):
         return fem_plan_array(self.h, which)
+
+
+class Batch(Mesh):
+    """A batch of independent meshes (fem_batch_create) built from several
+    ``meshgen.Problem``-like objects; the parts are released once copied."""
+
+    def __init__(self, probs, precision="fp32", reorder=1, block_elems=0, threads=0):
+        parts = []
+        try:
+            for p in probs:
+                parts.append(Mesh(p, precision, reorder=reorder, variant="block",
+                                  block_elems=block_elems, threads=threads))
+            self.h = fem_batch_create([q.h for q in parts])
+        finally:
+            for q in parts:
+                q.close()
+        self.n_inst = len(parts)
+        self.node_start = np.cumsum([0] + [int(p.xyz.shape[0]) for p in probs])
+        self.n_nodes = int(self.node_start[-1])
+        self.n_tets = int(sum(int(p.tets.shape[0]) for p in probs))
+
+    def instance_stable_dt(self):
+        return fem_instance_stable_dt(self.h, self.n_inst)
+
+    def set_instance_dt(self, dt):
+        fem_set_instance_dt(self.h, dt)
+
+    def advance(self, t_end):
+        fem_advance(self.h, t_end)
+
+    def instance_times(self):
+        return fem_get_instance_times(self.h, self.n_inst)
+
+    def instance_energy(self, i):
+        return fem_get_instance_energy(self.h, i)
+
+    def instance_temperature(self, i, T=None):
+        T = self.temperature() if T is None else T
+        return T[self.node_start[i]:self.node_start[i + 1]]

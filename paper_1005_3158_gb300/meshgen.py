@@ -221,6 +221,84 @@ def flanged_casting(nx: int = 70, ny: int = 70, nz: int = 68,
                    name=f"flanged_casting_{nx}x{ny}x{nz}")
 
 
+def casting_instance(target_tets: float, seed: int) -> Problem:
+    """One procedural casting + mold of about target_tets tets.
+
+    Seeded parameters: 1-3 flanged-cylinder cavities side by side along x
+    (body radius 4-8 cm, height 10-25 cm, flange radius 1.3-1.8 x the body
+    radius, flange thickness 1-3 cm, 2-5 cm apart), mold wall thickness
+    3-8 cm around them.  The hex spacing is chosen so that 6 nx ny nz is
+    close to target_tets; interior nodes jittered by 5 %.  Materials,
+    initial temperatures and Robin faces as in flanged_casting.
+    """
+    rng = rng_of(seed)
+    k = int(rng.integers(1, 4))
+    body_r = rng.uniform(0.04, 0.08)
+    body_h = rng.uniform(0.10, 0.25)
+    flange_r = body_r * rng.uniform(1.3, 1.8)
+    flange_t = rng.uniform(0.01, 0.03)
+    gap = rng.uniform(0.02, 0.05)
+    wall = rng.uniform(0.03, 0.08)
+    lx = 2 * wall + k * 2 * flange_r + (k - 1) * gap
+    ly = 2 * wall + 2 * flange_r
+    lz = 2 * wall + body_h
+    hsz = (lx * ly * lz * 6.0 / float(target_tets)) ** (1.0 / 3.0)
+    nx, ny, nz = (max(2, int(round(v / hsz))) for v in (lx, ly, lz))
+    xyz, tets, _, flags = box_grid(nx, ny, nz, lx, ly, lz, jitter=0.05, seed=seed + 7)
+    c = centroids(xyz, tets)
+    z0 = wall
+    alloy = np.zeros(tets.shape[0], dtype=bool)
+    for j in range(k):
+        xc = wall + flange_r + j * (2 * flange_r + gap)
+        r = np.hypot(c[:, 0] - xc, c[:, 1] - ly / 2)
+        zin = (c[:, 2] >= z0) & (c[:, 2] <= z0 + body_h)
+        alloy |= (r <= body_r) & zin
+        alloy |= (r <= flange_r) & (c[:, 2] >= z0) & (c[:, 2] <= z0 + flange_t)
+    mat = np.where(alloy, 0, 1).astype(np.int32)
+    faces = box_boundary_faces(tets, flags)
+    hh, ti, q = _robin(faces)
+    T0 = np.where(_node_touches(xyz.shape[0], tets, alloy), T_POUR, T_MOLD)
+    return Problem(xyz=xyz, tets=tets, mat=mat, materials=np.array([ALLOY, STEEL]),
+                   faces=faces, h=hh, t_inf=ti, q=q, T0=T0.astype(np.float64),
+                   name=f"casting_instance_{seed}_{nx}x{ny}x{nz}")
+
+
+def batched_castings(n_inst: int = 256, seed: int = 1009, lo: float = 2.0e4,
+                     hi: float = 5.0e5) -> list:
+    """n_inst casting instances with sizes log-uniform in [lo, hi] tets
+    (about 38M tets in all for the defaults); instance i uses seed + 1 + i."""
+    rng = rng_of(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_inst))
+    return [casting_instance(float(sz), seed + 1 + i) for i, sz in enumerate(sizes)]
+
+
+def concat_problems(probs) -> Problem:
+    """The disjoint union of several problems (part k's node i becomes node
+    offset_k + i; material ids offset by the parts' material counts)."""
+    xyz, tets, mat, mats, faces, hh, ti, q, T0, dn, dT = ([] for _ in range(11))
+    no = mo = 0
+    for p in probs:
+        xyz.append(p.xyz)
+        tets.append(p.tets + no)
+        mat.append(p.mat + mo)
+        mats.append(p.materials)
+        faces.append(p.faces + no)
+        hh.append(p.h)
+        ti.append(p.t_inf)
+        q.append(p.q)
+        T0.append(p.T0)
+        dn.append(p.dir_nodes + no)
+        dT.append(p.dir_T)
+        no += p.n_nodes
+        mo += p.materials.shape[0]
+    return Problem(xyz=np.concatenate(xyz), tets=np.concatenate(tets).astype(np.int32),
+                   mat=np.concatenate(mat).astype(np.int32), materials=np.concatenate(mats),
+                   faces=np.concatenate(faces).astype(np.int32), h=np.concatenate(hh),
+                   t_inf=np.concatenate(ti), q=np.concatenate(q), T0=np.concatenate(T0),
+                   dir_nodes=np.concatenate(dn).astype(np.int32), dir_T=np.concatenate(dT),
+                   name="+".join(p.name for p in probs))
+
+
 def block_with_cores(n: int = 220, n_cores: int = 32, seed: int = 1007,
                      side: float = 1.0) -> Problem:
     """Alloy block (side^3 m, n^3 hexes, 5% jitter) with seeded spherical
