@@ -417,24 +417,50 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
 
 // Shared nodes: sum the partials of every copy in a fixed order (Eq. 22),
 // update E and refresh the copies' mirrors in the blocks' local arrays.
-// With update == false only the mirrors are refreshed.
-template <typename real, int NT>
+// With update == false only the mirrors are refreshed.  Each thread takes
+// NPT nodes NT apart, so that their independent load chains overlap.
+template <typename real, int NT, int NPT>
 __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, const real dt,
                                                       const bool update)
 {
-    const int64_t s = a.s_first + (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (s >= a.s_end) return;
-    const int k0 = __ldg(a.sh_ptr + s), k1 = __ldg(a.sh_ptr + s + 1);
-    real E = a.Esh[s];
-    if (update) {
-        if (__ldg(a.ph + a.n_int + s) & kDirichletBit) return;
-        const real dts = a.sh_dt ? a.sh_dt[s] : dt;
-        real R = real(0);
-        for (int k = k0; k < k1; ++k) R += a.P[k];   // block order
-        E += dts * R;
-        a.Esh[s] = E;
+    const int64_t base = a.s_first + (int64_t)blockIdx.x * NT * NPT + threadIdx.x;
+    int k0[NPT], k1[NPT];
+    real E[NPT], dts[NPT];
+    bool act[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; j++) {
+        const int64_t s = base + (int64_t)j * NT;
+        act[j] = s < a.s_end;
+        k0[j] = k1[j] = 0;
+        E[j] = dts[j] = real(0);
+        if (act[j]) {
+            k0[j] = __ldg(a.sh_ptr + s);
+            k1[j] = __ldg(a.sh_ptr + s + 1);
+            E[j] = a.Esh[s];
+            if (update) {
+                if (__ldg(a.ph + a.n_int + s) & kDirichletBit) act[j] = false;
+                dts[j] = a.sh_dt ? a.sh_dt[s] : dt;
+            }
+        }
     }
-    for (int k = k0; k < k1; ++k) a.Eloc[__ldg(a.mpos + k)] = E;
+    if (update) {
+        real R[NPT];
+#pragma unroll
+        for (int j = 0; j < NPT; j++) {
+            R[j] = real(0);
+            for (int k = k0[j]; k < k1[j]; ++k) R[j] += a.P[k];   // block order
+        }
+#pragma unroll
+        for (int j = 0; j < NPT; j++)
+            if (act[j]) {
+                E[j] += dts[j] * R[j];
+                a.Esh[base + (int64_t)j * NT] = E[j];
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; j++)
+        if (act[j])
+            for (int k = k0[j]; k < k1[j]; ++k) a.Eloc[__ldg(a.mpos + k)] = E[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -661,23 +687,25 @@ int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes
     return (int)cudaGetLastError();
 }
 
+constexpr int kShNT = 256, kShNPT = 2;   // exchange kernel: threads, nodes per thread
+
 template <typename real>
 int launch_mirror_copies(const BlockArgs<real> &a, void *stream)
 {
-    const int64_t n = a.s_end - a.s_first;
+    const int64_t n = a.s_end - a.s_first, per = (int64_t)kShNT * kShNPT;
     if (n > 0)
-        k_shared_update<real, 256><<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-            a, real(0), false);
+        k_shared_update<real, kShNT, kShNPT><<<(int)((n + per - 1) / per), kShNT, 0,
+                                               (cudaStream_t)stream>>>(a, real(0), false);
     return (int)cudaGetLastError();
 }
 
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream)
 {
-    const int64_t n = a.s_end - a.s_first;
+    const int64_t n = a.s_end - a.s_first, per = (int64_t)kShNT * kShNPT;
     if (n > 0)
-        k_shared_update<real, 256><<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-            a, (real)dt, true);
+        k_shared_update<real, kShNT, kShNPT><<<(int)((n + per - 1) / per), kShNT, 0,
+                                               (cudaStream_t)stream>>>(a, (real)dt, true);
     return (int)cudaGetLastError();
 }
 
