@@ -24,6 +24,10 @@
  *   - the explicit update E += dt (F - K T) (Eq. 14 with theta = 0 in Eq. 10,
  *     written for the enthalpy unknown of Eq. 5),
  *   - Dirichlet nodes (Eq. 3) held at E(T_D),
+ *   - the cast-mold interface of Eq. 8: faces of two regions meshed
+ *     separately, each exchanging h_i (T_sister - T) with the mean
+ *     temperature of its sister, the nearest face of the other region
+ *     (found once, Section 3),
  *   - FP64 energy bookkeeping: U = sum E, cumulative boundary heat, latent
  *     heat still to be released,
  *   - a Gershgorin stable time step for the explicit scheme (reading of
@@ -46,6 +50,7 @@
 
 typedef struct oracle_problem {
     int64_t n_nodes, n_tets, n_faces;
+    double *xyz;     /* [N][3] coordinates (interface centroids and areas) */
     /* element data */
     int32_t *tets;   /* [E][4], re-oriented to positive volume */
     double *Ke;      /* [E][4][4] dense conductance matrices */
@@ -58,6 +63,13 @@ typedef struct oracle_problem {
     /* Robin faces */
     int32_t *faces;  /* [F][3] */
     double *fh, *ftinf, *fq, *farea;
+    /* cast-mold interface (Eq. 8): faces of side 0 then side 1; each face
+     * sees the mean temperature of its sister, the other side's face with
+     * the nearest centroid, as its ambient temperature */
+    int64_t n_if;
+    int32_t *if_faces;   /* [n_if][3] */
+    double *if_h, *if_area;
+    int64_t *if_sister;  /* index into the interface list */
     /* Dirichlet */
     uint8_t *is_dir;
     double *T_dir;
@@ -174,6 +186,7 @@ void oracle_destroy(oracle_problem *p)
     free(p->tets); free(p->Ke); free(p->vol);
     free(p->C); free(p->m); free(p->Lc); free(p->Ts); free(p->Tl);
     free(p->faces); free(p->fh); free(p->ftinf); free(p->fq); free(p->farea);
+    free(p->if_faces); free(p->if_h); free(p->if_area); free(p->if_sister); free(p->xyz);
     free(p->is_dir); free(p->T_dir);
     free(p->E); free(p->T); free(p->R);
     free(p);
@@ -199,6 +212,7 @@ oracle_problem *oracle_create(int64_t n_nodes, const double *xyz,
     if (!p) { *status = ORACLE_ENOMEM; return NULL; }
     p->n_nodes = n_nodes; p->n_tets = n_tets; p->n_faces = n_faces;
     size_t N = (size_t)n_nodes, E = (size_t)n_tets, F = (size_t)n_faces;
+    p->xyz = malloc(3 * N * sizeof(double));
     p->tets = malloc(4 * E * sizeof(int32_t));
     p->Ke = malloc(16 * E * sizeof(double));
     p->vol = malloc(E * sizeof(double));
@@ -217,11 +231,12 @@ oracle_problem *oracle_create(int64_t n_nodes, const double *xyz,
     p->E = calloc(N, sizeof(double));
     p->T = calloc(N, sizeof(double));
     p->R = calloc(N, sizeof(double));
-    if (!p->tets || !p->Ke || !p->vol || !p->C || !p->m || !p->Lc || !p->Ts || !p->Tl ||
+    if (!p->xyz || !p->tets || !p->Ke || !p->vol || !p->C || !p->m || !p->Lc || !p->Ts || !p->Tl ||
         !p->faces || !p->fh || !p->ftinf || !p->fq || !p->farea || !p->is_dir ||
         !p->T_dir || !p->E || !p->T || !p->R) {
         oracle_destroy(p); *status = ORACLE_ENOMEM; return NULL;
     }
+    memcpy(p->xyz, xyz, 3 * N * sizeof(double));
     uint8_t *has_range = calloc(N, 1);
     if (!has_range) { oracle_destroy(p); *status = ORACLE_ENOMEM; return NULL; }
 
@@ -352,7 +367,79 @@ double oracle_residual_part(const oracle_problem *p, const double *T, double *R,
             qin += r;
         }
     }
+    /* interface faces (whole residual only): Robin terms with h = h_i and
+     * the sister face's mean temperature as the ambient one, q = 0 */
+    if (!face_part)
+        for (int64_t f = 0; f < p->n_if; f++) {
+            const int32_t *n = p->if_faces + 3 * f;
+            const int32_t *sn = p->if_faces + 3 * p->if_sister[f];
+            double Tamb = (T[sn[0]] + T[sn[1]] + T[sn[2]]) / 3.0;
+            double hA12 = p->if_h[f] * p->if_area[f] / 12.0;
+            double load = p->if_area[f] / 3.0 * p->if_h[f] * Tamb;
+            for (int a = 0; a < 3; a++) {
+                double s = 0.0;
+                for (int b = 0; b < 3; b++) s += hA12 * (a == b ? 2.0 : 1.0) * T[n[b]];
+                double r = load - s;
+                R[n[a]] += r;
+                qin += r;
+            }
+        }
     return qin;
+}
+
+/* Interface of Eq. 8 between two regions meshed separately: side-0 faces
+ * [n0][3] with coefficients h0, side-1 faces [n1][3] with h1 (each face a
+ * face of exactly one tet is not checked here).  The sister of a face is the
+ * face of the other side whose centroid is nearest (ties: the lower index),
+ * found once, as the paper does at the start of a simulation (Section 3).
+ * Returns ORACLE_OK, ORACLE_EINVAL or ORACLE_ENOMEM. */
+int oracle_set_interface(oracle_problem *p, int64_t n0, const int32_t *f0, const double *h0,
+                         int64_t n1, const int32_t *f1, const double *h1)
+{
+    if (n0 < 0 || n1 < 0 || (n0 > 0) != (n1 > 0)) return ORACLE_EINVAL;
+    free(p->if_faces); free(p->if_h); free(p->if_area); free(p->if_sister);
+    p->if_faces = NULL; p->if_h = p->if_area = NULL; p->if_sister = NULL;
+    p->n_if = 0;
+    if (n0 == 0) return ORACLE_OK;
+    int64_t n = n0 + n1;
+    p->if_faces = malloc((size_t)n * 3 * sizeof(int32_t));
+    p->if_h = malloc((size_t)n * sizeof(double));
+    p->if_area = malloc((size_t)n * sizeof(double));
+    p->if_sister = malloc((size_t)n * sizeof(int64_t));
+    double *cen = malloc((size_t)n * 3 * sizeof(double));
+    if (!p->if_faces || !p->if_h || !p->if_area || !p->if_sister || !cen) { free(cen); return ORACLE_ENOMEM; }
+    for (int64_t f = 0; f < n; f++) {
+        const int32_t *src = f < n0 ? f0 + 3 * f : f1 + 3 * (f - n0);
+        for (int a = 0; a < 3; a++) {
+            if (src[a] < 0 || src[a] >= p->n_nodes) { free(cen); p->n_if = 0; return ORACLE_EINVAL; }
+            p->if_faces[3 * f + a] = src[a];
+        }
+        p->if_h[f] = f < n0 ? h0[f] : h1[f - n0];
+        const double *x0 = p->xyz + 3 * (size_t)src[0], *x1 = p->xyz + 3 * (size_t)src[1],
+                     *x2 = p->xyz + 3 * (size_t)src[2];
+        p->if_area[f] = tri_area(x0, x1, x2);
+        for (int d = 0; d < 3; d++) cen[3 * f + d] = (x0[d] + x1[d] + x2[d]) / 3.0;
+    }
+    for (int64_t f = 0; f < n; f++) {
+        int64_t lo = f < n0 ? n0 : 0, hi = f < n0 ? n : n0;
+        int64_t best = -1;
+        double bd = 0.0;
+        for (int64_t g = lo; g < hi; g++) {
+            double dx = cen[3 * g] - cen[3 * f], dy = cen[3 * g + 1] - cen[3 * f + 1],
+                   dz = cen[3 * g + 2] - cen[3 * f + 2];
+            double d = dx * dx + dy * dy + dz * dz;
+            if (best < 0 || d < bd) { best = g; bd = d; }
+        }
+        p->if_sister[f] = best;
+    }
+    free(cen);
+    p->n_if = n;
+    return ORACLE_OK;
+}
+
+int64_t oracle_interface_sister(const oracle_problem *p, int64_t f)
+{
+    return (f >= 0 && f < p->n_if) ? p->if_sister[f] : -1;
 }
 
 double oracle_residual(const oracle_problem *p, const double *T, double *R)
@@ -433,6 +520,8 @@ double oracle_stable_dt(const oracle_problem *p)
         for (int a = 0; a < 4; a++) cnt[p->tets[4 * e + a] + 1] += 4;
     for (int64_t f = 0; f < p->n_faces; f++)
         for (int a = 0; a < 3; a++) cnt[p->faces[3 * f + a] + 1] += 3;
+    for (int64_t f = 0; f < p->n_if; f++)
+        for (int a = 0; a < 3; a++) cnt[p->if_faces[3 * f + a] + 1] += 6;
     for (int64_t i = 0; i < N; i++) cnt[i + 1] += cnt[i];
     int64_t total = cnt[N];
     int32_t *col = malloc((size_t)total * sizeof(int32_t));
@@ -455,6 +544,23 @@ double oracle_stable_dt(const oracle_problem *p)
             for (int b = 0; b < 3; b++) {
                 col[fill[i]] = p->faces[3 * f + b];
                 val[fill[i]] = hA12 * (a == b ? 2.0 : 1.0);
+                fill[i]++;
+            }
+        }
+    }
+    /* interface faces: the face matrix h A/12 (1 + delta) and the coupling
+     * to the sister's nodes, -h A/9 per (face node, sister node) pair */
+    for (int64_t f = 0; f < p->n_if; f++) {
+        double hA12 = p->if_h[f] * p->if_area[f] / 12.0, hA9 = p->if_h[f] * p->if_area[f] / 9.0;
+        const int32_t *sn = p->if_faces + 3 * p->if_sister[f];
+        for (int a = 0; a < 3; a++) {
+            int32_t i = p->if_faces[3 * f + a];
+            for (int b = 0; b < 3; b++) {
+                col[fill[i]] = p->if_faces[3 * f + b];
+                val[fill[i]] = hA12 * (a == b ? 2.0 : 1.0);
+                fill[i]++;
+                col[fill[i]] = sn[b];
+                val[fill[i]] = -hA9;
                 fill[i]++;
             }
         }

@@ -75,6 +75,10 @@ def _load():
         lib.oracle_liquid_fraction.argtypes = [ctypes.c_double] * 3
         lib.oracle_tet_matrix.restype = ctypes.c_int
         lib.oracle_tet_matrix.argtypes = [_dp, ctypes.c_double, _dp, _dp]
+        lib.oracle_set_interface.restype = ctypes.c_int
+        lib.oracle_set_interface.argtypes = [ctypes.c_void_p, _i64, _ip, _dp, _i64, _ip, _dp]
+        lib.oracle_interface_sister.restype = _i64
+        lib.oracle_interface_sister.argtypes = [ctypes.c_void_p, _i64]
         _lib = lib
         return lib
 
@@ -145,6 +149,17 @@ class OracleProblem:
         if not self._h:
             raise ValueError(f"oracle_create failed with status {st.value}")
         self._keep = (xyz, tets, mat, mats, fc, fh, ft, fq, dn, dT)
+        ia = getattr(prob, "iface_a", None)
+        if faces and ia is not None and ia.shape[0] > 0:
+            a, ha = _i(prob.iface_a), _d(prob.h_ia)
+            b, hb = _i(prob.iface_b), _d(prob.h_ib)
+            rc = lib.oracle_set_interface(self._h, a.shape[0], _pi(a), _pd(ha), b.shape[0],
+                                          _pi(b), _pd(hb))
+            if rc != 0:
+                raise ValueError(f"oracle_set_interface failed with status {rc}")
+            self.n_interface = a.shape[0] + b.shape[0]
+        else:
+            self.n_interface = 0
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -189,6 +204,12 @@ class OracleProblem:
             q = self._lib.oracle_residual_part(self._h, _pd(T), _pd(R), _pi(ep), _pi(fp),
                                                int(part))
         return R, q
+
+    def interface_sisters(self) -> np.ndarray:
+        """Sister of every interface face (side-A faces first, then side B),
+        as an index into that combined list."""
+        return np.array([self._lib.oracle_interface_sister(self._h, f)
+                         for f in range(self.n_interface)], np.int64)
 
     def stable_dt(self) -> float:
         return self._lib.oracle_stable_dt(self._h)

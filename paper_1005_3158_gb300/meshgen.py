@@ -46,6 +46,14 @@ class Problem:
         default_factory=lambda: np.zeros(0, np.int32))   # Dirichlet nodes, Eq. 3
     dir_T: np.ndarray = dataclasses.field(
         default_factory=lambda: np.zeros(0, np.float64))
+    # cast-mold interface (Eq. 8): two face lists lying on each other without
+    # matching nodes, with their interface coefficients
+    iface_a: np.ndarray = dataclasses.field(
+        default_factory=lambda: np.zeros((0, 3), np.int32))
+    iface_b: np.ndarray = dataclasses.field(
+        default_factory=lambda: np.zeros((0, 3), np.int32))
+    h_ia: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.float64))
+    h_ib: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.float64))
     name: str = ""
 
     @property
@@ -276,8 +284,13 @@ def concat_problems(probs) -> Problem:
     """The disjoint union of several problems (part k's node i becomes node
     offset_k + i; material ids offset by the parts' material counts)."""
     xyz, tets, mat, mats, faces, hh, ti, q, T0, dn, dT = ([] for _ in range(11))
+    ia, ib, ha, hb = [], [], [], []
     no = mo = 0
     for p in probs:
+        ia.append(p.iface_a + no)
+        ib.append(p.iface_b + no)
+        ha.append(p.h_ia)
+        hb.append(p.h_ib)
         xyz.append(p.xyz)
         tets.append(p.tets + no)
         mat.append(p.mat + mo)
@@ -296,7 +309,59 @@ def concat_problems(probs) -> Problem:
                    faces=np.concatenate(faces).astype(np.int32), h=np.concatenate(hh),
                    t_inf=np.concatenate(ti), q=np.concatenate(q), T0=np.concatenate(T0),
                    dir_nodes=np.concatenate(dn).astype(np.int32), dir_T=np.concatenate(dT),
+                   iface_a=np.concatenate(ia).astype(np.int32),
+                   iface_b=np.concatenate(ib).astype(np.int32),
+                   h_ia=np.concatenate(ha), h_ib=np.concatenate(hb),
                    name="+".join(p.name for p in probs))
+
+
+def cast_in_mold(n_cast: int = 9, n_mold: int = 8, h_i: float = 2000.0,
+                 side: float = 0.4) -> Problem:
+    """Cube casting meshed on its own inside a box mold with a cubic hole:
+    the two meshes meet at the hole's surface without matching nodes.
+
+    Mold: [0, side]^3 with n_mold hexes per axis (a multiple of 4), steel,
+    300 K, the hexes of the middle half [side/4, 3 side/4]^3 removed; Robin h =
+    1000 W/m^2K to 300 K on its outer faces.  Casting: that middle cube with
+    n_cast hexes per axis, alloy, 973 K.  Interface (Eq. 8): the casting's
+    boundary faces (side A) and the hole's faces (side B), both with h_i.
+    No jitter, so both face sets lie exactly on the hole's surface.
+    """
+    if n_mold % 4:
+        raise ValueError("n_mold must be a multiple of 4")
+    xm, tm, hexm, flm = box_grid(n_mold, n_mold, n_mold, side, side, side)
+    q = n_mold // 4
+    hi, hj, hk = hexm % n_mold, (hexm // n_mold) % n_mold, hexm // (n_mold * n_mold)
+    hole = ((hi >= q) & (hi < 3 * q) & (hj >= q) & (hj < 3 * q) & (hk >= q) & (hk < 3 * q))
+    tm = tm[~hole]   # hex_index is per tet
+    used = np.unique(tm)
+    remap = np.full(xm.shape[0], -1, np.int64)
+    remap[used] = np.arange(used.shape[0])
+    xm, flm, tm = xm[used], flm[used], remap[tm].astype(np.int32)
+    # boundary faces of the mold: faces of exactly one tet; outer ones lie in
+    # a box plane, the rest on the hole
+    allf = np.concatenate([np.delete(tm, k, axis=1) for k in range(4)])
+    key = np.sort(allf, axis=1)
+    _, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    bnd = allf[cnt[inv.ravel()] == 1]
+    outer = (flm[bnd[:, 0]] & flm[bnd[:, 1]] & flm[bnd[:, 2]]) != 0
+    robin, hole_faces = bnd[outer], bnd[~outer]
+    lc = side / 2
+    xc, tc, _, flc = box_grid(n_cast, n_cast, n_cast, lc, lc, lc)
+    xc = xc + side / 4
+    cast_faces = box_boundary_faces(tc, flc)
+    no = xm.shape[0]
+    xyz = np.concatenate([xm, xc])
+    tets = np.concatenate([tm, tc + no]).astype(np.int32)
+    mat = np.concatenate([np.ones(tm.shape[0], np.int32), np.zeros(tc.shape[0], np.int32)])
+    T0 = np.concatenate([np.full(xm.shape[0], T_MOLD), np.full(xc.shape[0], T_POUR)])
+    hh, ti, qq = _robin(robin)
+    return Problem(xyz=xyz, tets=tets, mat=mat, materials=np.array([ALLOY, STEEL]),
+                   faces=robin.astype(np.int32), h=hh, t_inf=ti, q=qq, T0=T0,
+                   iface_a=(cast_faces + no).astype(np.int32),
+                   iface_b=hole_faces.astype(np.int32),
+                   h_ia=np.full(cast_faces.shape[0], h_i), h_ib=np.full(hole_faces.shape[0], h_i),
+                   name=f"cast_in_mold_{n_cast}_{n_mold}")
 
 
 def block_with_cores(n: int = 220, n_cores: int = 32, seed: int = 1007,
