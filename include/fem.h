@@ -112,7 +112,7 @@ typedef struct {
                                   first call that needs the GPU) */
     int32_t smem_per_cta;      /* dynamic shared memory of one block-kernel CTA, bytes */
     int32_t n_instances;       /* parts of a batch (fem_batch_create), else 0 */
-    int32_t reserved_info;
+    int32_t n_interface_faces; /* faces given to fem_set_interface (both sides) */
 } fem_info;
 
 /* Create a mesh (Section 3: unstructured four-node tetrahedra).
@@ -157,6 +157,20 @@ fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_ma
  * exactly one tet, h < 0, or a non-finite value. */
 fem_status fem_set_boundary(fem_mesh *m, const int32_t *faces, int64_t n_faces,
                             const double *h, const double *T_inf, const double *q);
+
+/* Cast-mold interface (Eq. 8): two regions meshed separately meet on a
+ * surface without matching nodes.  faces_a [n_a][3] are the faces of one
+ * side (e.g. the casting's), faces_b [n_b][3] the other side's, each a face
+ * of exactly one tet; h_a / h_b their interface heat-transfer coefficients
+ * (W/m^2K, >= 0).  Every face exchanges heat like a Robin face with
+ * coefficient h_i whose ambient temperature is the mean temperature of its
+ * sister at step n: the face of the other side whose centroid is nearest
+ * (ties to the lower index), found once here (Section 3).  The heat shows
+ * in the energy account's boundary term.  n_a == n_b == 0 removes the
+ * interface.  Errors: FEM_EINVAL (ids out of range, a face that is not a
+ * face of exactly one tet, one side empty, h negative or not finite). */
+fem_status fem_set_interface(fem_mesh *m, const int32_t *faces_a, int64_t n_a, const double *h_a,
+                             const int32_t *faces_b, int64_t n_b, const double *h_b);
 
 /* Dirichlet boundary Gamma_T, Eq. 3: nodes [n] held at temperatures T [n]
  * (their enthalpy is never updated).  Replaces any previous set; n == 0
@@ -259,6 +273,9 @@ fem_status fem_rcm_order(int64_t n_nodes, const int32_t *tets, int64_t n_tets,
  *  13 inst_block_start int32 [n_inst+1] first block of each instance, in plan
  *                                     order
  *  14 inst_order int32 [n_inst]       plan position -> instance
+ *  15 if_sister  int32 [n_if]         sister of every interface face (index
+ *                                     into side A's faces followed by side
+ *                                     B's); both variants
  * *data points into the mesh (valid until the next fem_set_* or destroy);
  * *count is the number of scalar entries.  Builds the plan if needed. */
 fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t *count);

@@ -49,7 +49,8 @@ def _compile(src: str, tool: str, verbose: bool) -> str:
         cmd = [NVCC, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
                "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", path, "-o", obj]
     else:
-        cmd = ["g++", "-std=c++17", "-O3", "-fPIC", "-Wall", "-Wextra",
+        # -ffp-contract=off: host geometry rounds the same on every machine
+        cmd = ["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fPIC", "-Wall", "-Wextra",
                "-I", os.path.join(CUDA_HOME, "include"), *inc, "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

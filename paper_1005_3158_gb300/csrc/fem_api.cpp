@@ -86,9 +86,19 @@ struct fem_mesh {
     std::vector<double> Cn, mn, Lcn;  // lumped per node
     std::vector<uint8_t> rng_id;      // phase-range index per node
     std::vector<double> ranges;       // [nr][2]
-    // boundary
+    // boundary: Robin faces (fem_set_boundary) and interface faces
+    // (fem_set_interface, Eq. 8), kept apart and combined into faces/fa/fg
+    // (Robin first) for the plan, the uploads and the stable step
+    std::vector<int32_t> rb_faces;
+    std::vector<double> rb_fa, rb_fg;
+    int64_t F_rb = 0;
+    std::vector<int32_t> if_faces;    // [F_if][3], side A then side B
+    std::vector<double> if_fa, if_g;  // h_i A / 12, h_i A / 3
+    std::vector<int64_t> if_sister;   // index into the interface list
+    std::vector<int32_t> if_sister32; // fem_plan_array view
+    int64_t F_if = 0;
     std::vector<int32_t> faces;
-    std::vector<double> fa, fg;       // h A / 12, A/3 (h T_inf - q)
+    std::vector<double> fa, fg;       // h A / 12, A/3 (h T_inf - q); fg = 0 on interface faces
     // Dirichlet
     std::vector<uint8_t> is_dir;
     std::vector<double> dir_T;        // caller order (valid where is_dir)
@@ -121,6 +131,8 @@ struct fem_mesh {
             *dNodeOld = nullptr, *dConn = nullptr, *dFconn = nullptr, *dNfPtr = nullptr,
             *dNfIdx = nullptr;
     uint32_t *dSched = nullptr;
+    int32_t *dIfPos = nullptr, *dIfSis = nullptr;   // interface: face position, sister nodes
+    void *dIfG = nullptr;
     double *dEpart = nullptr, *dQcum = nullptr, *dIo = nullptr,
            *dDirT = nullptr, *dOut = nullptr;
     int *dErr = nullptr;
@@ -134,7 +146,7 @@ struct fem_mesh {
     // ---- batch of independent instances (fem_batch_create); n_inst == 0
     // for a plain mesh.  Ranges are in caller order, [n_inst + 1] each.
     int32_t n_inst = 0;
-    std::vector<int64_t> inst_node, inst_elem, inst_face;
+    std::vector<int64_t> inst_node, inst_elem;
     std::vector<int32_t> inst_plan_order;      // plan position -> caller instance
     std::vector<double> inst_stable, inst_dt;  // stable and chosen time steps
     std::vector<double> inst_t, inst_U0, inst_q; // time, initial energy, boundary heat
@@ -174,6 +186,8 @@ void release_device(fem_mesh *m)
     m->dEpart = m->dQcum = m->dIo = m->dDirT = m->dOut = nullptr;
     m->dErr = nullptr;
     m->dBlkDt = m->dShDt = nullptr;
+    m->dIfPos = m->dIfSis = nullptr;
+    m->dIfG = nullptr;
     m->dt_uploaded.clear();
     if (m->graph) cudaGraphExecDestroy(m->graph);
     m->graph = nullptr;
@@ -190,6 +204,28 @@ int default_block_elems(const fem_mesh *m)
 }
 
 bool is_block(const fem_mesh *m) { return m->opt.variant == FEM_VARIANT_BLOCK; }
+
+// faces/fa/fg = Robin faces, then interface faces (whose load term the
+// interface kernel rewrites every step)
+void combine_faces(fem_mesh *m)
+{
+    m->faces = m->rb_faces;
+    m->faces.insert(m->faces.end(), m->if_faces.begin(), m->if_faces.end());
+    m->fa = m->rb_fa;
+    m->fa.insert(m->fa.end(), m->if_fa.begin(), m->if_fa.end());
+    m->fg = m->rb_fg;
+    m->fg.insert(m->fg.end(), (size_t)m->F_if, 0.0);
+    m->F = m->F_rb + m->F_if;
+}
+
+// caller node ids of the sister face of every interface face [F_if][3]
+std::vector<int32_t> sister_nodes(const fem_mesh *m)
+{
+    std::vector<int32_t> out((size_t)(3 * m->F_if));
+    for (int64_t f = 0; f < m->F_if; f++)
+        for (int c = 0; c < 3; c++) out[3 * f + c] = m->if_faces[3 * (size_t)m->if_sister[f] + c];
+    return out;
+}
 
 // number of per-CTA cumulative boundary-heat entries
 int64_t n_qcum(const fem_mesh *m)
@@ -320,6 +356,31 @@ fem_status upload_nodes(fem_mesh *m)
             if (m->is_dir[old[i]]) dT[i] = m->dir_T[old[i]];
         if ((st = upload<double>(m, &m->dDirT, dT.data(), dT.size()))) return st;
     }
+    return FEM_OK;
+}
+
+// Interface faces (Eq. 8): the device position of each one in the face
+// arrays (face_order: position -> caller face), its h_i A / 3 and the
+// internal ids of its sister's nodes.
+template <typename real>
+fem_status upload_interface(fem_mesh *m, const std::vector<int32_t> &face_order)
+{
+    if (m->F_if == 0) return FEM_OK;
+    std::vector<int32_t> pos((size_t)m->F_if, -1), sis((size_t)(3 * m->F_if));
+    for (size_t q = 0; q < face_order.size(); q++)
+        if (face_order[q] >= m->F_rb) pos[(size_t)(face_order[q] - m->F_rb)] = (int32_t)q;
+    const auto &nn = node_new_of(m);
+    const std::vector<int32_t> sn = sister_nodes(m);
+    for (size_t k = 0; k < sn.size(); k++) sis[k] = nn[(size_t)sn[k]];
+    for (int32_t v : pos)
+        if (v < 0) return fail(FEM_EINVAL, "interface face bookkeeping failed");
+    std::vector<real> g(m->if_g.begin(), m->if_g.end());
+    fem_status st;
+    if ((st = upload<int32_t>(m, &m->dIfPos, pos.data(), pos.size()))) return st;
+    if ((st = upload<int32_t>(m, &m->dIfSis, sis.data(), sis.size()))) return st;
+    real *p = nullptr;
+    if ((st = upload<real>(m, &p, g.data(), g.size()))) return st;
+    m->dIfG = p;
     return FEM_OK;
 }
 
@@ -467,7 +528,7 @@ fem_status upload_block(fem_mesh *m)
     KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm), "occupancy query");
     if (per_sm < 1) return fail(FEM_EINVAL, "the block kernel does not fit on an SM; lower block_elems");
     m->ctas_per_sm = per_sm;
-    return FEM_OK;
+    return upload_interface<real>(m, bp.face_order);
 }
 
 template <typename real>
@@ -515,7 +576,7 @@ fem_status upload_flat(fem_mesh *m)
     m->n_node_ctas = (int)std::max<int64_t>(1, (m->N + 255) / 256);
     if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * (size_t)m->n_node_ctas))) return st;
     if ((st = upload<double>(m, &m->dQcum, nullptr, (size_t)m->n_node_ctas))) return st;
-    return FEM_OK;
+    return upload_interface<real>(m, fp.face_order);
 }
 
 template <typename real>
@@ -745,13 +806,28 @@ fem_status invalidate_plan(fem_mesh *m)
     return FEM_OK;
 }
 
-// Kernels of one step, in launch order: block variant {block step, shared
-// update}; flat variants {temperatures, element pass, node update}.
-int step_kernel_count(const fem_mesh *m) { return is_block(m) ? 2 : 3; }
+// Kernels of one step, in launch order: {interface faces, when there are
+// any}, then block variant {block step, shared update}; flat variants
+// {temperatures, element pass, node update}.
+int step_kernel_count(const fem_mesh *m) { return (is_block(m) ? 2 : 3) + (m->F_if > 0 ? 1 : 0); }
+
+template <typename real>
+fem_status launch_interface_kernel(fem_mesh *m, cudaStream_t st)
+{
+    KERNEL(launch_interface<real>(view_of<real>(m), (const real *)m->dC, (const real *)m->dLc, m->dPh,
+                                  (const real *)m->dRanges, (real *)m->dFg, m->dIfPos, m->dIfSis,
+                                  (const real *)m->dIfG, m->F_if, st),
+           "interface kernel");
+    return FEM_OK;
+}
 
 template <typename real>
 fem_status launch_step_kernel(fem_mesh *m, int k, double dt)
 {
+    if (m->F_if > 0) {
+        if (k == 0) return launch_interface_kernel<real>(m, m->stream);
+        k--;
+    }
     if (is_block(m)) {
         const BlockArgs<real> a = block_args<real>(m);
         if (k == 0)
@@ -1061,10 +1137,63 @@ fem_status fem_set_boundary(fem_mesh *m, const int32_t *faces, int64_t n_faces, 
     }
     fem_status st = invalidate_plan(m);
     if (st) return st;
-    m->faces.swap(fc);
-    m->fa.swap(fa);
-    m->fg.swap(fg);
-    m->F = n_faces;
+    m->rb_faces.swap(fc);
+    m->rb_fa.swap(fa);
+    m->rb_fg.swap(fg);
+    m->F_rb = n_faces;
+    combine_faces(m);
+    return ok();
+}
+
+fem_status fem_set_interface(fem_mesh *m, const int32_t *faces_a, int64_t n_a, const double *h_a,
+                             const int32_t *faces_b, int64_t n_b, const double *h_b)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (m->n_inst > 0) return fail(FEM_ESTATE, "a batch takes its materials and boundaries from its parts");
+    if (n_a < 0 || n_b < 0 || (n_a > 0) != (n_b > 0))
+        return fail(FEM_EINVAL, "an interface needs faces on both sides (or none)");
+    if (n_a > 0 && (!faces_a || !faces_b || !h_a || !h_b)) return fail(FEM_EINVAL, "NULL array argument");
+    if (n_a + n_b > INT32_MAX / 3) return fail(FEM_EINVAL, "too many interface faces");
+    const int64_t n = n_a + n_b;
+    std::vector<int32_t> fc((size_t)(3 * n));
+    std::vector<double> fa((size_t)n), g((size_t)n);
+    std::vector<int64_t> sis;
+    try {
+        for (int64_t f = 0; f < n; f++) {
+            const int32_t *src = f < n_a ? faces_a + 3 * f : faces_b + 3 * (f - n_a);
+            const double hh = f < n_a ? h_a[f] : h_b[f - n_a];
+            for (int c = 0; c < 3; c++) {
+                if (src[c] < 0 || src[c] >= m->N)
+                    return fail(FEM_EINVAL, "interface face %lld: node id out of range", (long long)f);
+                fc[3 * f + c] = src[c];
+            }
+            if (!std::isfinite(hh) || hh < 0)
+                return fail(FEM_EINVAL, "interface face %lld: h must be finite and >= 0", (long long)f);
+            const double *xa = &m->xyz[3 * (size_t)fc[3 * f]], *xb = &m->xyz[3 * (size_t)fc[3 * f + 1]],
+                         *xc = &m->xyz[3 * (size_t)fc[3 * f + 2]];
+            double u[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+            double v[3] = {xc[0] - xa[0], xc[1] - xa[1], xc[2] - xa[2]};
+            double nx = u[1] * v[2] - u[2] * v[1], ny = u[2] * v[0] - u[0] * v[2],
+                   nz = u[0] * v[1] - u[1] * v[0];
+            double A = 0.5 * std::sqrt(nx * nx + ny * ny + nz * nz);
+            fa[f] = hh * A / 12.0;
+            g[f] = A / 3.0 * hh;
+        }
+        std::vector<int32_t> owner;
+        std::string err = face_owners(n, fc.data(), m->tets.data(), m->adj, owner);
+        if (!err.empty()) return fail(FEM_EINVAL, "interface: %s", err.c_str());
+        interface_sisters(m->xyz.data(), n_a, n_b, fc.data(), sis);
+    } catch (const std::bad_alloc &) {
+        return fail(FEM_ENOMEM, "host allocation failed");
+    }
+    fem_status st = invalidate_plan(m);
+    if (st) return st;
+    m->if_faces.swap(fc);
+    m->if_fa.swap(fa);
+    m->if_g.swap(g);
+    m->if_sister.swap(sis);
+    m->F_if = n;
+    combine_faces(m);
     return ok();
 }
 
@@ -1158,9 +1287,11 @@ fem_status fem_stable_dt(fem_mesh *m, double *dt_out)
     if (!m || !dt_out) return fail(FEM_EINVAL, "NULL argument");
     if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
     try {
+        const std::vector<int32_t> sn = sister_nodes(m);
         *dt_out = gershgorin_dt(m->N, m->E, m->tets.data(), m->w.data(), m->adj, m->F,
                                 m->faces.data(), m->fa.data(), m->Cn.data(),
-                                m->is_dir.empty() ? nullptr : m->is_dir.data());
+                                m->is_dir.empty() ? nullptr : m->is_dir.data(), m->F_if,
+                                sn.data());
     } catch (const std::bad_alloc &) {
         return fail(FEM_ENOMEM, "host allocation failed");
     }
@@ -1303,6 +1434,8 @@ fem_status fem_mesh_info(fem_mesh *m, fem_info *out)
     out->ctas_per_sm = m->ctas_per_sm;
     out->smem_per_cta = (int32_t)m->smem_bytes;
     out->n_instances = m->n_inst;
+    out->n_faces = m->F_rb;
+    out->n_interface_faces = (int32_t)m->F_if;
     return ok();
 }
 
@@ -1345,6 +1478,10 @@ fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t
     case 3: return block ? give(m->bp.face_order.data(), m->bp.face_order.size())
                          : give(m->fp.face_order.data(), m->fp.face_order.size());
     default: break;
+    }
+    if (which == 15) {
+        m->if_sister32.assign(m->if_sister.begin(), m->if_sister.end());
+        return give(m->if_sister32.data(), m->if_sister32.size());
     }
     if (!block) return fail(FEM_EINVAL, "plan array %d exists only for the block variant", which);
     switch (which) {
@@ -1394,16 +1531,15 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
         m->n_inst = n_parts;
         m->inst_node.assign(1, 0);
         m->inst_elem.assign(1, 0);
-        m->inst_face.assign(1, 0);
         for (int32_t i = 0; i < n_parts; i++) {
             m->inst_node.push_back(m->inst_node.back() + parts[i]->N);
             m->inst_elem.push_back(m->inst_elem.back() + parts[i]->E);
-            m->inst_face.push_back(m->inst_face.back() + parts[i]->F);
         }
         m->N = m->inst_node.back();
         m->E = m->inst_elem.back();
-        m->F = m->inst_face.back();
-        if (m->N > INT32_MAX - 1 || m->E > INT32_MAX / 8 || m->F > INT32_MAX / 3)
+        int64_t F_all = 0;
+        for (int32_t i = 0; i < n_parts; i++) F_all += parts[i]->F;
+        if (m->N > INT32_MAX - 1 || m->E > INT32_MAX / 8 || F_all > INT32_MAX / 3)
             return fail(FEM_EINVAL, "batch too large for 32-bit ids");
         // distinct phase-change ranges over all parts
         std::vector<std::vector<uint8_t>> rmap((size_t)n_parts);
@@ -1439,9 +1575,14 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
             m->mn.insert(m->mn.end(), p->mn.begin(), p->mn.end());
             m->Lcn.insert(m->Lcn.end(), p->Lcn.begin(), p->Lcn.end());
             for (uint8_t r : p->rng_id) m->rng_id.push_back(rmap[(size_t)i].empty() ? 0 : rmap[(size_t)i][r]);
-            for (int32_t v : p->faces) m->faces.push_back(v + no);
-            m->fa.insert(m->fa.end(), p->fa.begin(), p->fa.end());
-            m->fg.insert(m->fg.end(), p->fg.begin(), p->fg.end());
+            for (int32_t v : p->rb_faces) m->rb_faces.push_back(v + no);
+            m->rb_fa.insert(m->rb_fa.end(), p->rb_fa.begin(), p->rb_fa.end());
+            m->rb_fg.insert(m->rb_fg.end(), p->rb_fg.begin(), p->rb_fg.end());
+            const int64_t io = (int64_t)m->if_fa.size();
+            for (int32_t v : p->if_faces) m->if_faces.push_back(v + no);
+            m->if_fa.insert(m->if_fa.end(), p->if_fa.begin(), p->if_fa.end());
+            m->if_g.insert(m->if_g.end(), p->if_g.begin(), p->if_g.end());
+            for (int64_t v : p->if_sister) m->if_sister.push_back(v + io);
             if (any_dir) {
                 if (p->is_dir.empty()) {
                     m->is_dir.insert(m->is_dir.end(), (size_t)p->N, 0);
@@ -1454,13 +1595,17 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
             m->pending.insert(m->pending.end(), p->pending.begin(), p->pending.end());
             m->bw_input = std::max(m->bw_input, p->bw_input);
             m->bw_rank = std::max(m->bw_rank, p->bw_rank);
-            double dt = 0.0;
-            dt = gershgorin_dt(p->N, p->E, p->tets.data(), p->w.data(), p->adj, p->F,
-                               p->faces.data(), p->fa.data(), p->Cn.data(),
-                               p->is_dir.empty() ? nullptr : p->is_dir.data());
+            const std::vector<int32_t> sn = sister_nodes(p);
+            const double dt = gershgorin_dt(p->N, p->E, p->tets.data(), p->w.data(), p->adj, p->F,
+                                            p->faces.data(), p->fa.data(), p->Cn.data(),
+                                            p->is_dir.empty() ? nullptr : p->is_dir.data(),
+                                            p->F_if, sn.data());
             m->inst_stable.push_back(dt);
         }
         if (m->ranges.empty()) { m->ranges.push_back(0.0); m->ranges.push_back(0.0); }
+        m->F_rb = (int64_t)m->rb_fa.size();
+        m->F_if = (int64_t)m->if_fa.size();
+        combine_faces(m.get());
         build_node_elems(m->N, m->E, m->tets.data(), m->adj);
         m->have_mat = true;
         m->state = fem_mesh::ST_PENDING_T;
@@ -1531,6 +1676,10 @@ fem_status advance_launches(fem_mesh *m, const std::vector<int64_t> &nk, cudaStr
     int64_t max_n = 0;
     for (int64_t v : nk) max_n = std::max(max_n, v);
     for (int64_t step = 0; step < max_n; step++) {
+        if (m->F_if > 0) {
+            fem_status fs = launch_interface_kernel<real>(m, st);
+            if (fs) return fs;
+        }
         for (int64_t k0 = 0; k0 < K;) {
             if (nk[(size_t)k0] <= step) { k0++; continue; }
             int64_t k1 = k0;

@@ -175,6 +175,12 @@ int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes
                         void *stream);
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream);
+// Interface faces (Eq. 8): fg[pos[f]] = g[f] * mean T of nodes sis[f][0..2]
+// (internal ids), before every step's element pass.
+template <typename real>
+int launch_interface(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
+                     const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
+                     const real *g, int64_t n, void *stream);
 template <typename real>
 int configure_block_kernel(int threads, size_t smem_bytes);
 template <typename real>

@@ -463,6 +463,28 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
             for (int k = k0[j]; k < k1[j]; ++k) a.Eloc[__ldg(a.mpos + k)] = E[j];
 }
 
+// Interface faces (Eq. 8): every interface face is a Robin face whose
+// ambient temperature is the mean temperature of its sister face (the
+// nearest face of the other region, Section 3) at step n.  This kernel
+// writes the face's load term A/3 h_i T_sister into the face arrays before
+// the step's element pass; its h_i A / 12 matrix term is static.
+template <typename real>
+__global__ void k_interface(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
+                            const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
+                            const real *g, int64_t n)
+{
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        real T = real(0);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const int32_t i = sis[3 * f + c];
+            T += temperature_of(v.E(i), C[i], Lc[i], ph[i], ranges);
+        }
+        fg[pos[f]] = g[f] * (T / real(3));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Flat variants (atomic / coloured), for comparison
 // ---------------------------------------------------------------------------
@@ -690,6 +712,17 @@ int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes
 constexpr int kShNT = 256, kShNPT = 2;   // exchange kernel: threads, nodes per thread
 
 template <typename real>
+int launch_interface(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
+                     const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
+                     const real *g, int64_t n, void *stream)
+{
+    if (n > 0)
+        k_interface<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, C, Lc, ph, ranges, fg,
+                                                                           pos, sis, g, n);
+    return (int)cudaGetLastError();
+}
+
+template <typename real>
 int launch_mirror_copies(const BlockArgs<real> &a, void *stream)
 {
     const int64_t n = a.s_end - a.s_first, per = (int64_t)kShNT * kShNPT;
@@ -797,6 +830,9 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
     template int configure_block_kernel<real>(int, size_t);                                       \
     template int block_kernel_occupancy<real>(int, size_t, int *);                                \
     template int launch_mirror_copies<real>(const BlockArgs<real> &, void *);                     \
+    template int launch_interface<real>(StateView<real>, const real *, const real *,              \
+                                        const uint8_t *, const real *, real *, const int32_t *,   \
+                                        const int32_t *, const real *, int64_t, void *);          \
     template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *); \
     template int launch_shared_update<real>(const BlockArgs<real> &, double, void *);             \
     template int launch_flat_temperature<real>(const FlatArgs<real> &, void *);                   \

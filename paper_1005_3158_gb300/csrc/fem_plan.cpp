@@ -781,7 +781,8 @@ std::string build_flat_plan(int64_t N, int64_t E, const int32_t *tets,
 
 double gershgorin_dt(int64_t N, int64_t E, const int32_t *tets, const double *w,
                      const NodeElems &adj, int64_t F, const int32_t *faces, const double *fa,
-                     const double *C, const uint8_t *is_dir)
+                     const double *C, const uint8_t *is_dir, int64_t F_if,
+                     const int32_t *sister_nodes)
 {
     (void)E;
     // node -> faces
@@ -824,12 +825,103 @@ double gershgorin_dt(int64_t N, int64_t E, const int32_t *tets, const double *w,
                 int32_t j = faces[3 * f + c];
                 add(j, j == i ? 2.0 * fa[f] : fa[f]);
             }
+            // an interface face also couples to its sister's nodes through
+            // the ambient temperature: -h A / 9 = -(4/3) fa per pair
+            const int64_t fi = f - (F - F_if);
+            if (fi >= 0)
+                for (int c = 0; c < 3; c++) add(sister_nodes[3 * fi + c], -4.0 / 3.0 * fa[f]);
         }
         double s = 0.0;
         for (double v : val) s += std::fabs(v);
         lam = std::max(lam, s / C[i]);
     }
     return lam > 0.0 ? 2.0 / lam : INFINITY;
+}
+
+void interface_sisters(const double *xyz, int64_t n_a, int64_t n_b, const int32_t *faces,
+                       std::vector<int64_t> &sister)
+{
+    const int64_t n = n_a + n_b;
+    sister.assign((size_t)n, -1);
+    if (n_a == 0 || n_b == 0) return;
+    std::vector<double> cen((size_t)(3 * n));
+    for (int64_t f = 0; f < n; f++) {
+        const double *x0 = xyz + 3 * (size_t)faces[3 * f], *x1 = xyz + 3 * (size_t)faces[3 * f + 1],
+                     *x2 = xyz + 3 * (size_t)faces[3 * f + 2];
+        for (int d = 0; d < 3; d++) cen[3 * f + d] = (x0[d] + x1[d] + x2[d]) / 3.0;
+    }
+    // one uniform grid per side over its centroids; a query scans rings of
+    // cells around its own cell until no unscanned cell can be nearer
+    struct Grid {
+        double lo[3], h;
+        int64_t n[3];
+        std::vector<int64_t> ptr, idx;
+    };
+    auto build = [&](int64_t f0, int64_t cnt, Grid &g) {
+        double hi[3];
+        for (int d = 0; d < 3; d++) g.lo[d] = hi[d] = cen[3 * f0 + d];
+        for (int64_t f = f0; f < f0 + cnt; f++)
+            for (int d = 0; d < 3; d++) {
+                g.lo[d] = std::min(g.lo[d], cen[3 * f + d]);
+                hi[d] = std::max(hi[d], cen[3 * f + d]);
+            }
+        double ext = 0.0;
+        for (int d = 0; d < 3; d++) ext = std::max(ext, hi[d] - g.lo[d]);
+        // about two centroids per occupied cell of a surface
+        g.h = std::max(ext / std::max(1.0, std::sqrt((double)cnt / 2.0)), 1e-30);
+        for (;;) {   // at most ~8 cells per centroid
+            for (int d = 0; d < 3; d++) g.n[d] = (int64_t)std::floor((hi[d] - g.lo[d]) / g.h) + 1;
+            if ((double)g.n[0] * (double)g.n[1] * (double)g.n[2] <= 8.0 * (double)cnt + 64.0) break;
+            g.h *= 1.5;
+        }
+        const int64_t cells = g.n[0] * g.n[1] * g.n[2];
+        g.ptr.assign((size_t)cells + 1, 0);
+        auto cell_of = [&](int64_t f) {
+            int64_t c[3];
+            for (int d = 0; d < 3; d++)
+                c[d] = std::min(g.n[d] - 1, (int64_t)std::floor((cen[3 * f + d] - g.lo[d]) / g.h));
+            return c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+        };
+        for (int64_t f = f0; f < f0 + cnt; f++) g.ptr[(size_t)cell_of(f) + 1]++;
+        for (int64_t c = 0; c < cells; c++) g.ptr[c + 1] += g.ptr[c];
+        g.idx.assign((size_t)cnt, 0);
+        std::vector<int64_t> fill(g.ptr.begin(), g.ptr.end() - 1);
+        for (int64_t f = f0; f < f0 + cnt; f++) g.idx[(size_t)fill[(size_t)cell_of(f)]++] = f;
+    };
+    Grid ga, gb;
+    build(0, n_a, ga);
+    build(n_a, n_b, gb);
+    for (int64_t f = 0; f < n; f++) {
+        const Grid &g = f < n_a ? gb : ga;
+        int64_t c[3];
+        for (int d = 0; d < 3; d++)
+            c[d] = std::max<int64_t>(0, std::min(g.n[d] - 1,
+                                                 (int64_t)std::floor((cen[3 * f + d] - g.lo[d]) / g.h)));
+        int64_t best = -1;
+        double bd = 0.0;
+        const int64_t rmax = std::max(g.n[0], std::max(g.n[1], g.n[2]));
+        for (int64_t r = 0; r <= rmax; r++) {
+            // every cell at Chebyshev distance r from c
+            for (int64_t k = c[2] - r; k <= c[2] + r; k++)
+                for (int64_t j = c[1] - r; j <= c[1] + r; j++)
+                    for (int64_t i = c[0] - r; i <= c[0] + r; i++) {
+                        if (std::max(std::abs(i - c[0]), std::max(std::abs(j - c[1]), std::abs(k - c[2]))) != r)
+                            continue;
+                        if (i < 0 || j < 0 || k < 0 || i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
+                        const int64_t cell = i + g.n[0] * (j + g.n[1] * k);
+                        for (int64_t q = g.ptr[(size_t)cell]; q < g.ptr[(size_t)cell + 1]; q++) {
+                            const int64_t o = g.idx[(size_t)q];
+                            const double dx = cen[3 * o] - cen[3 * f], dy = cen[3 * o + 1] - cen[3 * f + 1],
+                                         dz = cen[3 * o + 2] - cen[3 * f + 2];
+                            const double dd = dx * dx + dy * dy + dz * dz;
+                            if (best < 0 || dd < bd || (dd == bd && o < best)) { best = o; bd = dd; }
+                        }
+                    }
+            // cells beyond ring r are at least r * h away from the query
+            if (best >= 0 && (double)r * g.h > 0.0 && ((double)r * g.h) * ((double)r * g.h) > bd) break;
+        }
+        sister[(size_t)f] = best;
+    }
 }
 
 }  // namespace fem

@@ -108,9 +108,18 @@ std::string build_flat_plan(int64_t N, int64_t E, const int32_t *tets,
                             FlatPlan &out);
 
 // Gershgorin stable step (reading of Eq. 13): 2 / max_i sum_j |(K+H)_ij| / C_i.
-// w: [E][6] conductances in the caller's corner order; fa: [F] h A/12.
+// w: [E][6] conductances in the caller's corner order; fa: [F] h A/12.  The
+// last F_if faces are interface faces (Eq. 8) whose ambient temperature is
+// the mean of the sister face's nodes sister_nodes[F_if][3].
 double gershgorin_dt(int64_t N, int64_t E, const int32_t *tets, const double *w,
                      const NodeElems &adj, int64_t F, const int32_t *faces,
-                     const double *fa, const double *C, const uint8_t *is_dir);
+                     const double *fa, const double *C, const uint8_t *is_dir,
+                     int64_t F_if = 0, const int32_t *sister_nodes = nullptr);
+
+// Sister of every interface face (Eq. 8, Section 3): faces [n_a + n_b][3]
+// (side A first), the index of the other side's face with the nearest
+// centroid, ties to the lower index.
+void interface_sisters(const double *xyz, int64_t n_a, int64_t n_b, const int32_t *faces,
+                       std::vector<int64_t> &sister);
 
 }  // namespace fem

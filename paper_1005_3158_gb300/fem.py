@@ -27,6 +27,7 @@ PRECISIONS = {"fp64": FEM_FP64, "f64": FEM_FP64, "fp32": FEM_FP32, "f32": FEM_FP
 # names declared in include/fem.h
 ABI_SYMBOLS = (
     "fem_mesh_create", "fem_mesh_create_ex", "fem_set_materials", "fem_set_boundary",
+    "fem_set_interface",
     "fem_set_dirichlet", "fem_set_temperature", "fem_stable_dt", "fem_step", "fem_step_profile",
     "fem_get_temperature", "fem_get_enthalpy", "fem_get_energy", "fem_set_stream",
     "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
@@ -54,7 +55,7 @@ class FemInfo(ctypes.Structure):
         "bandwidth_internal", "max_block_elems", "device_bytes")] + [
         (n, ctypes.c_int32) for n in ("precision", "variant", "threads", "reorder",
                                       "ctas_per_sm", "smem_per_cta", "n_instances",
-                                      "reserved_info")]
+                                      "n_interface_faces")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -83,6 +84,7 @@ def _load():
         "fem_set_materials": [P, ctypes.POINTER(FemMaterial), ctypes.c_int32],
         "fem_set_boundary": [P, ip, i64, dp, dp, dp],
         "fem_set_dirichlet": [P, ip, i64, dp],
+        "fem_set_interface": [P, ip, i64, dp, ip, i64, dp],
         "fem_set_temperature": [P, dp],
         "fem_stable_dt": [P, dp],
         "fem_step": [P, i64, ctypes.c_double],
@@ -204,6 +206,13 @@ def fem_set_dirichlet(h, nodes, T):
     _check(_lib.fem_set_dirichlet(h, _pi(nodes), nodes.shape[0], _pd(T)))
 
 
+def fem_set_interface(h, faces_a, h_a, faces_b, h_b):
+    fa_, fb_ = _i(faces_a).reshape(-1, 3), _i(faces_b).reshape(-1, 3)
+    ha, hb = _d(h_a), _d(h_b)
+    _check(_lib.fem_set_interface(h, _pi(fa_), fa_.shape[0], _pd(ha), _pi(fb_), fb_.shape[0],
+                                  _pd(hb)))
+
+
 def fem_set_temperature(h, T0):
     T0 = _d(T0)
     _check(_lib.fem_set_temperature(h, _pd(T0)))
@@ -282,11 +291,11 @@ def fem_rcm_order(n_nodes, tets):
 
 _PLAN_TYPES = {0: np.int32, 1: np.int32, 2: np.int32, 3: np.int32, 4: np.int32, 5: np.int32,
                6: np.int32, 7: np.int32, 8: np.uint16, 9: np.int32, 10: np.int32, 11: np.int32,
-               12: np.int32, 13: np.int32, 14: np.int32}
+               12: np.int32, 13: np.int32, 14: np.int32, 15: np.int32}
 PLAN_ARRAYS = {"node_new": 0, "blocks": 1, "elem_order": 2, "face_order": 3, "copy_node": 4,
                "sh_ptr": 5, "sh_copy": 6, "grp": 7, "sched": 8, "elem_nodes": 9,
                "face_nodes": 10, "copy_pos": 11, "block_inst": 12, "inst_block_start": 13,
-               "inst_order": 14}
+               "inst_order": 14, "if_sister": 15}
 
 
 def fem_plan_array(h, which):
@@ -374,6 +383,9 @@ class Mesh:
                 fem_set_boundary(self.h, prob.faces, prob.h, prob.t_inf, prob.q)
             if dirichlet and prob.dir_nodes.shape[0] > 0:
                 fem_set_dirichlet(self.h, prob.dir_nodes, prob.dir_T)
+            ia = getattr(prob, "iface_a", None)
+            if faces and ia is not None and ia.shape[0] > 0:
+                fem_set_interface(self.h, prob.iface_a, prob.h_ia, prob.iface_b, prob.h_ib)
             if set_temperature:
                 fem_set_temperature(self.h, prob.T0)
         except Exception:

@@ -1,0 +1,49 @@
+"""Library interface (Eq. 8) on the host: the sister of every interface
+face, the stable step and the plan agree with the oracle's own search and
+bound (no GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1005_3158_gb300 import meshgen as mg
+
+fem = pytest.importorskip("paper_1005_3158_gb300.fem")
+
+from test_host_plan import _check_plan  # noqa: E402
+
+
+@pytest.mark.parametrize("nc,nm", [(5, 8), (4, 8), (7, 12), (3, 4)])
+@pytest.mark.parametrize("variant", ["block", "atomic"])
+def test_sisters_and_stable_dt_match_oracle(nc, nm, variant):
+    p = mg.cast_in_mold(n_cast=nc, n_mold=nm)
+    o = oracle.OracleProblem(p)
+    with fem.Mesh(p, "fp64", variant=variant, block_elems=128) as m:
+        assert np.array_equal(m.plan("if_sister"), o.interface_sisters())
+        assert m.stable_dt() == pytest.approx(o.stable_dt(), rel=1e-13)
+        info = m.info()
+        assert info["n_faces"] == p.faces.shape[0]
+        assert info["n_interface_faces"] == p.iface_a.shape[0] + p.iface_b.shape[0]
+        if variant == "block":
+            _check_plan(p, m)
+
+
+def test_interface_validation():
+    p = mg.cast_in_mold(n_cast=3, n_mold=4)
+    with fem.Mesh(p, "fp64") as m:
+        a, b = p.iface_a, p.iface_b
+        ha, hb = p.h_ia, p.h_ib
+        with pytest.raises(fem.FemError):
+            fem.fem_set_interface(m.h, a, ha, np.zeros((0, 3)), np.zeros(0))   # one side empty
+        bad = a.copy()
+        bad[0] = [0, 1, 2] if not {0, 1, 2} <= set(a[0]) else [0, 1, 3]
+        with pytest.raises(fem.FemError):
+            fem.fem_set_interface(m.h, np.array([[0, 1, 9999]]), ha[:1], b, hb)   # id out of range
+        with pytest.raises(fem.FemError):
+            fem.fem_set_interface(m.h, a, -ha, b, hb)                           # negative h
+        # removing the interface gives the plain mesh's stable step
+        fem.fem_set_interface(m.h, np.zeros((0, 3)), np.zeros(0), np.zeros((0, 3)), np.zeros(0))
+        q = mg.cast_in_mold(n_cast=3, n_mold=4)
+        q.iface_a = q.iface_b = np.zeros((0, 3), np.int32)
+        q.h_ia = q.h_ib = np.zeros(0)
+        assert m.stable_dt() == pytest.approx(oracle.OracleProblem(q).stable_dt(), rel=1e-13)
+        assert m.info()["n_interface_faces"] == 0

@@ -104,8 +104,11 @@ def _check_plan(p, m):
     node_old[node_new] = np.arange(p.n_nodes)
     assert np.array_equal(np.sort(node_new), np.arange(p.n_nodes))
     n_int = int(blocks[:, 5].sum())
+    # Robin faces, then interface faces (side A, side B)
+    allf = np.concatenate([p.faces, getattr(p, "iface_a", np.zeros((0, 3), np.int32)),
+                           getattr(p, "iface_b", np.zeros((0, 3), np.int32))]).astype(np.int64)
     seen_elem = np.zeros(p.n_tets, int)
-    seen_face = np.zeros(p.n_faces, int)
+    seen_face = np.zeros(allf.shape[0], int)
     touched_by = [set() for _ in range(p.n_nodes)]
     for b, (e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad, nep, r0, nrounds, _) in enumerate(blocks):
         assert e0 % 8 == 0 and f0 % 8 == 0 and ne_pad >= ne and nf_pad >= nf
@@ -151,7 +154,7 @@ def _check_plan(p, m):
             f = face_order[f0 + i]
             seen_face[f] += 1
             for c in range(3):
-                assert slot_owner[4 * ne_pad + c * nf_pad + i] == node_new[p.faces[f, c]]
+                assert slot_owner[4 * ne_pad + c * nf_pad + i] == node_new[allf[f, c]]
         # padding slots are never scheduled
         used = np.zeros(nslot, bool)
         for c in range(4):
