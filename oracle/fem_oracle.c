@@ -24,6 +24,9 @@
  *   - the explicit update E += dt (F - K T) (Eq. 14 with theta = 0 in Eq. 10,
  *     written for the enthalpy unknown of Eq. 5),
  *   - Dirichlet nodes (Eq. 3) held at E(T_D),
+ *   - optional temperature-dependent conductivity k(T) per material (Eq. 9
+ *     allows K(T)): a piecewise-linear table evaluated at the element's mean
+ *     temperature at step n, K^e(T) = k(T_mean) x (K^e for k = 1),
  *   - the cast-mold interface of Eq. 8: faces of two regions meshed
  *     separately, each exchanging h_i (T_sister - T) with the mean
  *     temperature of its sister, the nearest face of the other region
@@ -44,6 +47,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#define ORACLE_KT_MAX 16
 #define ORACLE_OK 0
 #define ORACLE_EINVAL 1
 #define ORACLE_ENOMEM 2
@@ -54,6 +58,13 @@ typedef struct oracle_problem {
     /* element data */
     int32_t *tets;   /* [E][4], re-oriented to positive volume */
     double *Ke;      /* [E][4][4] dense conductance matrices */
+    double *Kg;      /* [E][4][4] the same for k = 1 (geometric part) */
+    int32_t *emat;   /* [E] material id */
+    /* optional conductivity tables k(T) per material (Eq. 9's K(T)):
+     * kt_n[m] points (kt_T ascending, kt_k), 0 = constant k */
+    int32_t n_mat;
+    int32_t *kt_n;
+    double *kt_T, *kt_k;  /* [n_mat][ORACLE_KT_MAX] */
     double *vol;     /* [E] */
     /* lumped nodal data */
     double *C;       /* sensible heat capacity, J/K */
@@ -183,7 +194,8 @@ static double tri_area(const double *xa, const double *xb, const double *xc)
 void oracle_destroy(oracle_problem *p)
 {
     if (!p) return;
-    free(p->tets); free(p->Ke); free(p->vol);
+    free(p->tets); free(p->Ke); free(p->Kg); free(p->emat); free(p->vol);
+    free(p->kt_n); free(p->kt_T); free(p->kt_k);
     free(p->C); free(p->m); free(p->Lc); free(p->Ts); free(p->Tl);
     free(p->faces); free(p->fh); free(p->ftinf); free(p->fq); free(p->farea);
     free(p->if_faces); free(p->if_h); free(p->if_area); free(p->if_sister); free(p->xyz);
@@ -215,6 +227,12 @@ oracle_problem *oracle_create(int64_t n_nodes, const double *xyz,
     p->xyz = malloc(3 * N * sizeof(double));
     p->tets = malloc(4 * E * sizeof(int32_t));
     p->Ke = malloc(16 * E * sizeof(double));
+    p->Kg = malloc(16 * E * sizeof(double));
+    p->emat = malloc(E * sizeof(int32_t));
+    p->n_mat = n_mat;
+    p->kt_n = calloc((size_t)n_mat, sizeof(int32_t));
+    p->kt_T = calloc((size_t)n_mat * ORACLE_KT_MAX, sizeof(double));
+    p->kt_k = calloc((size_t)n_mat * ORACLE_KT_MAX, sizeof(double));
     p->vol = malloc(E * sizeof(double));
     p->C = calloc(N, sizeof(double));
     p->m = calloc(N, sizeof(double));
@@ -231,7 +249,8 @@ oracle_problem *oracle_create(int64_t n_nodes, const double *xyz,
     p->E = calloc(N, sizeof(double));
     p->T = calloc(N, sizeof(double));
     p->R = calloc(N, sizeof(double));
-    if (!p->xyz || !p->tets || !p->Ke || !p->vol || !p->C || !p->m || !p->Lc || !p->Ts || !p->Tl ||
+    if (!p->xyz || !p->tets || !p->Ke || !p->Kg || !p->emat || !p->kt_n || !p->kt_T || !p->kt_k ||
+        !p->vol || !p->C || !p->m || !p->Lc || !p->Ts || !p->Tl ||
         !p->faces || !p->fh || !p->ftinf || !p->fq || !p->farea || !p->is_dir ||
         !p->T_dir || !p->E || !p->T || !p->R) {
         oracle_destroy(p); *status = ORACLE_ENOMEM; return NULL;
@@ -270,6 +289,8 @@ oracle_problem *oracle_create(int64_t n_nodes, const double *xyz,
         for (int a = 0; a < 4; a++)
             for (int d = 0; d < 3; d++) x[3 * a + d] = xyz[3 * (size_t)n[a] + d];
         oracle_tet_matrix(x, k, p->Ke + 16 * e, &V);
+        oracle_tet_matrix(x, 1.0, p->Kg + 16 * e, &V);
+        p->emat[e] = mat[e];
         p->vol[e] = V;
         for (int a = 0; a < 4; a++) p->tets[4 * e + a] = n[a];
         /* row-sum lumping of the consistent capacity rho c V/20 (1 + delta):
@@ -332,6 +353,36 @@ void oracle_set_temperature(oracle_problem *p, const double *T0)
 /* Right-hand side F - K T (Eqs. 4, 9, 15-18)                                */
 /* ------------------------------------------------------------------------ */
 
+/* Temperature-dependent conductivity (Eq. 9 allows K(T)): material mt's
+ * table of n points (T_j ascending, k_j), linear between points, constant
+ * beyond the first and last.  Returns ORACLE_EINVAL for a bad table. */
+int oracle_set_conductivity(oracle_problem *p, int32_t mt, int32_t n, const double *T,
+                            const double *k)
+{
+    if (mt < 0 || mt >= p->n_mat || n < 0 || n > ORACLE_KT_MAX) return ORACLE_EINVAL;
+    for (int32_t j = 0; j < n; j++) {
+        if (!(k[j] > 0.0) || !isfinite(T[j]) || !isfinite(k[j])) return ORACLE_EINVAL;
+        if (j > 0 && !(T[j] > T[j - 1])) return ORACLE_EINVAL;
+    }
+    p->kt_n[mt] = n;
+    for (int32_t j = 0; j < n; j++) {
+        p->kt_T[ORACLE_KT_MAX * mt + j] = T[j];
+        p->kt_k[ORACLE_KT_MAX * mt + j] = k[j];
+    }
+    return ORACLE_OK;
+}
+
+double oracle_conductivity(const oracle_problem *p, int32_t mt, double T)
+{
+    int32_t n = p->kt_n[mt];
+    const double *Tj = p->kt_T + ORACLE_KT_MAX * mt, *kj = p->kt_k + ORACLE_KT_MAX * mt;
+    if (T <= Tj[0]) return kj[0];
+    if (T >= Tj[n - 1]) return kj[n - 1];
+    int32_t j = 0;
+    while (T > Tj[j + 1]) j++;
+    return kj[j] + (kj[j + 1] - kj[j]) * (T - Tj[j]) / (Tj[j + 1] - Tj[j]);
+}
+
 /* R = F - K T for the nodal temperatures T, summing element contributions
  * one element at a time (Eq. 18) and then the Robin faces.  Elements with
  * elem_part[e] != part (and faces with face_part[f] != part) are skipped
@@ -346,6 +397,19 @@ double oracle_residual_part(const oracle_problem *p, const double *T, double *R,
     for (int64_t e = 0; e < p->n_tets; e++) {
         if (elem_part && elem_part[e] != part) continue;
         const int32_t *n = p->tets + 4 * e;
+        const int32_t mt = p->emat[e];
+        if (p->kt_n[mt] > 0) {
+            /* K^e(T) = k(mean element temperature at step n) x geometric part */
+            double Tm = (T[n[0]] + T[n[1]] + T[n[2]] + T[n[3]]) / 4.0;
+            double kk = oracle_conductivity(p, mt, Tm);
+            const double *K = p->Kg + 16 * e;
+            for (int a = 0; a < 4; a++) {
+                double s = 0.0;
+                for (int b = 0; b < 4; b++) s += kk * K[4 * a + b] * T[n[b]];
+                R[n[a]] -= s;
+            }
+            continue;
+        }
         const double *K = p->Ke + 16 * e;
         for (int a = 0; a < 4; a++) {
             double s = 0.0;
@@ -531,9 +595,15 @@ double oracle_stable_dt(const oracle_problem *p)
     for (int64_t e = 0; e < p->n_tets; e++)
         for (int a = 0; a < 4; a++) {
             int32_t i = p->tets[4 * e + a];
+            /* with a k(T) table the largest k of the table bounds K^e(T) */
+            int32_t mt = p->emat[e];
+            double kmax = 0.0;
+            for (int32_t j = 0; j < p->kt_n[mt]; j++)
+                if (p->kt_k[ORACLE_KT_MAX * mt + j] > kmax) kmax = p->kt_k[ORACLE_KT_MAX * mt + j];
             for (int b = 0; b < 4; b++) {
                 col[fill[i]] = p->tets[4 * e + b];
-                val[fill[i]] = p->Ke[16 * e + 4 * a + b];
+                val[fill[i]] = p->kt_n[mt] > 0 ? kmax * p->Kg[16 * e + 4 * a + b]
+                                               : p->Ke[16 * e + 4 * a + b];
                 fill[i]++;
             }
         }

@@ -77,6 +77,10 @@ def _load():
         lib.oracle_tet_matrix.argtypes = [_dp, ctypes.c_double, _dp, _dp]
         lib.oracle_set_interface.restype = ctypes.c_int
         lib.oracle_set_interface.argtypes = [ctypes.c_void_p, _i64, _ip, _dp, _i64, _ip, _dp]
+        lib.oracle_set_conductivity.restype = ctypes.c_int
+        lib.oracle_set_conductivity.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, _dp, _dp]
+        lib.oracle_conductivity.restype = ctypes.c_double
+        lib.oracle_conductivity.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double]
         lib.oracle_interface_sister.restype = _i64
         lib.oracle_interface_sister.argtypes = [ctypes.c_void_p, _i64]
         _lib = lib
@@ -149,6 +153,8 @@ class OracleProblem:
         if not self._h:
             raise ValueError(f"oracle_create failed with status {st.value}")
         self._keep = (xyz, tets, mat, mats, fc, fh, ft, fq, dn, dT)
+        for mt, Tk, kk in getattr(prob, "k_tables", ()):
+            self.set_conductivity(mt, Tk, kk)
         ia = getattr(prob, "iface_a", None)
         if faces and ia is not None and ia.shape[0] > 0:
             a, ha = _i(prob.iface_a), _d(prob.h_ia)
@@ -204,6 +210,18 @@ class OracleProblem:
             q = self._lib.oracle_residual_part(self._h, _pd(T), _pd(R), _pi(ep), _pi(fp),
                                                int(part))
         return R, q
+
+    def set_conductivity(self, mt: int, T, k) -> None:
+        """Piecewise-linear k(T) table for material mt (evaluated at the
+        element's mean temperature); an empty table restores constant k."""
+        T, k = _d(T), _d(k)
+        rc = self._lib.oracle_set_conductivity(self._h, int(mt), T.shape[0], _pd(T), _pd(k))
+        if rc != 0:
+            raise ValueError(f"oracle_set_conductivity failed with status {rc}")
+        self._keep = self._keep + (T, k)
+
+    def conductivity(self, mt: int, T: float) -> float:
+        return self._lib.oracle_conductivity(self._h, int(mt), float(T))
 
     def interface_sisters(self) -> np.ndarray:
         """Sister of every interface face (side-A faces first, then side B),

@@ -54,6 +54,9 @@ class Problem:
         default_factory=lambda: np.zeros((0, 3), np.int32))
     h_ia: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.float64))
     h_ib: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.float64))
+    # temperature-dependent conductivity: (material, T points, k points)
+    # tables, piecewise linear, evaluated at an element's mean temperature
+    k_tables: tuple = ()
     name: str = ""
 
     @property
