@@ -158,6 +158,17 @@ fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_ma
 fem_status fem_set_boundary(fem_mesh *m, const int32_t *faces, int64_t n_faces,
                             const double *h, const double *T_inf, const double *q);
 
+/* Temperature-dependent conductivity of material mat (Eq. 9 allows K(T)):
+ * a table of n (<= 16) points, T [n] ascending (K) and k [n] > 0 (W/mK),
+ * linear between points and constant beyond the ends; n == 0 restores the
+ * material's constant k.  Each step evaluates k at every element's mean
+ * nodal temperature of step n (explicit), K^e(T) = k(T_mean) K^e(k = 1).
+ * The stable step (fem_stable_dt) uses each table's largest k.  Call after
+ * fem_set_materials (which clears the tables); at most 255 materials.
+ * Errors: FEM_EINVAL (material out of range, bad table), FEM_ESTATE. */
+fem_status fem_set_conductivity(fem_mesh *m, int32_t mat, int32_t n, const double *T,
+                                const double *k);
+
 /* Cast-mold interface (Eq. 8): two regions meshed separately meet on a
  * surface without matching nodes.  faces_a [n_a][3] are the faces of one
  * side (e.g. the casting's), faces_b [n_b][3] the other side's, each a face

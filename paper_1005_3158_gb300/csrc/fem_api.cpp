@@ -86,6 +86,12 @@ struct fem_mesh {
     std::vector<double> Cn, mn, Lcn;  // lumped per node
     std::vector<uint8_t> rng_id;      // phase-range index per node
     std::vector<double> ranges;       // [nr][2]
+    int32_t n_mat = 0;
+    std::vector<double> mat_k;        // constant conductivity per material
+    // temperature-dependent conductivity: per material a table of (T, k)
+    // points (empty: constant k); has_kt when any table is set
+    std::vector<std::vector<double>> kt_T, kt_k;
+    bool has_kt = false;
     // boundary: Robin faces (fem_set_boundary) and interface faces
     // (fem_set_interface, Eq. 8), kept apart and combined into faces/fa/fg
     // (Robin first) for the plan, the uploads and the stable step
@@ -133,6 +139,9 @@ struct fem_mesh {
     uint32_t *dSched = nullptr;
     int32_t *dIfPos = nullptr, *dIfSis = nullptr;   // interface: face position, sister nodes
     void *dIfG = nullptr;
+    uint8_t *dEmat = nullptr;                      // k(T): material per element position
+    void *dKtT = nullptr, *dKtK = nullptr;         // k(T) tables [n_mat][kKtMax]
+    int32_t *dKtN = nullptr;
     double *dEpart = nullptr, *dQcum = nullptr, *dIo = nullptr,
            *dDirT = nullptr, *dOut = nullptr;
     int *dErr = nullptr;
@@ -188,6 +197,9 @@ void release_device(fem_mesh *m)
     m->dBlkDt = m->dShDt = nullptr;
     m->dIfPos = m->dIfSis = nullptr;
     m->dIfG = nullptr;
+    m->dEmat = nullptr;
+    m->dKtT = m->dKtK = nullptr;
+    m->dKtN = nullptr;
     m->dt_uploaded.clear();
     if (m->graph) cudaGraphExecDestroy(m->graph);
     m->graph = nullptr;
@@ -216,6 +228,29 @@ void combine_faces(fem_mesh *m)
     m->fg = m->rb_fg;
     m->fg.insert(m->fg.end(), (size_t)m->F_if, 0.0);
     m->F = m->F_rb + m->F_if;
+}
+
+// Element weights to upload: the constant-k conductances, or with k(T)
+// tables those of k = 1 (the kernels scale them by k(mean T)); scale_kmax
+// multiplies the latter by each material's largest k (stable-step bound).
+std::vector<double> element_weights(const fem_mesh *m, bool scale_kmax)
+{
+    if (!m->has_kt) return m->w;
+    std::vector<double> w((size_t)m->E * 6);
+    for (int64_t e = 0; e < m->E; e++) {
+        const int32_t *t = &m->tets[4 * (size_t)e];
+        double V;
+        tet_conductances(&m->xyz[3 * (size_t)t[0]], &m->xyz[3 * (size_t)t[1]], &m->xyz[3 * (size_t)t[2]],
+                         &m->xyz[3 * (size_t)t[3]], 1.0, &w[6 * e], &V);
+        if (scale_kmax) {
+            const int32_t mt = m->mat[e];
+            double kmax = m->mat_k[(size_t)mt];
+            if (!m->kt_k[(size_t)mt].empty())
+                kmax = *std::max_element(m->kt_k[(size_t)mt].begin(), m->kt_k[(size_t)mt].end());
+            for (int k = 0; k < 6; k++) w[6 * e + k] *= kmax;
+        }
+    }
+    return w;
 }
 
 // caller node ids of the sister face of every interface face [F_if][3]
@@ -359,6 +394,41 @@ fem_status upload_nodes(fem_mesh *m)
     return FEM_OK;
 }
 
+// k(T) device tables (every material: its table, or one point at its
+// constant k) and the material of every element position (-1: padding ->
+// material 0, whose weights are zero there anyway).
+template <typename real>
+fem_status upload_kt(fem_mesh *m, const std::vector<int32_t> &elem_order)
+{
+    if (!m->has_kt) return FEM_OK;
+    std::vector<real> T((size_t)m->n_mat * kKtMax, real(0)), k((size_t)m->n_mat * kKtMax, real(0));
+    std::vector<int32_t> n((size_t)m->n_mat);
+    for (int32_t mt = 0; mt < m->n_mat; mt++) {
+        if (m->kt_T[(size_t)mt].empty()) {
+            n[(size_t)mt] = 1;
+            k[(size_t)mt * kKtMax] = (real)m->mat_k[(size_t)mt];
+        } else {
+            n[(size_t)mt] = (int32_t)m->kt_T[(size_t)mt].size();
+            for (int32_t j = 0; j < n[(size_t)mt]; j++) {
+                T[(size_t)mt * kKtMax + j] = (real)m->kt_T[(size_t)mt][(size_t)j];
+                k[(size_t)mt * kKtMax + j] = (real)m->kt_k[(size_t)mt][(size_t)j];
+            }
+        }
+    }
+    std::vector<uint8_t> em(elem_order.size() + 8, 0);
+    for (size_t q = 0; q < elem_order.size(); q++)
+        if (elem_order[q] >= 0) em[q] = (uint8_t)m->mat[(size_t)elem_order[q]];
+    fem_status st;
+    real *p = nullptr;
+    if ((st = upload<real>(m, &p, T.data(), T.size()))) return st;
+    m->dKtT = p;
+    if ((st = upload<real>(m, &p, k.data(), k.size()))) return st;
+    m->dKtK = p;
+    if ((st = upload<int32_t>(m, &m->dKtN, n.data(), n.size()))) return st;
+    if ((st = upload<uint8_t>(m, &m->dEmat, em.data(), em.size()))) return st;
+    return FEM_OK;
+}
+
 // Interface faces (Eq. 8): the device position of each one in the face
 // arrays (face_order: position -> caller face), its h_i A / 3 and the
 // internal ids of its sister's nodes.
@@ -396,17 +466,26 @@ fem_status upload_block(fem_mesh *m)
     const int32_t nes = bp.blocks.empty() ? 8 : bp.blocks[0].nep;
     m->nes = nes;
     {
+        const std::vector<double> src = element_weights(m, false);
         std::vector<real> w((size_t)bp.blocks.size() * 6 * nes, real(0));
         for (size_t bi = 0; bi < bp.blocks.size(); bi++) {
             const BlockInfo &b = bp.blocks[bi];
             for (int32_t i = 0; i < b.ne; i++) {
                 int32_t e = bp.elem_order[(size_t)b.e0 + i];
                 for (int k = 0; k < 6; k++)
-                    w[(6 * bi + k) * (size_t)nes + i] = (real)m->w[6 * (size_t)e + k];
+                    w[(6 * bi + k) * (size_t)nes + i] = (real)src[6 * (size_t)e + k];
             }
         }
         if ((st = upload<real>(m, &p, w.data(), w.size()))) return st;
         m->dW = p;
+        // k(T): the material of element i of block b at b*nes + i
+        if (m->has_kt) {
+            std::vector<int32_t> eo((size_t)bp.blocks.size() * nes, -1);
+            for (size_t bi = 0; bi < bp.blocks.size(); bi++)
+                for (int32_t i = 0; i < bp.blocks[bi].ne; i++)
+                    eo[bi * nes + i] = bp.elem_order[(size_t)bp.blocks[bi].e0 + i];
+            if ((st = upload_kt<real>(m, eo))) return st;
+        }
     }
     std::vector<real> fa((size_t)bp.F_pad, real(0)), fg((size_t)bp.F_pad, real(0));
     for (int64_t q = 0; q < bp.F_pad; q++) {
@@ -523,9 +602,9 @@ fem_status upload_block(fem_mesh *m)
     if ((size_t)optin < m->smem_bytes + 1024)
         return fail(FEM_EINVAL, "a block needs %zu bytes of shared memory (device limit %d); lower block_elems",
                     m->smem_bytes, optin);
-    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes), "configuring the block kernel");
+    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes, m->has_kt), "configuring the block kernel");
     int per_sm = 0;
-    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm), "occupancy query");
+    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm, m->has_kt), "occupancy query");
     if (per_sm < 1) return fail(FEM_EINVAL, "the block kernel does not fit on an SM; lower block_elems");
     m->ctas_per_sm = per_sm;
     return upload_interface<real>(m, bp.face_order);
@@ -539,12 +618,13 @@ fem_status upload_flat(fem_mesh *m)
     if ((st = upload_nodes<real>(m))) return st;
     real *p = nullptr;
     {
+        const std::vector<double> wsrc = element_weights(m, false);
         std::vector<real> w((size_t)fp.E_pad * 6, real(0));
         std::vector<int32_t> conn((size_t)fp.E_pad * 4, -1);
         for (int64_t q = 0; q < fp.E_pad; q++) {
             int32_t e = fp.elem_order[q];
             if (e < 0) continue;
-            for (int k = 0; k < 6; k++) w[(size_t)k * fp.E_pad + q] = (real)m->w[6 * (size_t)e + k];
+            for (int k = 0; k < 6; k++) w[(size_t)k * fp.E_pad + q] = (real)wsrc[6 * (size_t)e + k];
             for (int c = 0; c < 4; c++)
                 conn[(size_t)c * fp.E_pad + q] = fp.node_new[m->tets[4 * (size_t)e + c]];
         }
@@ -576,6 +656,7 @@ fem_status upload_flat(fem_mesh *m)
     m->n_node_ctas = (int)std::max<int64_t>(1, (m->N + 255) / 256);
     if ((st = upload<double>(m, &m->dEpart, nullptr, 2 * (size_t)m->n_node_ctas))) return st;
     if ((st = upload<double>(m, &m->dQcum, nullptr, (size_t)m->n_node_ctas))) return st;
+    if ((st = upload_kt<real>(m, fp.elem_order))) return st;
     return upload_interface<real>(m, fp.face_order);
 }
 
@@ -613,6 +694,10 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.s_end = m->bp.n_sh;
     a.blk_dt = nullptr;
     a.sh_dt = nullptr;
+    a.emat = m->dEmat;
+    a.kt_T = (const real *)m->dKtT;
+    a.kt_k = (const real *)m->dKtK;
+    a.kt_n = m->dKtN;
     // test hook: a bounded wait that runs out (see BlockArgs)
     const char *skip = getenv("FEM_FAULT_SKIP_WEIGHT_COPY");
     a.fault_skip_weights = (skip && *skip && *skip != '0') ? 1 : 0;
@@ -658,6 +743,10 @@ FlatArgs<real> flat_args(const fem_mesh *m)
     a.n_faces = m->F;
     a.f_stride = m->fp.F_pad;
     a.qcum = m->dQcum;
+    a.emat = m->dEmat;
+    a.kt_T = (const real *)m->dKtT;
+    a.kt_k = (const real *)m->dKtK;
+    a.kt_n = m->dKtN;
     return a;
 }
 
@@ -831,7 +920,8 @@ fem_status launch_step_kernel(fem_mesh *m, int k, double dt)
     if (is_block(m)) {
         const BlockArgs<real> a = block_args<real>(m);
         if (k == 0)
-            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream), "block kernel");
+            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream, m->has_kt),
+                   "block kernel");
         else
             KERNEL(launch_shared_update<real>(a, dt, m->stream), "shared-node kernel");
     } else {
@@ -1090,6 +1180,12 @@ fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_ma
         m->Lcn.swap(Lc);
         m->rng_id.swap(rid);
         m->ranges.swap(ranges);
+        m->n_mat = n_mat;
+        m->mat_k.resize((size_t)n_mat);
+        for (int32_t i = 0; i < n_mat; i++) m->mat_k[(size_t)i] = mats[i].k;
+        m->kt_T.assign((size_t)n_mat, {});
+        m->kt_k.assign((size_t)n_mat, {});
+        m->has_kt = false;
         m->have_mat = true;
     } catch (const std::bad_alloc &) {
         return fail(FEM_ENOMEM, "host allocation failed");
@@ -1142,6 +1238,30 @@ fem_status fem_set_boundary(fem_mesh *m, const int32_t *faces, int64_t n_faces, 
     m->rb_fg.swap(fg);
     m->F_rb = n_faces;
     combine_faces(m);
+    return ok();
+}
+
+fem_status fem_set_conductivity(fem_mesh *m, int32_t mat, int32_t n, const double *T,
+                                const double *k)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (m->n_inst > 0) return fail(FEM_ESTATE, "a batch takes its materials and boundaries from its parts");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    if (mat < 0 || mat >= m->n_mat) return fail(FEM_EINVAL, "material %d out of range", mat);
+    if (m->n_mat > 255) return fail(FEM_EINVAL, "k(T) tables need at most 255 materials");
+    if (n < 0 || n > kKtMax) return fail(FEM_EINVAL, "a k(T) table has 0 to %d points", kKtMax);
+    if (n > 0 && (!T || !k)) return fail(FEM_EINVAL, "NULL array argument");
+    for (int32_t j = 0; j < n; j++) {
+        if (!std::isfinite(T[j]) || !std::isfinite(k[j]) || !(k[j] > 0.0))
+            return fail(FEM_EINVAL, "k(T) point %d: T finite and k > 0 required", j);
+        if (j > 0 && !(T[j] > T[j - 1])) return fail(FEM_EINVAL, "k(T) points must have ascending T");
+    }
+    fem_status st = invalidate_plan(m);
+    if (st) return st;
+    m->kt_T[(size_t)mat].assign(T, T + n);
+    m->kt_k[(size_t)mat].assign(k, k + n);
+    m->has_kt = false;
+    for (const auto &v : m->kt_T) m->has_kt |= !v.empty();
     return ok();
 }
 
@@ -1288,7 +1408,8 @@ fem_status fem_stable_dt(fem_mesh *m, double *dt_out)
     if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
     try {
         const std::vector<int32_t> sn = sister_nodes(m);
-        *dt_out = gershgorin_dt(m->N, m->E, m->tets.data(), m->w.data(), m->adj, m->F,
+        const std::vector<double> wk = element_weights(m, true);
+        *dt_out = gershgorin_dt(m->N, m->E, m->tets.data(), wk.data(), m->adj, m->F,
                                 m->faces.data(), m->fa.data(), m->Cn.data(),
                                 m->is_dir.empty() ? nullptr : m->is_dir.data(), m->F_if,
                                 sn.data());
@@ -1567,7 +1688,12 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
             const int32_t no = (int32_t)m->inst_node[(size_t)i];
             m->xyz.insert(m->xyz.end(), p->xyz.begin(), p->xyz.end());
             for (int32_t v : p->tets) m->tets.push_back(v + no);
-            m->mat.insert(m->mat.end(), p->mat.begin(), p->mat.end());
+            for (int32_t v : p->mat) m->mat.push_back(v + m->n_mat);
+            m->mat_k.insert(m->mat_k.end(), p->mat_k.begin(), p->mat_k.end());
+            m->kt_T.insert(m->kt_T.end(), p->kt_T.begin(), p->kt_T.end());
+            m->kt_k.insert(m->kt_k.end(), p->kt_k.begin(), p->kt_k.end());
+            m->has_kt |= p->has_kt;
+            m->n_mat += p->n_mat;
             m->vol.insert(m->vol.end(), p->vol.begin(), p->vol.end());
             for (int32_t r : p->rank) m->rank.push_back(r + no);
             m->w.insert(m->w.end(), p->w.begin(), p->w.end());
@@ -1596,7 +1722,8 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
             m->bw_input = std::max(m->bw_input, p->bw_input);
             m->bw_rank = std::max(m->bw_rank, p->bw_rank);
             const std::vector<int32_t> sn = sister_nodes(p);
-            const double dt = gershgorin_dt(p->N, p->E, p->tets.data(), p->w.data(), p->adj, p->F,
+            const std::vector<double> wk = element_weights(p, true);
+            const double dt = gershgorin_dt(p->N, p->E, p->tets.data(), wk.data(), p->adj, p->F,
                                             p->faces.data(), p->fa.data(), p->Cn.data(),
                                             p->is_dir.empty() ? nullptr : p->is_dir.data(),
                                             p->F_if, sn.data());
@@ -1688,7 +1815,8 @@ fem_status advance_launches(fem_mesh *m, const std::vector<int64_t> &nk, cudaStr
             a.b_count = bp.inst_block_start[(size_t)k1] - a.b_first;
             a.s_first = bp.inst_sh_start[(size_t)k0];
             a.s_end = bp.inst_sh_start[(size_t)k1];
-            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, 0.0, st), "block kernel");
+            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, 0.0, st, m->has_kt),
+                   "block kernel");
             KERNEL(launch_shared_update<real>(a, 0.0, st), "shared-node kernel");
             k0 = k1;
         }

@@ -79,7 +79,9 @@ constexpr int kErrBadInput = 2;      // fem_set_state received a non-finite valu
 constexpr int kErrNonFinite = 4;     // a read-back temperature was non-finite
 
 constexpr uint8_t kDirichletBit = 0x80;  // in the per-node phase byte
-constexpr int kMaxRanges = 127;          // distinct (Ts, Tl) pairs
+constexpr int kMaxRanges = 127;
+// points of one material's k(T) table; materials with tables: at most 255
+constexpr int kKtMax = 16;          // distinct (Ts, Tl) pairs
 
 // Where the nodal enthalpy of internal node i lives.  Flat variants: one
 // dense array (home == null, n_int == n_nodes).  Block variant: interior
@@ -143,6 +145,13 @@ struct BlockArgs {
     int64_t s_first, s_end;
     const real *blk_dt;
     const real *sh_dt;
+    // temperature-dependent conductivity (instantiations with KT = true):
+    // the weights are those of k = 1, element e of block b has material
+    // emat[b*nes + e], whose table kt_n[m] points (kt_T, kt_k)[m*kKtMax + j]
+    // gives k at the element's mean temperature
+    const uint8_t *emat;
+    const real *kt_T, *kt_k;
+    const int32_t *kt_n;
     // test hook (FEM_FAULT_SKIP_WEIGHT_COPY): announce the conductance copy
     // but never issue it, so that the wait for it runs out
     int32_t fault_skip_weights;
@@ -166,13 +175,19 @@ struct FlatArgs {
     const real *fa, *fg;
     int64_t n_faces, f_stride;
     double *qcum;             // [n_node_ctas] cumulative boundary heat
+    // temperature-dependent conductivity (KT instantiations): material of
+    // element position p, tables as in BlockArgs
+    const uint8_t *emat;
+    const real *kt_T, *kt_k;
+    const int32_t *kt_n;
 };
 
 // Launchers (fem_kernels.cu).  All return a cudaError_t as int.
 // Block variant, one step = launch_block_kernel + launch_shared_update.
+// kt: the instantiation with temperature-dependent conductivity
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream);
+                        void *stream, bool kt = false);
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream);
 // Interface faces (Eq. 8): fg[pos[f]] = g[f] * mean T of nodes sis[f][0..2]
@@ -182,9 +197,9 @@ int launch_interface(StateView<real> v, const real *C, const real *Lc, const uin
                      const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
                      const real *g, int64_t n, void *stream);
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes);
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false);
 template <typename real>
-int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm);
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt = false);
 // Mirrors of the shared nodes' E in the block-local arrays follow Esh
 // (after the state was set from outside).
 template <typename real>

@@ -174,6 +174,22 @@ __device__ __forceinline__ void give_up(int *err, uint32_t bar_s, uint32_t bar_w
     __syncthreads();
 }
 
+// k(T) of material m: its table of n points (T_j ascending), linear between
+// points, constant beyond the ends (the reading of Eq. 9's K(T)).
+template <typename real>
+__device__ __forceinline__ real conductivity_of(const real *kt_T, const real *kt_k,
+                                                const int32_t *kt_n, int m, real T)
+{
+    const int n = __ldg(kt_n + m);
+    const real *Tj = kt_T + m * kKtMax, *kj = kt_k + m * kKtMax;
+    if (T <= __ldg(Tj)) return __ldg(kj);
+    if (T >= __ldg(Tj + n - 1)) return __ldg(kj + n - 1);
+    int j = 0;
+    while (T > __ldg(Tj + j + 1)) j++;
+    const real T0 = __ldg(Tj + j), k0 = __ldg(kj + j);
+    return k0 + (__ldg(kj + j + 1) - k0) * (T - T0) / (__ldg(Tj + j + 1) - T0);
+}
+
 // Element product of one tet: r_a = sum_b w_ab (T_b - T_a), w_ab = -K^e_ab
 // (the row of -K^e T^e; K^e symmetric with zero row sums, Eq. 9).
 template <typename real>
@@ -223,7 +239,7 @@ __device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
 // rows (fixed stride 6*b*nes) into shared memory meanwhile.
 // Thread t owns local nodes t, t+NT, ... (the 32-lane schedule group
 // g = warp + j*NW covers nodes 32 g + lane) and element quad(s) t, t+NT, ...
-template <typename real, int NT>
+template <typename real, int NT, bool KT>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     k_block_step(const BlockArgs<real> a, const real dt)
 {
@@ -283,6 +299,14 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     // this block's time step (a batch gives every instance its own; the
     // load's latency is hidden behind the passes)
     const real dtb = a.blk_dt ? a.blk_dt[b] : dt;
+    // k(T): the materials of this thread's first element quad, loaded now
+    // and used in pass 2
+    uint32_t mat_q = 0;
+    if (KT && (int)threadIdx.x * VN < bi.ne) {
+        const uint8_t *pm = a.emat + (size_t)b * nes + threadIdx.x * VN;
+        mat_q = VN == 4 ? *reinterpret_cast<const uint32_t *>(pm)
+                        : (uint32_t)*reinterpret_cast<const uint16_t *>(pm);
+    }
     // this thread's first face
     real fa0 = real(0), fg0 = real(0);
     if ((int)threadIdx.x < bi.nf) {
@@ -355,6 +379,21 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         V T1 = *reinterpret_cast<const V *>(sv + ne_pad + e);
         V T2 = *reinterpret_cast<const V *>(sv + 2 * ne_pad + e);
         V T3 = *reinterpret_cast<const V *>(sv + 3 * ne_pad + e);
+        if (KT) {   // K^e(T) = k(mean element temperature) x the k = 1 weights
+            uint32_t mq = mat_q;
+            if (qd != (int)threadIdx.x) {
+                const uint8_t *pm = a.emat + (size_t)b * nes + e;
+                mq = VN == 4 ? *reinterpret_cast<const uint32_t *>(pm)
+                             : (uint32_t)*reinterpret_cast<const uint16_t *>(pm);
+            }
+#pragma unroll
+            for (int i = 0; i < VN; i++) {
+                const real Tm = (vat(T0, i) + vat(T1, i) + vat(T2, i) + vat(T3, i)) * real(0.25);
+                const real kk = conductivity_of(a.kt_T, a.kt_k, a.kt_n, (int)((mq >> (8 * i)) & 0xFFu), Tm);
+#pragma unroll
+                for (int k = 0; k < 6; k++) vat(wq[k], i) *= kk;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < VN; i++)
             tet_products(vat(wq[0], i), vat(wq[1], i), vat(wq[2], i), vat(wq[3], i), vat(wq[4], i),
@@ -498,7 +537,7 @@ __global__ void k_flat_temperature(const FlatArgs<real> a)
     }
 }
 
-template <typename real, bool kAtomic>
+template <typename real, bool kAtomic, bool KT>
 __global__ void k_flat_elements(const FlatArgs<real> a, const int64_t p0, const int64_t p1)
 {
     const int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -509,10 +548,15 @@ __global__ void k_flat_elements(const FlatArgs<real> a, const int64_t p0, const 
     const int32_t n1 = __ldg(a.conn + st + p), n2 = __ldg(a.conn + 2 * st + p),
                   n3 = __ldg(a.conn + 3 * st + p);
     const real T0 = __ldg(a.T + n0), T1 = __ldg(a.T + n1), T2 = __ldg(a.T + n2), T3 = __ldg(a.T + n3);
-    const real p01 = __ldg(a.w + p) * (T1 - T0), p02 = __ldg(a.w + st + p) * (T2 - T0),
-               p03 = __ldg(a.w + 2 * st + p) * (T3 - T0);
-    const real p12 = __ldg(a.w + 3 * st + p) * (T2 - T1), p13 = __ldg(a.w + 4 * st + p) * (T3 - T1),
-               p23 = __ldg(a.w + 5 * st + p) * (T3 - T2);
+    real kk = real(1);
+    if (KT)   // K^e(T) = k(mean element temperature) x the k = 1 weights
+        kk = conductivity_of(a.kt_T, a.kt_k, a.kt_n, (int)__ldg(a.emat + p),
+                             (T0 + T1 + T2 + T3) * real(0.25));
+    const real p01 = (kk * __ldg(a.w + p)) * (T1 - T0), p02 = (kk * __ldg(a.w + st + p)) * (T2 - T0),
+               p03 = (kk * __ldg(a.w + 2 * st + p)) * (T3 - T0);
+    const real p12 = (kk * __ldg(a.w + 3 * st + p)) * (T2 - T1),
+               p13 = (kk * __ldg(a.w + 4 * st + p)) * (T3 - T1),
+               p23 = (kk * __ldg(a.w + 5 * st + p)) * (T3 - T2);
     const real r0 = p01 + p02 + p03, r1 = (p12 + p13) - p01, r2 = p23 - (p02 + p12),
                r3 = -(p03 + p13 + p23);
     if (kAtomic) {
@@ -662,50 +706,46 @@ inline int grid_for(int64_t n, int threads)
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// The block kernel instantiation for (threads, kt), as a function pointer.
 template <typename real>
-int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm)
+using BlockKernel = void (*)(const BlockArgs<real>, const real);
+template <typename real>
+BlockKernel<real> block_kernel_for(int threads, bool kt)
 {
-    cudaError_t e = cudaErrorInvalidValue;
     switch (threads) {
-    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 128>, 128, smem_bytes); break;
-    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 256>, 256, smem_bytes); break;
-    case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 512>, 512, smem_bytes); break;
-    case 1024: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_block_step<real, 1024>, 1024, smem_bytes); break;
-    default: break;
+    case 128: return kt ? k_block_step<real, 128, true> : k_block_step<real, 128, false>;
+    case 256: return kt ? k_block_step<real, 256, true> : k_block_step<real, 256, false>;
+    case 512: return kt ? k_block_step<real, 512, true> : k_block_step<real, 512, false>;
+    case 1024: return kt ? k_block_step<real, 1024, true> : k_block_step<real, 1024, false>;
+    default: return nullptr;
     }
-    return (int)e;
 }
 
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes)
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt)
 {
-    cudaError_t e = cudaSuccess;
-    const int s = (int)smem_bytes;
-    switch (threads) {
-    case 128: e = cudaFuncSetAttribute(k_block_step<real, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
-    case 256: e = cudaFuncSetAttribute(k_block_step<real, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
-    case 512: e = cudaFuncSetAttribute(k_block_step<real, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
-    case 1024: e = cudaFuncSetAttribute(k_block_step<real, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, s); break;
-    default: return (int)cudaErrorInvalidValue;
-    }
-    return (int)e;
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt);
+    if (!f) return (int)cudaErrorInvalidValue;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, f, threads, smem_bytes);
+}
+
+template <typename real>
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt)
+{
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt);
+    if (!f) return (int)cudaErrorInvalidValue;
+    return (int)cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream)
+                        void *stream, bool kt)
 {
-    cudaStream_t st = (cudaStream_t)stream;
-    const real rdt = (real)dt;
     const int grid = a.b_count;
     if (grid <= 0) return 0;
-    switch (threads) {
-    case 128: k_block_step<real, 128><<<grid, 128, smem_bytes, st>>>(a, rdt); break;
-    case 256: k_block_step<real, 256><<<grid, 256, smem_bytes, st>>>(a, rdt); break;
-    case 512: k_block_step<real, 512><<<grid, 512, smem_bytes, st>>>(a, rdt); break;
-    case 1024: k_block_step<real, 1024><<<grid, 1024, smem_bytes, st>>>(a, rdt); break;
-    default: return (int)cudaErrorInvalidValue;
-    }
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt);
+    if (!f) return (int)cudaErrorInvalidValue;
+    f<<<grid, threads, smem_bytes, (cudaStream_t)stream>>>(a, (real)dt);
     return (int)cudaGetLastError();
 }
 
@@ -754,14 +794,21 @@ int launch_flat_elements(const FlatArgs<real> &a, bool atomic, const int64_t *co
                          int n_colors, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
+    const bool kt = a.emat != nullptr;
     if (atomic) {
         const int64_t ne = a.e_stride;
-        k_flat_elements<real, true><<<(int)((ne + 255) / 256), 256, 0, st>>>(a, 0, ne);
+        if (kt)
+            k_flat_elements<real, true, true><<<(int)((ne + 255) / 256), 256, 0, st>>>(a, 0, ne);
+        else
+            k_flat_elements<real, true, false><<<(int)((ne + 255) / 256), 256, 0, st>>>(a, 0, ne);
     } else {
         for (int c = 0; c < n_colors; c++) {
             const int64_t p0 = color_start[c], p1 = color_start[c + 1];
-            if (p1 > p0)
-                k_flat_elements<real, false><<<(int)((p1 - p0 + 255) / 256), 256, 0, st>>>(a, p0, p1);
+            if (p1 <= p0) continue;
+            if (kt)
+                k_flat_elements<real, false, true><<<(int)((p1 - p0 + 255) / 256), 256, 0, st>>>(a, p0, p1);
+            else
+                k_flat_elements<real, false, false><<<(int)((p1 - p0 + 255) / 256), 256, 0, st>>>(a, p0, p1);
         }
     }
     return (int)cudaGetLastError();
@@ -827,13 +874,14 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
 }
 
 #define FEM_INSTANTIATE(real)                                                                     \
-    template int configure_block_kernel<real>(int, size_t);                                       \
-    template int block_kernel_occupancy<real>(int, size_t, int *);                                \
+    template int configure_block_kernel<real>(int, size_t, bool);                                 \
+    template int block_kernel_occupancy<real>(int, size_t, int *, bool);                          \
     template int launch_mirror_copies<real>(const BlockArgs<real> &, void *);                     \
     template int launch_interface<real>(StateView<real>, const real *, const real *,              \
                                         const uint8_t *, const real *, real *, const int32_t *,   \
                                         const int32_t *, const real *, int64_t, void *);          \
-    template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *); \
+    template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *,  \
+                                           bool);                                                 \
     template int launch_shared_update<real>(const BlockArgs<real> &, double, void *);             \
     template int launch_flat_temperature<real>(const FlatArgs<real> &, void *);                   \
     template int launch_flat_elements<real>(const FlatArgs<real> &, bool, const int64_t *, int,  \

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": FEM_FP64, "f64": FEM_FP64, "fp32": FEM_FP32, "f32": FEM_FP
 # names declared in include/fem.h
 ABI_SYMBOLS = (
     "fem_mesh_create", "fem_mesh_create_ex", "fem_set_materials", "fem_set_boundary",
-    "fem_set_interface",
+    "fem_set_interface", "fem_set_conductivity",
     "fem_set_dirichlet", "fem_set_temperature", "fem_stable_dt", "fem_step", "fem_step_profile",
     "fem_get_temperature", "fem_get_enthalpy", "fem_get_energy", "fem_set_stream",
     "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
@@ -85,6 +85,7 @@ def _load():
         "fem_set_boundary": [P, ip, i64, dp, dp, dp],
         "fem_set_dirichlet": [P, ip, i64, dp],
         "fem_set_interface": [P, ip, i64, dp, ip, i64, dp],
+        "fem_set_conductivity": [P, ctypes.c_int32, ctypes.c_int32, dp, dp],
         "fem_set_temperature": [P, dp],
         "fem_stable_dt": [P, dp],
         "fem_step": [P, i64, ctypes.c_double],
@@ -211,6 +212,11 @@ def fem_set_interface(h, faces_a, h_a, faces_b, h_b):
     ha, hb = _d(h_a), _d(h_b)
     _check(_lib.fem_set_interface(h, _pi(fa_), fa_.shape[0], _pd(ha), _pi(fb_), fb_.shape[0],
                                   _pd(hb)))
+
+
+def fem_set_conductivity(h, mat, T, k):
+    T, k = _d(T), _d(k)
+    _check(_lib.fem_set_conductivity(h, int(mat), T.shape[0], _pd(T), _pd(k)))
 
 
 def fem_set_temperature(h, T0):
@@ -383,6 +389,8 @@ class Mesh:
                 fem_set_boundary(self.h, prob.faces, prob.h, prob.t_inf, prob.q)
             if dirichlet and prob.dir_nodes.shape[0] > 0:
                 fem_set_dirichlet(self.h, prob.dir_nodes, prob.dir_T)
+            for mt, Tk, kk in getattr(prob, "k_tables", ()):
+                fem_set_conductivity(self.h, mt, Tk, kk)
             ia = getattr(prob, "iface_a", None)
             if faces and ia is not None and ia.shape[0] > 0:
                 fem_set_interface(self.h, prob.iface_a, prob.h_ia, prob.iface_b, prob.h_ib)

@@ -287,9 +287,10 @@ def concat_problems(probs) -> Problem:
     """The disjoint union of several problems (part k's node i becomes node
     offset_k + i; material ids offset by the parts' material counts)."""
     xyz, tets, mat, mats, faces, hh, ti, q, T0, dn, dT = ([] for _ in range(11))
-    ia, ib, ha, hb = [], [], [], []
+    ia, ib, ha, hb, kts = [], [], [], [], []
     no = mo = 0
     for p in probs:
+        kts.extend((mt + mo, Tk, kk) for mt, Tk, kk in p.k_tables)
         ia.append(p.iface_a + no)
         ib.append(p.iface_b + no)
         ha.append(p.h_ia)
@@ -315,6 +316,7 @@ def concat_problems(probs) -> Problem:
                    iface_a=np.concatenate(ia).astype(np.int32),
                    iface_b=np.concatenate(ib).astype(np.int32),
                    h_ia=np.concatenate(ha), h_ib=np.concatenate(hb),
+                   k_tables=tuple(kt for kt in kts),
                    name="+".join(p.name for p in probs))
 
 

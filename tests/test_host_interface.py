@@ -47,3 +47,19 @@ def test_interface_validation():
         q.h_ia = q.h_ib = np.zeros(0)
         assert m.stable_dt() == pytest.approx(oracle.OracleProblem(q).stable_dt(), rel=1e-13)
         assert m.info()["n_interface_faces"] == 0
+
+
+def test_conductivity_tables_stable_dt_matches_oracle():
+    p = mg.random_small(6, nx=5, ny=4, nz=4, n_mat=3)
+    p.k_tables = ((0, [300.0, 600.0, 1000.0], [20.0, 180.0, 90.0]), (2, [500.0], [7.0]))
+    o = oracle.OracleProblem(p)
+    for variant in ("block", "atomic"):
+        with fem.Mesh(p, "fp64", variant=variant) as m:
+            assert m.stable_dt() == pytest.approx(o.stable_dt(), rel=1e-13)
+    with fem.Mesh(p, "fp64") as m:
+        with pytest.raises(fem.FemError):
+            fem.fem_set_conductivity(m.h, 5, [300.0], [1.0])            # no material 5
+        with pytest.raises(fem.FemError):
+            fem.fem_set_conductivity(m.h, 0, [600.0, 300.0], [1.0, 2.0])  # not ascending
+        with pytest.raises(fem.FemError):
+            fem.fem_set_conductivity(m.h, 0, [300.0], [0.0])             # k <= 0
