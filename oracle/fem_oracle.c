@@ -23,6 +23,9 @@
  *     Galerkin face matrix h A / 12 (1 + delta_ij) and load A/3 (h T_inf - q),
  *   - the explicit update E += dt (F - K T) (Eq. 14 with theta = 0 in Eq. 10,
  *     written for the enthalpy unknown of Eq. 5),
+ *   - alternatively the paper's apparent-heat-capacity form (Eqs. 6-7,
+ *     Lemmon's method) with T as the unknown: C_app (T^{n+1} - T^n) / dt =
+ *     F - K T^n, C_app lumped from each element's apparent specific heat,
  *   - Dirichlet nodes (Eq. 3) held at E(T_D),
  *   - optional temperature-dependent conductivity k(T) per material (Eq. 9
  *     allows K(T)): a piecewise-linear table evaluated at the element's mean
@@ -63,6 +66,12 @@ typedef struct oracle_problem {
     /* optional conductivity tables k(T) per material (Eq. 9's K(T)):
      * kt_n[m] points (kt_T ascending, kt_k), 0 = constant k */
     int32_t n_mat;
+    double *mats;    /* [n_mat][6] rho, c, k, latent, T_solidus, T_liquidus */
+    /* formulation: 0 = enthalpy (Eq. 5), 1 = apparent heat capacity by
+     * Lemmon's method (Eqs. 6-7) with T as the unknown */
+    int form;
+    double *Tst;     /* [N] temperatures, the unknowns of formulation 1 */
+    double *cap;     /* [N] lumped apparent capacity of the current step */
     int32_t *kt_n;
     double *kt_T, *kt_k;  /* [n_mat][ORACLE_KT_MAX] */
     double *vol;     /* [E] */
@@ -195,7 +204,7 @@ void oracle_destroy(oracle_problem *p)
 {
     if (!p) return;
     free(p->tets); free(p->Ke); free(p->Kg); free(p->emat); free(p->vol);
-    free(p->kt_n); free(p->kt_T); free(p->kt_k);
+    free(p->kt_n); free(p->kt_T); free(p->kt_k); free(p->mats); free(p->Tst); free(p->cap);
     free(p->C); free(p->m); free(p->Lc); free(p->Ts); free(p->Tl);
     free(p->faces); free(p->fh); free(p->ftinf); free(p->fq); free(p->farea);
     free(p->if_faces); free(p->if_h); free(p->if_area); free(p->if_sister); free(p->xyz);
@@ -230,6 +239,9 @@ oracle_problem *oracle_create(int64_t n_nodes, const double *xyz,
     p->Kg = malloc(16 * E * sizeof(double));
     p->emat = malloc(E * sizeof(int32_t));
     p->n_mat = n_mat;
+    p->mats = malloc((size_t)n_mat * 6 * sizeof(double));
+    p->Tst = calloc(N, sizeof(double));
+    p->cap = calloc(N, sizeof(double));
     p->kt_n = calloc((size_t)n_mat, sizeof(int32_t));
     p->kt_T = calloc((size_t)n_mat * ORACLE_KT_MAX, sizeof(double));
     p->kt_k = calloc((size_t)n_mat * ORACLE_KT_MAX, sizeof(double));
@@ -250,12 +262,14 @@ oracle_problem *oracle_create(int64_t n_nodes, const double *xyz,
     p->T = calloc(N, sizeof(double));
     p->R = calloc(N, sizeof(double));
     if (!p->xyz || !p->tets || !p->Ke || !p->Kg || !p->emat || !p->kt_n || !p->kt_T || !p->kt_k ||
+        !p->mats || !p->Tst || !p->cap ||
         !p->vol || !p->C || !p->m || !p->Lc || !p->Ts || !p->Tl ||
         !p->faces || !p->fh || !p->ftinf || !p->fq || !p->farea || !p->is_dir ||
         !p->T_dir || !p->E || !p->T || !p->R) {
         oracle_destroy(p); *status = ORACLE_ENOMEM; return NULL;
     }
     memcpy(p->xyz, xyz, 3 * N * sizeof(double));
+    memcpy(p->mats, mats, (size_t)n_mat * 6 * sizeof(double));
     uint8_t *has_range = calloc(N, 1);
     if (!has_range) { oracle_destroy(p); *status = ORACLE_ENOMEM; return NULL; }
 
@@ -340,6 +354,7 @@ void oracle_set_temperature(oracle_problem *p, const double *T0)
     double U = 0.0;
     for (int64_t i = 0; i < p->n_nodes; i++) {
         double T = p->is_dir[i] ? p->T_dir[i] : T0[i];
+        p->Tst[i] = T;
         p->E[i] = oracle_E_from_T(T, p->C[i], p->Lc[i], p->Ts[i], p->Tl[i]);
         U += p->E[i];
     }
@@ -517,12 +532,87 @@ double oracle_residual(const oracle_problem *p, const double *T, double *R)
 
 void oracle_temperatures(const oracle_problem *p, double *T)
 {
+    if (p->form == 1) {
+        memcpy(T, p->Tst, (size_t)p->n_nodes * sizeof(double));
+        return;
+    }
     for (int64_t i = 0; i < p->n_nodes; i++)
         T[i] = oracle_T_from_E(p->E[i], p->C[i], p->Lc[i], p->Ts[i], p->Tl[i]);
 }
 
+/* Apparent specific heat of element e by Lemmon's method (Eq. 7): the
+ * ratio of the gradient magnitudes of the specific enthalpy H(T) = c T +
+ * L f_l(T) of the element's material and of T, both interpolated linearly
+ * from the nodal values.  With K_g the k = 1 element matrix (zero row sums,
+ * off-diagonals -w_ab), |grad x|^2 V = x^T K_g x = sum_{a<b} w_ab (x_a -
+ * x_b)^2, so cp = sqrt(sum w (H_a - H_b)^2 / sum w (T_a - T_b)^2).  When T
+ * is uniform over the element (every difference below a micro-kelvin),
+ * dH/dT at the mean temperature is taken instead. */
+double oracle_apparent_cp(const oracle_problem *p, int64_t e, const double *T)
+{
+    const double *M = p->mats + 6 * (size_t)p->emat[e];
+    double c = M[1], L = M[3], Ts = M[4], Tl = M[5];
+    if (!(L > 0.0)) return c;
+    const int32_t *n = p->tets + 4 * e;
+    const double *K = p->Kg + 16 * e;
+    double H[4];
+    for (int a = 0; a < 4; a++) H[a] = c * T[n[a]] + L * oracle_liquid_fraction(T[n[a]], Ts, Tl);
+    double num = 0.0, den = 0.0, wsum = 0.0;
+    for (int a = 0; a < 4; a++)
+        for (int b = a + 1; b < 4; b++) {
+            double w = -K[4 * a + b], dH = H[a] - H[b], dT = T[n[a]] - T[n[b]];
+            num += w * dH * dH;
+            den += w * dT * dT;
+            wsum += w;
+        }
+    if (den > 1e-12 * wsum) return sqrt(num / den);
+    double Tm = (T[n[0]] + T[n[1]] + T[n[2]] + T[n[3]]) / 4.0;
+    return (Tm >= Ts && Tm < Tl) ? c + L / (Tl - Ts) : c;
+}
+
+/* Formulation 1 (apparent capacity) is defined for phase-change ranges of
+ * positive width only. */
+int oracle_set_formulation(oracle_problem *p, int form)
+{
+    if (form != 0 && form != 1) return ORACLE_EINVAL;
+    if (form == 1)
+        for (int32_t m = 0; m < p->n_mat; m++)
+            if (p->mats[6 * m + 3] > 0.0 && !(p->mats[6 * m + 5] > p->mats[6 * m + 4])) return ORACLE_EINVAL;
+    p->form = form;
+    for (int64_t i = 0; i < p->n_nodes; i++)
+        p->Tst[i] = oracle_T_from_E(p->E[i], p->C[i], p->Lc[i], p->Ts[i], p->Tl[i]);
+    return ORACLE_OK;
+}
+
+/* One explicit step of formulation 1 (Eqs. 9, 10 with theta = 0 and the
+ * lumped apparent capacity C_i = sum_e rho V / 4 cp_app,e of step n). */
+static void oracle_step_apparent(oracle_problem *p, double dt)
+{
+    double qin = oracle_residual(p, p->Tst, p->R);
+    p->Qb += dt * qin;
+    for (int64_t i = 0; i < p->n_nodes; i++) p->cap[i] = 0.0;
+    for (int64_t e = 0; e < p->n_tets; e++) {
+        double rho = p->mats[6 * (size_t)p->emat[e]];
+        double cp = oracle_apparent_cp(p, e, p->Tst);
+        for (int a = 0; a < 4; a++) p->cap[p->tets[4 * e + a]] += rho * p->vol[e] / 4.0 * cp;
+    }
+    for (int64_t i = 0; i < p->n_nodes; i++) {
+        if (p->is_dir[i]) p->Tst[i] = p->T_dir[i];
+        else p->Tst[i] += dt * p->R[i] / p->cap[i];
+        p->E[i] = oracle_E_from_T(p->Tst[i], p->C[i], p->Lc[i], p->Ts[i], p->Tl[i]);
+    }
+}
+
 void oracle_step(oracle_problem *p, int64_t n_steps, double dt)
 {
+    if (p->form == 1) {
+        for (int64_t s = 0; s < n_steps; s++) {
+            oracle_step_apparent(p, dt);
+            p->step += 1;
+            p->time += dt;
+        }
+        return;
+    }
     for (int64_t s = 0; s < n_steps; s++) {
         oracle_temperatures(p, p->T);
         double qin = oracle_residual(p, p->T, p->R);
@@ -677,6 +767,8 @@ void oracle_get_E(const oracle_problem *p, double *out)
 void oracle_set_E(oracle_problem *p, const double *E)
 {
     memcpy(p->E, E, (size_t)p->n_nodes * sizeof(double));
+    for (int64_t i = 0; i < p->n_nodes; i++)
+        p->Tst[i] = oracle_T_from_E(p->E[i], p->C[i], p->Lc[i], p->Ts[i], p->Tl[i]);
 }
 
 void oracle_get_lumped(const oracle_problem *p, double *C, double *m, double *Lc)

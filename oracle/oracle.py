@@ -81,6 +81,10 @@ def _load():
         lib.oracle_set_conductivity.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, _dp, _dp]
         lib.oracle_conductivity.restype = ctypes.c_double
         lib.oracle_conductivity.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double]
+        lib.oracle_set_formulation.restype = ctypes.c_int
+        lib.oracle_set_formulation.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_apparent_cp.restype = ctypes.c_double
+        lib.oracle_apparent_cp.argtypes = [ctypes.c_void_p, _i64, _dp]
         lib.oracle_interface_sister.restype = _i64
         lib.oracle_interface_sister.argtypes = [ctypes.c_void_p, _i64]
         _lib = lib
@@ -219,6 +223,18 @@ class OracleProblem:
         if rc != 0:
             raise ValueError(f"oracle_set_conductivity failed with status {rc}")
         self._keep = self._keep + (T, k)
+
+    def set_formulation(self, form: int) -> None:
+        """0: enthalpy (Eq. 5); 1: apparent heat capacity by Lemmon's method
+        (Eqs. 6-7) with T as the unknown (positive-width phase-change ranges
+        only).  The current state carries over."""
+        rc = self._lib.oracle_set_formulation(self._h, int(form))
+        if rc != 0:
+            raise ValueError(f"oracle_set_formulation failed with status {rc}")
+
+    def apparent_cp(self, e: int, T) -> float:
+        T = _d(T)
+        return self._lib.oracle_apparent_cp(self._h, int(e), _pd(T))
 
     def conductivity(self, mt: int, T: float) -> float:
         return self._lib.oracle_conductivity(self._h, int(mt), float(T))
