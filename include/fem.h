@@ -70,6 +70,19 @@ typedef enum { FEM_FP64 = 0, FEM_FP32 = 1 } fem_precision;
  *                          (deterministic; for comparison). */
 typedef enum { FEM_VARIANT_BLOCK = 0, FEM_VARIANT_ATOMIC = 1, FEM_VARIANT_COLORED = 2 } fem_variant;
 
+/* Nonlinear formulation of the phase change.
+ * FEM_ENTHALPY: the enthalpy method (Eq. 5), nodal enthalpy content E as
+ *   the unknown, T = T(E); conserves energy exactly.
+ * FEM_APPARENT_CAPACITY: the paper's apparent heat capacity (Eqs. 6-7) by
+ *   Lemmon's method, T as the unknown: every element's apparent specific
+ *   heat is |grad H| / |grad T| from its nodal values (dH/dT at the mean
+ *   temperature where T is uniform over it), lumped rho V / 4 per node; each
+ *   step solves C_app (T^{n+1} - T^n) / dt = F - K T^n.  Energy is conserved
+ *   only approximately.  Block variant only; every phase-change material
+ *   needs T_liquidus > T_solidus.  The state I/O (fem_get_state /
+ *   fem_set_state) still exchanges E = E(T). */
+typedef enum { FEM_ENTHALPY = 0, FEM_APPARENT_CAPACITY = 1 } fem_formulation;
+
 /* One material (Section 2): density rho (kg/m^3), specific heat c (J/kgK),
  * conductivity k (W/mK), latent heat (J/kg) released linearly between
  * T_solidus and T_liquidus (K).  latent == 0 means no phase change (the
@@ -89,7 +102,8 @@ typedef struct {
     int32_t threads;     /* threads per CTA of the block kernel, 0 = auto (the
                             fewest threads whose 16-byte element accesses
                             cover the largest block); 128, 256, 512 or 1024 */
-    int32_t reserved[5];
+    int32_t formulation; /* fem_formulation, default FEM_ENTHALPY */
+    int32_t reserved[4];
 } fem_options;
 
 /* Statistics of the execution plan (fem_mesh_info). */

@@ -88,6 +88,7 @@ struct fem_mesh {
     std::vector<double> ranges;       // [nr][2]
     int32_t n_mat = 0;
     std::vector<double> mat_k;        // constant conductivity per material
+    std::vector<fem_material> mats;   // the material table (apparent capacity)
     // temperature-dependent conductivity: per material a table of (T, k)
     // points (empty: constant k); has_kt when any table is set
     std::vector<std::vector<double>> kt_T, kt_k;
@@ -139,7 +140,9 @@ struct fem_mesh {
     uint32_t *dSched = nullptr;
     int32_t *dIfPos = nullptr, *dIfSis = nullptr;   // interface: face position, sister nodes
     void *dIfG = nullptr;
-    uint8_t *dEmat = nullptr;                      // k(T): material per element position
+    uint8_t *dEmat = nullptr;                      // k(T), apparent capacity: material per element
+    void *dRv = nullptr, *dLmC = nullptr, *dLmL = nullptr, *dLmTs = nullptr, *dLmTl = nullptr,
+         *dPc = nullptr;                           // apparent capacity (see BlockArgs)
     void *dKtT = nullptr, *dKtK = nullptr;         // k(T) tables [n_mat][kKtMax]
     int32_t *dKtN = nullptr;
     double *dEpart = nullptr, *dQcum = nullptr, *dIo = nullptr,
@@ -198,6 +201,7 @@ void release_device(fem_mesh *m)
     m->dIfPos = m->dIfSis = nullptr;
     m->dIfG = nullptr;
     m->dEmat = nullptr;
+    m->dRv = m->dLmC = m->dLmL = m->dLmTs = m->dLmTl = m->dPc = nullptr;
     m->dKtT = m->dKtK = nullptr;
     m->dKtN = nullptr;
     m->dt_uploaded.clear();
@@ -216,6 +220,7 @@ int default_block_elems(const fem_mesh *m)
 }
 
 bool is_block(const fem_mesh *m) { return m->opt.variant == FEM_VARIANT_BLOCK; }
+bool is_lm(const fem_mesh *m) { return m->opt.formulation == FEM_APPARENT_CAPACITY; }
 
 // faces/fa/fg = Robin faces, then interface faces (whose load term the
 // interface kernel rewrites every step)
@@ -400,7 +405,13 @@ fem_status upload_nodes(fem_mesh *m)
 template <typename real>
 fem_status upload_kt(fem_mesh *m, const std::vector<int32_t> &elem_order)
 {
-    if (!m->has_kt) return FEM_OK;
+    if (!m->has_kt) {
+        if (!is_lm(m)) return FEM_OK;
+        std::vector<uint8_t> em(elem_order.size() + 8, 0);
+        for (size_t q = 0; q < elem_order.size(); q++)
+            if (elem_order[q] >= 0) em[q] = (uint8_t)m->mat[(size_t)elem_order[q]];
+        return upload<uint8_t>(m, &m->dEmat, em.data(), em.size());
+    }
     std::vector<real> T((size_t)m->n_mat * kKtMax, real(0)), k((size_t)m->n_mat * kKtMax, real(0));
     std::vector<int32_t> n((size_t)m->n_mat);
     for (int32_t mt = 0; mt < m->n_mat; mt++) {
@@ -478,8 +489,38 @@ fem_status upload_block(fem_mesh *m)
         }
         if ((st = upload<real>(m, &p, w.data(), w.size()))) return st;
         m->dW = p;
-        // k(T): the material of element i of block b at b*nes + i
-        if (m->has_kt) {
+        // apparent capacity: rho V / 4 of element i of block b at b*nes + i,
+        // the material table and the capacity partials of shared copies
+        if (is_lm(m)) {
+            std::vector<real> rv((size_t)bp.blocks.size() * nes + 8, real(0));
+            for (size_t bi = 0; bi < bp.blocks.size(); bi++)
+                for (int32_t i = 0; i < bp.blocks[bi].ne; i++) {
+                    const int32_t e = bp.elem_order[(size_t)bp.blocks[bi].e0 + i];
+                    rv[bi * nes + i] = (real)(m->mats[(size_t)m->mat[(size_t)e]].rho * m->vol[(size_t)e] / 4.0);
+                }
+            if ((st = upload<real>(m, &p, rv.data(), rv.size()))) return st;
+            m->dRv = p;
+            std::vector<real> c((size_t)m->n_mat), L((size_t)m->n_mat), Ts((size_t)m->n_mat),
+                Tl((size_t)m->n_mat);
+            for (int32_t mt = 0; mt < m->n_mat; mt++) {
+                c[(size_t)mt] = (real)m->mats[(size_t)mt].c;
+                L[(size_t)mt] = (real)m->mats[(size_t)mt].latent;
+                Ts[(size_t)mt] = (real)m->mats[(size_t)mt].T_solidus;
+                Tl[(size_t)mt] = (real)m->mats[(size_t)mt].T_liquidus;
+            }
+            if ((st = upload<real>(m, &p, c.data(), c.size()))) return st;
+            m->dLmC = p;
+            if ((st = upload<real>(m, &p, L.data(), L.size()))) return st;
+            m->dLmL = p;
+            if ((st = upload<real>(m, &p, Ts.data(), Ts.size()))) return st;
+            m->dLmTs = p;
+            if ((st = upload<real>(m, &p, Tl.data(), Tl.size()))) return st;
+            m->dLmTl = p;
+            if ((st = upload<real>(m, &p, nullptr, (size_t)std::max<int64_t>(bp.n_copies, 1)))) return st;
+            m->dPc = p;
+        }
+        // k(T) / apparent capacity: the material of element i of block b at b*nes + i
+        if (m->has_kt || is_lm(m)) {
             std::vector<int32_t> eo((size_t)bp.blocks.size() * nes, -1);
             for (size_t bi = 0; bi < bp.blocks.size(); bi++)
                 for (int32_t i = 0; i < bp.blocks[bi].ne; i++)
@@ -602,9 +643,11 @@ fem_status upload_block(fem_mesh *m)
     if ((size_t)optin < m->smem_bytes + 1024)
         return fail(FEM_EINVAL, "a block needs %zu bytes of shared memory (device limit %d); lower block_elems",
                     m->smem_bytes, optin);
-    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes, m->has_kt), "configuring the block kernel");
+    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes, m->has_kt, is_lm(m)),
+           "configuring the block kernel");
     int per_sm = 0;
-    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm, m->has_kt), "occupancy query");
+    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm, m->has_kt, is_lm(m)),
+           "occupancy query");
     if (per_sm < 1) return fail(FEM_EINVAL, "the block kernel does not fit on an SM; lower block_elems");
     m->ctas_per_sm = per_sm;
     return upload_interface<real>(m, bp.face_order);
@@ -698,6 +741,12 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.kt_T = (const real *)m->dKtT;
     a.kt_k = (const real *)m->dKtK;
     a.kt_n = m->dKtN;
+    a.rv = (const real *)m->dRv;
+    a.lm_c = (const real *)m->dLmC;
+    a.lm_L = (const real *)m->dLmL;
+    a.lm_Ts = (const real *)m->dLmTs;
+    a.lm_Tl = (const real *)m->dLmTl;
+    a.Pc = (real *)m->dPc;
     // test hook: a bounded wait that runs out (see BlockArgs)
     const char *skip = getenv("FEM_FAULT_SKIP_WEIGHT_COPY");
     a.fault_skip_weights = (skip && *skip && *skip != '0') ? 1 : 0;
@@ -718,6 +767,11 @@ StateView<real> view_of(const fem_mesh *m)
         v.Eloc = (real *)m->dE;
         v.n_int = m->N;
     }
+    v.is_T = m->opt.formulation == FEM_APPARENT_CAPACITY;
+    v.C = (const real *)m->dC;
+    v.Lc = (const real *)m->dLc;
+    v.ph = m->dPh;
+    v.ranges = (const real *)m->dRanges;
     return v;
 }
 
@@ -920,7 +974,8 @@ fem_status launch_step_kernel(fem_mesh *m, int k, double dt)
     if (is_block(m)) {
         const BlockArgs<real> a = block_args<real>(m);
         if (k == 0)
-            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream, m->has_kt),
+            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream, m->has_kt,
+                                             is_lm(m)),
                    "block kernel");
         else
             KERNEL(launch_shared_update<real>(a, dt, m->stream), "shared-node kernel");
@@ -1036,6 +1091,10 @@ fem_status fem_mesh_create_ex(const double *xyz, int64_t n_nodes, const int32_t 
     fem_options opt{};
     if (opts) opt = *opts;
     if (opt.variant < 0 || opt.variant > 2) return fail(FEM_EINVAL, "unknown variant %d", opt.variant);
+    if (opt.formulation != FEM_ENTHALPY && opt.formulation != FEM_APPARENT_CAPACITY)
+        return fail(FEM_EINVAL, "unknown formulation %d", opt.formulation);
+    if (opt.formulation == FEM_APPARENT_CAPACITY && opt.variant != FEM_VARIANT_BLOCK)
+        return fail(FEM_EINVAL, "the apparent-capacity formulation uses the block variant");
     if (opt.threads != 0 && opt.threads != 128 && opt.threads != 256 && opt.threads != 512 &&
         opt.threads != 1024)
         return fail(FEM_EINVAL, "threads must be 0, 128, 256, 512 or 1024");
@@ -1123,6 +1182,9 @@ fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_ma
         if (q.latent < 0) return fail(FEM_EINVAL, "material %d: negative latent heat", i);
         if (q.latent > 0 && q.T_liquidus < q.T_solidus)
             return fail(FEM_EINVAL, "material %d: T_liquidus < T_solidus", i);
+        if (q.latent > 0 && is_lm(m) && !(q.T_liquidus > q.T_solidus))
+            return fail(FEM_EINVAL, "material %d: the apparent-capacity formulation needs "
+                                    "T_liquidus > T_solidus", i);
     }
     for (int64_t e = 0; e < m->E; e++)
         if (m->mat[e] >= n_mat)
@@ -1181,6 +1243,7 @@ fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_ma
         m->rng_id.swap(rid);
         m->ranges.swap(ranges);
         m->n_mat = n_mat;
+        m->mats.assign(mats, mats + n_mat);
         m->mat_k.resize((size_t)n_mat);
         for (int32_t i = 0; i < n_mat; i++) m->mat_k[(size_t)i] = mats[i].k;
         m->kt_T.assign((size_t)n_mat, {});
@@ -1642,6 +1705,8 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
         if (p->prec != p0->prec) return fail(FEM_EINVAL, "part %d: precision differs from part 0", i);
         if (p->opt.variant != FEM_VARIANT_BLOCK)
             return fail(FEM_EINVAL, "part %d: batches use the block variant", i);
+        if (p->opt.formulation != p0->opt.formulation)
+            return fail(FEM_EINVAL, "part %d: formulation differs from part 0", i);
     }
     std::unique_ptr<fem_mesh> m;
     try {
@@ -1688,12 +1753,30 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
             const int32_t no = (int32_t)m->inst_node[(size_t)i];
             m->xyz.insert(m->xyz.end(), p->xyz.begin(), p->xyz.end());
             for (int32_t v : p->tets) m->tets.push_back(v + no);
-            for (int32_t v : p->mat) m->mat.push_back(v + m->n_mat);
-            m->mat_k.insert(m->mat_k.end(), p->mat_k.begin(), p->mat_k.end());
-            m->kt_T.insert(m->kt_T.end(), p->kt_T.begin(), p->kt_T.end());
-            m->kt_k.insert(m->kt_k.end(), p->kt_k.begin(), p->kt_k.end());
+            // materials: identical ones (same properties and k(T) table) are
+            // merged, so that many parts of a few alloys stay few materials
+            std::vector<int32_t> mmap((size_t)p->n_mat);
+            for (int32_t q = 0; q < p->n_mat; q++) {
+                const fem_material &a = p->mats[(size_t)q];
+                int32_t found = -1;
+                for (int32_t r = 0; r < m->n_mat && found < 0; r++) {
+                    const fem_material &b = m->mats[(size_t)r];
+                    if (a.rho == b.rho && a.c == b.c && a.k == b.k && a.latent == b.latent &&
+                        a.T_solidus == b.T_solidus && a.T_liquidus == b.T_liquidus &&
+                        p->kt_T[(size_t)q] == m->kt_T[(size_t)r] && p->kt_k[(size_t)q] == m->kt_k[(size_t)r])
+                        found = r;
+                }
+                if (found < 0) {
+                    found = m->n_mat++;
+                    m->mats.push_back(a);
+                    m->mat_k.push_back(p->mat_k[(size_t)q]);
+                    m->kt_T.push_back(p->kt_T[(size_t)q]);
+                    m->kt_k.push_back(p->kt_k[(size_t)q]);
+                }
+                mmap[(size_t)q] = found;
+            }
+            for (int32_t v : p->mat) m->mat.push_back(mmap[(size_t)v]);
             m->has_kt |= p->has_kt;
-            m->n_mat += p->n_mat;
             m->vol.insert(m->vol.end(), p->vol.begin(), p->vol.end());
             for (int32_t r : p->rank) m->rank.push_back(r + no);
             m->w.insert(m->w.end(), p->w.begin(), p->w.end());
@@ -1730,6 +1813,9 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
             m->inst_stable.push_back(dt);
         }
         if (m->ranges.empty()) { m->ranges.push_back(0.0); m->ranges.push_back(0.0); }
+        if ((m->has_kt || is_lm(m.get())) && m->n_mat > 255)
+            return fail(FEM_EINVAL, "k(T) tables and the apparent-capacity formulation need at most 255 "
+                                    "distinct materials in a batch");
         m->F_rb = (int64_t)m->rb_fa.size();
         m->F_if = (int64_t)m->if_fa.size();
         combine_faces(m.get());
@@ -1815,7 +1901,8 @@ fem_status advance_launches(fem_mesh *m, const std::vector<int64_t> &nk, cudaStr
             a.b_count = bp.inst_block_start[(size_t)k1] - a.b_first;
             a.s_first = bp.inst_sh_start[(size_t)k0];
             a.s_end = bp.inst_sh_start[(size_t)k1];
-            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, 0.0, st, m->has_kt),
+            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, 0.0, st, m->has_kt,
+                                             is_lm(m)),
                    "block kernel");
             KERNEL(launch_shared_update<real>(a, 0.0, st), "shared-node kernel");
             k0 = k1;

@@ -93,6 +93,12 @@ struct StateView {
     real *Esh;
     const int32_t *home;
     int64_t n_int;
+    // the state holds T instead of E (apparent-capacity formulation); the
+    // node properties convert between the two
+    bool is_T;
+    const real *C, *Lc;
+    const uint8_t *ph;
+    const real *ranges;
 #ifdef __CUDACC__
     __device__ __forceinline__ real &E(int64_t i) const
     {
@@ -152,6 +158,13 @@ struct BlockArgs {
     const uint8_t *emat;
     const real *kt_T, *kt_k;
     const int32_t *kt_n;
+    // apparent-capacity formulation (instantiations with LM = true): the
+    // state is T; rv[b*nes + e] = rho V / 4 of the element, material m's
+    // specific heat, latent heat and range (lm_c, lm_L, lm_Ts, lm_Tl)[m];
+    // shared copies also write their capacity partials Pc (like P)
+    const real *rv;
+    const real *lm_c, *lm_L, *lm_Ts, *lm_Tl;
+    real *Pc;
     // test hook (FEM_FAULT_SKIP_WEIGHT_COPY): announce the conductance copy
     // but never issue it, so that the wait for it runs out
     int32_t fault_skip_weights;
@@ -187,7 +200,7 @@ struct FlatArgs {
 // kt: the instantiation with temperature-dependent conductivity
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream, bool kt = false);
+                        void *stream, bool kt = false, bool lm = false);
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream);
 // Interface faces (Eq. 8): fg[pos[f]] = g[f] * mean T of nodes sis[f][0..2]
@@ -197,9 +210,10 @@ int launch_interface(StateView<real> v, const real *C, const real *Lc, const uin
                      const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
                      const real *g, int64_t n, void *stream);
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false);
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false, bool lm = false);
 template <typename real>
-int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt = false);
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt = false,
+                           bool lm = false);
 // Mirrors of the shared nodes' E in the block-local arrays follow Esh
 // (after the state was set from outside).
 template <typename real>

@@ -100,6 +100,32 @@ __device__ __forceinline__ void block_sum(double (&v)[K])
     }
 }
 
+// Node state access: the state is E (enthalpy formulation) or T
+// (apparent-capacity formulation, v.is_T); these convert with the node's
+// capacities and phase-change range.
+template <typename real>
+__device__ __forceinline__ real state_T(const StateView<real> &v, int64_t i)
+{
+    const real s = v.E(i);
+    return v.is_T ? s : temperature_of(s, v.C[i], v.Lc[i], v.ph[i], v.ranges);
+}
+template <typename real>
+__device__ __forceinline__ real state_E(const StateView<real> &v, int64_t i)
+{
+    const real s = v.E(i);
+    return v.is_T ? enthalpy_of(s, v.C[i], v.Lc[i], v.ph[i], v.ranges) : s;
+}
+template <typename real>
+__device__ __forceinline__ void state_set_T(const StateView<real> &v, int64_t i, real T)
+{
+    v.E(i) = v.is_T ? T : enthalpy_of(T, v.C[i], v.Lc[i], v.ph[i], v.ranges);
+}
+template <typename real>
+__device__ __forceinline__ void state_set_E(const StateView<real> &v, int64_t i, real E)
+{
+    v.E(i) = v.is_T ? temperature_of(E, v.C[i], v.Lc[i], v.ph[i], v.ranges) : E;
+}
+
 // ---------------------------------------------------------------------------
 // Block variant
 // ---------------------------------------------------------------------------
@@ -190,6 +216,49 @@ __device__ __forceinline__ real conductivity_of(const real *kt_T, const real *kt
     return k0 + (__ldg(kj + j + 1) - k0) * (T - T0) / (__ldg(Tj + j + 1) - T0);
 }
 
+// Apparent specific heat of one element by Lemmon's method (Eq. 7): the
+// ratio of the gradient magnitudes of H(T) = c T + L f_l(T) and of T over the
+// element.  With the six conductances (K^e has zero row sums), |grad x|^2 is
+// proportional to sum_{a<b} w_ab (x_a - x_b)^2, so the common factor cancels;
+// where T is uniform over the element (every difference below a
+// micro-kelvin) dH/dT at the mean temperature is used.
+template <typename real>
+__device__ __forceinline__ real apparent_cp(const BlockArgs<real> &a, int m, real T0, real T1, real T2,
+                                            real T3, real w01, real w02, real w03, real w12,
+                                            real w13, real w23)
+{
+    const real c = __ldg(a.lm_c + m), L = __ldg(a.lm_L + m);
+    if (!(L > real(0))) return c;
+    const real Ts = __ldg(a.lm_Ts + m), Tl = __ldg(a.lm_Tl + m), inv = real(1) / (Tl - Ts);
+    auto H = [&](real T) {
+        const real f = T <= Ts ? real(0) : (T >= Tl ? real(1) : (T - Ts) * inv);
+        return c * T + L * f;
+    };
+    const real H0 = H(T0), H1 = H(T1), H2 = H(T2), H3 = H(T3);
+    const real num = w01 * (H0 - H1) * (H0 - H1) + w02 * (H0 - H2) * (H0 - H2) +
+                     w03 * (H0 - H3) * (H0 - H3) + w12 * (H1 - H2) * (H1 - H2) +
+                     w13 * (H1 - H3) * (H1 - H3) + w23 * (H2 - H3) * (H2 - H3);
+    const real den = w01 * (T0 - T1) * (T0 - T1) + w02 * (T0 - T2) * (T0 - T2) +
+                     w03 * (T0 - T3) * (T0 - T3) + w12 * (T1 - T2) * (T1 - T2) +
+                     w13 * (T1 - T3) * (T1 - T3) + w23 * (T2 - T3) * (T2 - T3);
+    const real wsum = ((w01 + w02) + (w03 + w12)) + (w13 + w23);
+    if (den > real(1e-12) * wsum) return sqrt(num / den);
+    const real Tm = (T0 + T1 + T2 + T3) * real(0.25);
+    return (Tm >= Ts && Tm < Tl) ? c + L * inv : c;
+}
+
+// Capacity behind a slot of the block's slot array: element-corner slots
+// (below 4 ne_pad) name element slot - corner * ne_pad, whose capacity pass
+// 2 left at sw[element]; face and padding slots carry none.
+template <typename real>
+__device__ __forceinline__ real slot_capacity(const real *sw, uint32_t v, int ne_pad)
+{
+    const int sl = (int)v;
+    if (sl >= 4 * ne_pad) return real(0);
+    const int c = (sl >= ne_pad) + (sl >= 2 * ne_pad) + (sl >= 3 * ne_pad);
+    return sw[sl - c * ne_pad];
+}
+
 // Element product of one tet: r_a = sum_b w_ab (T_b - T_a), w_ab = -K^e_ab
 // (the row of -K^e T^e; K^e symmetric with zero row sums, Eq. 9).
 template <typename real>
@@ -239,7 +308,7 @@ __device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
 // rows (fixed stride 6*b*nes) into shared memory meanwhile.
 // Thread t owns local nodes t, t+NT, ... (the 32-lane schedule group
 // g = warp + j*NW covers nodes 32 g + lane) and element quad(s) t, t+NT, ...
-template <typename real, int NT, bool KT>
+template <typename real, int NT, bool KT, bool LM>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     k_block_step(const BlockArgs<real> a, const real dt)
 {
@@ -302,10 +371,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     // k(T): the materials of this thread's first element quad, loaded now
     // and used in pass 2
     uint32_t mat_q = 0;
-    if (KT && (int)threadIdx.x * VN < bi.ne) {
+    V rv_q{};   // apparent capacity: rho V / 4 of the quad's elements
+    if ((KT || LM) && (int)threadIdx.x * VN < bi.ne) {
         const uint8_t *pm = a.emat + (size_t)b * nes + threadIdx.x * VN;
         mat_q = VN == 4 ? *reinterpret_cast<const uint32_t *>(pm)
                         : (uint32_t)*reinterpret_cast<const uint16_t *>(pm);
+        if (LM) rv_q = *reinterpret_cast<const V *>(a.rv + (size_t)b * nes + threadIdx.x * VN);
     }
     // this thread's first face
     real fa0 = real(0), fg0 = real(0);
@@ -332,8 +403,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         const int l = threadIdx.x + j * NT;
         Tl[j] = real(0);
         if (l < ls) {
-            const V2 cl = reinterpret_cast<const V2 *>(sv)[l];
-            Tl[j] = temperature_of(sE[l], cl.x, cl.y, sPh[l], a.ranges);
+            if (LM) {   // the state is T
+                Tl[j] = sE[l];
+            } else {
+                const V2 cl = reinterpret_cast<const V2 *>(sv)[l];
+                Tl[j] = temperature_of(sE[l], cl.x, cl.y, sPh[l], a.ranges);
+            }
         }
     }
     // the vote below is also the barrier that ends the reads of (C, Lc)
@@ -379,13 +454,26 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         V T1 = *reinterpret_cast<const V *>(sv + ne_pad + e);
         V T2 = *reinterpret_cast<const V *>(sv + 2 * ne_pad + e);
         V T3 = *reinterpret_cast<const V *>(sv + 3 * ne_pad + e);
-        if (KT) {   // K^e(T) = k(mean element temperature) x the k = 1 weights
-            uint32_t mq = mat_q;
-            if (qd != (int)threadIdx.x) {
-                const uint8_t *pm = a.emat + (size_t)b * nes + e;
-                mq = VN == 4 ? *reinterpret_cast<const uint32_t *>(pm)
-                             : (uint32_t)*reinterpret_cast<const uint16_t *>(pm);
+        uint32_t mq = mat_q;
+        V rvq = rv_q;
+        if ((KT || LM) && qd != (int)threadIdx.x) {
+            const uint8_t *pm = a.emat + (size_t)b * nes + e;
+            mq = VN == 4 ? *reinterpret_cast<const uint32_t *>(pm)
+                         : (uint32_t)*reinterpret_cast<const uint16_t *>(pm);
+            if (LM) rvq = *reinterpret_cast<const V *>(a.rv + (size_t)b * nes + e);
+        }
+        V capq{};
+        if (LM) {   // apparent specific heat (Eq. 7) x rho V / 4 per element
+#pragma unroll
+            for (int i = 0; i < VN; i++) {
+                const int mt = (int)((mq >> (8 * i)) & 0xFFu);
+                vat(capq, i) = vat(rvq, i) * apparent_cp(a, mt, vat(T0, i), vat(T1, i), vat(T2, i),
+                                                         vat(T3, i), vat(wq[0], i), vat(wq[1], i),
+                                                         vat(wq[2], i), vat(wq[3], i), vat(wq[4], i),
+                                                         vat(wq[5], i));
             }
+        }
+        if (KT) {   // K^e(T) = k(mean element temperature) x the k = 1 weights
 #pragma unroll
             for (int i = 0; i < VN; i++) {
                 const real Tm = (vat(T0, i) + vat(T1, i) + vat(T2, i) + vat(T3, i)) * real(0.25);
@@ -403,6 +491,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         *reinterpret_cast<V *>(sv + ne_pad + e) = T1;
         *reinterpret_cast<V *>(sv + 2 * ne_pad + e) = T2;
         *reinterpret_cast<V *>(sv + 3 * ne_pad + e) = T3;
+        // the element capacities go over the first conductance row, which
+        // only this thread reads (its own quad, already in registers)
+        if (LM) *reinterpret_cast<V *>(sw + e) = capq;
     }
     if (threadIdx.x == 0) sv[dummy] = real(0);   // padding adds nothing in pass 3
     // Robin faces (Eq. 4): r_c = A/3 (h T_inf - q) - h A/12 (T_c + T_0 + T_1 + T_2)
@@ -434,16 +525,22 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         if (g >= bi.ngrp) continue;
         const int l = 32 * g + lane;
         const int p0 = (int)chunk[g], p1 = (int)chunk[g + 1];
-        real R = real(0);
+        real R = real(0), Cap = real(0);
         for (int pr = p0; pr < p1; ++pr) {
             const uint32_t v = pairs[pr * 32 + lane];
             R += sv[v & 0xFFFFu];
             R += sv[v >> 16];
+            if (LM) {   // capacity of the element behind each element-corner slot
+                Cap += slot_capacity(sw, v & 0xFFFFu, ne_pad);
+                Cap += slot_capacity(sw, v >> 16, ne_pad);
+            }
         }
         if (l < bi.nint) {
-            if (!(sPh[l] & kDirichletBit)) a.Eloc[lb + l] = sE[l] + dtb * R;
+            if (!(sPh[l] & kDirichletBit))
+                a.Eloc[lb + l] = LM ? sE[l] + dtb * R / Cap : sE[l] + dtb * R;
         } else if (l < nloc) {
             a.P[sPos[l]] = R;
+            if (LM) a.Pc[sPos[l]] = Cap;
         }
     }
     // cumulative boundary heat of the blocks that own Robin faces (FP64)
@@ -483,16 +580,18 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
         }
     }
     if (update) {
-        real R[NPT];
+        real R[NPT], Cp[NPT];
 #pragma unroll
         for (int j = 0; j < NPT; j++) {
-            R[j] = real(0);
+            R[j] = Cp[j] = real(0);
             for (int k = k0[j]; k < k1[j]; ++k) R[j] += a.P[k];   // block order
+            if (a.Pc)   // apparent capacity: T += dt R / C_app
+                for (int k = k0[j]; k < k1[j]; ++k) Cp[j] += a.Pc[k];
         }
 #pragma unroll
         for (int j = 0; j < NPT; j++)
             if (act[j]) {
-                E[j] += dts[j] * R[j];
+                E[j] += a.Pc ? dts[j] * R[j] / Cp[j] : dts[j] * R[j];
                 a.Esh[base + (int64_t)j * NT] = E[j];
             }
     }
@@ -518,7 +617,7 @@ __global__ void k_interface(StateView<real> v, const real *C, const real *Lc, co
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const int32_t i = sis[3 * f + c];
-            T += temperature_of(v.E(i), C[i], Lc[i], ph[i], ranges);
+            T += state_T(v, i);
         }
         fg[pos[f]] = g[f] * (T / real(3));
     }
@@ -610,7 +709,7 @@ __global__ void k_set_temperature(StateView<real> v, const real *C, const real *
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t p = ph[i];
         const double T = (dirT_int && (p & kDirichletBit)) ? dirT_int[i] : T_in[node_old[i]];
-        v.E(i) = enthalpy_of((real)T, C[i], Lc[i], p, ranges);
+        state_set_T(v, i, (real)T);
     }
 }
 
@@ -623,7 +722,7 @@ __global__ void k_set_state(StateView<real> v, const double *E_in, const int32_t
          i += (int64_t)gridDim.x * blockDim.x) {
         const double E = E_in[node_old[i]];
         bad |= !isfinite(E);
-        v.E(i) = (real)E;
+        state_set_E(v, i, (real)E);
     }
     if (bad && err) atomicOr(err, kErrBadInput);
 }
@@ -636,7 +735,7 @@ __global__ void k_get_temperature(StateView<real> v, const real *C, const real *
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double T = (double)temperature_of(v.E(i), C[i], Lc[i], ph[i], ranges);
+        const double T = (double)state_T(v, i);
         bad |= !isfinite(T);
         T_out[node_old[i]] = T;
     }
@@ -648,7 +747,7 @@ __global__ void k_get_state(StateView<real> v, double *E_out, const int32_t *nod
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        E_out[node_old[i]] = (double)v.E(i);
+        E_out[node_old[i]] = (double)state_E(v, i);
 }
 
 template <typename real, int NT>
@@ -658,7 +757,7 @@ __global__ void __launch_bounds__(NT) k_energy_snapshot(StateView<real> v, const
 {
     double acc[2] = {0.0, 0.0};
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
-        const real E = v.E(i);
+        const real E = state_E(v, i);
         acc[0] += (double)E;
         acc[1] += latent_of(E, C[i], Lc[i], ph[i], ranges);
     }
@@ -709,41 +808,47 @@ inline int grid_for(int64_t n, int threads)
 // The block kernel instantiation for (threads, kt), as a function pointer.
 template <typename real>
 using BlockKernel = void (*)(const BlockArgs<real>, const real);
+template <typename real, int NT>
+BlockKernel<real> block_kernel_nt(bool kt, bool lm)
+{
+    if (lm) return kt ? k_block_step<real, NT, true, true> : k_block_step<real, NT, false, true>;
+    return kt ? k_block_step<real, NT, true, false> : k_block_step<real, NT, false, false>;
+}
 template <typename real>
-BlockKernel<real> block_kernel_for(int threads, bool kt)
+BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm)
 {
     switch (threads) {
-    case 128: return kt ? k_block_step<real, 128, true> : k_block_step<real, 128, false>;
-    case 256: return kt ? k_block_step<real, 256, true> : k_block_step<real, 256, false>;
-    case 512: return kt ? k_block_step<real, 512, true> : k_block_step<real, 512, false>;
-    case 1024: return kt ? k_block_step<real, 1024, true> : k_block_step<real, 1024, false>;
+    case 128: return block_kernel_nt<real, 128>(kt, lm);
+    case 256: return block_kernel_nt<real, 256>(kt, lm);
+    case 512: return block_kernel_nt<real, 512>(kt, lm);
+    case 1024: return block_kernel_nt<real, 1024>(kt, lm);
     default: return nullptr;
     }
 }
 
 template <typename real>
-int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt)
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt, bool lm)
 {
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, f, threads, smem_bytes);
 }
 
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes, bool kt)
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt, bool lm)
 {
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream, bool kt)
+                        void *stream, bool kt, bool lm)
 {
     const int grid = a.b_count;
     if (grid <= 0) return 0;
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
     if (!f) return (int)cudaErrorInvalidValue;
     f<<<grid, threads, smem_bytes, (cudaStream_t)stream>>>(a, (real)dt);
     return (int)cudaGetLastError();
@@ -874,14 +979,14 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
 }
 
 #define FEM_INSTANTIATE(real)                                                                     \
-    template int configure_block_kernel<real>(int, size_t, bool);                                 \
-    template int block_kernel_occupancy<real>(int, size_t, int *, bool);                          \
+    template int configure_block_kernel<real>(int, size_t, bool, bool);                           \
+    template int block_kernel_occupancy<real>(int, size_t, int *, bool, bool);                    \
     template int launch_mirror_copies<real>(const BlockArgs<real> &, void *);                     \
     template int launch_interface<real>(StateView<real>, const real *, const real *,              \
                                         const uint8_t *, const real *, real *, const int32_t *,   \
                                         const int32_t *, const real *, int64_t, void *);          \
     template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *,  \
-                                           bool);                                                 \
+                                           bool, bool);                                           \
     template int launch_shared_update<real>(const BlockArgs<real> &, double, void *);             \
     template int launch_flat_temperature<real>(const FlatArgs<real> &, void *);                   \
     template int launch_flat_elements<real>(const FlatArgs<real> &, bool, const int64_t *, int,  \

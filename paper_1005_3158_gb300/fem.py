@@ -16,6 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfem.so")
 
 FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_ESTATE, FEM_EUNSTABLE, FEM_ETIMEOUT = range(7)
+FEM_ENTHALPY, FEM_APPARENT_CAPACITY = 0, 1
+FORMULATIONS = {"enthalpy": FEM_ENTHALPY, "apparent": FEM_APPARENT_CAPACITY}
 FEM_FP64, FEM_FP32 = 0, 1
 FEM_VARIANT_BLOCK, FEM_VARIANT_ATOMIC, FEM_VARIANT_COLORED = 0, 1, 2
 STATUS_NAMES = {0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_ENOMEM", 3: "FEM_ECUDA", 4: "FEM_ESTATE",
@@ -45,7 +47,8 @@ class FemMaterial(ctypes.Structure):
 
 class FemOptions(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block_elems", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("threads", ctypes.c_int32), ("formulation", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class FemInfo(ctypes.Structure):
@@ -177,6 +180,7 @@ def fem_mesh_create(xyz, tets, mat_id, prec=FEM_FP64, reorder=0, options=None):
         opt.variant = int(options.get("variant", 0))
         opt.block_elems = int(options.get("block_elems", 0))
         opt.threads = int(options.get("threads", 0))
+        opt.formulation = int(options.get("formulation", 0))
     if opt is None:
         st = _lib.fem_mesh_create(_pd(xyz), xyz.shape[0], _pi(tets), tets.shape[0], _pi(mat_id),
                                   prec, reorder, ctypes.byref(h))
@@ -376,13 +380,16 @@ class Mesh:
     """One libfem mesh handle built from a ``meshgen.Problem``-like object."""
 
     def __init__(self, prob, precision="fp64", reorder=1, variant="block", block_elems=0,
-                 threads=0, faces=True, dirichlet=True, set_temperature=True):
+                 threads=0, faces=True, dirichlet=True, set_temperature=True,
+                 formulation="enthalpy"):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        form = FORMULATIONS[formulation] if isinstance(formulation, str) else int(formulation)
         self.n_nodes = int(prob.xyz.shape[0])
         self.n_tets = int(prob.tets.shape[0])
         self.h = fem_mesh_create(prob.xyz, prob.tets, prob.mat, prec, reorder,
-                                 {"variant": var, "block_elems": block_elems, "threads": threads})
+                                 {"variant": var, "block_elems": block_elems, "threads": threads,
+                                  "formulation": form})
         try:
             fem_set_materials(self.h, prob.materials)
             if faces and prob.faces.shape[0] > 0:
@@ -459,12 +466,14 @@ class Batch(Mesh):
     """A batch of independent meshes (fem_batch_create) built from several
     ``meshgen.Problem``-like objects; the parts are released once copied."""
 
-    def __init__(self, probs, precision="fp32", reorder=1, block_elems=0, threads=0):
+    def __init__(self, probs, precision="fp32", reorder=1, block_elems=0, threads=0,
+                 formulation="enthalpy"):
         parts = []
         try:
             for p in probs:
                 parts.append(Mesh(p, precision, reorder=reorder, variant="block",
-                                  block_elems=block_elems, threads=threads))
+                                  block_elems=block_elems, threads=threads,
+                                  formulation=formulation))
             self.h = fem_batch_create([q.h for q in parts])
         finally:
             for q in parts:

@@ -63,3 +63,15 @@ def test_conductivity_tables_stable_dt_matches_oracle():
             fem.fem_set_conductivity(m.h, 0, [600.0, 300.0], [1.0, 2.0])  # not ascending
         with pytest.raises(fem.FemError):
             fem.fem_set_conductivity(m.h, 0, [300.0], [0.0])             # k <= 0
+
+
+def test_formulation_validation():
+    p = mg.unit_cube(3)
+    with pytest.raises(fem.FemError):
+        fem.Mesh(p, "fp64", variant="atomic", formulation="apparent")
+    q = mg.unit_cube(3)
+    q.materials = np.array([[2700.0, 900.0, 150.0, 3.9e5, 933.0, 933.0]])
+    with pytest.raises(fem.FemError):
+        fem.Mesh(q, "fp64", formulation="apparent")
+    with fem.Mesh(p, "fp64", formulation="apparent") as m:
+        assert m.stable_dt() == pytest.approx(oracle.OracleProblem(p).stable_dt(), rel=1e-13)
