@@ -86,7 +86,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="block_with_cores_220")
+    ap.add_argument("--workload", default=None,
+                    help="default block_with_cores_220 (or the one --config names)")
+    ap.add_argument("--config", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="1: unit_cube_20 FP64 (parity case), 2: flanged_casting, "
+                         "3: block_with_cores_220 (the default), 4: batched_castings_256")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", default="block", choices=["block", "atomic", "colored"])
     ap.add_argument("--reorder", type=int, default=1)
@@ -99,7 +103,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-sequential", action="store_true",
                     help="batched workload: skip the instance-by-instance comparison")
-    return ap.parse_args()
+    a = ap.parse_args()
+    named = {1: "unit_cube_20", 2: "flanged_casting", 3: "block_with_cores_220",
+             4: "batched_castings_256"}
+    if a.workload is None:
+        a.workload = named.get(a.config, "block_with_cores_220")
+    if a.config == 1 and "--precision" not in sys.argv:
+        a.precision = "fp64"
+    return a
 
 
 def make_problem(name: str):

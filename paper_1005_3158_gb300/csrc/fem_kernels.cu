@@ -378,12 +378,15 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
                         : (uint32_t)*reinterpret_cast<const uint16_t *>(pm);
         if (LM) rv_q = *reinterpret_cast<const V *>(a.rv + (size_t)b * nes + threadIdx.x * VN);
     }
-    // this thread's first face
+    // this thread's first face; thread 0: the block's boundary heat so far
+    // (loads whose latency the passes below hide)
     real fa0 = real(0), fg0 = real(0);
     if ((int)threadIdx.x < bi.nf) {
         fa0 = __ldg(a.fa + bi.f0 + threadIdx.x);
         fg0 = __ldg(a.fg + bi.f0 + threadIdx.x);
     }
+    double qprev = 0.0;
+    if (threadIdx.x == 0 && bi.nf > 0) qprev = a.qcum[b];
 
     // the mbarriers were initialised by thread 0 before any other thread
     // polls them: the barrier below orders the two
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     if (bi.nf > 0 && threadIdx.x == 0) {
         double q = 0.0;
         for (int k = 0; k < NW; k++) q += qwarp[k];
-        a.qcum[b] += (double)dtb * q;
+        a.qcum[b] = qprev + (double)dtb * q;
     }
 }
 
