@@ -31,9 +31,10 @@ namespace fem {
 //             slot indices) per lane and pair of rounds; padding entries
 //             name the dummy slot 4*ne_pad + 3*nf_pad
 //   chunk     the block's schedule chunk in the device stream starts at
-//             32-bit word s0: a header of ngrp+1 group offsets (in pairs of
-//             rounds, padded to a multiple of 4 words), then the pairs
-//             (pair p, lane l at word p*32 + l); one bulk copy moves it
+//             32-bit word s0 = b * stride (stride: the largest chunk): a
+//             header of ngrp+1 group offsets (in pairs of rounds, padded to a
+//             multiple of 4 words), then the pairs (pair p, lane l at word
+//             p*32 + l); one bulk copy of the whole stride moves it
 struct BlockInfo {
     int32_t e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad;
     int32_t nep, r0, nrounds, s0;
@@ -130,7 +131,7 @@ struct BlockArgs {
     const real *fg;
     // schedule chunks (see BlockInfo)
     const uint32_t *sched;
-    int32_t chunk_words;       // largest schedule chunk (32-bit words)
+    int32_t chunk_words;       // schedule chunk stride = largest chunk (32-bit words)
     int32_t max_slots;         // largest slot count (+ dummy), a multiple of 4
     // shared-node exchange: node s owns P[sh_ptr[s] .. sh_ptr[s+1]); entry k
     // of that range is the partial of one copy, whose mirror sits at

@@ -259,6 +259,25 @@ __device__ __forceinline__ real slot_capacity(const real *sw, uint32_t v, int ne
     return sw[sl - c * ne_pad];
 }
 
+// The 32-lane schedule group that warp `warp` handles in its j-th slot (-1:
+// none), for NW warps and ngrp groups.  Groups come longest first (nodes are
+// ordered by slot count); when there are between NW and 2 NW of them the
+// longest get a warp each and the rest are paired long with short on the
+// remaining warps, so that no warp's work exceeds the longest group's.
+template <int NW, int MAXJ>
+__device__ __forceinline__ int block_group(int warp, int j, int ngrp)
+{
+    if (ngrp <= NW) return j == 0 && warp < ngrp ? warp : -1;
+    if (MAXJ >= 2 && ngrp <= 2 * NW) {
+        const int extra = ngrp - NW;
+        if (warp < NW - extra) return j == 0 ? warp : -1;
+        const int i = warp - (NW - extra);
+        return j == 0 ? NW - extra + i : (j == 1 ? ngrp - 1 - i : -1);
+    }
+    const int g = warp + j * NW;
+    return g < ngrp ? g : -1;
+}
+
 // Element product of one tet: r_a = sum_b w_ab (T_b - T_a), w_ab = -K^e_ab
 // (the row of -K^e T^e; K^e symmetric with zero row sums, Eq. 9).
 template <typename real>
@@ -302,12 +321,12 @@ struct Vec4Of<double> {
 __device__ __forceinline__ float &vat(float4 &v, int i) { return (&v.x)[i]; }
 __device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
 
-// One CTA per element block b, NT threads.  The block's local node data sit
-// at a fixed stride (b*ls) and are loaded at kernel start from blockIdx
-// alone; thread 0 bulk-copies the schedule chunk and the six conductance
-// rows (fixed stride 6*b*nes) into shared memory meanwhile.
-// Thread t owns local nodes t, t+NT, ... (the 32-lane schedule group
-// g = warp + j*NW covers nodes 32 g + lane) and element quad(s) t, t+NT, ...
+// One CTA per element block b, NT threads.  The block's local node data
+// (stride b*ls), schedule chunk (stride b*chunk_words) and six conductance
+// rows (stride 6*b*nes) all sit at fixed strides, so thread 0 bulk-copies
+// them into shared memory at kernel start from blockIdx alone.
+// A warp owns the 32-lane schedule groups block_group() gives it (group g
+// covers local nodes 32 g + lane); thread t owns element quad(s) t, t+NT, ...
 template <typename real, int NT, bool KT, bool LM>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     k_block_step(const BlockArgs<real> a, const real dt)
@@ -351,20 +370,20 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         bulk_load(smem_addr(sv), a.CLloc + 2 * lb, 2 * eb, bar_n);
         bulk_load(smem_addr(sPh), a.phloc + lb, (uint32_t)ls, bar_n);
         bulk_load(smem_addr(sPos), a.posloc + lb, (uint32_t)ls * 4u, bar_n);
+        // the schedule chunk (fixed stride) and the six conductance rows:
+        // every copy is in flight before the block header is read
+        const uint32_t bytes = (uint32_t)a.chunk_words * 4u;
+        mbar_arrive_expect_tx(bar_s, bytes);
+        bulk_load(smem_addr(chunk), a.sched + (size_t)b * a.chunk_words, bytes, bar_s);
+        const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
+        mbar_arrive_expect_tx(bar_w, wbytes);
+        if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
     }
     const BlockInfo &bi = a.blocks[b];
     const int nloc = bi.nint + bi.nsh;
     const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad;
     const int dummy = 4 * ne_pad + 3 * nf_pad;
     const int hdr = (bi.ngrp + 4) & ~3;   // header words: ngrp+1 group offsets, padded to 16 B
-    if (threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)(hdr + 16 * bi.nrounds) * 4u;
-        mbar_arrive_expect_tx(bar_s, bytes);
-        bulk_load(smem_addr(chunk), a.sched + (size_t)bi.s0, bytes, bar_s);
-        const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
-        mbar_arrive_expect_tx(bar_w, wbytes);
-        if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
-    }
     // this block's time step (a batch gives every instance its own; the
     // load's latency is hidden behind the passes)
     const real dtb = a.blk_dt ? a.blk_dt[b] : dt;
@@ -403,9 +422,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     real Tl[MAXJ];
 #pragma unroll
     for (int j = 0; j < MAXJ; j++) {
-        const int l = threadIdx.x + j * NT;
+        const int g = block_group<NW, MAXJ>(warp, j, bi.ngrp);
+        const int l = 32 * g + lane;
         Tl[j] = real(0);
-        if (l < ls) {
+        if (g >= 0 && l < ls) {
             if (LM) {   // the state is T
                 Tl[j] = sE[l];
             } else {
@@ -428,10 +448,11 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     // (padding entries all name the dummy slot)
 #pragma unroll
     for (int j = 0; j < MAXJ; j++) {
-        const int g = warp + j * NW;
-        if (g < bi.ngrp) {
+        const int g = block_group<NW, MAXJ>(warp, j, bi.ngrp);
+        if (g >= 0) {
             const int p0 = (int)chunk[g], p1 = (int)chunk[g + 1];
             const real T = Tl[j];
+#pragma unroll 4
             for (int pr = p0; pr < p1; ++pr) {
                 const uint32_t v = pairs[pr * 32 + lane];
                 sv[v & 0xFFFFu] = T;
@@ -524,11 +545,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     // pass 3: fixed-order node sums; interior update or shared partial
 #pragma unroll
     for (int j = 0; j < MAXJ; j++) {
-        const int g = warp + j * NW;
-        if (g >= bi.ngrp) continue;
+        const int g = block_group<NW, MAXJ>(warp, j, bi.ngrp);
+        if (g < 0) continue;
         const int l = 32 * g + lane;
         const int p0 = (int)chunk[g], p1 = (int)chunk[g + 1];
         real R = real(0), Cap = real(0);
+#pragma unroll 4
         for (int pr = p0; pr < p1; ++pr) {
             const uint32_t v = pairs[pr * 32 + lane];
             R += sv[v & 0xFFFFu];

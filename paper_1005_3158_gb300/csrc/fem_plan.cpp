@@ -683,9 +683,7 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         }
         out.grp.push_back((int32_t)rounds);
         bi.nrounds = (int32_t)(rounds - bi.r0);
-        bi.s0 = (int32_t)swords;
-        swords += chunk_words(bi);
-        if (swords > INT32_MAX) return "schedule too large for 32-bit offsets";
+        swords = std::max<int64_t>(swords, chunk_words(bi));   // the largest chunk
         // element / face positions
         for (int32_t i = 0; i < bi.ne; i++) elem_order.push_back(pe[i]);
         for (int32_t i = 0; i < bi.nf; i++) face_order.push_back(pf[i]);
@@ -702,7 +700,12 @@ std::string build_block_plan(int64_t N, int64_t E, const double *xyz, const int3
         out.blocks[(size_t)p] = bi;
     }
     if (ipos != n_int || cpos != out.n_copies) return "node classification bookkeeping failed";
-    out.n_sched_words = swords;
+    // every block's schedule chunk sits at a fixed stride (the largest
+    // chunk), so a CTA can copy it in before it has read its block header
+    if (nparts * swords > INT32_MAX) return "schedule too large for 32-bit offsets";
+    for (int64_t p = 0; p < nparts; p++) out.blocks[(size_t)p].s0 = (int32_t)(p * swords);
+    out.chunk_stride = swords;
+    out.n_sched_words = nparts * swords;
     out.E_pad = nparts * nes;
     out.F_pad = round_up(std::max<int64_t>(fpos, 1), 8);
     elem_order.resize((size_t)out.E_pad, -1);

@@ -49,6 +49,7 @@ int greedy_color(int64_t N, int64_t E, const int32_t *tets, const int32_t *order
 struct BlockPlan {
     int64_t N = 0, E = 0, F = 0;
     int64_t n_int = 0, n_sh = 0, n_copies = 0, n_rounds = 0, n_sched_words = 0;
+    int64_t chunk_stride = 0;         // 32-bit words between blocks' schedule chunks
     int64_t E_pad = 0, F_pad = 0;
     int32_t max_ne = 0;
     size_t max_slots = 0, max_nloc = 0;

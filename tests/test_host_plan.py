@@ -110,14 +110,16 @@ def _check_plan(p, m):
     seen_elem = np.zeros(p.n_tets, int)
     seen_face = np.zeros(allf.shape[0], int)
     touched_by = [set() for _ in range(p.n_nodes)]
+    stride = max(((g + 4) // 4) * 4 + 16 * r for g, r in zip(blocks[:, 9], blocks[:, 14]))
     for b, (e0, ne, f0, nf, n0, nint, c0, nsh, g0, ngrp, ne_pad, nf_pad, nep, r0, nrounds, _) in enumerate(blocks):
         assert e0 % 8 == 0 and f0 % 8 == 0 and ne_pad >= ne and nf_pad >= nf
         assert nep % 8 == 0 and ne <= nep and e0 == b * nep   # uniform element stride
         assert grp[g0] == r0 and grp[g0 + ngrp] == r0 + nrounds
         if b + 1 < len(blocks):
             assert blocks[b + 1][0] == e0 + nep and blocks[b + 1][13] == r0 + nrounds
-            # schedule chunks: header (ngrp+1 offsets padded to 4 words) + 16 words per round
-            assert blocks[b + 1][15] == blocks[b][15] + ((ngrp + 4) // 4) * 4 + 16 * nrounds
+        # schedule chunks: header (ngrp+1 offsets padded to 4 words) + 16
+        # words per round, at a fixed stride = the largest chunk
+        assert blocks[b][15] == b * stride and ((ngrp + 4) // 4) * 4 + 16 * nrounds <= stride
         nslot = 4 * ne_pad + 3 * nf_pad
         assert nslot <= 65535
         nloc = nint + nsh
