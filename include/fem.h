@@ -32,6 +32,7 @@
 #ifndef FEM_H
 #define FEM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -387,6 +388,18 @@ fem_status fem_get_instance_times(fem_mesh *m, double *t_out, int64_t *steps_out
  * heat that entered through its Robin faces, out[3] = latent heat it still
  * holds; FP64.  Synchronises (reads the state back to the host). */
 fem_status fem_get_instance_energy(fem_mesh *m, int32_t inst, double out[4]);
+
+/* Device memory from the caller's allocator instead of cudaMalloc (for
+ * example a framework's caching allocator, so that one pool serves both).
+ * alloc(bytes, ctx) returns device memory on the current device, 256-byte
+ * aligned (FEM_EINVAL otherwise), or NULL (FEM_ENOMEM); free_fn(ptr, ctx)
+ * returns it; both are called on the thread that calls the library, while
+ * the mesh's device memory is (re)built and when it is released.  Set
+ * before the first call that needs the GPU (FEM_ESTATE afterwards); NULL
+ * for both restores cudaMalloc. */
+typedef void *(*fem_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*fem_free_fn)(void *ptr, void *ctx);
+fem_status fem_set_allocator(fem_mesh *m, fem_alloc_fn alloc, fem_free_fn free_fn, void *ctx);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fem_last_error(void);

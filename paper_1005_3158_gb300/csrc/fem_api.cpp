@@ -48,15 +48,13 @@ fem_status ok()
 // ---------------------------------------------------------------------------
 long g_alloc_count = 0;
 
-cudaError_t dev_alloc(void **p, size_t bytes)
+// false when the test hook says this allocation must fail
+bool alloc_allowed()
 {
     const char *env = getenv("FEM_FAULT_ALLOC_AFTER");
-    if (env && *env) {
-        long k = atol(env);
-        if (g_alloc_count >= k) { *p = nullptr; return cudaErrorMemoryAllocation; }
-    }
+    if (env && *env && g_alloc_count >= atol(env)) return false;
     g_alloc_count++;
-    return cudaMalloc(p, bytes == 0 ? 16 : bytes);
+    return true;
 }
 
 struct DevBuf {
@@ -120,6 +118,10 @@ struct fem_mesh {
     int device = -1;
     cudaStream_t stream = nullptr;
     std::vector<DevBuf> bufs;
+    // device memory from the caller's allocator (fem_set_allocator), else cudaMalloc
+    fem_alloc_fn alloc_fn = nullptr;
+    fem_free_fn free_fn = nullptr;
+    void *alloc_ctx = nullptr;
     size_t dev_bytes = 0;
     size_t smem_bytes = 0;
     int threads = 256;
@@ -182,7 +184,13 @@ bool finite_all(const double *p, int64_t n)
 void release_device(fem_mesh *m)
 {
     if (m->device >= 0) cudaSetDevice(m->device);
-    for (auto &b : m->bufs) cudaFree(b.p);
+    // a caller's allocator may hand the memory out again at once: let every
+    // kernel that uses it finish first
+    if (m->free_fn && !m->bufs.empty()) cudaDeviceSynchronize();
+    for (auto &b : m->bufs) {
+        if (m->free_fn) m->free_fn(b.p, m->alloc_ctx);
+        else cudaFree(b.p);
+    }
     m->bufs.clear();
     m->dev_bytes = 0;
     m->dev_ok = false;
@@ -347,7 +355,19 @@ fem_status upload(fem_mesh *m, T **dst, const T *src, size_t count)
 {
     void *p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T) + kAllocTailPad;
-    cudaError_t e = dev_alloc(&p, bytes);
+    cudaError_t e = cudaErrorMemoryAllocation;
+    if (alloc_allowed()) {
+        if (m->alloc_fn) {   // the caller's allocator (fem_set_allocator)
+            p = m->alloc_fn(bytes, m->alloc_ctx);
+            e = p ? cudaSuccess : cudaErrorMemoryAllocation;
+            if (p && (uintptr_t)p % 256 != 0) {
+                m->free_fn(p, m->alloc_ctx);
+                return fail(FEM_EINVAL, "the caller's allocator returned a pointer not aligned to 256 bytes");
+            }
+        } else {
+            e = cudaMalloc(&p, bytes);
+        }
+    }
     if (e != cudaSuccess)
         return fail(e == cudaErrorMemoryAllocation ? FEM_ENOMEM : FEM_ECUDA,
                     "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -1455,6 +1475,17 @@ fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
     }
     m->step = step;
     m->time = t;
+    return ok();
+}
+
+fem_status fem_set_allocator(fem_mesh *m, fem_alloc_fn alloc, fem_free_fn free_fn, void *ctx)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(FEM_EINVAL, "give both functions or neither");
+    if (m->dev_ok) return fail(FEM_ESTATE, "the mesh already holds device memory");
+    m->alloc_fn = alloc;
+    m->free_fn = free_fn;
+    m->alloc_ctx = ctx;
     return ok();
 }
 

@@ -35,7 +35,7 @@ ABI_SYMBOLS = (
     "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
     "fem_last_error", "fem_mesh_destroy", "fem_energy_sums_noalloc", "fem_batch_create",
     "fem_instance_stable_dt", "fem_set_instance_dt", "fem_advance", "fem_get_instance_times",
-    "fem_get_instance_energy",
+    "fem_get_instance_energy", "fem_set_allocator",
 )
 
 
@@ -105,6 +105,7 @@ def _load():
         "fem_plan_array": [P, ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(i64)],
         "fem_energy_sums_noalloc": [ctypes.c_int, P, P, P, P, P, i64, P, P],
         "fem_batch_create": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(P)],
+        "fem_set_allocator": [P, P, P, P],
         "fem_instance_stable_dt": [P, dp],
         "fem_set_instance_dt": [P, dp],
         "fem_advance": [P, ctypes.c_double],
@@ -364,6 +365,32 @@ def fem_get_instance_energy(h, inst):
     return out
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def torch_allocator():
+    """(alloc, free) callbacks over PyTorch's CUDA caching allocator, for
+    fem_set_allocator; keep them referenced while the mesh lives."""
+    import torch
+
+    def alloc(n, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(n))
+        except RuntimeError:   # out of memory: the library reports FEM_ENOMEM
+            return None
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
+def fem_set_allocator(h, alloc_cb=None, free_cb=None):
+    _check(_lib.fem_set_allocator(h, ctypes.cast(alloc_cb, ctypes.c_void_p) if alloc_cb else None,
+                                  ctypes.cast(free_cb, ctypes.c_void_p) if free_cb else None, None))
+
+
 def fem_last_error():
     return _lib.fem_last_error().decode()
 
@@ -381,7 +408,7 @@ class Mesh:
 
     def __init__(self, prob, precision="fp64", reorder=1, variant="block", block_elems=0,
                  threads=0, faces=True, dirichlet=True, set_temperature=True,
-                 formulation="enthalpy"):
+                 formulation="enthalpy", allocator=None):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         form = FORMULATIONS[formulation] if isinstance(formulation, str) else int(formulation)
@@ -390,7 +417,11 @@ class Mesh:
         self.h = fem_mesh_create(prob.xyz, prob.tets, prob.mat, prec, reorder,
                                  {"variant": var, "block_elems": block_elems, "threads": threads,
                                   "formulation": form})
+        self._alloc_cbs = None
         try:
+            if allocator == "torch":   # device memory from PyTorch's caching allocator
+                self._alloc_cbs = torch_allocator()
+                fem_set_allocator(self.h, *self._alloc_cbs)
             fem_set_materials(self.h, prob.materials)
             if faces and prob.faces.shape[0] > 0:
                 fem_set_boundary(self.h, prob.faces, prob.h, prob.t_inf, prob.q)
@@ -467,7 +498,7 @@ class Batch(Mesh):
     ``meshgen.Problem``-like objects; the parts are released once copied."""
 
     def __init__(self, probs, precision="fp32", reorder=1, block_elems=0, threads=0,
-                 formulation="enthalpy"):
+                 formulation="enthalpy", allocator=None):
         parts = []
         try:
             for p in probs:
@@ -475,6 +506,10 @@ class Batch(Mesh):
                                   block_elems=block_elems, threads=threads,
                                   formulation=formulation))
             self.h = fem_batch_create([q.h for q in parts])
+            self._alloc_cbs = None
+            if allocator == "torch":
+                self._alloc_cbs = torch_allocator()
+                fem_set_allocator(self.h, *self._alloc_cbs)
         finally:
             for q in parts:
                 q.close()

@@ -140,3 +140,28 @@ def test_bounded_wait_gives_up(fem, monkeypatch):
         o.set_temperature(p.T0)
         o.step(10, dt)
         assert np.abs(m.temperature() - o.temperature()).max() <= 0.05
+
+
+def test_torch_caching_allocator(fem):
+    """Device memory through fem_set_allocator from PyTorch's caching
+    allocator: the same results bit for bit, the memory shows in torch's
+    accounting while the mesh lives and returns to it afterwards."""
+    import torch
+    p = mg.unit_cube(8)
+    dt = 0.9 * oracle.OracleProblem(p).stable_dt()
+    with fem.Mesh(p, "fp32") as m:
+        m.step(30, dt)
+        T_ref = m.temperature()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    with fem.Mesh(p, "fp32", allocator="torch") as m:
+        m.step(30, dt)
+        T = m.temperature()
+        held = torch.cuda.memory_allocated() - before
+        assert held >= m.info()["device_bytes"]
+        with pytest.raises(fem.FemError) as ei:   # too late once on the device
+            fem.fem_set_allocator(m.h, None, None)
+        assert ei.value.status == fem.FEM_ESTATE
+    assert np.array_equal(T, T_ref)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
