@@ -47,9 +47,11 @@ FEM_HD inline int64_t chunk_words(const BlockInfo &b)
 static_assert(sizeof(BlockInfo) == 64, "BlockInfo layout");
 
 // Dynamic shared memory of a block-kernel CTA (16-byte aligned parts):
-// [3 mbarriers][conductances][schedule chunk][slots + dummy][local nodes: E,
-// partial position, phase byte], sized for the largest block.
-constexpr size_t kSmemBarBytes = 32;
+// [3 mbarriers, block header][conductances][schedule chunk][slots + dummy]
+// [local nodes: E, partial position, phase byte], sized for the largest
+// block.
+constexpr size_t kSmemHdrOffset = 32;
+constexpr size_t kSmemBarBytes = kSmemHdrOffset + sizeof(BlockInfo);
 FEM_HD inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 FEM_HD inline size_t block_slots(const BlockInfo &b)
 {

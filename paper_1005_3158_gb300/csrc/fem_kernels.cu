@@ -342,9 +342,11 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     const int b = a.b_first + (int)blockIdx.x;
     const int ls = a.ls, nes = a.nes;
 
-    // shared memory: [3 barriers][conductances 6 x nes][schedule chunk]
-    // [slots + dummy][per local node: E, partial position, phase byte]
+    // shared memory: [3 barriers, block header][conductances 6 x nes]
+    // [schedule chunk][slots + dummy][per local node: E, partial position,
+    // phase byte]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    const BlockInfo &bi = *reinterpret_cast<const BlockInfo *>(smem_raw + kSmemHdrOffset);
     real *sw = reinterpret_cast<real *>(smem_raw + kSmemBarBytes);
     uint32_t *chunk = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sw) +
                                                     align16(6 * (size_t)nes * sizeof(real)));
@@ -365,7 +367,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         mbar_init(bar_n, 1);
         mbar_fence_init();
         const uint32_t eb = (uint32_t)(ls * sizeof(real));
-        mbar_arrive_expect_tx(bar_n, 3u * eb + 5u * (uint32_t)ls);   // E, (C, Lc), phase, position
+        // E, (C, Lc), phase, position, and the block header
+        mbar_arrive_expect_tx(bar_n, 3u * eb + 5u * (uint32_t)ls + (uint32_t)sizeof(BlockInfo));
+        bulk_load(smem_addr(smem_raw + kSmemHdrOffset), a.blocks + b, (uint32_t)sizeof(BlockInfo), bar_n);
         bulk_load(smem_addr(sE), a.Eloc + lb, eb, bar_n);
         bulk_load(smem_addr(sv), a.CLloc + 2 * lb, 2 * eb, bar_n);
         bulk_load(smem_addr(sPh), a.phloc + lb, (uint32_t)ls, bar_n);
@@ -379,14 +383,25 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         mbar_arrive_expect_tx(bar_w, wbytes);
         if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
     }
-    const BlockInfo &bi = a.blocks[b];
+    // this block's time step (a batch gives every instance its own; the
+    // load's latency is hidden behind the passes)
+    const real dtb = a.blk_dt ? a.blk_dt[b] : dt;
+
+    // the mbarriers were initialised by thread 0 before any other thread
+    // polls them: the barrier below orders the two
+    __syncthreads();
+    int failed = 0;
+    if (threadIdx.x == 0) failed = !mbar_wait(bar_n, 0);
+    if (__syncthreads_or(failed)) {
+        give_up(a.err, bar_s, bar_w, bar_n);
+        return;
+    }
+    mbar_try_wait(bar_n, 0);
+    // the block header is in shared memory from here on
     const int nloc = bi.nint + bi.nsh;
     const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad;
     const int dummy = 4 * ne_pad + 3 * nf_pad;
     const int hdr = (bi.ngrp + 4) & ~3;   // header words: ngrp+1 group offsets, padded to 16 B
-    // this block's time step (a batch gives every instance its own; the
-    // load's latency is hidden behind the passes)
-    const real dtb = a.blk_dt ? a.blk_dt[b] : dt;
     // k(T): the materials of this thread's first element quad, loaded now
     // and used in pass 2
     uint32_t mat_q = 0;
@@ -407,16 +422,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     double qprev = 0.0;
     if (threadIdx.x == 0 && bi.nf > 0) qprev = a.qcum[b];
 
-    // the mbarriers were initialised by thread 0 before any other thread
-    // polls them: the barrier below orders the two
-    __syncthreads();
-    int failed = 0;
-    if (threadIdx.x == 0) failed = !mbar_wait(bar_n, 0);
-    if (__syncthreads_or(failed)) {
-        give_up(a.err, bar_s, bar_w, bar_n);
-        return;
-    }
-    mbar_try_wait(bar_n, 0);
     // local nodes: enthalpy -> temperature (Eqs. 5, 11); padding entries
     // hold C = 1, Lc = 0 and give a harmless T
     real Tl[MAXJ];
