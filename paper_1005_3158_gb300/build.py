@@ -14,6 +14,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfem.so")
+# the checked build: the same library with device-side bounds checks on every
+# indexed shared/global access (FEM_CHECKED), for tests
+LIB_CHECKED = os.path.join(PKG, "libfem_checked.so")
 
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
@@ -34,17 +37,17 @@ def _deps():
     return files
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def _compile(src: str, tool: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, src + ".o")
+def _compile(src: str, tool: str, verbose: bool, checked: bool = False) -> str:
+    obj = os.path.join(BUILD, src + (".checked.o" if checked else ".o"))
     path = os.path.join(CSRC, src)
-    inc = ["-I", INCLUDE, "-I", CSRC]
+    inc = ["-I", INCLUDE, "-I", CSRC] + (["-DFEM_CHECKED"] if checked else [])
     if tool == "nvcc":
         cmd = [NVCC, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
                "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", path, "-o", obj]
@@ -60,28 +63,35 @@ def _compile(src: str, tool: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link paper_1005_3158_gb300/libfem.so if any source is newer."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link paper_1005_3158_gb300/libfem.so (libfem_checked.so
+    with checked=True: kernels with device-side bounds checks) if any source
+    is newer."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda kv: _compile(kv[0], kv[1], verbose), SOURCES.items()))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda kv: _compile(kv[0], kv[1], verbose,
+                                               checked and kv[0] == "fem_kernels.cu"),
+                           SOURCES.items()))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp, "-lcudart_static",
            "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"linking libfem.so failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 def clean() -> None:
     shutil.rmtree(BUILD, ignore_errors=True)
-    if os.path.exists(LIB):
-        os.remove(LIB)
+    for lib in (LIB, LIB_CHECKED):
+        if os.path.exists(lib):
+            os.remove(lib)
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -749,6 +749,7 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.ph = m->dPh;
     a.n_int = m->bp.n_int;
     a.n_sh = m->bp.n_sh;
+    a.n_copies = m->bp.n_copies;
     a.qcum = m->dQcum;
     a.err = m->dErr;
     a.b_first = 0;
@@ -821,6 +822,7 @@ FlatArgs<real> flat_args(const fem_mesh *m)
     a.kt_T = (const real *)m->dKtT;
     a.kt_k = (const real *)m->dKtK;
     a.kt_n = m->dKtN;
+    a.err = m->dErr;
     return a;
 }
 
@@ -1073,6 +1075,8 @@ fem_status check_device_flag(fem_mesh *m)
     CU(cudaMemsetAsync(m->dErr, 0, sizeof(int), m->stream));
     if (flag & kErrWaitTimeout)
         return fail(FEM_ETIMEOUT, "a bounded device wait gave up; the state is not valid");
+    if (flag & kErrBadIndex)
+        return fail(FEM_ECUDA, "a device index failed its bounds check (checked build)");
     if (flag & kErrBadInput)
         return fail(FEM_EINVAL, "fem_set_state received a non-finite enthalpy");
     return fail(FEM_EUNSTABLE, "non-finite temperature: dt above the stable limit?");

@@ -80,6 +80,7 @@ constexpr int kMaxLocalNodes = 1024;
 constexpr int kErrWaitTimeout = 1;   // a bounded wait gave up
 constexpr int kErrBadInput = 2;      // fem_set_state received a non-finite value
 constexpr int kErrNonFinite = 4;     // a read-back temperature was non-finite
+constexpr int kErrBadIndex = 8;      // checked build: an index failed its bounds check
 
 constexpr uint8_t kDirichletBit = 0x80;  // in the per-node phase byte
 constexpr int kMaxRanges = 127;
@@ -144,6 +145,7 @@ struct BlockArgs {
     real *Esh;                 // [n_sh] E of the shared nodes
     const uint8_t *ph;         // [n_nodes] internal order (Dirichlet flag of shared nodes)
     int64_t n_int, n_sh;
+    int64_t n_copies;          // entries of P (and Pc)
     // FP64 energy bookkeeping
     double *qcum;             // [n_blocks] cumulative heat through the Robin faces
     int *err;                 // device error flag (kErrWaitTimeout)
@@ -191,6 +193,7 @@ struct FlatArgs {
     const real *fa, *fg;
     int64_t n_faces, f_stride;
     double *qcum;             // [n_node_ctas] cumulative boundary heat
+    int *err;                 // device error flag (checked build: kErrBadIndex)
     // temperature-dependent conductivity (KT instantiations): material of
     // element position p, tables as in BlockArgs
     const uint8_t *emat;

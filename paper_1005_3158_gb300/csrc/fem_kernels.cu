@@ -25,6 +25,16 @@
 
 #include "fem_internal.h"
 
+// Checked build (FEM_CHECKED): every shared-memory slot, partial, mirror and
+// node index is tested before use; a failure sets kErrBadIndex in the
+// device error flag (reported by the next synchronising call) and skips the
+// access.  The release build compiles the tests out.
+#ifdef FEM_CHECKED
+#define FEM_IN(i, n, err) fem::index_ok((int64_t)(i), (int64_t)(n), (err))
+#else
+#define FEM_IN(i, n, err) true
+#endif
+
 namespace fem {
 
 namespace {
@@ -125,6 +135,15 @@ __device__ __forceinline__ void state_set_E(const StateView<real> &v, int64_t i,
 {
     v.E(i) = v.is_T ? temperature_of(E, v.C[i], v.Lc[i], v.ph[i], v.ranges) : E;
 }
+
+#ifdef FEM_CHECKED
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n, int *err)
+{
+    const bool ok = i >= 0 && i < n;
+    if (!ok && err) atomicOr(err, kErrBadIndex);
+    return ok;
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // Block variant
@@ -460,8 +479,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
 #pragma unroll 4
             for (int pr = p0; pr < p1; ++pr) {
                 const uint32_t v = pairs[pr * 32 + lane];
-                sv[v & 0xFFFFu] = T;
-                sv[v >> 16] = T;
+                if (FEM_IN(v & 0xFFFFu, a.max_slots, a.err)) sv[v & 0xFFFFu] = T;
+                if (FEM_IN(v >> 16, a.max_slots, a.err)) sv[v >> 16] = T;
             }
         }
     }
@@ -476,6 +495,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     // pass 2: element products, VN elements per 16-byte access
     for (int qd = threadIdx.x; qd * VN < bi.ne; qd += NT) {
         const int e = qd * VN;
+        if (!FEM_IN(e + VN - 1, nes, a.err) || !FEM_IN(3 * ne_pad + e + VN - 1, a.max_slots, a.err)) break;
         V wq[6];
 #pragma unroll
         for (int k = 0; k < 6; k++) wq[k] = *reinterpret_cast<const V *>(sw + k * nes + e);
@@ -558,17 +578,17 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
 #pragma unroll 4
         for (int pr = p0; pr < p1; ++pr) {
             const uint32_t v = pairs[pr * 32 + lane];
-            R += sv[v & 0xFFFFu];
-            R += sv[v >> 16];
+            if (FEM_IN(v & 0xFFFFu, a.max_slots, a.err)) R += sv[v & 0xFFFFu];
+            if (FEM_IN(v >> 16, a.max_slots, a.err)) R += sv[v >> 16];
             if (LM) {   // capacity of the element behind each element-corner slot
                 Cap += slot_capacity(sw, v & 0xFFFFu, ne_pad);
                 Cap += slot_capacity(sw, v >> 16, ne_pad);
             }
         }
         if (l < bi.nint) {
-            if (!(sPh[l] & kDirichletBit))
+            if (!(sPh[l] & kDirichletBit) && FEM_IN(l, ls, a.err))
                 a.Eloc[lb + l] = LM ? sE[l] + dtb * R / Cap : sE[l] + dtb * R;
-        } else if (l < nloc) {
+        } else if (l < nloc && FEM_IN(l, ls, a.err) && FEM_IN(sPos[l], a.n_copies, a.err)) {
             a.P[sPos[l]] = R;
             if (LM) a.Pc[sPos[l]] = Cap;
         }
@@ -614,6 +634,7 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
 #pragma unroll
         for (int j = 0; j < NPT; j++) {
             R[j] = Cp[j] = real(0);
+            if (k1[j] > k0[j] && !FEM_IN(k1[j] - 1, a.n_copies, a.err)) k1[j] = k0[j];
             for (int k = k0[j]; k < k1[j]; ++k) R[j] += a.P[k];   // block order
             if (a.Pc)   // apparent capacity: T += dt R / C_app
                 for (int k = k0[j]; k < k1[j]; ++k) Cp[j] += a.Pc[k];
@@ -628,7 +649,10 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
 #pragma unroll
     for (int j = 0; j < NPT; j++)
         if (act[j])
-            for (int k = k0[j]; k < k1[j]; ++k) a.Eloc[__ldg(a.mpos + k)] = E[j];
+            for (int k = k0[j]; k < k1[j]; ++k) {
+                const int32_t mp = __ldg(a.mpos + k);
+                if (FEM_IN(mp, (int64_t)a.n_blocks * a.ls, a.err)) a.Eloc[mp] = E[j];
+            }
 }
 
 // Interface faces (Eq. 8): every interface face is a Robin face whose
@@ -676,6 +700,9 @@ __global__ void k_flat_elements(const FlatArgs<real> a, const int64_t p0, const 
     if (n0 < 0) return;   // padding
     const int32_t n1 = __ldg(a.conn + st + p), n2 = __ldg(a.conn + 2 * st + p),
                   n3 = __ldg(a.conn + 3 * st + p);
+    if (!FEM_IN(n0, a.n_nodes, a.err) || !FEM_IN(n1, a.n_nodes, a.err) ||
+        !FEM_IN(n2, a.n_nodes, a.err) || !FEM_IN(n3, a.n_nodes, a.err))
+        return;
     const real T0 = __ldg(a.T + n0), T1 = __ldg(a.T + n1), T2 = __ldg(a.T + n2), T3 = __ldg(a.T + n3);
     real kk = real(1);
     if (KT)   // K^e(T) = k(mean element temperature) x the k = 1 weights

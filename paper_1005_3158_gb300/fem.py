@@ -13,7 +13,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfem.so")
+# FEM_CHECKED=1 selects the checked build (device-side bounds checks on every
+# indexed access; build it with build.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "libfem_checked.so" if os.environ.get("FEM_CHECKED") == "1"
+                        else "libfem.so")
 
 FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_ESTATE, FEM_EUNSTABLE, FEM_ETIMEOUT = range(7)
 FEM_ENTHALPY, FEM_APPARENT_CAPACITY = 0, 1
