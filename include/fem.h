@@ -10,6 +10,10 @@
  * enthalpy form Eq. 5 (H = integral of C dT, Eq. 11), Galerkin linear tets
  * Eq. 9 with row-sum lumped capacity, explicit update Eq. 14 (theta = 0 of
  * Eq. 10) evaluated as sums of element contributions, Eqs. 15-22.
+ * Optional: the apparent-heat-capacity formulation (Eqs. 6-7, Lemmon),
+ * temperature-dependent conductivity (Eq. 9's K(T)), the cast-mold
+ * interface between non-matching meshes (Eq. 8), and batches of independent
+ * meshes advanced together with their own time steps.
  *
  * Conventions for every call
  *   - All array arguments are HOST pointers unless stated otherwise.  The
@@ -24,7 +28,8 @@
  *     message for the calling thread.
  *   - A fem_mesh is not thread-safe; use one mesh from one thread at a time.
  *   - Device memory belongs to the library, allocated on the current CUDA
- *     device the first time the mesh needs it and released by
+ *     device the first time the mesh needs it (with cudaMalloc, or the
+ *     caller's allocator, fem_set_allocator) and released by
  *     fem_mesh_destroy.  Work is enqueued on the mesh's stream (the legacy
  *     default stream unless fem_set_stream was called); the fem_get_* calls
  *     synchronise that stream.
@@ -204,20 +209,24 @@ fem_status fem_set_interface(fem_mesh *m, const int32_t *faces_a, int64_t n_a, c
 fem_status fem_set_dirichlet(fem_mesh *m, const int32_t *nodes, int64_t n, const double *T);
 
 /* Initial condition, Eq. 2: T0 [n_nodes].  Sets the nodal enthalpy
- * E_i = C_i T0_i + Lc_i f_l(T0_i), resets the step count, time and the
- * energy account (U0 = sum E_i).  Requires fem_set_materials (FEM_ESTATE).
+ * E_i = C_i T0_i + Lc_i f_l(T0_i) (the apparent-capacity formulation keeps
+ * T0 itself), resets the step count, time and the energy account (U0 = sum
+ * E_i).  Requires fem_set_materials (FEM_ESTATE).
  * Errors: FEM_EINVAL for a non-finite T0. */
 fem_status fem_set_temperature(fem_mesh *m, const double *T0);
 
 /* Stable explicit step (reading of Eq. 13): 2 / max_i sum_j |(K + H)_ij| / C_i
- * over non-Dirichlet nodes, K the assembled conductance, H the assembled
- * Robin face matrix, C the sensible lumped capacity.  Host computation.
- * Requires fem_set_materials (FEM_ESTATE). */
+ * over non-Dirichlet nodes, K the assembled conductance (with a k(T) table:
+ * at the table's largest k), H the assembled Robin and interface face
+ * matrices including an interface face's coupling to its sister's nodes,
+ * C the sensible lumped capacity.  Host computation.  Requires
+ * fem_set_materials (FEM_ESTATE). */
 fem_status fem_stable_dt(fem_mesh *m, double *dt_out);
 
 /* Advance n_steps explicit steps of size dt (Eq. 14 in enthalpy form):
- * T_i = T(E_i); R = F - K T; E_i += dt R_i.  Asynchronous on the mesh's
- * stream.  n_steps == 0 is a no-op.  Errors: FEM_EINVAL for n_steps < 0 or
+ * T_i = T(E_i); R = F - K T; E_i += dt R_i (apparent-capacity formulation:
+ * T_i += dt R_i / C_app,i).  Asynchronous on the mesh's stream.  On a batch
+ * every instance takes the same steps.  n_steps == 0 is a no-op.  Errors: FEM_EINVAL for n_steps < 0 or
  * dt <= 0 / non-finite; FEM_ESTATE before fem_set_materials and
  * fem_set_temperature (or fem_set_state); FEM_ECUDA. */
 fem_status fem_step(fem_mesh *m, int64_t n_steps, double dt);
@@ -228,7 +237,9 @@ fem_status fem_step(fem_mesh *m, int64_t n_steps, double dt);
  * kernel over the n_steps steps, *n_used the number of kernels per step:
  * block variant {0: block step (passes 1-3), 1: shared-node update}; atomic
  * and coloured variants {0: temperatures, 1: element pass (all colours),
- * 2: node update}.  Errors as fem_step; FEM_EINVAL if capacity is too small. */
+ * 2: node update}; with an interface (fem_set_interface) its kernel comes
+ * first and the others move up by one.  Errors as fem_step; FEM_EINVAL if
+ * capacity is too small. */
 fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_out,
                             int32_t capacity, int32_t *n_used);
 
@@ -243,9 +254,11 @@ fem_status fem_get_enthalpy(fem_mesh *m, double *h_out);
 
 /* FP64 energy account (device reduction): out[0] = U = sum_i E_i (J),
  * out[1] = U0 at the initial condition, out[2] = cumulative heat that
- * entered through the Robin faces, out[3] = latent heat not yet released
- * sum_i Lc_i f_l(T_i).  Without Dirichlet nodes U - U0 - out[2] is zero up to
- * rounding.  Synchronises.  FEM_EUNSTABLE if U is non-finite. */
+ * entered through the Robin and interface faces, out[3] = latent heat not
+ * yet released sum_i Lc_i f_l(T_i).  Without Dirichlet nodes U - U0 -
+ * out[2] is zero up to rounding in the enthalpy formulation (only
+ * approximately in the apparent-capacity one).  Synchronises.
+ * FEM_EUNSTABLE if U is non-finite. */
 fem_status fem_get_energy(fem_mesh *m, double out[4]);
 
 /* Use the given cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)
