@@ -9,7 +9,10 @@ benchmark step is one explicit time step over the whole mesh (all kernels of
 the step).  Inputs (~2.7 GB of per-step traffic) are larger than the 129 MB
 L2, so no flush is needed between steps.
 
-Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+Prints one JSON line.  Beside the GPU figures it times, on a 1.5M-tet sample
+of the same recipe, the FP64 oracle on one host core (``cpu_baseline``) and
+the threaded OpenMP baseline in FP32 and FP64 on all host cores
+(``cpu_threaded``).  ``--impl reference`` times the FP64 CPU oracle on the
 host instead (bounded sample of the same workload recipe).
 """
 from __future__ import annotations
@@ -101,6 +104,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-threaded", action="store_true")
+    ap.add_argument("--cpu-threaded-seconds", type=float, default=4.0)
     ap.add_argument("--no-sequential", action="store_true",
                     help="batched workload: skip the instance-by-instance comparison")
     a = ap.parse_args()
@@ -230,9 +235,33 @@ def cpu_baseline(workload: str, seconds: float):
         el = time.perf_counter() - t0
         if el >= seconds or steps >= 1000:
             break
-    return {"value": p.n_tets * steps / el, "unit": "tet-updates/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{name} ({p.n_tets} tets), {steps} FP64 steps, {el:.1f} s single-thread"}
+    return ({"value": p.n_tets * steps / el, "unit": "tet-updates/s", "cores": 1,
+             "kind": "oracle",
+             "sample": f"{name} ({p.n_tets} tets), {steps} FP64 steps, {el:.1f} s single-thread"},
+            p, name, dt)
+
+
+def cpu_threaded(p, name: str, dt: float, seconds: float):
+    """The threaded CPU baseline (OpenMP, colour-parallel element loop) on
+    the oracle's sample, FP32 and FP64, all host cores; tet-updates/s."""
+    import cpu_threaded as ct
+    out = {}
+    for prec in ("fp32", "fp64"):
+        with ct.ThreadedBaseline(p, prec) as b:
+            b.step(3, dt)
+            steps, t0 = 0, time.perf_counter()
+            while True:
+                b.step(10, dt)
+                steps += 10
+                el = time.perf_counter() - t0
+                if el >= seconds or steps >= 20000:
+                    break
+            inf = b.info()
+        out[prec] = {"value": p.n_tets * steps / el, "unit": "tet-updates/s",
+                     "cores": inf["threads"], "kind": "threaded",
+                     "sample": f"{name} ({p.n_tets} tets), {steps} {prec.upper()} steps, "
+                               f"{el:.1f} s, {inf['colours']} element colours"}
+    return out
 
 
 def run_reference(args):
@@ -478,11 +507,16 @@ def main():
         e2e = {"value": job_throughput(E, ke, world, el), "unit": "tet-updates/s",
                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "steps": ke}
 
-    cpu = None
+    cpu = thr = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        cpu = cpu_baseline(args.workload, args.cpu_seconds)
+        cpu, sp, sname, sdt = cpu_baseline(args.workload, args.cpu_seconds)
+        if not args.no_cpu_threaded:
+            try:
+                thr = cpu_threaded(sp, sname, sdt, args.cpu_threaded_seconds)
+            except Exception as e:   # noqa: BLE001  (no OpenMP compiler on the host)
+                thr = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
 
     if rank == 0:
         line = {
@@ -500,8 +534,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)",
                        "dt_s": dt, "setup_s": round(t_setup, 1)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": n_launch_per_step * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_threaded": thr, "e2e": e2e,
+            "clocks": clk, "gpu_launches": n_launch_per_step * args.steps,
         }
         print(json.dumps(line), flush=True)
     mesh.close()
