@@ -100,6 +100,11 @@ def parse():
     ap.add_argument("--block-elems", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--autotune", default="",
+                    help="comma list of candidate partitions, block_elems or "
+                         "block_elems x threads (e.g. 1024,2048,2048x1024): "
+                         "fem_autotune keeps the fastest before timing")
+    ap.add_argument("--autotune-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=200, help="0 = same as --steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -116,6 +121,20 @@ def parse():
     if a.config == 1 and "--precision" not in sys.argv:
         a.precision = "fp64"
     return a
+
+
+def autotune(m, spec: str, steps: int, dt: float):
+    """fem_autotune over the --autotune candidates; returns the config record."""
+    be, th = [], []
+    for c in spec.split(","):
+        x = c.strip().lower().split("x")
+        be.append(int(x[0]))
+        th.append(int(x[1]) if len(x) > 1 else 0)
+    t0 = time.perf_counter()
+    best, ms = m.autotune(be, th, steps=steps, dt=dt)
+    return {"candidates": [f"{b}x{t}" if t else str(b) for b, t in zip(be, th)],
+            "ms_per_step": [round(float(v), 5) for v in ms], "chosen": best,
+            "steps": steps, "seconds": round(time.perf_counter() - t0, 1)}
 
 
 def make_problem(name: str):
@@ -321,6 +340,7 @@ def run_batched(args):
     dt = 0.9 * b.instance_stable_dt()
     b.advance(float(dt.min()))   # device set-up, graph of a one-step pattern
     t_setup = time.perf_counter() - t_setup
+    tuned = autotune(b, args.autotune, args.autotune_steps, float(dt.min())) if args.autotune else None
     span = args.steps * float(dt.min())
 
     def counts(sp):
@@ -387,7 +407,7 @@ def run_batched(args):
                    "steps_per_instance_min": int(n.min()), "steps_per_instance_max": int(n.max()),
                    "tet_updates": updates, "ms_advance": ms, "n_blocks": info["n_blocks"],
                    "threads": info["threads"], "precision": args.precision,
-                   "sequential_value": seq,
+                   "sequential_value": seq, "autotune": tuned,
                    "l2": "inputs larger than L2 (no flush)", "setup_s": round(t_setup, 1)},
         "roofline": {"bound": "hbm", "kernel": "whole advance (block + shared-node kernels)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -431,8 +451,9 @@ def main():
     stream = torch.cuda.Stream()
     mesh.set_stream(stream.cuda_stream)
     mesh.step(1, dt)
-    info = mesh.info()
     t_setup = time.perf_counter() - t_setup
+    tuned = autotune(mesh, args.autotune, args.autotune_steps, dt) if args.autotune else None
+    info = mesh.info()
     E, N = p.n_tets, p.n_nodes
 
     # warm-up, then K timed steps between barriers, CUDA events on the stream
@@ -533,7 +554,7 @@ def main():
                        "block_elems": args.block_elems,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)",
-                       "dt_s": dt, "setup_s": round(t_setup, 1)},
+                       "dt_s": dt, "setup_s": round(t_setup, 1), "autotune": tuned},
             "roofline": roofline, "cpu_baseline": cpu, "cpu_threaded": thr, "e2e": e2e,
             "clocks": clk, "gpu_launches": n_launch_per_step * args.steps,
         }

@@ -243,6 +243,24 @@ fem_status fem_step(fem_mesh *m, int64_t n_steps, double dt);
 fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_out,
                             int32_t capacity, int32_t *n_used);
 
+/* Partition autotuning (block variant, single meshes and batches).  For
+ * each of the n candidates (block_elems[i] tets per element block, 64 ..
+ * 12288; threads[i] threads per CTA, 0 = the default for that size, else
+ * 128, 256, 512 or 1024; threads may be NULL = all 0) it rebuilds the
+ * element-block partition, runs 2 warm-up steps and then `steps` timed
+ * steps of size dt on the mesh's stream (CUDA events), and writes the
+ * mean device time per step in ms to ms_out[i] (may be NULL; +inf for a
+ * candidate whose blocks do not fit in shared memory).  The fastest
+ * candidate's partition is kept and its index written to *best_out.
+ * The state, time, step count and energy accounts after the call are
+ * those before it (the timed steps are undone).  Synchronises.  n in
+ * 1..64, steps >= 1, dt as for fem_step.  FEM_ESTATE for a flat variant
+ * or without an initial state; FEM_EINVAL for an out-of-range candidate
+ * or when no candidate fits; FEM_ECUDA / FEM_ETIMEOUT as for fem_step. */
+fem_status fem_autotune(fem_mesh *m, const int32_t *block_elems, const int32_t *threads,
+                        int32_t n, int32_t steps, double dt, int32_t *best_out,
+                        double *ms_out);
+
 /* Nodal temperatures T(E) [n_nodes] in the caller's order.  Synchronises.
  * FEM_EUNSTABLE if any value is non-finite (checked on the device; the
  * output is still written); FEM_EINVAL / FEM_ETIMEOUT for an error an

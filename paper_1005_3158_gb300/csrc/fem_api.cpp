@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <memory>
 #include <new>
 #include <string>
@@ -1091,6 +1092,54 @@ fem_status ready_for_io(fem_mesh *m)
     return m->prec == FEM_FP32 ? apply_pending<float>(m) : apply_pending<double>(m);
 }
 
+// Batches: add every block's cumulative boundary heat to its instance's
+// account (before the device buffers are released).
+fem_status fold_instance_heat(fem_mesh *m)
+{
+    if (m->n_inst == 0 || !m->dev_ok || m->state != fem_mesh::ST_DEVICE) return FEM_OK;
+    std::vector<double> q(m->bp.blocks.size());
+    CU(cudaMemcpyAsync(q.data(), m->dQcum, q.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    for (size_t b = 0; b < q.size(); b++) m->inst_q[(size_t)m->bp.block_inst[b]] += q[b];
+    return FEM_OK;
+}
+
+// Drop the device data and the partition; the next ready_for_io rebuilds
+// both from the options and uploads E (caller order) as the state.
+void reset_partition(fem_mesh *m, const std::vector<double> &E)
+{
+    release_device(m);
+    m->plan_ok = false;
+    m->bp = BlockPlan();
+    m->pending = E;
+    m->state = fem_mesh::ST_PENDING_E;
+}
+
+// Mean device ms per step of `steps` steps after two warm-up steps.
+template <typename real>
+fem_status time_steps(fem_mesh *m, int32_t steps, double dt, double *ms)
+{
+    fem_status st = step_impl<real>(m, 2, dt);
+    if (st) return st;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(FEM_ECUDA, "event creation failed");
+    }
+    cudaEventRecord(e0, m->stream);
+    st = step_impl<real>(m, steps, dt);
+    cudaEventRecord(e1, m->stream);
+    float t = 0.f;
+    if (!st && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        st = fail(FEM_ECUDA, "event timing failed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    *ms = (double)t / (double)steps;
+    return check_device_flag(m);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1553,6 +1602,82 @@ fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_
     st = m->prec == FEM_FP32 ? step_profile_impl<float>(m, n_steps, dt, ms_out)
                              : step_profile_impl<double>(m, n_steps, dt, ms_out);
     return st ? st : ok();
+}
+
+fem_status fem_autotune(fem_mesh *m, const int32_t *block_elems, const int32_t *threads, int32_t n,
+                        int32_t steps, double dt, int32_t *best_out, double *ms_out)
+{
+    if (!m || !block_elems || !best_out) return fail(FEM_EINVAL, "NULL argument");
+    if (n < 1 || n > 64) return fail(FEM_EINVAL, "n = %d candidates (1..64)", n);
+    if (steps < 1) return fail(FEM_EINVAL, "steps must be >= 1");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(FEM_EINVAL, "dt must be positive and finite");
+    for (int32_t i = 0; i < n; i++) {
+        const int32_t th = threads ? threads[i] : 0;
+        if (block_elems[i] < 64 || block_elems[i] > 12288)
+            return fail(FEM_EINVAL, "candidate %d: block_elems %d outside 64..12288", i, block_elems[i]);
+        if (th != 0 && th != 128 && th != 256 && th != 512 && th != 1024)
+            return fail(FEM_EINVAL, "candidate %d: threads %d (0, 128, 256, 512 or 1024)", i, th);
+    }
+    if (!is_block(m)) return fail(FEM_ESTATE, "autotuning applies to the block variant");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    if ((st = check_device_flag(m))) return st;
+    if ((st = fold_instance_heat(m))) return st;
+    if ((st = stash_state(m))) return st;
+    // what the timed steps change, put back afterwards
+    const std::vector<double> E0 = m->pending;
+    const int64_t step0 = m->step;
+    const double time0 = m->time, q0 = m->q_carry;
+    const fem_options opt0 = m->opt;
+    const std::vector<double> it0 = m->inst_t, iq0 = m->inst_q;
+    const std::vector<int64_t> is0 = m->inst_steps;
+    auto restore = [&](const fem_options &o) {
+        m->opt = o;
+        reset_partition(m, E0);
+        m->step = step0;
+        m->time = time0;
+        m->q_carry = q0;
+        m->inst_t = it0;
+        m->inst_q = iq0;
+        m->inst_steps = is0;
+    };
+    int32_t best = -1;
+    double best_ms = 0.0;
+    for (int32_t i = 0; i < n; i++) {
+        fem_options o = opt0;
+        o.block_elems = block_elems[i];
+        o.threads = threads ? threads[i] : 0;
+        restore(o);
+        double ms = std::numeric_limits<double>::infinity();
+        st = ready_for_io(m);
+        if (st == FEM_OK)
+            st = m->prec == FEM_FP32 ? time_steps<float>(m, steps, dt, &ms)
+                                     : time_steps<double>(m, steps, dt, &ms);
+        else if (st == FEM_EINVAL)
+            st = FEM_OK;   // this partition does not fit (shared memory, local nodes)
+        if (st) {
+            std::string keep = g_err;
+            restore(opt0);
+            g_err = keep;
+            return st;
+        }
+        if (ms_out) ms_out[i] = ms;
+        if (std::isfinite(ms) && (best < 0 || ms < best_ms)) {
+            best = i;
+            best_ms = ms;
+        }
+    }
+    fem_options o = opt0;
+    if (best >= 0) {
+        o.block_elems = block_elems[best];
+        o.threads = threads ? threads[best] : 0;
+    }
+    restore(o);
+    if ((st = ready_for_io(m))) return st;
+    if (best < 0) return fail(FEM_EINVAL, "no candidate partition fits on this device");
+    *best_out = best;
+    return ok();
 }
 
 fem_status fem_get_temperature(fem_mesh *m, double *T_out)

@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
     "fem_last_error", "fem_mesh_destroy", "fem_energy_sums_noalloc", "fem_batch_create",
     "fem_instance_stable_dt", "fem_set_instance_dt", "fem_advance", "fem_get_instance_times",
-    "fem_get_instance_energy", "fem_set_allocator",
+    "fem_get_instance_energy", "fem_set_allocator", "fem_autotune",
 )
 
 
@@ -114,6 +114,7 @@ def _load():
         "fem_advance": [P, ctypes.c_double],
         "fem_get_instance_times": [P, dp, ctypes.POINTER(i64)],
         "fem_get_instance_energy": [P, ctypes.c_int32, dp],
+        "fem_autotune": [P, ip, ip, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ip, dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -248,6 +249,23 @@ def fem_step_profile(h, n_steps, dt):
     n = ctypes.c_int32()
     _check(_lib.fem_step_profile(h, int(n_steps), float(dt), _pd(ms), 8, ctypes.byref(n)))
     return ms[:n.value].copy()
+
+
+def fem_autotune(h, block_elems, threads=None, steps=20, dt=None):
+    """Time each candidate partition (block_elems[i], threads[i]) and keep
+    the fastest; returns (best index, ms per step of every candidate).
+    dt defaults to 0.9 x the stable step."""
+    if dt is None:
+        dt = 0.9 * fem_stable_dt(h)
+    be = np.ascontiguousarray(block_elems, np.int32)
+    th = None if threads is None else np.ascontiguousarray(threads, np.int32)
+    if th is not None and th.shape != be.shape:
+        raise ValueError("block_elems and threads differ in length")
+    ms = np.zeros(be.shape[0])
+    best = ctypes.c_int32(-1)
+    _check(_lib.fem_autotune(h, _pi(be), None if th is None else _pi(th), be.shape[0], int(steps),
+                             float(dt), ctypes.byref(best), _pd(ms)))
+    return best.value, ms
 
 
 def fem_get_temperature(h, n_nodes, out=None):
@@ -467,6 +485,9 @@ class Mesh:
 
     def step_profile(self, n, dt):
         return fem_step_profile(self.h, n, dt)
+
+    def autotune(self, block_elems, threads=None, steps=20, dt=None):
+        return fem_autotune(self.h, block_elems, threads, steps, dt)
 
     def set_temperature(self, T0):
         fem_set_temperature(self.h, T0)
