@@ -1,0 +1,59 @@
+"""Precision of the stepping against the FP64 oracle over the casting
+workload's full run: the flanged casting in its steel mold (1,999,200 tets),
+nodes and elements randomly renumbered (seed 1006), 5000 steps at 0.9 x the
+stable step.  One oracle trajectory is compared every 1000 steps with the
+GPU in FP64 (RCM order), FP32 (RCM order) and FP32 (the random order as
+given).  Bounds: 1e-9 K (FP64) and 0.05 K (FP32); the worst errors are
+printed (run with -s) and stated beside the bounds in the design notes."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1005_3158_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 0.05}
+STEPS, EVERY = 5000, 1000
+
+
+@pytest.fixture(scope="module")
+def fem():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_3158_gb300 import fem as f
+    return f
+
+
+def test_casting_5000_steps(fem):
+    rng = np.random.Generator(np.random.PCG64(1006))
+    p = mg.permute_elements(mg.permute_nodes(mg.flanged_casting(), rng), rng)
+    o = oracle.OracleProblem(p)
+    o.set_temperature(p.T0)
+    dt = 0.9 * o.stable_dt()
+    runs = [("fp64", 1), ("fp32", 1), ("fp32", 0)]
+    meshes = [fem.Mesh(p, prec, reorder=r) for prec, r in runs]
+    worst = [0.0] * len(runs)
+    try:
+        for k in range(STEPS // EVERY):
+            o.step(EVERY, dt)
+            T_ref = o.temperature()
+            for i, m in enumerate(meshes):
+                m.step(EVERY, dt)
+                worst[i] = max(worst[i], float(np.abs(m.temperature() - T_ref).max()))
+        U_ref = o.energy()[0]
+        for (prec, r), m, w in zip(runs, meshes, worst):
+            U, U0, Qb, _ = m.energy()
+            print(f"casting {prec} reorder={r}: max |T - oracle| over {STEPS} steps {w:.3e} K, "
+                  f"energy residual {(U - U0 - Qb) / U0:.2e}, U vs oracle {(U - U_ref) / U_ref:.2e}")
+            assert w <= TOL[prec]
+            assert abs(U - U0 - Qb) <= (1e-12 if prec == "fp64" else 1e-5) * abs(U0)
+        # the casting has started to solidify by the end of the run
+        lat = o.energy()[3]
+        assert 0 < lat
+    finally:
+        for m in meshes:
+            m.close()
