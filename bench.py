@@ -506,6 +506,26 @@ def main():
                 "kernel_ms": {n: round(float(v), 4) for n, v in zip(names, kms)},
                 "step_alg_bytes_per_tet": round((E * (16 + 6 * s) + N * 4 * s) / E, 2)}
 
+    if args.precision == "fp64" and args.variant == "block":
+        # FP64 on GB300 is bound by its FP64 pipe (2 FMA per clock per SM),
+        # not by HBM: report the block kernel against that pipe's peak.
+        # Algorithmic FP64 flops: 28 per tet (pass 2: 6 differences, 6
+        # products, 12 corner-sum adds; pass 3: 4 slot adds), 5 per interior
+        # node (T(E), update), 3 per shared-node copy (T(E)).
+        flops = E * 28 + info["n_interior_nodes"] * 5 + info["n_shared_copies"] * 3
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        fpeak = sms * 2 * 2 * mhz * 1e6 / 1e9
+        fach = flops / (kms[0] / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_block_step", "achieved": round(fach, 1),
+                    "peak": round(fpeak, 1), "unit": "GFLOP/s", "frac": round(fach / fpeak, 4),
+                    "traffic": roofline["traffic"],
+                    "peak_source": f"derived: {sms} SMs x 2 FP64 FMA/clock x {mhz:.0f} MHz",
+                    "alg_flops_per_launch": int(flops), "hbm": {
+                        "achieved": roofline["achieved"], "peak": peak, "unit": "GB/s",
+                        "frac": roofline["frac"]},
+                    "kernel_ms": roofline["kernel_ms"]}
+
     # end to end through the C ABI with pinned host buffers: every step
     # uploads the state, steps once and reads the temperatures back
     e2e = None
