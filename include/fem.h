@@ -297,6 +297,37 @@ fem_status fem_get_state(fem_mesh *m, double *E_out, int64_t *step, double *t);
  * call (before the mesh is on the device: by this call). */
 fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t);
 
+/* Pipelined host I/O.  A host loop of "upload a state, step, read the
+ * temperatures back" overlaps the copies of neighbouring iterations with
+ * the steps when it uses these three calls.  Each direction has two device
+ * staging buffers and its own copy stream.  Events order every buffer's
+ * reuse after its last reader, and the state update and the read-back
+ * kernels run on the mesh's stream in call order.
+ *
+ * fem_set_state_async: as fem_set_state (E [n_nodes] in J, caller order;
+ * step count and time), once the mesh has an initial state.  It returns
+ * before the copy.  E must stay unchanged until fem_sync (or another
+ * synchronising call) returns.  E should be page-locked (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) for the copy to overlap.
+ *
+ * fem_get_temperature_async: enqueues T(E) of the state after every
+ * earlier call on this mesh, and its copy into T_out [n_nodes] (caller
+ * order).  It returns before the copy.  T_out is valid after fem_sync, and
+ * page-locked memory overlaps.
+ *
+ * fem_sync: waits for all asynchronous work of the mesh (both copy
+ * streams and the mesh's stream) and reports what the device flagged:
+ * FEM_EINVAL for a non-finite uploaded state, FEM_EUNSTABLE for a
+ * non-finite temperature, FEM_ETIMEOUT for a bounded wait that gave up.
+ *
+ * Errors of the first two calls: FEM_EINVAL for NULL arguments, FEM_ESTATE
+ * without materials or an initial state, FEM_ENOMEM / FEM_ECUDA for the
+ * staging buffers (4 x n_nodes doubles on the device, allocated by the
+ * first call). */
+fem_status fem_set_state_async(fem_mesh *m, const double *E, int64_t step, double t);
+fem_status fem_get_temperature_async(fem_mesh *m, double *T_out);
+fem_status fem_sync(fem_mesh *m);
+
 /* Plan statistics (host computation; builds the plan if needed). */
 fem_status fem_mesh_info(fem_mesh *m, fem_info *out);
 

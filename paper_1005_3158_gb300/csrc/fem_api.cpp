@@ -171,6 +171,14 @@ struct fem_mesh {
     cudaStream_t own_stream = nullptr;         // graph launches when stream is NULL
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> graph_key;            // per-plan-position step counts of graph
+    // asynchronous state I/O (fem_set_state_async, fem_get_temperature_async):
+    // two device staging buffers each way, a copy stream each way, and
+    // events that order every buffer's reuse after its last reader
+    bool async_ok = false;
+    cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {}, ev_out_ready[2] = {}, ev_out_free[2] = {};
+    double *dIn[2] = {nullptr, nullptr}, *dOutT[2] = {nullptr, nullptr};
+    int in_idx = 0, out_idx = 0;
 };
 
 namespace {
@@ -182,9 +190,30 @@ bool finite_all(const double *p, int64_t n)
     return true;
 }
 
+// Streams and events of the asynchronous I/O; their copies finish first.
+// The staging buffers are in m->bufs and go with the other buffers.
+void release_async(fem_mesh *m)
+{
+    for (cudaStream_t s : {m->up_stream, m->down_stream})
+        if (s) cudaStreamSynchronize(s);
+    for (int i = 0; i < 2; i++)
+        for (cudaEvent_t *e : {&m->ev_in_ready[i], &m->ev_in_free[i], &m->ev_out_ready[i], &m->ev_out_free[i]}) {
+            if (*e) cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    for (cudaStream_t *s : {&m->up_stream, &m->down_stream}) {
+        if (*s) cudaStreamDestroy(*s);
+        *s = nullptr;
+    }
+    m->dIn[0] = m->dIn[1] = m->dOutT[0] = m->dOutT[1] = nullptr;
+    m->in_idx = m->out_idx = 0;
+    m->async_ok = false;
+}
+
 void release_device(fem_mesh *m)
 {
     if (m->device >= 0) cudaSetDevice(m->device);
+    release_async(m);
     // a caller's allocator may hand the memory out again at once: let every
     // kernel that uses it finish first
     if (m->free_fn && !m->bufs.empty()) cudaDeviceSynchronize();
@@ -1140,6 +1169,23 @@ fem_status time_steps(fem_mesh *m, int32_t steps, double dt, double *ms)
     return check_device_flag(m);
 }
 
+fem_status ensure_async(fem_mesh *m)
+{
+    if (m->async_ok) return FEM_OK;
+    for (int i = 0; i < 2; i++) {
+        fem_status st = upload<double>(m, &m->dIn[i], nullptr, (size_t)m->N);
+        if (!st) st = upload<double>(m, &m->dOutT[i], nullptr, (size_t)m->N);
+        if (st) return st;
+    }
+    CU(cudaStreamCreateWithFlags(&m->up_stream, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&m->down_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; i++)
+        for (cudaEvent_t *e : {&m->ev_in_ready[i], &m->ev_in_free[i], &m->ev_out_ready[i], &m->ev_out_free[i]})
+            CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    m->async_ok = true;
+    return FEM_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1678,6 +1724,72 @@ fem_status fem_autotune(fem_mesh *m, const int32_t *block_elems, const int32_t *
     if (best < 0) return fail(FEM_EINVAL, "no candidate partition fits on this device");
     *best_out = best;
     return ok();
+}
+
+fem_status fem_set_state_async(fem_mesh *m, const double *E, int64_t step, double t)
+{
+    if (!m || !E) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    if ((st = ensure_async(m))) return st;
+    const int i = m->in_idx;
+    // the copy into staging buffer i waits for the last kernel that read it
+    CU(cudaStreamWaitEvent(m->up_stream, m->ev_in_free[i], 0));
+    CU(cudaMemcpyAsync(m->dIn[i], E, (size_t)m->N * sizeof(double), cudaMemcpyHostToDevice, m->up_stream));
+    CU(cudaEventRecord(m->ev_in_ready[i], m->up_stream));
+    CU(cudaStreamWaitEvent(m->stream, m->ev_in_ready[i], 0));
+    KERNEL(m->prec == FEM_FP32
+               ? launch_set_state<float>(view_of<float>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream)
+               : launch_set_state<double>(view_of<double>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream),
+           "state kernel");
+    KERNEL(m->prec == FEM_FP32 ? refresh_mirror<float>(m) : refresh_mirror<double>(m), "mirror kernel");
+    CU(cudaEventRecord(m->ev_in_free[i], m->stream));
+    m->in_idx = 1 - i;
+    m->step = step;
+    m->time = t;
+    return ok();
+}
+
+fem_status fem_get_temperature_async(fem_mesh *m, double *T_out)
+{
+    if (!m || !T_out) return fail(FEM_EINVAL, "NULL argument");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    if ((st = ensure_async(m))) return st;
+    const int j = m->out_idx;
+    // staging buffer j is rewritten once its previous copy to the host is done
+    CU(cudaStreamWaitEvent(m->stream, m->ev_out_free[j], 0));
+    KERNEL(m->prec == FEM_FP32
+               ? launch_get_temperature<float>(view_of<float>(m), (const float *)m->dC,
+                                               (const float *)m->dLc, m->dPh,
+                                               (const float *)m->dRanges, m->dOutT[j], m->dNodeOld,
+                                               m->N, m->dErr, m->stream)
+               : launch_get_temperature<double>(view_of<double>(m), (const double *)m->dC,
+                                                (const double *)m->dLc, m->dPh,
+                                                (const double *)m->dRanges, m->dOutT[j],
+                                                m->dNodeOld, m->N, m->dErr, m->stream),
+           "read-back kernel");
+    CU(cudaEventRecord(m->ev_out_ready[j], m->stream));
+    CU(cudaStreamWaitEvent(m->down_stream, m->ev_out_ready[j], 0));
+    CU(cudaMemcpyAsync(T_out, m->dOutT[j], (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost,
+                       m->down_stream));
+    CU(cudaEventRecord(m->ev_out_free[j], m->down_stream));
+    m->out_idx = 1 - j;
+    return ok();
+}
+
+fem_status fem_sync(fem_mesh *m)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->dev_ok) return ok();
+    cudaSetDevice(m->device);
+    if (m->async_ok) {
+        CU(cudaStreamSynchronize(m->up_stream));
+        CU(cudaStreamSynchronize(m->down_stream));
+    }
+    fem_status st = check_device_flag(m);   // synchronises the mesh's stream
+    return st ? st : ok();
 }
 
 fem_status fem_get_temperature(fem_mesh *m, double *T_out)

@@ -38,7 +38,8 @@ ABI_SYMBOLS = (
     "fem_get_state", "fem_set_state", "fem_mesh_info", "fem_rcm_order", "fem_plan_array",
     "fem_last_error", "fem_mesh_destroy", "fem_energy_sums_noalloc", "fem_batch_create",
     "fem_instance_stable_dt", "fem_set_instance_dt", "fem_advance", "fem_get_instance_times",
-    "fem_get_instance_energy", "fem_set_allocator", "fem_autotune",
+    "fem_get_instance_energy", "fem_set_allocator", "fem_autotune", "fem_set_state_async",
+    "fem_get_temperature_async", "fem_sync",
 )
 
 
@@ -115,6 +116,9 @@ def _load():
         "fem_get_instance_times": [P, dp, ctypes.POINTER(i64)],
         "fem_get_instance_energy": [P, ctypes.c_int32, dp],
         "fem_autotune": [P, ip, ip, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ip, dp],
+        "fem_set_state_async": [P, P, i64, ctypes.c_double],
+        "fem_get_temperature_async": [P, P],
+        "fem_sync": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -306,6 +310,26 @@ def fem_set_state(h, n_nodes, E, step=0, t=0.0):
     _check(_lib.fem_set_state(h, p, int(step), float(t)))
 
 
+def fem_set_state_async(h, n_nodes, E, step=0, t=0.0):
+    """Enqueue a state upload (see fem.h); E must stay alive and unchanged
+    until fem_sync.  Returns the buffer to keep alive."""
+    p, keep = _host_ptr(E, n_nodes, False)
+    _check(_lib.fem_set_state_async(h, p, int(step), float(t)))
+    return keep
+
+
+def fem_get_temperature_async(h, n_nodes, out):
+    """Enqueue T(E) and its copy into `out` (valid after fem_sync).
+    Returns the buffer to keep alive."""
+    p, keep = _host_ptr(out, n_nodes, True)
+    _check(_lib.fem_get_temperature_async(h, p))
+    return keep
+
+
+def fem_sync(h):
+    _check(_lib.fem_sync(h))
+
+
 def fem_mesh_info(h):
     info = FemInfo()
     _check(_lib.fem_mesh_info(h, ctypes.byref(info)))
@@ -435,6 +459,7 @@ class Mesh:
         form = FORMULATIONS[formulation] if isinstance(formulation, str) else int(formulation)
         self.n_nodes = int(prob.xyz.shape[0])
         self.n_tets = int(prob.tets.shape[0])
+        self._inflight = []   # host buffers of asynchronous calls, until sync()
         self.h = fem_mesh_create(prob.xyz, prob.tets, prob.mat, prec, reorder,
                                  {"variant": var, "block_elems": block_elems, "threads": threads,
                                   "formulation": form})
@@ -510,6 +535,19 @@ class Mesh:
     def set_stream(self, stream):
         fem_set_stream(self.h, stream)
 
+    def set_state_async(self, E, step=0, t=0.0):
+        self._inflight.append(fem_set_state_async(self.h, self.n_nodes, E, step, t))
+
+    def temperature_async(self, out):
+        self._inflight.append(fem_get_temperature_async(self.h, self.n_nodes, out))
+        return out
+
+    def sync(self):
+        try:
+            fem_sync(self.h)
+        finally:
+            self._inflight.clear()
+
     def info(self):
         return fem_mesh_info(self.h)
 
@@ -524,6 +562,7 @@ class Batch(Mesh):
     def __init__(self, probs, precision="fp32", reorder=1, block_elems=0, threads=0,
                  formulation="enthalpy", allocator=None):
         parts = []
+        self._inflight = []
         try:
             for p in probs:
                 parts.append(Mesh(p, precision, reorder=reorder, variant="block",

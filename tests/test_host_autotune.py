@@ -32,3 +32,18 @@ def test_autotune_needs_block_variant():
         with pytest.raises(fem.FemError) as e:
             m.autotune([256, 512], dt=1.0)
         assert e.value.status == fem.FEM_ESTATE
+
+
+def test_async_io_argument_checks():
+    """The asynchronous I/O calls reject NULL buffers and a mesh without a
+    state before any device work."""
+    import ctypes
+    p = mg.unit_cube(3)
+    with fem.Mesh(p, "fp32", set_temperature=False) as m:
+        assert fem.lib().fem_set_state_async(m.h, None, 0, 0.0) == fem.FEM_EINVAL
+        assert fem.lib().fem_get_temperature_async(m.h, None) == fem.FEM_EINVAL
+        buf = np.zeros(m.n_nodes)
+        st = fem.lib().fem_get_temperature_async(m.h, ctypes.c_void_p(buf.ctypes.data))
+        assert st == fem.FEM_ESTATE
+        assert fem.lib().fem_sync(None) == fem.FEM_EINVAL
+        assert fem.lib().fem_sync(m.h) == fem.FEM_OK   # nothing on the device yet
