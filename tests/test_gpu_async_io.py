@@ -1,8 +1,9 @@
 """Pipelined host I/O (fem_set_state_async / fem_get_temperature_async /
 fem_sync): a host loop that uploads a different state every iteration,
 steps and reads the temperatures back gives, iteration by iteration, the
-bits of the same loop through the synchronous calls -- whatever the
-overlap of the copies with the steps."""
+bits of the same loop through the synchronous calls (the deterministic
+block variant; the atomic variant to its rounding) -- whatever the overlap
+of the copies with the steps."""
 import numpy as np
 import pytest
 
@@ -46,10 +47,14 @@ def test_async_loop_equals_sync_loop(env, prec, variant):
             m.step(2, dt)
             m.temperature_async(outs[k])
         m.sync()
+        # the block variant is deterministic (bitwise); the atomic variant
+        # adds in a run-dependent order (last-bit differences)
+        same = np.array_equal if variant == "block" else \
+            (lambda x, y: np.allclose(x, y, rtol=0, atol=1e-3))
         for k in range(n_iter):
-            assert np.array_equal(outs[k].numpy(), ref[k]), f"iteration {k}"
+            assert same(outs[k].numpy(), ref[k]), f"iteration {k}"
         # the state after the loop is that of the last iteration
-        assert np.array_equal(m.temperature(), ref[-1])
+        assert same(m.temperature(), ref[-1])
 
 
 def test_async_reuses_one_host_buffer_in_order(env):
