@@ -174,6 +174,10 @@ struct fem_mesh {
     // asynchronous state I/O (fem_set_state_async, fem_get_temperature_async):
     // two device staging buffers each way, a copy stream each way, and
     // events that order every buffer's reuse after its last reader
+    cudaGraphExec_t step_graph = nullptr;      // kGraphSteps steps of size step_graph_dt
+    double step_graph_dt = 0.0;
+    int step_graph_fault = 0;
+    cudaStream_t cap_stream = nullptr;         // capture stream of step_graph
     bool async_ok = false;
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
     cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {}, ev_out_ready[2] = {}, ev_out_free[2] = {};
@@ -245,6 +249,10 @@ void release_device(fem_mesh *m)
     m->dt_uploaded.clear();
     if (m->graph) cudaGraphExecDestroy(m->graph);
     m->graph = nullptr;
+    if (m->step_graph) cudaGraphExecDestroy(m->step_graph);
+    m->step_graph = nullptr;
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    m->cap_stream = nullptr;
     m->graph_key.clear();
     if (m->own_stream) cudaStreamDestroy(m->own_stream);
     m->own_stream = nullptr;
@@ -1017,32 +1025,69 @@ fem_status launch_interface_kernel(fem_mesh *m, cudaStream_t st)
 }
 
 template <typename real>
-fem_status launch_step_kernel(fem_mesh *m, int k, double dt)
+fem_status launch_step_kernel(fem_mesh *m, int k, double dt, cudaStream_t st)
 {
     if (m->F_if > 0) {
-        if (k == 0) return launch_interface_kernel<real>(m, m->stream);
+        if (k == 0) return launch_interface_kernel<real>(m, st);
         k--;
     }
     if (is_block(m)) {
         const BlockArgs<real> a = block_args<real>(m);
         if (k == 0)
-            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, m->stream, m->has_kt,
+            KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, st, m->has_kt,
                                              is_lm(m)),
                    "block kernel");
         else
-            KERNEL(launch_shared_update<real>(a, dt, m->stream), "shared-node kernel");
+            KERNEL(launch_shared_update<real>(a, dt, st), "shared-node kernel");
     } else {
         const FlatArgs<real> a = flat_args<real>(m);
         if (k == 0)
-            KERNEL(launch_flat_temperature<real>(a, m->stream), "temperature kernel");
+            KERNEL(launch_flat_temperature<real>(a, st), "temperature kernel");
         else if (k == 1)
             KERNEL(launch_flat_elements<real>(a, m->opt.variant == FEM_VARIANT_ATOMIC,
-                                              m->fp.color_start.data(), m->fp.n_colors, m->stream),
+                                              m->fp.color_start.data(), m->fp.n_colors, st),
                    "element kernel");
         else
-            KERNEL(launch_flat_update<real>(a, m->dNfPtr, m->dNfIdx, m->n_node_ctas, dt, m->stream),
+            KERNEL(launch_flat_update<real>(a, m->dNfPtr, m->dNfIdx, m->n_node_ctas, dt, st),
                    "update kernel");
     }
+    return FEM_OK;
+}
+
+constexpr int64_t kGraphSteps = 32;   // steps per captured graph
+
+// The launches of kGraphSteps steps of size dt, captured once into a graph
+// (on a private stream) and replayed on the mesh's stream: a small mesh's
+// step is a few tens of microseconds, of which launch gaps are a visible part.
+template <typename real>
+fem_status ensure_step_graph(fem_mesh *m, double dt)
+{
+    const char *skip = std::getenv("FEM_FAULT_SKIP_WEIGHTS");
+    const int fault = (skip && *skip && *skip != '0') ? 1 : 0;
+    if (m->step_graph && m->step_graph_dt == dt && m->step_graph_fault == fault) return FEM_OK;
+    if (m->step_graph) cudaGraphExecDestroy(m->step_graph);
+    m->step_graph = nullptr;
+    if (!m->cap_stream) CU(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    CU(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int nk = step_kernel_count(m);
+    fem_status st = FEM_OK;
+    for (int64_t s = 0; s < kGraphSteps && !st; s++)
+        for (int k = 0; k < nk && !st; k++) st = launch_step_kernel<real>(m, k, dt, m->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ce != cudaSuccess) return fail(FEM_ECUDA, "step graph capture: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&m->step_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        m->step_graph = nullptr;
+        return fail(FEM_ECUDA, "step graph instantiation: %s", cudaGetErrorString(ie));
+    }
+    m->step_graph_dt = dt;
+    m->step_graph_fault = fault;
     return FEM_OK;
 }
 
@@ -1050,9 +1095,16 @@ template <typename real>
 fem_status step_impl(fem_mesh *m, int64_t n, double dt)
 {
     const int nk = step_kernel_count(m);
-    for (int64_t s = 0; s < n; s++)
+    int64_t done = 0;
+    if (n >= kGraphSteps) {
+        fem_status st = ensure_step_graph<real>(m, dt);
+        if (st) return st;
+        for (; done + kGraphSteps <= n; done += kGraphSteps)
+            CU(cudaGraphLaunch(m->step_graph, m->stream));
+    }
+    for (int64_t s = done; s < n; s++)
         for (int k = 0; k < nk; k++) {
-            fem_status st = launch_step_kernel<real>(m, k, dt);
+            fem_status st = launch_step_kernel<real>(m, k, dt, m->stream);
             if (st) return st;
         }
     m->step += n;
@@ -1072,7 +1124,7 @@ fem_status step_profile_impl(fem_mesh *m, int64_t n, double dt, double *ms)
     for (int64_t s = 0; s < n && st == FEM_OK; s++) {
         for (int k = 0; k < nk && st == FEM_OK; k++) {
             cudaEventRecord(ev[k], m->stream);
-            st = launch_step_kernel<real>(m, k, dt);
+            st = launch_step_kernel<real>(m, k, dt, m->stream);
         }
         if (st) break;
         cudaEventRecord(ev[nk], m->stream);
