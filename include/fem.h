@@ -13,7 +13,9 @@
  * Optional: the apparent-heat-capacity formulation (Eqs. 6-7, Lemmon),
  * temperature-dependent conductivity (Eq. 9's K(T)), the cast-mold
  * interface between non-matching meshes (Eq. 8), and batches of independent
- * meshes advanced together with their own time steps.
+ * meshes advanced together with their own time steps.  Around the step:
+ * partition autotuning (fem_autotune) and pipelined host I/O
+ * (fem_set_state_async, fem_get_temperature_async, fem_sync).
  *
  * Conventions for every call
  *   - All array arguments are HOST pointers unless stated otherwise.  The
@@ -32,7 +34,8 @@
  *     caller's allocator, fem_set_allocator) and released by
  *     fem_mesh_destroy.  Work is enqueued on the mesh's stream (the legacy
  *     default stream unless fem_set_stream was called); the fem_get_* calls
- *     synchronise that stream.
+ *     synchronise that stream.  fem_step(n) with n >= 32 replays a CUDA
+ *     graph of 32 steps, captured once per time-step size.
  */
 #ifndef FEM_H
 #define FEM_H
