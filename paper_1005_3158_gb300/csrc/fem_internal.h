@@ -153,6 +153,7 @@ struct BlockArgs {
     // s_end) one launch processes (a batch steps only its active instances);
     // per-block / per-shared-node time steps (null: the launch's dt)
     int32_t b_first, b_count;
+    int32_t buf_bytes;         // persistent kernel: offset of its second block buffer
     int64_t s_first, s_end;
     const real *blk_dt;
     const real *sh_dt;
@@ -203,10 +204,13 @@ struct FlatArgs {
 
 // Launchers (fem_kernels.cu).  All return a cudaError_t as int.
 // Block variant, one step = launch_block_kernel + launch_shared_update.
-// kt: the instantiation with temperature-dependent conductivity
+// kt: the instantiation with temperature-dependent conductivity; lm: the
+// apparent-capacity formulation; pipe_grid > 0: the persistent kernel with
+// two block buffers of a.buf_bytes each (smem_bytes = both) on at most
+// pipe_grid CTAs.
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream, bool kt = false, bool lm = false);
+                        void *stream, bool kt = false, bool lm = false, int pipe_grid = 0);
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream);
 // Interface faces (Eq. 8): fg[pos[f]] = g[f] * mean T of nodes sis[f][0..2]
@@ -216,10 +220,11 @@ int launch_interface(StateView<real> v, const real *C, const real *Lc, const uin
                      const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
                      const real *g, int64_t n, void *stream);
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false, bool lm = false);
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false, bool lm = false,
+                           bool pipe = false);
 template <typename real>
 int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt = false,
-                           bool lm = false);
+                           bool lm = false, bool pipe = false);
 // Mirrors of the shared nodes' E in the block-local arrays follow Esh
 // (after the state was set from outside).
 template <typename real>
