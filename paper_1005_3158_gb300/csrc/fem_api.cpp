@@ -815,6 +815,10 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.b_first = 0;
     a.b_count = (int32_t)m->bp.blocks.size();
     a.buf_bytes = (int32_t)m->buf_bytes;
+    {
+        const char *pf = std::getenv("FEM_PIPE_PREFETCH");
+        a.pipe_prefetch = pf && *pf ? std::max(0, std::atoi(pf)) : 2;
+    }
     a.s_first = 0;
     a.s_end = m->bp.n_sh;
     a.blk_dt = nullptr;

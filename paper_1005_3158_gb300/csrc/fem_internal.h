@@ -154,6 +154,7 @@ struct BlockArgs {
     // per-block / per-shared-node time steps (null: the launch's dt)
     int32_t b_first, b_count;
     int32_t buf_bytes;         // persistent kernel: offset of its second block buffer
+    int32_t pipe_prefetch;     // persistent kernel: blocks prefetched into L2 beyond the buffers
     int64_t s_first, s_end;
     const real *blk_dt;
     const real *sh_dt;

@@ -176,6 +176,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// Bulk prefetch of [src, src + bytes) into L2 (no completion to wait for;
+// 16-byte aligned address and size).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t done;
@@ -401,6 +407,23 @@ __device__ __forceinline__ void issue_block_copies(const BlockArgs<real> &a, int
     const uint32_t wbytes = (uint32_t)(6 * (size_t)a.nes * sizeof(real));
     mbar_arrive_expect_tx(L.bar_w, wbytes);
     if (!a.fault_skip_weights) bulk_load(smem_addr(L.sw), a.w + 6 * (size_t)b * a.nes, wbytes, L.bar_w);
+}
+
+// Thread 0: L2 prefetch of everything issue_block_copies reads for block b
+// (the persistent kernel runs these a few blocks ahead, so that DRAM has
+// more bytes in flight than its two shared-memory buffers hold).
+template <typename real>
+__device__ __forceinline__ void prefetch_block_l2(const BlockArgs<real> &a, int b)
+{
+    const size_t lb = (size_t)b * a.ls;
+    const uint32_t eb = (uint32_t)(a.ls * sizeof(real));
+    bulk_prefetch_l2(a.blocks + b, (uint32_t)sizeof(BlockInfo));
+    bulk_prefetch_l2(a.Eloc + lb, eb);
+    bulk_prefetch_l2(a.CLloc + 2 * lb, 2 * eb);
+    bulk_prefetch_l2(a.phloc + lb, (uint32_t)a.ls);
+    bulk_prefetch_l2(a.posloc + lb, (uint32_t)a.ls * 4u);
+    bulk_prefetch_l2(a.sched + (size_t)b * a.chunk_words, (uint32_t)a.chunk_words * 4u);
+    bulk_prefetch_l2(a.w + 6 * (size_t)b * a.nes, (uint32_t)(6 * (size_t)a.nes * sizeof(real)));
 }
 
 // One element block's step from its buffer L, whose copies complete phase
@@ -683,6 +706,7 @@ __global__ void __launch_bounds__(NT, 1) k_block_step_pipe(const BlockArgs<real>
         mbar_fence_init();
         if (nk > 0) issue_block_copies<real>(a, a.b_first + c, L0);
         if (nk > 1) issue_block_copies<real>(a, a.b_first + c + G, L1);
+        for (int k = 2; k < 2 + a.pipe_prefetch && k < nk; ++k) prefetch_block_l2<real>(a, a.b_first + c + k * G);
     }
     __syncthreads();
     for (int k = 0; k < nk; ++k) {
@@ -699,7 +723,11 @@ __global__ void __launch_bounds__(NT, 1) k_block_step_pipe(const BlockArgs<real>
         }
         // every thread is done with this buffer: refill it with block k + 2
         __syncthreads();
-        if (threadIdx.x == 0 && k + 2 < nk) issue_block_copies<real>(a, a.b_first + c + (k + 2) * G, L);
+        if (threadIdx.x == 0) {
+            if (k + 2 < nk) issue_block_copies<real>(a, a.b_first + c + (k + 2) * G, L);
+            if (k + 2 + a.pipe_prefetch < nk)
+                prefetch_block_l2<real>(a, a.b_first + c + (k + 2 + a.pipe_prefetch) * G);
+        }
     }
 }
 
