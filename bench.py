@@ -99,8 +99,6 @@ def parse():
     ap.add_argument("--reorder", type=int, default=1)
     ap.add_argument("--block-elems", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--persistent", type=int, default=0,
-                    help="1: the persistent block kernel (one CTA per SM, two block buffers)")
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--autotune", default="",
                     help="comma list of candidate partitions, block_elems or "
@@ -448,8 +446,7 @@ def main():
     p = make_problem(args.workload)
     t_setup = time.perf_counter()
     mesh = fem.Mesh(p, args.precision, reorder=args.reorder, variant=args.variant,
-                    block_elems=args.block_elems, threads=args.threads,
-                    persistent=args.persistent)
+                    block_elems=args.block_elems, threads=args.threads)
     dt = 0.9 * mesh.stable_dt()
     stream = torch.cuda.Stream()
     mesh.set_stream(stream.cuda_stream)
@@ -591,7 +588,7 @@ def main():
                        "precision": args.precision, "reorder": args.reorder,
                        "n_blocks": info["n_blocks"], "threads": info["threads"],
                        "ctas_per_sm": info["ctas_per_sm"], "smem_per_cta": info["smem_per_cta"],
-                       "block_elems": args.block_elems, "persistent": args.persistent,
+                       "block_elems": args.block_elems,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (no flush)",
                        "dt_s": dt, "setup_s": round(t_setup, 1), "autotune": tuned},

@@ -112,11 +112,7 @@ typedef struct {
                             fewest threads whose 16-byte element accesses
                             cover the largest block); 128, 256, 512 or 1024 */
     int32_t formulation; /* fem_formulation, default FEM_ENTHALPY */
-    int32_t persistent;  /* block variant, constant k, enthalpy formulation:
-                            1 = one persistent CTA per SM that double-buffers
-                            its element blocks (threads 512 or 1024, default
-                            1024); 0 = one CTA per block (default) */
-    int32_t reserved[3];
+    int32_t reserved[4];
 } fem_options;
 
 /* Statistics of the execution plan (fem_mesh_info). */

@@ -124,9 +124,7 @@ struct fem_mesh {
     fem_free_fn free_fn = nullptr;
     void *alloc_ctx = nullptr;
     size_t dev_bytes = 0;
-    size_t smem_bytes = 0;                     // dynamic shared memory of a block-kernel CTA
-    size_t buf_bytes = 0;                      // persistent kernel: one block buffer
-    int pipe_grid = 0;                         // persistent kernel: CTAs (0: one CTA per block)
+    size_t smem_bytes = 0;
     int threads = 256;
     int32_t chunk_words = 0, max_slots = 0, ctas_per_sm = 0;
     int n_node_ctas = 0;
@@ -693,43 +691,23 @@ fem_status upload_block(fem_mesh *m)
         m->threads = 128;
         while (m->threads < 1024 && m->threads * vn < max_nep) m->threads *= 2;
     }
-    const size_t buf = block_kernel_smem((size_t)m->nes, cw, slots, (size_t)m->ls, sizeof(real));
+    m->smem_bytes = block_kernel_smem((size_t)m->nes, cw, slots, (size_t)m->ls, sizeof(real));
     if (m->ls > kMaxLocalNodes)
         return fail(FEM_EINVAL, "a block has %zu local nodes (> %d); lower block_elems", bp.max_nloc,
                     kMaxLocalNodes);
-    // the persistent kernel holds two block buffers (128-byte aligned)
-    const bool pipe = m->opt.persistent != 0;
-    if (pipe) {
-        if (m->has_kt || is_lm(m))
-            return fail(FEM_EINVAL, "the persistent block kernel takes constant k and the enthalpy formulation");
-        if (m->opt.threads == 0) m->threads = 1024;
-        if (m->threads != 512 && m->threads != 1024)
-            return fail(FEM_EINVAL, "the persistent block kernel takes 512 or 1024 threads");
-        m->buf_bytes = (buf + 127) & ~size_t(127);
-        m->smem_bytes = 2 * m->buf_bytes;
-    } else {
-        m->buf_bytes = 0;
-        m->smem_bytes = buf;
-    }
     int dev = 0, optin = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if ((size_t)optin < m->smem_bytes + 1024)
         return fail(FEM_EINVAL, "a block needs %zu bytes of shared memory (device limit %d); lower block_elems",
                     m->smem_bytes, optin);
-    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes, m->has_kt, is_lm(m), pipe),
+    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes, m->has_kt, is_lm(m)),
            "configuring the block kernel");
     int per_sm = 0;
-    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm, m->has_kt, is_lm(m), pipe),
+    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm, m->has_kt, is_lm(m)),
            "occupancy query");
     if (per_sm < 1) return fail(FEM_EINVAL, "the block kernel does not fit on an SM; lower block_elems");
     m->ctas_per_sm = per_sm;
-    m->pipe_grid = 0;
-    if (pipe) {
-        int sms = 0;
-        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        m->pipe_grid = sms * per_sm;
-    }
     return upload_interface<real>(m, bp.face_order);
 }
 
@@ -814,11 +792,6 @@ BlockArgs<real> block_args(const fem_mesh *m)
     a.err = m->dErr;
     a.b_first = 0;
     a.b_count = (int32_t)m->bp.blocks.size();
-    a.buf_bytes = (int32_t)m->buf_bytes;
-    {
-        const char *pf = std::getenv("FEM_PIPE_PREFETCH");
-        a.pipe_prefetch = pf && *pf ? std::max(0, std::atoi(pf)) : 2;
-    }
     a.s_first = 0;
     a.s_end = m->bp.n_sh;
     a.blk_dt = nullptr;
@@ -1062,7 +1035,7 @@ fem_status launch_step_kernel(fem_mesh *m, int k, double dt, cudaStream_t st)
         const BlockArgs<real> a = block_args<real>(m);
         if (k == 0)
             KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, st, m->has_kt,
-                                             is_lm(m), m->pipe_grid),
+                                             is_lm(m)),
                    "block kernel");
         else
             KERNEL(launch_shared_update<real>(a, dt, st), "shared-node kernel");
@@ -1296,9 +1269,6 @@ fem_status fem_mesh_create_ex(const double *xyz, int64_t n_nodes, const int32_t 
     if (opt.threads != 0 && opt.threads != 128 && opt.threads != 256 && opt.threads != 512 &&
         opt.threads != 1024)
         return fail(FEM_EINVAL, "threads must be 0, 128, 256, 512 or 1024");
-    if (opt.persistent != 0 && opt.persistent != 1) return fail(FEM_EINVAL, "persistent must be 0 or 1");
-    if (opt.persistent && opt.variant != FEM_VARIANT_BLOCK)
-        return fail(FEM_EINVAL, "the persistent kernel belongs to the block variant");
     std::unique_ptr<fem_mesh> m;
     try {
         if (!finite_all(xyz, 3 * n_nodes)) return fail(FEM_EINVAL, "non-finite coordinate");
@@ -2256,7 +2226,7 @@ fem_status advance_launches(fem_mesh *m, const std::vector<int64_t> &nk, cudaStr
             a.s_first = bp.inst_sh_start[(size_t)k0];
             a.s_end = bp.inst_sh_start[(size_t)k1];
             KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, 0.0, st, m->has_kt,
-                                             is_lm(m), m->pipe_grid),
+                                             is_lm(m)),
                    "block kernel");
             KERNEL(launch_shared_update<real>(a, 0.0, st), "shared-node kernel");
             k0 = k1;

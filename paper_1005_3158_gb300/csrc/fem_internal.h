@@ -153,8 +153,6 @@ struct BlockArgs {
     // s_end) one launch processes (a batch steps only its active instances);
     // per-block / per-shared-node time steps (null: the launch's dt)
     int32_t b_first, b_count;
-    int32_t buf_bytes;         // persistent kernel: offset of its second block buffer
-    int32_t pipe_prefetch;     // persistent kernel: blocks prefetched into L2 beyond the buffers
     int64_t s_first, s_end;
     const real *blk_dt;
     const real *sh_dt;
@@ -206,12 +204,10 @@ struct FlatArgs {
 // Launchers (fem_kernels.cu).  All return a cudaError_t as int.
 // Block variant, one step = launch_block_kernel + launch_shared_update.
 // kt: the instantiation with temperature-dependent conductivity; lm: the
-// apparent-capacity formulation; pipe_grid > 0: the persistent kernel with
-// two block buffers of a.buf_bytes each (smem_bytes = both) on at most
-// pipe_grid CTAs.
+// apparent-capacity formulation.
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream, bool kt = false, bool lm = false, int pipe_grid = 0);
+                        void *stream, bool kt = false, bool lm = false);
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream);
 // Interface faces (Eq. 8): fg[pos[f]] = g[f] * mean T of nodes sis[f][0..2]
@@ -221,11 +217,10 @@ int launch_interface(StateView<real> v, const real *C, const real *Lc, const uin
                      const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
                      const real *g, int64_t n, void *stream);
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false, bool lm = false,
-                           bool pipe = false);
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false, bool lm = false);
 template <typename real>
 int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt = false,
-                           bool lm = false, bool pipe = false);
+                           bool lm = false);
 // Mirrors of the shared nodes' E in the block-local arrays follow Esh
 // (after the state was set from outside).
 template <typename real>

@@ -21,8 +21,6 @@
 // are FP64 reductions of the state (k_energy_snapshot) taken on demand.
 #include <cuda_runtime.h>
 
-#include <algorithm>
-
 #include <cstdint>
 
 #include "fem_internal.h"
@@ -175,12 +173,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
-}
-// Bulk prefetch of [src, src + bytes) into L2 (no completion to wait for;
-// 16-byte aligned address and size).
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
@@ -407,23 +399,6 @@ __device__ __forceinline__ void issue_block_copies(const BlockArgs<real> &a, int
     const uint32_t wbytes = (uint32_t)(6 * (size_t)a.nes * sizeof(real));
     mbar_arrive_expect_tx(L.bar_w, wbytes);
     if (!a.fault_skip_weights) bulk_load(smem_addr(L.sw), a.w + 6 * (size_t)b * a.nes, wbytes, L.bar_w);
-}
-
-// Thread 0: L2 prefetch of everything issue_block_copies reads for block b
-// (the persistent kernel runs these a few blocks ahead, so that DRAM has
-// more bytes in flight than its two shared-memory buffers hold).
-template <typename real>
-__device__ __forceinline__ void prefetch_block_l2(const BlockArgs<real> &a, int b)
-{
-    const size_t lb = (size_t)b * a.ls;
-    const uint32_t eb = (uint32_t)(a.ls * sizeof(real));
-    bulk_prefetch_l2(a.blocks + b, (uint32_t)sizeof(BlockInfo));
-    bulk_prefetch_l2(a.Eloc + lb, eb);
-    bulk_prefetch_l2(a.CLloc + 2 * lb, 2 * eb);
-    bulk_prefetch_l2(a.phloc + lb, (uint32_t)a.ls);
-    bulk_prefetch_l2(a.posloc + lb, (uint32_t)a.ls * 4u);
-    bulk_prefetch_l2(a.sched + (size_t)b * a.chunk_words, (uint32_t)a.chunk_words * 4u);
-    bulk_prefetch_l2(a.w + 6 * (size_t)b * a.nes, (uint32_t)(6 * (size_t)a.nes * sizeof(real)));
 }
 
 // One element block's step from its buffer L, whose copies complete phase
@@ -679,55 +654,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
             drain_block_copies<real>(L, 0u);
         }
         __syncthreads();
-    }
-}
-
-// Persistent variant: one CTA per SM with two block buffers.  CTA c takes
-// the blocks c, c + G, c + 2G, ... of the launch (G = gridDim.x); while it
-// works on one buffer, the copies of its next block land in the other, and
-// a buffer is refilled (its barriers' next phase) as soon as its block is
-// done.  Buffer k & 1 holds the k-th block, in phase (k >> 1) & 1.
-template <typename real, int NT, bool KT, bool LM>
-__global__ void __launch_bounds__(NT, 1) k_block_step_pipe(const BlockArgs<real> a, const real dt)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double qwarp[NT / 32];
-    const BlockSmem<real> L0 = block_smem<real>(smem_raw, a);
-    const BlockSmem<real> L1 = block_smem<real>(smem_raw + a.buf_bytes, a);
-    const int G = (int)gridDim.x, c = (int)blockIdx.x;
-    const int nk = c < a.b_count ? (a.b_count - 1 - c) / G + 1 : 0;   // blocks of this CTA
-    if (threadIdx.x == 0) {
-        mbar_init(L0.bar_s, 1);
-        mbar_init(L0.bar_w, 1);
-        mbar_init(L0.bar_n, 1);
-        mbar_init(L1.bar_s, 1);
-        mbar_init(L1.bar_w, 1);
-        mbar_init(L1.bar_n, 1);
-        mbar_fence_init();
-        if (nk > 0) issue_block_copies<real>(a, a.b_first + c, L0);
-        if (nk > 1) issue_block_copies<real>(a, a.b_first + c + G, L1);
-        for (int k = 2; k < 2 + a.pipe_prefetch && k < nk; ++k) prefetch_block_l2<real>(a, a.b_first + c + k * G);
-    }
-    __syncthreads();
-    for (int k = 0; k < nk; ++k) {
-        const BlockSmem<real> &L = (k & 1) ? L1 : L0;
-        const uint32_t par = (uint32_t)(k >> 1) & 1u;
-        if (!block_body<real, NT, KT, LM>(a, dt, a.b_first + c + k * G, L, par, qwarp)) {
-            if (threadIdx.x == 0) {
-                atomicExch(a.err, kErrWaitTimeout);
-                drain_block_copies<real>(L, par);
-                if (k + 1 < nk) drain_block_copies<real>((k & 1) ? L0 : L1, (uint32_t)((k + 1) >> 1) & 1u);
-            }
-            __syncthreads();
-            return;
-        }
-        // every thread is done with this buffer: refill it with block k + 2
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (k + 2 < nk) issue_block_copies<real>(a, a.b_first + c + (k + 2) * G, L);
-            if (k + 2 + a.pipe_prefetch < nk)
-                prefetch_block_l2<real>(a, a.b_first + c + (k + 2 + a.pipe_prefetch) * G);
-        }
     }
 }
 
@@ -1001,17 +927,9 @@ BlockKernel<real> block_kernel_nt(bool kt, bool lm)
     if (lm) return kt ? k_block_step<real, NT, true, true> : k_block_step<real, NT, false, true>;
     return kt ? k_block_step<real, NT, true, false> : k_block_step<real, NT, false, false>;
 }
-// The persistent kernel exists for constant k and the enthalpy formulation,
-// with 512 or 1024 threads.
 template <typename real>
-BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm, bool pipe)
+BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm)
 {
-    if (pipe) {
-        if (kt || lm) return nullptr;
-        if (threads == 512) return k_block_step_pipe<real, 512, false, false>;
-        if (threads == 1024) return k_block_step_pipe<real, 1024, false, false>;
-        return nullptr;
-    }
     switch (threads) {
     case 128: return block_kernel_nt<real, 128>(kt, lm);
     case 256: return block_kernel_nt<real, 256>(kt, lm);
@@ -1022,28 +940,28 @@ BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm, bool pipe)
 }
 
 template <typename real>
-int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt, bool lm, bool pipe)
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt, bool lm)
 {
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm, pipe);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, f, threads, smem_bytes);
 }
 
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes, bool kt, bool lm, bool pipe)
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt, bool lm)
 {
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm, pipe);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream, bool kt, bool lm, int pipe_grid)
+                        void *stream, bool kt, bool lm)
 {
-    const int grid = pipe_grid > 0 ? std::min(a.b_count, pipe_grid) : a.b_count;
+    const int grid = a.b_count;
     if (grid <= 0) return 0;
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm, pipe_grid > 0);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
     if (!f) return (int)cudaErrorInvalidValue;
     f<<<grid, threads, smem_bytes, (cudaStream_t)stream>>>(a, (real)dt);
     return (int)cudaGetLastError();
@@ -1174,14 +1092,14 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
 }
 
 #define FEM_INSTANTIATE(real)                                                                     \
-    template int configure_block_kernel<real>(int, size_t, bool, bool, bool);                     \
-    template int block_kernel_occupancy<real>(int, size_t, int *, bool, bool, bool);              \
+    template int configure_block_kernel<real>(int, size_t, bool, bool);                           \
+    template int block_kernel_occupancy<real>(int, size_t, int *, bool, bool);                    \
     template int launch_mirror_copies<real>(const BlockArgs<real> &, void *);                     \
     template int launch_interface<real>(StateView<real>, const real *, const real *,              \
                                         const uint8_t *, const real *, real *, const int32_t *,   \
                                         const int32_t *, const real *, int64_t, void *);          \
     template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *,  \
-                                           bool, bool, int);                                      \
+                                           bool, bool);                                           \
     template int launch_shared_update<real>(const BlockArgs<real> &, double, void *);             \
     template int launch_flat_temperature<real>(const FlatArgs<real> &, void *);                   \
     template int launch_flat_elements<real>(const FlatArgs<real> &, bool, const int64_t *, int,  \

@@ -47,14 +47,3 @@ def test_async_io_argument_checks():
         assert st == fem.FEM_ESTATE
         assert fem.lib().fem_sync(None) == fem.FEM_EINVAL
         assert fem.lib().fem_sync(m.h) == fem.FEM_OK   # nothing on the device yet
-
-
-def test_persistent_option_checks():
-    p = mg.unit_cube(3)
-    with pytest.raises(fem.FemError) as e:
-        fem.fem_mesh_create(p.xyz, p.tets, p.mat, fem.FEM_FP32, 1, {"persistent": 2})
-    assert e.value.status == fem.FEM_EINVAL
-    with pytest.raises(fem.FemError) as e:
-        fem.fem_mesh_create(p.xyz, p.tets, p.mat, fem.FEM_FP32, 1,
-                            {"variant": fem.VARIANTS["atomic"], "persistent": 1})
-    assert e.value.status == fem.FEM_EINVAL
