@@ -340,101 +340,82 @@ struct Vec4Of<double> {
 __device__ __forceinline__ float &vat(float4 &v, int i) { return (&v.x)[i]; }
 __device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
 
-// Shared-memory layout of one element block's buffer (16-byte aligned
-// parts): [3 mbarriers, block header][conductances 6 x nes][schedule chunk]
-// [slots + dummy][per local node: E, partial position, phase byte].
-template <typename real>
-struct BlockSmem {
-    unsigned char *base;
-    const BlockInfo *hdr;
-    real *sw;          // conductances; apparent capacity: element capacities over row 0
-    uint32_t *chunk;   // schedule chunk: group offsets, then slot pairs
-    real *sv;          // slots (and (C, Lc) of the local nodes until pass 1)
-    real *sE;
-    int32_t *sPos;
-    uint8_t *sPh;
-    uint32_t bar_s, bar_w, bar_n;
-};
-
-template <typename real>
-__device__ __forceinline__ BlockSmem<real> block_smem(unsigned char *base, const BlockArgs<real> &a)
-{
-    BlockSmem<real> L;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base);
-    L.base = base;
-    L.hdr = reinterpret_cast<const BlockInfo *>(base + kSmemHdrOffset);
-    L.sw = reinterpret_cast<real *>(base + kSmemBarBytes);
-    L.chunk = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(L.sw) +
-                                           align16(6 * (size_t)a.nes * sizeof(real)));
-    L.sv = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(L.chunk) +
-                                    align16((size_t)a.chunk_words * 4));
-    L.sE = L.sv + a.max_slots;
-    L.sPos = reinterpret_cast<int32_t *>(L.sE + a.ls);
-    L.sPh = reinterpret_cast<uint8_t *>(L.sPos + a.ls);
-    L.bar_s = smem_addr(bar);
-    L.bar_w = smem_addr(bar + 1);
-    L.bar_n = smem_addr(bar + 2);
-    return L;
-}
-
-// Thread 0: the bulk copies of block b into buffer L, each barrier told the
-// bytes to expect.  The local node data first (fixed stride, needed first;
-// (C, Lc) goes to the slot area, free until pass 1) with the block header,
-// then the schedule chunk (fixed stride) and the six conductance rows: every
-// copy is in flight before the block header is read.
-template <typename real>
-__device__ __forceinline__ void issue_block_copies(const BlockArgs<real> &a, int b, const BlockSmem<real> &L)
-{
-    const size_t lb = (size_t)b * a.ls;
-    const uint32_t eb = (uint32_t)(a.ls * sizeof(real));
-    mbar_arrive_expect_tx(L.bar_n, 3u * eb + 5u * (uint32_t)a.ls + (uint32_t)sizeof(BlockInfo));
-    bulk_load(smem_addr(L.base + kSmemHdrOffset), a.blocks + b, (uint32_t)sizeof(BlockInfo), L.bar_n);
-    bulk_load(smem_addr(L.sE), a.Eloc + lb, eb, L.bar_n);
-    bulk_load(smem_addr(L.sv), a.CLloc + 2 * lb, 2 * eb, L.bar_n);
-    bulk_load(smem_addr(L.sPh), a.phloc + lb, (uint32_t)a.ls, L.bar_n);
-    bulk_load(smem_addr(L.sPos), a.posloc + lb, (uint32_t)a.ls * 4u, L.bar_n);
-    const uint32_t bytes = (uint32_t)a.chunk_words * 4u;
-    mbar_arrive_expect_tx(L.bar_s, bytes);
-    bulk_load(smem_addr(L.chunk), a.sched + (size_t)b * a.chunk_words, bytes, L.bar_s);
-    const uint32_t wbytes = (uint32_t)(6 * (size_t)a.nes * sizeof(real));
-    mbar_arrive_expect_tx(L.bar_w, wbytes);
-    if (!a.fault_skip_weights) bulk_load(smem_addr(L.sw), a.w + 6 * (size_t)b * a.nes, wbytes, L.bar_w);
-}
-
-// One element block's step from its buffer L, whose copies complete phase
-// `par` of its barriers: T(E), pass 1 (T into the element-corner slots),
-// pass 2 (element products), faces, pass 3 (node sums; interior update or
-// shared partial), boundary heat.  Returns false when a bounded wait gave
-// up (every thread returns false; nothing was written to global memory).
+// One CTA per element block b, NT threads.  The block's local node data
+// (stride b*ls), schedule chunk (stride b*chunk_words) and six conductance
+// rows (stride 6*b*nes) all sit at fixed strides, so thread 0 bulk-copies
+// them into shared memory at kernel start from blockIdx alone.
 // A warp owns the 32-lane schedule groups block_group() gives it (group g
 // covers local nodes 32 g + lane); thread t owns element quad(s) t, t+NT, ...
 template <typename real, int NT, bool KT, bool LM>
-__device__ __forceinline__ bool block_body(const BlockArgs<real> &a, const real dt, const int b,
-                                           const BlockSmem<real> &L, const uint32_t par,
-                                           double *qwarp)
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
+    k_block_step(const BlockArgs<real> a, const real dt)
 {
     constexpr int NW = NT / 32;
     constexpr int MAXJ = kMaxLocalNodes / NT;   // local nodes per thread
     using V = typename Vec4Of<real>::type;
     using V2 = typename Vec2Of<real>::type;
     constexpr int VN = Vec4Of<real>::n;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double qwarp[NW];   // per-warp boundary heat
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = a.b_first + (int)blockIdx.x;
     const int ls = a.ls, nes = a.nes;
-    const BlockInfo &bi = *L.hdr;
-    real *const sw = L.sw, *const sv = L.sv, *const sE = L.sE;
-    const uint32_t *const chunk = L.chunk;
-    const int32_t *const sPos = L.sPos;
-    const uint8_t *const sPh = L.sPh;
-    const uint32_t bar_s = L.bar_s, bar_w = L.bar_w, bar_n = L.bar_n;
+
+    // shared memory: [3 barriers, block header][conductances 6 x nes]
+    // [schedule chunk][slots + dummy][per local node: E, partial position,
+    // phase byte]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    const BlockInfo &bi = *reinterpret_cast<const BlockInfo *>(smem_raw + kSmemHdrOffset);
+    real *sw = reinterpret_cast<real *>(smem_raw + kSmemBarBytes);
+    uint32_t *chunk = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sw) +
+                                                    align16(6 * (size_t)nes * sizeof(real)));
+    real *sv = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(chunk) +
+                                        align16((size_t)a.chunk_words * 4));
+    real *sE = sv + a.max_slots;                                  // [ls]
+    int32_t *sPos = reinterpret_cast<int32_t *>(sE + ls);         // [ls]
+    uint8_t *sPh = reinterpret_cast<uint8_t *>(sPos + ls);        // [ls]
+    const uint32_t bar_s = smem_addr(bar), bar_w = smem_addr(bar + 1), bar_n = smem_addr(bar + 2);
     const size_t lb = (size_t)b * ls;
+
+    // bulk copies: the local node data first (fixed stride, needed first;
+    // (C, Lc) goes to the slot area, free until pass 1), then the schedule
+    // chunk and the six conductance rows named by the block header
+    if (threadIdx.x == 0) {
+        mbar_init(bar_s, 1);
+        mbar_init(bar_w, 1);
+        mbar_init(bar_n, 1);
+        mbar_fence_init();
+        const uint32_t eb = (uint32_t)(ls * sizeof(real));
+        // E, (C, Lc), phase, position, and the block header
+        mbar_arrive_expect_tx(bar_n, 3u * eb + 5u * (uint32_t)ls + (uint32_t)sizeof(BlockInfo));
+        bulk_load(smem_addr(smem_raw + kSmemHdrOffset), a.blocks + b, (uint32_t)sizeof(BlockInfo), bar_n);
+        bulk_load(smem_addr(sE), a.Eloc + lb, eb, bar_n);
+        bulk_load(smem_addr(sv), a.CLloc + 2 * lb, 2 * eb, bar_n);
+        bulk_load(smem_addr(sPh), a.phloc + lb, (uint32_t)ls, bar_n);
+        bulk_load(smem_addr(sPos), a.posloc + lb, (uint32_t)ls * 4u, bar_n);
+        // the schedule chunk (fixed stride) and the six conductance rows:
+        // every copy is in flight before the block header is read
+        const uint32_t bytes = (uint32_t)a.chunk_words * 4u;
+        mbar_arrive_expect_tx(bar_s, bytes);
+        bulk_load(smem_addr(chunk), a.sched + (size_t)b * a.chunk_words, bytes, bar_s);
+        const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
+        mbar_arrive_expect_tx(bar_w, wbytes);
+        if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
+    }
     // this block's time step (a batch gives every instance its own; the
     // load's latency is hidden behind the passes)
     const real dtb = a.blk_dt ? a.blk_dt[b] : dt;
 
+    // the mbarriers were initialised by thread 0 before any other thread
+    // polls them: the barrier below orders the two
+    __syncthreads();
     int failed = 0;
-    if (threadIdx.x == 0) failed = !mbar_wait(bar_n, par);
-    if (__syncthreads_or(failed)) return false;
-    mbar_try_wait(bar_n, par);
+    if (threadIdx.x == 0) failed = !mbar_wait(bar_n, 0);
+    if (__syncthreads_or(failed)) {
+        give_up(a.err, bar_s, bar_w, bar_n);
+        return;
+    }
+    mbar_try_wait(bar_n, 0);
     // the block header is in shared memory from here on
     const int nloc = bi.nint + bi.nsh;
     const int ne_pad = bi.ne_pad, nf_pad = bi.nf_pad;
@@ -479,9 +460,12 @@ __device__ __forceinline__ bool block_body(const BlockArgs<real> &a, const real 
     }
     // the vote below is also the barrier that ends the reads of (C, Lc)
     // from the slot area before pass 1 overwrites it
-    if (threadIdx.x == 0) failed = !mbar_wait(bar_s, par);
-    if (__syncthreads_or(failed)) return false;
-    mbar_try_wait(bar_s, par);
+    if (threadIdx.x == 0) failed = !mbar_wait(bar_s, 0);
+    if (__syncthreads_or(failed)) {
+        give_up(a.err, bar_s, bar_w, bar_n);
+        return;
+    }
+    mbar_try_wait(bar_s, 0);
     const uint32_t *pairs = chunk + hdr;   // pair p, lane l at pairs[p*32 + l]
 
     // pass 1: T of every local node into the slots of its element corners
@@ -501,9 +485,12 @@ __device__ __forceinline__ bool block_body(const BlockArgs<real> &a, const real 
         }
     }
 
-    if (threadIdx.x == 0) failed = !mbar_wait(bar_w, par);
-    if (__syncthreads_or(failed)) return false;
-    mbar_try_wait(bar_w, par);
+    if (threadIdx.x == 0) failed = !mbar_wait(bar_w, 0);
+    if (__syncthreads_or(failed)) {
+        give_up(a.err, bar_s, bar_w, bar_n);
+        return;
+    }
+    mbar_try_wait(bar_w, 0);
 
     // pass 2: element products, VN elements per 16-byte access
     for (int qd = threadIdx.x; qd * VN < bi.ne; qd += NT) {
@@ -611,49 +598,6 @@ __device__ __forceinline__ bool block_body(const BlockArgs<real> &a, const real 
         double q = 0.0;
         for (int k = 0; k < NW; k++) q += qwarp[k];
         a.qcum[b] = qprev + (double)dtb * q;
-    }
-    return true;
-}
-
-// Bounded second chance for the copies still in flight into buffer L
-// (phase par) before the CTA releases its shared memory (thread 0).
-template <typename real>
-__device__ __forceinline__ void drain_block_copies(const BlockSmem<real> &L, uint32_t par)
-{
-    mbar_wait(L.bar_n, par);
-    mbar_wait(L.bar_s, par);
-    mbar_wait(L.bar_w, par);
-}
-
-// One CTA per element block b = b_first + blockIdx.x, NT threads.  The
-// block's local node data (stride b*ls), schedule chunk (stride
-// b*chunk_words) and six conductance rows (stride 6*b*nes) all sit at fixed
-// strides, so thread 0 bulk-copies them into shared memory at kernel start
-// from blockIdx alone.
-template <typename real, int NT, bool KT, bool LM>
-__global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
-    k_block_step(const BlockArgs<real> a, const real dt)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double qwarp[NT / 32];   // per-warp boundary heat
-    const int b = a.b_first + (int)blockIdx.x;
-    const BlockSmem<real> L = block_smem<real>(smem_raw, a);
-    if (threadIdx.x == 0) {
-        mbar_init(L.bar_s, 1);
-        mbar_init(L.bar_w, 1);
-        mbar_init(L.bar_n, 1);
-        mbar_fence_init();
-        issue_block_copies<real>(a, b, L);
-    }
-    // the mbarriers were initialised by thread 0 before any other thread
-    // polls them: the barrier below orders the two
-    __syncthreads();
-    if (!block_body<real, NT, KT, LM>(a, dt, b, L, 0u, qwarp)) {
-        if (threadIdx.x == 0) {
-            atomicExch(a.err, kErrWaitTimeout);
-            drain_block_copies<real>(L, 0u);
-        }
-        __syncthreads();
     }
 }
 
