@@ -203,8 +203,7 @@ struct FlatArgs {
 
 // Launchers (fem_kernels.cu).  All return a cudaError_t as int.
 // Block variant, one step = launch_block_kernel + launch_shared_update.
-// kt: the instantiation with temperature-dependent conductivity; lm: the
-// apparent-capacity formulation.
+// kt: the instantiation with temperature-dependent conductivity
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
                         void *stream, bool kt = false, bool lm = false);
