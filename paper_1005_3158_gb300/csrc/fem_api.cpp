@@ -600,22 +600,13 @@ fem_status upload_block(fem_mesh *m)
     if ((st = upload<BlockInfo>(m, &m->dBlocks, bp.blocks.data(), bp.blocks.size()))) return st;
     {
         // device schedule stream: per block a header of group offsets (in
-        // pairs of rounds) and the block's rounds as 32-bit pairs of 16-bit
-        // slot entries.  FP32 entries are byte offsets into the slot array
-        // (slot id x 4), which the kernel adds to a constant address.
+        // pairs of rounds) and the block's rounds as 32-bit pairs
         std::vector<uint32_t> stream((size_t)bp.n_sched_words, 0u);
-        const bool bytes = sizeof(real) == 4;
         for (const BlockInfo &b : bp.blocks) {
-            if (bytes && block_slots(b) * 4 > 65536)
-                return fail(FEM_EINVAL, "a block has %zu slots (FP32 limit 16384); lower block_elems",
-                            block_slots(b));
             uint32_t *c = stream.data() + b.s0;
             for (int32_t g = 0; g <= b.ngrp; g++) c[g] = (uint32_t)((bp.grp[(size_t)b.g0 + g] - b.r0) / 2);
-            uint32_t *pr = c + chunk_header_words(b.ngrp);
-            std::memcpy(pr, bp.sched.data() + (size_t)b.r0 * 32, (size_t)b.nrounds * 64);
-            if (bytes)
-                for (int64_t k = 0; k < (int64_t)b.nrounds * 16; k++)
-                    pr[k] = ((pr[k] & 0xFFFFu) << 2) | ((pr[k] >> 16) << 18);
+            std::memcpy(c + chunk_header_words(b.ngrp), bp.sched.data() + (size_t)b.r0 * 32,
+                        (size_t)b.nrounds * 64);
         }
         if ((st = upload<uint32_t>(m, &m->dSched, stream.data(), stream.size()))) return st;
     }

@@ -266,27 +266,6 @@ __device__ __forceinline__ real apparent_cp(const BlockArgs<real> &a, int m, rea
     return (Tm >= Ts && Tm < Tl) ? c + L * inv : c;
 }
 
-// A 16-bit schedule entry names a slot of the block's slot array (which
-// starts at svb): FP32 schedules hold the slot's byte offset (slot id x 4),
-// FP64 schedules the slot id.
-template <typename real>
-__device__ __forceinline__ real &slot_ref(unsigned char *svb, uint32_t f);
-template <>
-__device__ __forceinline__ float &slot_ref<float>(unsigned char *svb, uint32_t f)
-{
-    return *reinterpret_cast<float *>(svb + f);
-}
-template <>
-__device__ __forceinline__ double &slot_ref<double>(unsigned char *svb, uint32_t f)
-{
-    return reinterpret_cast<double *>(svb)[f];
-}
-template <typename real>
-__device__ __forceinline__ uint32_t slot_id(uint32_t f)
-{
-    return sizeof(real) == 4 ? f >> 2 : f;
-}
-
 // Capacity behind a slot of the block's slot array: element-corner slots
 // (below 4 ne_pad) name element slot - corner * ne_pad, whose capacity pass
 // 2 left at sw[element]; face and padding slots carry none.
@@ -382,19 +361,17 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     const int b = a.b_first + (int)blockIdx.x;
     const int ls = a.ls, nes = a.nes;
 
-    // shared memory: [3 barriers, block header][slots + dummy][conductances
-    // 6 x nes][schedule chunk][per local node: E, partial position, phase
-    // byte].  The slots sit at a fixed offset, so that a schedule entry
-    // addresses its slot with no arithmetic (slot_ref).
+    // shared memory: [3 barriers, block header][conductances 6 x nes]
+    // [schedule chunk][slots + dummy][per local node: E, partial position,
+    // phase byte]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     const BlockInfo &bi = *reinterpret_cast<const BlockInfo *>(smem_raw + kSmemHdrOffset);
-    unsigned char *const svb = smem_raw + kSmemBarBytes;
-    real *sv = reinterpret_cast<real *>(svb);
-    real *sw = reinterpret_cast<real *>(svb + align16((size_t)a.max_slots * sizeof(real)));
+    real *sw = reinterpret_cast<real *>(smem_raw + kSmemBarBytes);
     uint32_t *chunk = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sw) +
                                                     align16(6 * (size_t)nes * sizeof(real)));
-    real *sE = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(chunk) +
-                                        align16((size_t)a.chunk_words * 4));   // [ls]
+    real *sv = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(chunk) +
+                                        align16((size_t)a.chunk_words * 4));
+    real *sE = sv + a.max_slots;                                  // [ls]
     int32_t *sPos = reinterpret_cast<int32_t *>(sE + ls);         // [ls]
     uint8_t *sPh = reinterpret_cast<uint8_t *>(sPos + ls);        // [ls]
     const uint32_t bar_s = smem_addr(bar), bar_w = smem_addr(bar + 1), bar_n = smem_addr(bar + 2);
@@ -502,8 +479,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
 #pragma unroll 4
             for (int pr = p0; pr < p1; ++pr) {
                 const uint32_t v = pairs[pr * 32 + lane];
-                if (FEM_IN(slot_id<real>(v & 0xFFFFu), a.max_slots, a.err)) slot_ref<real>(svb, v & 0xFFFFu) = T;
-                if (FEM_IN(slot_id<real>(v >> 16), a.max_slots, a.err)) slot_ref<real>(svb, v >> 16) = T;
+                if (FEM_IN(v & 0xFFFFu, a.max_slots, a.err)) sv[v & 0xFFFFu] = T;
+                if (FEM_IN(v >> 16, a.max_slots, a.err)) sv[v >> 16] = T;
             }
         }
     }
@@ -601,11 +578,11 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
 #pragma unroll 4
         for (int pr = p0; pr < p1; ++pr) {
             const uint32_t v = pairs[pr * 32 + lane];
-            if (FEM_IN(slot_id<real>(v & 0xFFFFu), a.max_slots, a.err)) R += slot_ref<real>(svb, v & 0xFFFFu);
-            if (FEM_IN(slot_id<real>(v >> 16), a.max_slots, a.err)) R += slot_ref<real>(svb, v >> 16);
+            if (FEM_IN(v & 0xFFFFu, a.max_slots, a.err)) R += sv[v & 0xFFFFu];
+            if (FEM_IN(v >> 16, a.max_slots, a.err)) R += sv[v >> 16];
             if (LM) {   // capacity of the element behind each element-corner slot
-                Cap += slot_capacity(sw, slot_id<real>(v & 0xFFFFu), ne_pad);
-                Cap += slot_capacity(sw, slot_id<real>(v >> 16), ne_pad);
+                Cap += slot_capacity(sw, v & 0xFFFFu, ne_pad);
+                Cap += slot_capacity(sw, v >> 16, ne_pad);
             }
         }
         if (l < bi.nint) {
