@@ -125,6 +125,7 @@ struct fem_mesh {
     void *alloc_ctx = nullptr;
     size_t dev_bytes = 0;
     size_t smem_bytes = 0;
+    bool wg = false;                           // block kernel reads the conductances from L2
     int threads = 256;
     int32_t chunk_words = 0, max_slots = 0, ctas_per_sm = 0;
     int n_node_ctas = 0;
@@ -691,7 +692,11 @@ fem_status upload_block(fem_mesh *m)
         m->threads = 128;
         while (m->threads < 1024 && m->threads * vn < max_nep) m->threads *= 2;
     }
-    m->smem_bytes = block_kernel_smem((size_t)m->nes, cw, slots, (size_t)m->ls, sizeof(real));
+    // conductances from L2 (fem_options.reserved[0] = 1): no shared-memory rows
+    m->wg = m->opt.reserved[0] == 1 && !m->has_kt && !is_lm(m);
+    if (m->wg && m->opt.threads == 0) m->threads = 256;
+    m->smem_bytes = block_kernel_smem((size_t)m->nes, cw, slots, (size_t)m->ls, sizeof(real)) -
+                    (m->wg ? align16(6 * (size_t)m->nes * sizeof(real)) : 0);
     if (m->ls > kMaxLocalNodes)
         return fail(FEM_EINVAL, "a block has %zu local nodes (> %d); lower block_elems", bp.max_nloc,
                     kMaxLocalNodes);
@@ -701,10 +706,10 @@ fem_status upload_block(fem_mesh *m)
     if ((size_t)optin < m->smem_bytes + 1024)
         return fail(FEM_EINVAL, "a block needs %zu bytes of shared memory (device limit %d); lower block_elems",
                     m->smem_bytes, optin);
-    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes, m->has_kt, is_lm(m)),
+    KERNEL(configure_block_kernel<real>(m->threads, m->smem_bytes, m->has_kt, is_lm(m), m->wg),
            "configuring the block kernel");
     int per_sm = 0;
-    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm, m->has_kt, is_lm(m)),
+    KERNEL(block_kernel_occupancy<real>(m->threads, m->smem_bytes, &per_sm, m->has_kt, is_lm(m), m->wg),
            "occupancy query");
     if (per_sm < 1) return fail(FEM_EINVAL, "the block kernel does not fit on an SM; lower block_elems");
     m->ctas_per_sm = per_sm;
@@ -1035,7 +1040,7 @@ fem_status launch_step_kernel(fem_mesh *m, int k, double dt, cudaStream_t st)
         const BlockArgs<real> a = block_args<real>(m);
         if (k == 0)
             KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, dt, st, m->has_kt,
-                                             is_lm(m)),
+                                             is_lm(m), m->wg),
                    "block kernel");
         else
             KERNEL(launch_shared_update<real>(a, dt, st), "shared-node kernel");
@@ -2226,7 +2231,7 @@ fem_status advance_launches(fem_mesh *m, const std::vector<int64_t> &nk, cudaStr
             a.s_first = bp.inst_sh_start[(size_t)k0];
             a.s_end = bp.inst_sh_start[(size_t)k1];
             KERNEL(launch_block_kernel<real>(a, m->threads, m->smem_bytes, 0.0, st, m->has_kt,
-                                             is_lm(m)),
+                                             is_lm(m), m->wg),
                    "block kernel");
             KERNEL(launch_shared_update<real>(a, 0.0, st), "shared-node kernel");
             k0 = k1;

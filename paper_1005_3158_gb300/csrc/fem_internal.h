@@ -206,7 +206,7 @@ struct FlatArgs {
 // kt: the instantiation with temperature-dependent conductivity
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream, bool kt = false, bool lm = false);
+                        void *stream, bool kt = false, bool lm = false, bool wg = false);
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream);
 // Interface faces (Eq. 8): fg[pos[f]] = g[f] * mean T of nodes sis[f][0..2]
@@ -216,10 +216,11 @@ int launch_interface(StateView<real> v, const real *C, const real *Lc, const uin
                      const real *ranges, real *fg, const int32_t *pos, const int32_t *sis,
                      const real *g, int64_t n, void *stream);
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false, bool lm = false);
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt = false, bool lm = false,
+                           bool wg = false);
 template <typename real>
 int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt = false,
-                           bool lm = false);
+                           bool lm = false, bool wg = false);
 // Mirrors of the shared nodes' E in the block-local arrays follow Esh
 // (after the state was set from outside).
 template <typename real>

@@ -174,6 +174,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned address and
+// size; nothing to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t done;
@@ -346,8 +352,13 @@ __device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
 // them into shared memory at kernel start from blockIdx alone.
 // A warp owns the 32-lane schedule groups block_group() gives it (group g
 // covers local nodes 32 g + lane); thread t owns element quad(s) t, t+NT, ...
-template <typename real, int NT, bool KT, bool LM>
-__global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
+// WG: the conductances are not staged in shared memory; pass 2 reads them
+// from global memory, into L2 by a bulk prefetch at the start of the CTA
+// (a 2,048-tet FP32 block then needs ~63 KB, three CTAs of 256 threads per
+// SM).
+template <typename real, int NT, bool KT, bool LM, bool WG = false>
+__global__ void __launch_bounds__(NT, WG ? (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1))
+                                         : (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     k_block_step(const BlockArgs<real> a, const real dt)
 {
     constexpr int NW = NT / 32;
@@ -368,7 +379,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     const BlockInfo &bi = *reinterpret_cast<const BlockInfo *>(smem_raw + kSmemHdrOffset);
     real *sw = reinterpret_cast<real *>(smem_raw + kSmemBarBytes);
     uint32_t *chunk = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(sw) +
-                                                    align16(6 * (size_t)nes * sizeof(real)));
+                                                    (WG ? 0 : align16(6 * (size_t)nes * sizeof(real))));
     real *sv = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(chunk) +
                                         align16((size_t)a.chunk_words * 4));
     real *sE = sv + a.max_slots;                                  // [ls]
@@ -399,8 +410,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         mbar_arrive_expect_tx(bar_s, bytes);
         bulk_load(smem_addr(chunk), a.sched + (size_t)b * a.chunk_words, bytes, bar_s);
         const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
-        mbar_arrive_expect_tx(bar_w, wbytes);
-        if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
+        if (WG) {   // bar_w completes at once; the rows go to L2 only
+            mbar_arrive_expect_tx(bar_w, 0u);
+            bulk_prefetch_l2(a.w + 6 * (size_t)b * nes, wbytes);
+        } else {
+            mbar_arrive_expect_tx(bar_w, wbytes);
+            if (!a.fault_skip_weights) bulk_load(smem_addr(sw), a.w + 6 * (size_t)b * nes, wbytes, bar_w);
+        }
     }
     // this block's time step (a batch gives every instance its own; the
     // load's latency is hidden behind the passes)
@@ -498,7 +514,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         if (!FEM_IN(e + VN - 1, nes, a.err) || !FEM_IN(3 * ne_pad + e + VN - 1, a.max_slots, a.err)) break;
         V wq[6];
 #pragma unroll
-        for (int k = 0; k < 6; k++) wq[k] = *reinterpret_cast<const V *>(sw + k * nes + e);
+        for (int k = 0; k < 6; k++)
+            wq[k] = WG ? __ldg(reinterpret_cast<const V *>(a.w + (6 * (size_t)b + k) * nes + e))
+                       : *reinterpret_cast<const V *>(sw + k * nes + e);
         V T0 = *reinterpret_cast<const V *>(sv + e);
         V T1 = *reinterpret_cast<const V *>(sv + ne_pad + e);
         V T2 = *reinterpret_cast<const V *>(sv + 2 * ne_pad + e);
@@ -872,8 +890,14 @@ BlockKernel<real> block_kernel_nt(bool kt, bool lm)
     return kt ? k_block_step<real, NT, true, false> : k_block_step<real, NT, false, false>;
 }
 template <typename real>
-BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm)
+BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm, bool wg)
 {
+    if (wg) {   // constant k, enthalpy formulation only
+        if (kt || lm) return nullptr;
+        if (threads == 256) return k_block_step<real, 256, false, false, true>;
+        if (threads == 512) return k_block_step<real, 512, false, false, true>;
+        return nullptr;
+    }
     switch (threads) {
     case 128: return block_kernel_nt<real, 128>(kt, lm);
     case 256: return block_kernel_nt<real, 256>(kt, lm);
@@ -884,28 +908,28 @@ BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm)
 }
 
 template <typename real>
-int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt, bool lm)
+int block_kernel_occupancy(int threads, size_t smem_bytes, int *ctas_per_sm, bool kt, bool lm, bool wg)
 {
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm, wg);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, f, threads, smem_bytes);
 }
 
 template <typename real>
-int configure_block_kernel(int threads, size_t smem_bytes, bool kt, bool lm)
+int configure_block_kernel(int threads, size_t smem_bytes, bool kt, bool lm, bool wg)
 {
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm, wg);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 template <typename real>
 int launch_block_kernel(const BlockArgs<real> &a, int threads, size_t smem_bytes, double dt,
-                        void *stream, bool kt, bool lm)
+                        void *stream, bool kt, bool lm, bool wg)
 {
     const int grid = a.b_count;
     if (grid <= 0) return 0;
-    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm);
+    BlockKernel<real> f = block_kernel_for<real>(threads, kt, lm, wg);
     if (!f) return (int)cudaErrorInvalidValue;
     f<<<grid, threads, smem_bytes, (cudaStream_t)stream>>>(a, (real)dt);
     return (int)cudaGetLastError();
@@ -1036,14 +1060,14 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
 }
 
 #define FEM_INSTANTIATE(real)                                                                     \
-    template int configure_block_kernel<real>(int, size_t, bool, bool);                           \
-    template int block_kernel_occupancy<real>(int, size_t, int *, bool, bool);                    \
+    template int configure_block_kernel<real>(int, size_t, bool, bool, bool);                     \
+    template int block_kernel_occupancy<real>(int, size_t, int *, bool, bool, bool);              \
     template int launch_mirror_copies<real>(const BlockArgs<real> &, void *);                     \
     template int launch_interface<real>(StateView<real>, const real *, const real *,              \
                                         const uint8_t *, const real *, real *, const int32_t *,   \
                                         const int32_t *, const real *, int64_t, void *);          \
     template int launch_block_kernel<real>(const BlockArgs<real> &, int, size_t, double, void *,  \
-                                           bool, bool);                                           \
+                                           bool, bool, bool);                                     \
     template int launch_shared_update<real>(const BlockArgs<real> &, double, void *);             \
     template int launch_flat_temperature<real>(const FlatArgs<real> &, void *);                   \
     template int launch_flat_elements<real>(const FlatArgs<real> &, bool, const int64_t *, int,  \
