@@ -99,7 +99,6 @@ def parse():
     ap.add_argument("--reorder", type=int, default=1)
     ap.add_argument("--block-elems", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--weights-l2", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=20)
     ap.add_argument("--autotune", default="",
                     help="comma list of candidate partitions, block_elems or "
@@ -447,8 +446,7 @@ def main():
     p = make_problem(args.workload)
     t_setup = time.perf_counter()
     mesh = fem.Mesh(p, args.precision, reorder=args.reorder, variant=args.variant,
-                    block_elems=args.block_elems, threads=args.threads,
-                    weights_l2=args.weights_l2)
+                    block_elems=args.block_elems, threads=args.threads)
     dt = 0.9 * mesh.stable_dt()
     stream = torch.cuda.Stream()
     mesh.set_stream(stream.cuda_stream)

@@ -259,10 +259,23 @@ void release_device(fem_mesh *m)
     m->own_stream = nullptr;
 }
 
+bool is_block(const fem_mesh *m);
+bool is_lm(const fem_mesh *m);
+
+// With constant k and the enthalpy formulation the block kernel runs with
+// 256 threads and reads the conductances from L2 instead of staging them
+// in shared memory: a 1,792-tet FP32 block then needs ~56 KB, and four
+// CTAs share an SM.  Other thread counts, k(T) and the apparent capacity
+// stage the conductances.
+bool weights_from_l2(const fem_mesh *m)
+{
+    return is_block(m) && !m->has_kt && !is_lm(m) && (m->opt.threads == 0 || m->opt.threads == 256);
+}
+
 int default_block_elems(const fem_mesh *m)
 {
     int be = m->opt.block_elems;
-    if (be <= 0) be = m->prec == FEM_FP32 ? 2048 : 1024;
+    if (be <= 0) be = m->prec == FEM_FP32 ? (weights_from_l2(m) ? 1792 : 2048) : 1024;
     return std::min(std::max(be, 64), 12288);
 }
 
@@ -687,14 +700,14 @@ fem_status upload_block(fem_mesh *m)
     slots = (slots + 3) & ~size_t(3);
     m->max_slots = (int32_t)slots;
     const int vn = sizeof(real) == 4 ? 4 : 2;
+    m->wg = weights_from_l2(m);
     m->threads = m->opt.threads;
-    if (m->threads == 0) {
+    if (m->threads == 0 && m->wg) {
+        m->threads = 256;
+    } else if (m->threads == 0) {
         m->threads = 128;
         while (m->threads < 1024 && m->threads * vn < max_nep) m->threads *= 2;
     }
-    // conductances from L2 (fem_options.reserved[0] = 1): no shared-memory rows
-    m->wg = m->opt.reserved[0] == 1 && !m->has_kt && !is_lm(m);
-    if (m->wg && m->opt.threads == 0) m->threads = 256;
     m->smem_bytes = block_kernel_smem((size_t)m->nes, cw, slots, (size_t)m->ls, sizeof(real)) -
                     (m->wg ? align16(6 * (size_t)m->nes * sizeof(real)) : 0);
     if (m->ls > kMaxLocalNodes)

@@ -353,12 +353,11 @@ __device__ __forceinline__ double &vat(double2 &v, int i) { return (&v.x)[i]; }
 // A warp owns the 32-lane schedule groups block_group() gives it (group g
 // covers local nodes 32 g + lane); thread t owns element quad(s) t, t+NT, ...
 // WG: the conductances are not staged in shared memory; pass 2 reads them
-// from global memory, into L2 by a bulk prefetch at the start of the CTA
-// (a 2,048-tet FP32 block then needs ~63 KB, three CTAs of 256 threads per
-// SM).
+// from global memory, brought into L2 by a bulk prefetch at the start of
+// the CTA.  A 1,792-tet FP32 block then needs ~56 KB, and four CTAs of 256
+// threads (64 registers) share an SM.
 template <typename real, int NT, bool KT, bool LM, bool WG = false>
-__global__ void __launch_bounds__(NT, WG ? (NT <= 256 ? 3 : (NT <= 512 ? 2 : 1))
-                                         : (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     k_block_step(const BlockArgs<real> a, const real dt)
 {
     constexpr int NW = NT / 32;
@@ -894,9 +893,7 @@ BlockKernel<real> block_kernel_for(int threads, bool kt, bool lm, bool wg)
 {
     if (wg) {   // constant k, enthalpy formulation only
         if (kt || lm) return nullptr;
-        if (threads == 256) return k_block_step<real, 256, false, false, true>;
-        if (threads == 512) return k_block_step<real, 512, false, false, true>;
-        return nullptr;
+        return threads == 256 ? k_block_step<real, 256, false, false, true> : nullptr;
     }
     switch (threads) {
     case 128: return block_kernel_nt<real, 128>(kt, lm);

@@ -190,7 +190,6 @@ def fem_mesh_create(xyz, tets, mat_id, prec=FEM_FP64, reorder=0, options=None):
         opt.block_elems = int(options.get("block_elems", 0))
         opt.threads = int(options.get("threads", 0))
         opt.formulation = int(options.get("formulation", 0))
-        opt.reserved[0] = int(options.get("weights_l2", 0))
     if opt is None:
         st = _lib.fem_mesh_create(_pd(xyz), xyz.shape[0], _pi(tets), tets.shape[0], _pi(mat_id),
                                   prec, reorder, ctypes.byref(h))
@@ -454,7 +453,7 @@ class Mesh:
 
     def __init__(self, prob, precision="fp64", reorder=1, variant="block", block_elems=0,
                  threads=0, faces=True, dirichlet=True, set_temperature=True,
-                 formulation="enthalpy", allocator=None, weights_l2=0):
+                 formulation="enthalpy", allocator=None):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         form = FORMULATIONS[formulation] if isinstance(formulation, str) else int(formulation)
@@ -463,7 +462,7 @@ class Mesh:
         self._inflight = []   # host buffers of asynchronous calls, until sync()
         self.h = fem_mesh_create(prob.xyz, prob.tets, prob.mat, prec, reorder,
                                  {"variant": var, "block_elems": block_elems, "threads": threads,
-                                  "formulation": form, "weights_l2": weights_l2})
+                                  "formulation": form})
         self._alloc_cbs = None
         try:
             if allocator == "torch":   # device memory from PyTorch's caching allocator
