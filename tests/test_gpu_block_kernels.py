@@ -37,7 +37,10 @@ def test_l2_and_staged_conductances_agree(fem, prec, be):
             out.append((m.temperature(), m.energy()))
             if threads == 0:
                 assert m.info()["threads"] == 256
-    assert np.array_equal(out[0][0], out[1][0])
-    assert out[0][1][2] == out[1][1][2]
     tol = 1e-9 if prec == "fp64" else 0.05
+    if be > 0 or prec == "fp64":   # the same partition: the same sums
+        assert np.array_equal(out[0][0], out[1][0])
+        assert out[0][1][2] == out[1][1][2]
+    else:   # FP32 defaults: 1,792-tet blocks (L2) against 2,048 (staged)
+        assert np.abs(out[0][0] - out[1][0]).max() <= tol
     assert np.abs(out[0][0] - o.temperature()).max() <= tol
