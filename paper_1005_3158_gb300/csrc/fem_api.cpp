@@ -1080,7 +1080,7 @@ constexpr int64_t kGraphSteps = 32;   // steps per captured graph
 template <typename real>
 fem_status ensure_step_graph(fem_mesh *m, double dt)
 {
-    const char *skip = std::getenv("FEM_FAULT_SKIP_WEIGHTS");
+    const char *skip = std::getenv("FEM_FAULT_SKIP_WEIGHT_COPY");
     const int fault = (skip && *skip && *skip != '0') ? 1 : 0;
     if (m->step_graph && m->step_graph_dt == dt && m->step_graph_fault == fault) return FEM_OK;
     if (m->step_graph) cudaGraphExecDestroy(m->step_graph);

@@ -409,8 +409,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
         mbar_arrive_expect_tx(bar_s, bytes);
         bulk_load(smem_addr(chunk), a.sched + (size_t)b * a.chunk_words, bytes, bar_s);
         const uint32_t wbytes = (uint32_t)(6 * (size_t)nes * sizeof(real));
-        if (WG) {   // bar_w completes at once; the rows go to L2 only
-            mbar_arrive_expect_tx(bar_w, 0u);
+        if (WG) {   // bar_w completes at once (the fault hook leaves it
+                    // waiting for bytes that never come); rows go to L2 only
+            mbar_arrive_expect_tx(bar_w, a.fault_skip_weights ? wbytes : 0u);
             bulk_prefetch_l2(a.w + 6 * (size_t)b * nes, wbytes);
         } else {
             mbar_arrive_expect_tx(bar_w, wbytes);

@@ -129,11 +129,14 @@ def test_bounded_wait_gives_up(fem, monkeypatch):
     o = oracle.OracleProblem(p)
     dt = 0.9 * o.stable_dt()
     monkeypatch.setenv("FEM_FAULT_SKIP_WEIGHT_COPY", "1")
-    with fem.Mesh(p, "fp32", reorder=1, block_elems=128) as m:
-        m.step(1, dt)
-        with pytest.raises(fem.FemError) as ei:
-            m.temperature()
-        assert ei.value.status == fem.FEM_ETIMEOUT
+    # both forms of the block kernel: conductances from L2 (default) and
+    # staged in shared memory (512 threads)
+    for threads, n in ((0, 1), (512, 1)):
+        with fem.Mesh(p, "fp32", reorder=1, block_elems=128, threads=threads) as m:
+            m.step(n, dt)
+            with pytest.raises(fem.FemError) as ei:
+                m.temperature()
+            assert ei.value.status == fem.FEM_ETIMEOUT
     monkeypatch.delenv("FEM_FAULT_SKIP_WEIGHT_COPY")
     with fem.Mesh(p, "fp32", reorder=1, block_elems=128) as m:
         m.step(10, dt)
