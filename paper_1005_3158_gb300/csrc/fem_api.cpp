@@ -272,6 +272,27 @@ bool weights_from_l2(const fem_mesh *m)
     return is_block(m) && !m->has_kt && !is_lm(m) && (m->opt.threads == 0 || m->opt.threads == 256);
 }
 
+// Dynamic shared memory of a block-kernel CTA for plan bp (largest block;
+// wg: without the conductance rows).
+size_t block_smem_of(const BlockPlan &bp, size_t real_size, bool wg)
+{
+    size_t cw = 0, slots = 0;
+    for (const BlockInfo &b : bp.blocks) {
+        cw = std::max(cw, (size_t)chunk_words(b));
+        slots = std::max(slots, block_slots(b));
+    }
+    const size_t nes = bp.blocks.empty() ? 8 : (size_t)bp.blocks[0].nep;
+    const size_t ls = (bp.max_nloc + 31) / 32 * 32;
+    // the slot area also receives the (C, Lc) pairs of the ls local nodes
+    slots = (std::max(slots, 2 * ls) + 3) & ~size_t(3);
+    return block_kernel_smem(nes, cw, slots, ls, real_size) - (wg ? align16(6 * nes * real_size) : 0);
+}
+
+// Four CTAs of the L2-conductance kernel share a GB300 SM (233,472 bytes)
+// when each needs at most this much dynamic shared memory (1 KB per CTA is
+// reserved, 64 bytes are static).
+constexpr size_t kFourCtaSmem = 57216;
+
 int default_block_elems(const fem_mesh *m)
 {
     int be = m->opt.block_elems;
@@ -346,10 +367,18 @@ fem_status ensure_plan(fem_mesh *m)
     std::string err;
     try {
         if (is_block(m)) {
-            err = build_block_plan(m->N, m->E, m->xyz.data(), m->tets.data(), m->rank, m->F,
-                                   m->faces.data(), owner, default_block_elems(m),
-                                   m->prec == FEM_FP32 ? 4 : 8, m->bp, m->inst_elem,
-                                   m->inst_plan_order);
+            // automatic size with L2 conductances: the largest block has to
+            // leave room for four CTAs per SM, else the size shrinks
+            const size_t rs = m->prec == FEM_FP32 ? 4 : 8;
+            const bool fit = m->opt.block_elems <= 0 && weights_from_l2(m);
+            for (int be = default_block_elems(m);; be -= 64) {
+                m->bp = BlockPlan();
+                err = build_block_plan(m->N, m->E, m->xyz.data(), m->tets.data(), m->rank, m->F,
+                                       m->faces.data(), owner, be, (int)rs, m->bp, m->inst_elem,
+                                       m->inst_plan_order);
+                if (!err.empty() || !fit || be <= 1024 || block_smem_of(m->bp, rs, true) <= kFourCtaSmem)
+                    break;
+            }
             if (err.empty()) {
                 m->blocks_flat.resize(m->bp.blocks.size() * 16);
                 std::memcpy(m->blocks_flat.data(), m->bp.blocks.data(),
@@ -708,8 +737,7 @@ fem_status upload_block(fem_mesh *m)
         m->threads = 128;
         while (m->threads < 1024 && m->threads * vn < max_nep) m->threads *= 2;
     }
-    m->smem_bytes = block_kernel_smem((size_t)m->nes, cw, slots, (size_t)m->ls, sizeof(real)) -
-                    (m->wg ? align16(6 * (size_t)m->nes * sizeof(real)) : 0);
+    m->smem_bytes = block_smem_of(bp, sizeof(real), m->wg);
     if (m->ls > kMaxLocalNodes)
         return fail(FEM_EINVAL, "a block has %zu local nodes (> %d); lower block_elems", bp.max_nloc,
                     kMaxLocalNodes);
