@@ -105,12 +105,22 @@ typedef struct {
  * zero fields take the defaults. */
 typedef struct {
     int32_t variant;     /* fem_variant, default FEM_VARIANT_BLOCK */
-    int32_t block_elems; /* target elements per shared-memory block, 0 = auto
-                            (2048 for FP32, 1024 for FP64); clamped to
-                            [64, 12288] */
-    int32_t threads;     /* threads per CTA of the block kernel, 0 = auto (the
-                            fewest threads whose 16-byte element accesses
-                            cover the largest block); 128, 256, 512 or 1024 */
+    int32_t block_elems; /* target elements per shared-memory block, 0 = auto;
+                            clamped to [64, 12288].  Auto: 1024 for FP64;
+                            for FP32 1792 when the block kernel reads the
+                            conductances from L2 (below), else 2048.  With
+                            L2 conductances the automatic size shrinks in
+                            64-element steps (not below 1024) until the
+                            largest block leaves room for four CTAs per SM. */
+    int32_t threads;     /* threads per CTA of the block kernel: 0 = auto,
+                            or 128, 256, 512 or 1024.  With constant k and
+                            the enthalpy formulation, 0 or 256 selects the
+                            kernel that reads the six conductances of each
+                            element from L2 (bulk-prefetched) instead of
+                            staging them in shared memory, at 256 threads.
+                            Otherwise auto is the fewest threads whose
+                            16-byte element accesses cover the largest
+                            block. */
     int32_t formulation; /* fem_formulation, default FEM_ENTHALPY */
     int32_t reserved[4];
 } fem_options;
