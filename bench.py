@@ -529,30 +529,37 @@ def main():
     # end to end through the C ABI with pinned host buffers: every step
     # uploads the state, steps once and reads the temperatures back.  The
     # headline uses the pipelined calls (each step's copies overlap the
-    # neighbouring steps); the serial loop through the synchronous calls is
-    # reported beside it.
+    # neighbouring steps) with host arrays in the mesh's own precision;
+    # the pipelined loop with FP64 arrays and the serial loop through the
+    # synchronous (FP64) calls are reported beside it.
     e2e = None
     if not args.no_e2e:
         ke = args.e2e_steps or args.steps
-        E_host = torch.empty(N, dtype=torch.float64, pin_memory=True)
-        T_host = [torch.empty(N, dtype=torch.float64, pin_memory=True) for _ in range(2)]
-        mesh.state(E_host.numpy())
+        io_dt = torch.float32 if args.precision == "fp32" else torch.float64
+        E64 = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        mesh.state(E64.numpy())
+        E_io = E64.to(io_dt).pin_memory()
+        T64 = [torch.empty(N, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        T_io = [torch.empty(N, dtype=io_dt, pin_memory=True) for _ in range(2)]
 
         def serial(n):
             for _ in range(n):
-                mesh.set_state(E_host, 0, 0.0)
+                mesh.set_state(E64, 0, 0.0)
                 mesh.step(1, dt)
-                mesh.temperature(T_host[0])
+                mesh.temperature(T64[0])
 
-        def pipelined(n):
-            for k in range(n):
-                mesh.set_state_async(E_host, 0, 0.0)
-                mesh.step(1, dt)
-                mesh.temperature_async(T_host[k % 2])
-            mesh.sync()
+        def pipelined(E_h, T_h):
+            def run(n):
+                for k in range(n):
+                    mesh.set_state_async(E_h, 0, 0.0)
+                    mesh.step(1, dt)
+                    mesh.temperature_async(T_h[k % 2])
+                mesh.sync()
+            return run
 
         rates = {}
-        for name, loop in (("serial", serial), ("pipelined", pipelined)):
+        for name, loop in (("serial", serial), ("pipelined_f64", pipelined(E64, T64)),
+                           ("pipelined", pipelined(E_io, T_io))):
             loop(3)
             if world > 1:
                 dist.barrier()
@@ -560,10 +567,12 @@ def main():
             loop(ke)
             el = max_over_ranks(time.perf_counter() - t0, world, "cuda")
             rates[name] = job_throughput(E, ke, world, el)
+        isz = E_io.element_size()
         e2e = {"value": rates["pipelined"], "unit": "tet-updates/s",
-               "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "steps": ke,
-               "api": "fem_set_state_async + fem_step + fem_get_temperature_async, fem_sync at the end",
-               "serial_value": rates["serial"]}
+               "h2d_bytes_per_step": N * isz, "d2h_bytes_per_step": N * isz, "steps": ke,
+               "api": f"fem_set_state_async{'_f32' if isz == 4 else ''} + fem_step + "
+                      f"fem_get_temperature_async{'_f32' if isz == 4 else ''}, fem_sync at the end",
+               "pipelined_f64_value": rates["pipelined_f64"], "serial_value": rates["serial"]}
 
     cpu = thr = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

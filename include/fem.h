@@ -341,6 +341,13 @@ fem_status fem_set_state_async(fem_mesh *m, const double *E, int64_t step, doubl
 fem_status fem_get_temperature_async(fem_mesh *m, double *T_out);
 fem_status fem_sync(fem_mesh *m);
 
+/* The same two calls with FP32 host arrays (E [n_nodes] in J, T_out
+ * [n_nodes] in K): half the bytes over the host link.  An FP32 mesh holds
+ * E and computes T in FP32, so they lose nothing there.  An FP64 mesh
+ * converts. */
+fem_status fem_set_state_async_f32(fem_mesh *m, const float *E, int64_t step, double t);
+fem_status fem_get_temperature_async_f32(fem_mesh *m, float *T_out);
+
 /* Plan statistics (host computation; builds the plan if needed). */
 fem_status fem_mesh_info(fem_mesh *m, fem_info *out);
 

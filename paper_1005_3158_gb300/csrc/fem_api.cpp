@@ -1824,7 +1824,14 @@ fem_status fem_autotune(fem_mesh *m, const int32_t *block_elems, const int32_t *
     return ok();
 }
 
-fem_status fem_set_state_async(fem_mesh *m, const double *E, int64_t step, double t)
+}  // extern "C"
+
+namespace {
+
+// Pipelined host I/O with the caller's arrays of element type io (double,
+// or float for the _f32 calls); see fem.h.
+template <typename io>
+fem_status set_state_async_impl(fem_mesh *m, const io *E, int64_t step, double t)
 {
     if (!m || !E) return fail(FEM_EINVAL, "NULL argument");
     if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
@@ -1834,13 +1841,21 @@ fem_status fem_set_state_async(fem_mesh *m, const double *E, int64_t step, doubl
     const int i = m->in_idx;
     // the copy into staging buffer i waits for the last kernel that read it
     CU(cudaStreamWaitEvent(m->up_stream, m->ev_in_free[i], 0));
-    CU(cudaMemcpyAsync(m->dIn[i], E, (size_t)m->N * sizeof(double), cudaMemcpyHostToDevice, m->up_stream));
+    CU(cudaMemcpyAsync(m->dIn[i], E, (size_t)m->N * sizeof(io), cudaMemcpyHostToDevice, m->up_stream));
     CU(cudaEventRecord(m->ev_in_ready[i], m->up_stream));
     CU(cudaStreamWaitEvent(m->stream, m->ev_in_ready[i], 0));
-    KERNEL(m->prec == FEM_FP32
-               ? launch_set_state<float>(view_of<float>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream)
-               : launch_set_state<double>(view_of<double>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream),
-           "state kernel");
+    if (sizeof(io) == 4) {
+        const float *src = reinterpret_cast<const float *>(m->dIn[i]);
+        KERNEL(m->prec == FEM_FP32
+                   ? launch_set_state_f32<float>(view_of<float>(m), src, m->dNodeOld, m->N, m->dErr, m->stream)
+                   : launch_set_state_f32<double>(view_of<double>(m), src, m->dNodeOld, m->N, m->dErr, m->stream),
+               "state kernel");
+    } else {
+        KERNEL(m->prec == FEM_FP32
+                   ? launch_set_state<float>(view_of<float>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream)
+                   : launch_set_state<double>(view_of<double>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream),
+               "state kernel");
+    }
     KERNEL(m->prec == FEM_FP32 ? refresh_mirror<float>(m) : refresh_mirror<double>(m), "mirror kernel");
     CU(cudaEventRecord(m->ev_in_free[i], m->stream));
     m->in_idx = 1 - i;
@@ -1849,7 +1864,8 @@ fem_status fem_set_state_async(fem_mesh *m, const double *E, int64_t step, doubl
     return ok();
 }
 
-fem_status fem_get_temperature_async(fem_mesh *m, double *T_out)
+template <typename io>
+fem_status get_temperature_async_impl(fem_mesh *m, io *T_out)
 {
     if (!m || !T_out) return fail(FEM_EINVAL, "NULL argument");
     fem_status st = ready_for_io(m);
@@ -1858,23 +1874,57 @@ fem_status fem_get_temperature_async(fem_mesh *m, double *T_out)
     const int j = m->out_idx;
     // staging buffer j is rewritten once its previous copy to the host is done
     CU(cudaStreamWaitEvent(m->stream, m->ev_out_free[j], 0));
-    KERNEL(m->prec == FEM_FP32
-               ? launch_get_temperature<float>(view_of<float>(m), (const float *)m->dC,
-                                               (const float *)m->dLc, m->dPh,
-                                               (const float *)m->dRanges, m->dOutT[j], m->dNodeOld,
-                                               m->N, m->dErr, m->stream)
-               : launch_get_temperature<double>(view_of<double>(m), (const double *)m->dC,
-                                                (const double *)m->dLc, m->dPh,
-                                                (const double *)m->dRanges, m->dOutT[j],
-                                                m->dNodeOld, m->N, m->dErr, m->stream),
-           "read-back kernel");
+    if (sizeof(io) == 4) {
+        float *dst = reinterpret_cast<float *>(m->dOutT[j]);
+        KERNEL(m->prec == FEM_FP32
+                   ? launch_get_temperature_f32<float>(view_of<float>(m), (const float *)m->dRanges, dst,
+                                                       m->dNodeOld, m->N, m->dErr, m->stream)
+                   : launch_get_temperature_f32<double>(view_of<double>(m), (const double *)m->dRanges, dst,
+                                                        m->dNodeOld, m->N, m->dErr, m->stream),
+               "read-back kernel");
+    } else {
+        KERNEL(m->prec == FEM_FP32
+                   ? launch_get_temperature<float>(view_of<float>(m), (const float *)m->dC,
+                                                   (const float *)m->dLc, m->dPh,
+                                                   (const float *)m->dRanges, m->dOutT[j], m->dNodeOld,
+                                                   m->N, m->dErr, m->stream)
+                   : launch_get_temperature<double>(view_of<double>(m), (const double *)m->dC,
+                                                    (const double *)m->dLc, m->dPh,
+                                                    (const double *)m->dRanges, m->dOutT[j],
+                                                    m->dNodeOld, m->N, m->dErr, m->stream),
+               "read-back kernel");
+    }
     CU(cudaEventRecord(m->ev_out_ready[j], m->stream));
     CU(cudaStreamWaitEvent(m->down_stream, m->ev_out_ready[j], 0));
-    CU(cudaMemcpyAsync(T_out, m->dOutT[j], (size_t)m->N * sizeof(double), cudaMemcpyDeviceToHost,
+    CU(cudaMemcpyAsync(T_out, m->dOutT[j], (size_t)m->N * sizeof(io), cudaMemcpyDeviceToHost,
                        m->down_stream));
     CU(cudaEventRecord(m->ev_out_free[j], m->down_stream));
     m->out_idx = 1 - j;
     return ok();
+}
+
+}  // namespace
+
+extern "C" {
+
+fem_status fem_set_state_async(fem_mesh *m, const double *E, int64_t step, double t)
+{
+    return set_state_async_impl<double>(m, E, step, t);
+}
+
+fem_status fem_set_state_async_f32(fem_mesh *m, const float *E, int64_t step, double t)
+{
+    return set_state_async_impl<float>(m, E, step, t);
+}
+
+fem_status fem_get_temperature_async(fem_mesh *m, double *T_out)
+{
+    return get_temperature_async_impl<double>(m, T_out);
+}
+
+fem_status fem_get_temperature_async_f32(fem_mesh *m, float *T_out)
+{
+    return get_temperature_async_impl<float>(m, T_out);
 }
 
 fem_status fem_sync(fem_mesh *m)

@@ -252,6 +252,14 @@ template <typename real>
 int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
                            int *err, void *stream);
+// The same with the caller's arrays in FP32 (fem_set_state_async_f32,
+// fem_get_temperature_async_f32).
+template <typename real>
+int launch_set_state_f32(StateView<real> v, const float *E_in, const int32_t *node_old, int64_t n,
+                         int *err, void *stream);
+template <typename real>
+int launch_get_temperature_f32(StateView<real> v, const real *ranges, float *T_out,
+                               const int32_t *node_old, int64_t n, int *err, void *stream);
 template <typename real>
 int launch_get_state(StateView<real> v, double *E_out, const int32_t *node_old, int64_t n,
                      void *stream);

@@ -788,23 +788,25 @@ __global__ void k_set_temperature(StateView<real> v, const real *C, const real *
     }
 }
 
-template <typename real>
-__global__ void k_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
+// io: the element type of the caller's array (double, or float for the
+// FP32 host I/O of fem_set_state_async_f32 / fem_get_temperature_async_f32)
+template <typename real, typename io = double>
+__global__ void k_set_state(StateView<real> v, const io *E_in, const int32_t *node_old, int64_t n,
                             int *err)
 {
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double E = E_in[node_old[i]];
+        const double E = (double)E_in[node_old[i]];
         bad |= !isfinite(E);
         state_set_E(v, i, (real)E);
     }
     if (bad && err) atomicOr(err, kErrBadInput);
 }
 
-template <typename real>
+template <typename real, typename io = double>
 __global__ void k_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
-                                  const real *ranges, double *T_out, const int32_t *node_old,
+                                  const real *ranges, io *T_out, const int32_t *node_old,
                                   int64_t n, int *err)
 {
     bool bad = false;
@@ -812,7 +814,7 @@ __global__ void k_get_temperature(StateView<real> v, const real *C, const real *
          i += (int64_t)gridDim.x * blockDim.x) {
         const double T = (double)state_T(v, i);
         bad |= !isfinite(T);
-        T_out[node_old[i]] = T;
+        T_out[node_old[i]] = (io)T;
     }
     if (bad && err) atomicOr(err, kErrNonFinite);
 }
@@ -1035,6 +1037,23 @@ int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, con
 }
 
 template <typename real>
+int launch_set_state_f32(StateView<real> v, const float *E_in, const int32_t *node_old, int64_t n,
+                         int *err, void *stream)
+{
+    k_set_state<real, float><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n, err);
+    return (int)cudaGetLastError();
+}
+
+template <typename real>
+int launch_get_temperature_f32(StateView<real> v, const real *ranges, float *T_out,
+                               const int32_t *node_old, int64_t n, int *err, void *stream)
+{
+    k_get_temperature<real, float><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
+        v, nullptr, nullptr, nullptr, ranges, T_out, node_old, n, err);
+    return (int)cudaGetLastError();
+}
+
+template <typename real>
 int launch_get_state(StateView<real> v, double *E_out, const int32_t *node_old, int64_t n,
                      void *stream)
 {
@@ -1080,6 +1099,10 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
     template int launch_get_temperature<real>(StateView<real>, const real *, const real *,        \
                                               const uint8_t *, const real *, double *,            \
                                               const int32_t *, int64_t, int *, void *);           \
+    template int launch_set_state_f32<real>(StateView<real>, const float *, const int32_t *, int64_t, \
+                                            int *, void *);                                           \
+    template int launch_get_temperature_f32<real>(StateView<real>, const real *, float *,             \
+                                                  const int32_t *, int64_t, int *, void *);            \
     template int launch_get_state<real>(StateView<real>, double *, const int32_t *, int64_t,      \
                                         void *);                                                  \
     template int launch_energy_snapshot<real>(StateView<real>, const real *, const real *,        \

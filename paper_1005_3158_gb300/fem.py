@@ -39,7 +39,8 @@ ABI_SYMBOLS = (
     "fem_last_error", "fem_mesh_destroy", "fem_energy_sums_noalloc", "fem_batch_create",
     "fem_instance_stable_dt", "fem_set_instance_dt", "fem_advance", "fem_get_instance_times",
     "fem_get_instance_energy", "fem_set_allocator", "fem_autotune", "fem_set_state_async",
-    "fem_get_temperature_async", "fem_sync",
+    "fem_get_temperature_async", "fem_sync", "fem_set_state_async_f32",
+    "fem_get_temperature_async_f32",
 )
 
 
@@ -118,6 +119,8 @@ def _load():
         "fem_autotune": [P, ip, ip, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ip, dp],
         "fem_set_state_async": [P, P, i64, ctypes.c_double],
         "fem_get_temperature_async": [P, P],
+        "fem_set_state_async_f32": [P, P, i64, ctypes.c_double],
+        "fem_get_temperature_async_f32": [P, P],
         "fem_sync": [P],
     }
     for name, args in sig.items():
@@ -159,21 +162,26 @@ def _pi(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
 
-def _host_ptr(buf, n, writable):
-    """Pointer to a host buffer of n doubles: a numpy array or a (pinned)
-    torch CPU tensor.  Returns (pointer, keep-alive)."""
+def _host_ptr(buf, n, writable, f32=False):
+    """Pointer to a host buffer of n doubles (n floats with f32): a numpy
+    array or a (pinned) torch CPU tensor.  Returns (pointer, keep-alive)."""
+    want = "float32" if f32 else "float64"
     if isinstance(buf, np.ndarray):
-        if buf.dtype != np.float64 or not buf.flags["C_CONTIGUOUS"] or buf.size < n:
-            raise ValueError("host buffer must be a C-contiguous float64 array of size >= n_nodes")
+        if buf.dtype != np.dtype(want) or not buf.flags["C_CONTIGUOUS"] or buf.size < n:
+            raise ValueError(f"host buffer must be a C-contiguous {want} array of size >= n_nodes")
         if writable and not buf.flags["WRITEABLE"]:
             raise ValueError("output buffer is read-only")
         return ctypes.c_void_p(buf.ctypes.data), buf
     # torch tensor (duck-typed so the binding does not import torch)
     if getattr(buf, "device", None) is not None and str(buf.device) != "cpu":
         raise ValueError("host buffer expected (got a device tensor)")
-    if str(buf.dtype) != "torch.float64" or not buf.is_contiguous() or buf.numel() < n:
-        raise ValueError("host tensor must be contiguous float64 of size >= n_nodes")
+    if str(buf.dtype) != "torch." + want or not buf.is_contiguous() or buf.numel() < n:
+        raise ValueError(f"host tensor must be contiguous {want} of size >= n_nodes")
     return ctypes.c_void_p(buf.data_ptr()), buf
+
+
+def _is_f32(buf):
+    return str(getattr(buf, "dtype", "")) in ("float32", "torch.float32")
 
 
 # ---------------------------------------------------------------------------
@@ -311,18 +319,23 @@ def fem_set_state(h, n_nodes, E, step=0, t=0.0):
 
 
 def fem_set_state_async(h, n_nodes, E, step=0, t=0.0):
-    """Enqueue a state upload (see fem.h); E must stay alive and unchanged
-    until fem_sync.  Returns the buffer to keep alive."""
-    p, keep = _host_ptr(E, n_nodes, False)
-    _check(_lib.fem_set_state_async(h, p, int(step), float(t)))
+    """Enqueue a state upload (see fem.h); E (float64, or float32 for the
+    _f32 call) must stay alive and unchanged until fem_sync.  Returns the
+    buffer to keep alive."""
+    f32 = _is_f32(E)
+    p, keep = _host_ptr(E, n_nodes, False, f32)
+    fn = _lib.fem_set_state_async_f32 if f32 else _lib.fem_set_state_async
+    _check(fn(h, p, int(step), float(t)))
     return keep
 
 
 def fem_get_temperature_async(h, n_nodes, out):
-    """Enqueue T(E) and its copy into `out` (valid after fem_sync).
-    Returns the buffer to keep alive."""
-    p, keep = _host_ptr(out, n_nodes, True)
-    _check(_lib.fem_get_temperature_async(h, p))
+    """Enqueue T(E) and its copy into `out` (float64, or float32 for the
+    _f32 call; valid after fem_sync).  Returns the buffer to keep alive."""
+    f32 = _is_f32(out)
+    p, keep = _host_ptr(out, n_nodes, True, f32)
+    fn = _lib.fem_get_temperature_async_f32 if f32 else _lib.fem_get_temperature_async
+    _check(fn(h, p))
     return keep
 
 

@@ -86,3 +86,26 @@ def test_async_non_finite_state_reported_by_sync(env):
         with pytest.raises(fem.FemError) as e:
             m.sync()
         assert e.value.status == fem.FEM_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_async_f32_host_arrays(env, prec):
+    """FP32 host arrays: the upload converts to the mesh's precision and
+    the read-back rounds T to FP32 -- the same numbers as the FP64 calls
+    (exactly the same for an FP32 mesh, whose E and T are FP32 anyway)."""
+    fem, torch = env
+    p = mg.random_small(52, nx=9, ny=8, nz=7, n_mat=3)
+    with fem.Mesh(p, prec) as m:
+        dt = 0.9 * m.stable_dt()
+        m.step(5, dt)
+        E32 = m.state()[0].astype(np.float32)
+        m.set_state(E32.astype(np.float64), 0, 0.0)
+        m.step(3, dt)
+        T_ref = m.temperature()
+        E_h = torch.from_numpy(E32).pin_memory()
+        T_h = torch.empty(m.n_nodes, dtype=torch.float32).pin_memory()
+        m.set_state_async(E_h, 0, 0.0)
+        m.step(3, dt)
+        m.temperature_async(T_h)
+        m.sync()
+        assert np.array_equal(T_h.numpy(), T_ref.astype(np.float32))

@@ -42,6 +42,8 @@ def test_async_io_argument_checks():
     with fem.Mesh(p, "fp32", set_temperature=False) as m:
         assert fem.lib().fem_set_state_async(m.h, None, 0, 0.0) == fem.FEM_EINVAL
         assert fem.lib().fem_get_temperature_async(m.h, None) == fem.FEM_EINVAL
+        assert fem.lib().fem_set_state_async_f32(m.h, None, 0, 0.0) == fem.FEM_EINVAL
+        assert fem.lib().fem_get_temperature_async_f32(m.h, None) == fem.FEM_EINVAL
         buf = np.zeros(m.n_nodes)
         st = fem.lib().fem_get_temperature_async(m.h, ctypes.c_void_p(buf.ctypes.data))
         assert st == fem.FEM_ESTATE
