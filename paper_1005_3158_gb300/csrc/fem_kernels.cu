@@ -790,16 +790,32 @@ __global__ void k_set_temperature(StateView<real> v, const real *C, const real *
 
 // io: the element type of the caller's array (double, or float for the
 // FP32 host I/O of fem_set_state_async_f32 / fem_get_temperature_async_f32)
+// The permuting I/O loops take kIoBatch nodes per thread per round, all
+// loads first: their index -> value -> store chains then overlap instead of
+// running one after another.
+constexpr int kIoBatch = 4;
+
 template <typename real, typename io = double>
 __global__ void k_set_state(StateView<real> v, const io *E_in, const int32_t *node_old, int64_t n,
                             int *err)
 {
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double E = (double)E_in[node_old[i]];
-        bad |= !isfinite(E);
-        state_set_E(v, i, (real)E);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kIoBatch * stride) {
+        double E[kIoBatch];
+#pragma unroll
+        for (int u = 0; u < kIoBatch; u++) {
+            const int64_t i = i0 + u * stride;
+            E[u] = i < n ? (double)E_in[node_old[i]] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kIoBatch; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                bad |= !isfinite(E[u]);
+                state_set_E(v, i, (real)E[u]);
+            }
+        }
     }
     if (bad && err) atomicOr(err, kErrBadInput);
 }
@@ -810,11 +826,22 @@ __global__ void k_get_temperature(StateView<real> v, const real *C, const real *
                                   int64_t n, int *err)
 {
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double T = (double)state_T(v, i);
-        bad |= !isfinite(T);
-        T_out[node_old[i]] = (io)T;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kIoBatch * stride) {
+        double T[kIoBatch];
+#pragma unroll
+        for (int u = 0; u < kIoBatch; u++) {
+            const int64_t i = i0 + u * stride;
+            T[u] = i < n ? (double)state_T(v, i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kIoBatch; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                bad |= !isfinite(T[u]);
+                T_out[node_old[i]] = (io)T[u];
+            }
+        }
     }
     if (bad && err) atomicOr(err, kErrNonFinite);
 }
