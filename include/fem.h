@@ -400,7 +400,10 @@ fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t
  *   E, C, Lc, phase   DEVICE arrays [n_nodes]: enthalpy content (J),
  *           sensible capacity (J/K), latent capacity (J), and a phase byte
  *           whose low 7 bits index the (Ts, Tl) pair of the node's
- *           phase-change range (ignored where Lc == 0).
+ *           phase-change range (ignored where Lc == 0; the high bit is
+ *           ignored).  The call takes no count of pairs: wherever Lc > 0,
+ *           (phase & 0x7F) must be below the number of pairs in ranges, or
+ *           the kernel reads past the caller's array.
  *   ranges  DEVICE array [n_ranges][2] of (Ts, Tl).
  *   out     DEVICE array of 2 doubles: out[0] = sum_i E_i,
  *           out[1] = sum_i (E_i - C_i T(E_i)), the latent heat still held,
@@ -412,9 +415,11 @@ fem_status fem_plan_array(fem_mesh *m, int32_t which, const void **data, int64_t
  * All calls share it, so calls whose kernels overlap on the GPU (for
  * example on two streams at once) race and give wrong sums; serialise them.
  * Each call overwrites every scratch entry it reads, so no clearing is
- * needed.  The first call on each device looks up the scratch's device
- * address (cudaGetSymbolAddress, no allocation) with that device current;
- * make that first call before any stream capture.
+ * needed.  Every call looks up the scratch's device address
+ * (cudaGetSymbolAddress, no allocation) with the caller's device current,
+ * so a context reset between calls is harmless.  The first call on a device
+ * may load the library's device code there: make it before any stream
+ * capture.
  * Errors: FEM_EINVAL for a NULL pointer, an unknown precision, or n_nodes
  * outside [1, 134217728] (the scratch holds one partial per 8192 nodes);
  * FEM_ECUDA if no device is current or the launch fails. */

@@ -9,9 +9,9 @@
 
 #include <cstdint>
 #include <cstdio>
-#include <mutex>
 
 #include "fem.h"
+#include "fem_device.cuh"
 #include "fem_internal.h"
 
 namespace {
@@ -24,25 +24,6 @@ constexpr int64_t kMaxNodes = kNodesPerCta * kMaxCtas;  // 134,217,728 nodes
 // Scratch: one (sum E, latent) pair per CTA.  Every GPU that loads the
 // library holds these 256 KiB until the process exits.  All calls share it.
 static __device__ __align__(256) double g_noalloc_partials[2 * kMaxCtas];
-
-template <typename real>
-__device__ __forceinline__ double node_latent(real E, real C, real Lc, uint8_t ph,
-                                              const real *__restrict__ ranges)
-{
-    // latent heat still held by the node: E - C T(E), T the inverse of the
-    // piecewise-linear enthalpy E(T) = C T + Lc f_l(T) between Ts and Tl
-    if (!(Lc > real(0))) return 0.0;
-    const int r = ph & 0x7F;
-    const real Ts = ranges[2 * r], Tl = ranges[2 * r + 1];
-    real T;
-    const real E_sol = C * Ts, E_liq = C * Tl + Lc;
-    if (E <= E_sol) T = E / C;
-    else if (E >= E_liq) T = (E - Lc) / C;
-    else if (Tl <= Ts) T = Ts;
-    else T = Ts + (E - E_sol) / (C + Lc / (Tl - Ts));
-    double l = (double)E - (double)C * (double)T;
-    return l < 0.0 ? 0.0 : (l > (double)Lc ? (double)Lc : l);
-}
 
 __device__ __forceinline__ double warp_total(double v)
 {
@@ -65,7 +46,7 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_partials(
     double u = 0.0, lat = 0.0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
         u += (double)E[i];
-        lat += node_latent(E[i], C[i], Lc[i], ph[i], ranges);
+        lat += fem::latent_of(E[i], C[i], Lc[i], ph[i], ranges);
     }
     u = warp_total(u);
     lat = warp_total(lat);
@@ -103,12 +84,6 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_final(const double *__rest
     }
 }
 
-// Device address of the scratch array, looked up once per device (with that
-// device current) by the first call made on it.
-constexpr int kMaxDevices = 64;
-std::mutex g_lock;
-double *g_scratch[kMaxDevices] = {};
-
 fem_status fail(fem_status st, const char *msg)
 {
     fem::set_last_error(msg);
@@ -132,27 +107,19 @@ extern "C" fem_status fem_energy_sums_noalloc(fem_precision prec, const void *E,
                  (long long)n_nodes, (long long)kMaxNodes);
         return fail(FEM_EINVAL, msg);
     }
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        snprintf(msg, sizeof msg, "no usable current CUDA device (%s)", cudaGetErrorString(e));
+    // The scratch's device address is looked up on every call, with the
+    // caller's device current: it belongs to the current context's copy of
+    // the module, which a context reset (cudaDeviceReset) replaces, so an
+    // address kept from an earlier call could be stale.  The lookup
+    // allocates nothing.
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p) {
+        snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the static scratch failed: %s",
+                 cudaGetErrorString(e));
         return fail(FEM_ECUDA, msg);
     }
-    double *scratch;
-    {
-        std::lock_guard<std::mutex> guard(g_lock);
-        if (!g_scratch[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-            if (e != cudaSuccess || !p) {
-                snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the scratch failed: %s",
-                         cudaGetErrorString(e));
-                return fail(FEM_ECUDA, msg);
-            }
-            g_scratch[dev] = (double *)p;
-        }
-        scratch = g_scratch[dev];
-    }
+    double *scratch = (double *)p;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int64_t n_ctas = (n_nodes + kNodesPerCta - 1) / kNodesPerCta;
     if (prec == FEM_FP32)

@@ -3,11 +3,18 @@
 Callers that cannot call cudaMalloc (code running during CUDA-graph
 capture, real-time loops with a no-allocation rule, processes whose device
 memory belongs to another allocator) hand the library device arrays they
-already own; the entry point keeps its per-CTA partial sums in a static
-device array inside the library.  Here its sums of a stepped state are
-checked, on two calls in a row, against the energy account that the mesh
-API (fem_get_energy) reports for the same state, with the tolerances of the
-other energy tests (FP64 1e-12 relative, FP32 1e-6 relative).
+already own; the entry point keeps its per-CTA partial sums (one pair per
+8192 nodes) in a static device array inside the library.  Its sums are
+checked, on two calls in a row, against
+
+* the energy account of the mesh API (fem_get_energy) for a stepped state,
+* the FP64 oracle's energy of the same state, at sizes that take one CTA,
+  several CTAs with a ragged tail, and an exact multiple of 8192 nodes,
+* the oracle on a mesh with two phase-change ranges, where the phase byte
+  selects the range (its high bit set on some nodes, which must be ignored),
+
+with the tolerances of the other energy tests (FP64 1e-12 relative, FP32
+1e-6 relative).  The two calls must agree bit for bit.
 
 The file is named to be collected last, so a run that stops at the first
 failure has run every other test first.
@@ -21,6 +28,7 @@ from paper_1005_3158_gb300 import meshgen as mg
 pytestmark = pytest.mark.gpu
 
 REL = {"fp64": 1e-12, "fp32": 1e-6}
+NODES_PER_CTA = 8192
 
 
 @pytest.fixture(scope="module")
@@ -34,17 +42,49 @@ def env():
     return torch, fem
 
 
-def _device_state(torch, p, E, prec):
+def _phase_of(p):
+    """Per node: index of its phase-change range in the sorted range list,
+    and that list (each node touches at most one phase-change material)."""
+    ranges = sorted({(m[4], m[5]) for m in p.materials if m[3] > 0}) or [(0.0, 0.0)]
+    ph = np.zeros(p.n_nodes, np.uint8)
+    for mt, m in enumerate(p.materials):
+        if m[3] > 0:
+            ph[p.tets[p.mat == mt].ravel()] = ranges.index((m[4], m[5]))
+    return ph, ranges
+
+
+def _device_state(torch, p, E, prec, ph=None):
     """Device copies of the state and of the node data the sums need."""
     dtype = torch.float64 if prec == "fp64" else torch.float32
     C, _, Lc = oracle.OracleProblem(p).lumped()
-    ranges = sorted({(m[4], m[5]) for m in p.materials if m[3] > 0}) or [(0.0, 0.0)]
-    assert len(ranges) == 1          # the problems below have one phase-change range
+    ph0, ranges = _phase_of(p)
+    ph = ph0 if ph is None else ph
     dev = torch.device("cuda")
     return (torch.tensor(E, dtype=dtype, device=dev), torch.tensor(C, dtype=dtype, device=dev),
-            torch.tensor(Lc, dtype=dtype, device=dev),
-            torch.zeros(p.n_nodes, dtype=torch.uint8, device=dev),
+            torch.tensor(Lc, dtype=dtype, device=dev), torch.tensor(ph, device=dev),
             torch.tensor(np.array(ranges).ravel(), dtype=dtype, device=dev))
+
+
+def _sums_twice(torch, fem, prec, dev_state, n):
+    Ed, Cd, Lcd, phd, rgd = dev_state
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    code = fem.FEM_FP64 if prec == "fp64" else fem.FEM_FP32
+    results = []
+    for _ in range(2):
+        out.fill_(float("nan"))
+        fem.fem_energy_sums_noalloc(code, Ed.data_ptr(), Cd.data_ptr(), Lcd.data_ptr(),
+                                    phd.data_ptr(), rgd.data_ptr(), n, out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        results.append(out.cpu().numpy().copy())
+    assert np.array_equal(results[0], results[1])
+    return results
+
+
+def _check(results, U_ref, lat_ref, prec):
+    for U, lat in results:
+        assert U == pytest.approx(U_ref, rel=REL[prec])
+        assert lat == pytest.approx(lat_ref, rel=REL[prec], abs=1e-9 * abs(U_ref))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -57,22 +97,78 @@ def test_matches_mesh_energy_two_calls(env, prec, case):
         m.step(150, dt)
         ref = m.energy()                    # U, U0, boundary heat, latent
         E = m.state()[0]
-    Ed, Cd, Lcd, phd, rgd = _device_state(torch, p, E, prec)
-    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
-    stream = torch.cuda.current_stream().cuda_stream
-    code = fem.FEM_FP64 if prec == "fp64" else fem.FEM_FP32
-    results = []
-    for _ in range(2):
-        out.fill_(float("nan"))
-        fem.fem_energy_sums_noalloc(code, Ed.data_ptr(), Cd.data_ptr(), Lcd.data_ptr(),
-                                    phd.data_ptr(), rgd.data_ptr(), p.n_nodes, out.data_ptr(),
-                                    stream)
-        torch.cuda.synchronize()
-        results.append(out.cpu().numpy().copy())
-    for U, lat in results:
-        assert U == pytest.approx(ref[0], rel=REL[prec])
-        assert lat == pytest.approx(ref[3], rel=REL[prec], abs=1e-9 * abs(ref[0]))
-    assert np.array_equal(results[0], results[1])
+    results = _sums_twice(torch, fem, prec, _device_state(torch, p, E, prec), p.n_nodes)
+    _check(results, ref[0], ref[3], prec)
+    # the same state's energy from the oracle
+    o = oracle.OracleProblem(p)
+    o.set_enthalpy(E)
+    ref_o = o.energy()
+    _check(results, ref_o[0], ref_o[3], prec)
+
+
+def _box(nx, ny, nz):
+    """One alloy box, all faces adiabatic, seeded temperatures across the
+    solid, mushy and liquid ranges."""
+    xyz, tets, _, _ = mg.box_grid(nx, ny, nz, jitter=0.1, seed=77)
+    n = xyz.shape[0]
+    T0 = mg.rng_of(78).uniform(700.0, 1000.0, size=n)
+    return mg.Problem(xyz=xyz, tets=tets, mat=np.zeros(tets.shape[0], np.int32),
+                      materials=np.array([mg.ALLOY]), faces=np.zeros((0, 3), np.int32),
+                      h=np.zeros(0), t_inf=np.zeros(0), q=np.zeros(0), T0=T0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims", [(24, 24, 24), (15, 31, 31), (40, 40, 40)],
+                         ids=["2ctas_ragged", "2ctas_exact", "9ctas_ragged"])
+def test_multi_cta_against_oracle(env, prec, dims):
+    torch, fem = env
+    p = _box(*dims)
+    n = p.n_nodes
+    n_ctas = -(-n // NODES_PER_CTA)
+    assert n_ctas >= 2
+    if dims == (15, 31, 31):
+        assert n % NODES_PER_CTA == 0
+    else:
+        assert n % NODES_PER_CTA != 0
+    o = oracle.OracleProblem(p)
+    o.set_temperature(p.T0)
+    E = o.enthalpy()
+    ref = o.energy()
+    results = _sums_twice(torch, fem, prec, _device_state(torch, p, E, prec), n)
+    _check(results, ref[0], ref[3], prec)
+
+
+def _two_ranges():
+    """Two alloys with different (Ts, Tl) separated by a steel layer, so no
+    node touches both phase-change materials."""
+    xyz, tets, _, _ = mg.box_grid(24, 8, 8, lx=3.0, jitter=0.1, seed=79)
+    cx = mg.centroids(xyz, tets)[:, 0]
+    mat = np.where(cx < 1.0, 0, np.where(cx < 2.0, 2, 1)).astype(np.int32)
+    alloy_b = (2500.0, 1000.0, 120.0, 3.0e5, 700.0, 760.0)
+    T0 = mg.rng_of(80).uniform(650.0, 950.0, size=xyz.shape[0])
+    return mg.Problem(xyz=xyz, tets=tets, mat=mat,
+                      materials=np.array([mg.ALLOY, alloy_b, mg.STEEL]),
+                      faces=np.zeros((0, 3), np.int32), h=np.zeros(0), t_inf=np.zeros(0),
+                      q=np.zeros(0), T0=T0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_phase_byte_selects_the_range(env, prec):
+    torch, fem = env
+    p = _two_ranges()
+    ph, ranges = _phase_of(p)
+    assert len(ranges) == 2 and (ph == 1).any() and (ph == 0).any()
+    ph = ph | np.where(mg.rng_of(81).random(p.n_nodes) < 0.5, 0x80, 0).astype(np.uint8)
+    o = oracle.OracleProblem(p)
+    o.set_temperature(p.T0)
+    E = o.enthalpy()
+    ref = o.energy()
+    results = _sums_twice(torch, fem, prec, _device_state(torch, p, E, prec, ph), p.n_nodes)
+    _check(results, ref[0], ref[3], prec)
+    # the wrong range for every node of the second alloy changes the latent sum
+    wrong = _sums_twice(torch, fem, prec, _device_state(torch, p, E, prec, ph & 0x80),
+                        p.n_nodes)
+    assert abs(wrong[0][1] - ref[3]) > 1e-3 * ref[3]
 
 
 def test_rejects_sizes_beyond_the_scratch(env):
