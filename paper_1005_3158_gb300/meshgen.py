@@ -490,3 +490,26 @@ def bar(n: int, length: float = 0.5, material=ALLOY, latent: float | None = None
     if latent is not None:
         mats[0, 3] = latent
     return xyz, tets, flags, mats
+
+
+# --------------------------------------------------------------------------
+# Learned surrogate: seeded initial parameters and training geometries
+# --------------------------------------------------------------------------
+
+def surrogate_init(shapes, seed: int = 2024) -> np.ndarray:
+    """Seeded initial parameters of a network whose flat parameter vector is
+    the concatenation of ``shapes`` ((name, shape) pairs; a 2-D shape is a
+    weight matrix (out, in), a 1-D shape a bias or a vector).  Weight
+    matrices are drawn from N(0, 2 / in) (He initialisation), the last
+    layer's vector (name "d2") from N(0, 0.01 / in); biases are 0.  FP32."""
+    rng = rng_of(seed)
+    out = []
+    for name, shape in shapes:
+        n = int(np.prod(shape))
+        if len(shape) == 2:
+            out.append(rng.normal(0.0, np.sqrt(2.0 / shape[1]), size=n))
+        elif name == "d2":
+            out.append(rng.normal(0.0, np.sqrt(0.01 / shape[0]), size=n))
+        else:
+            out.append(np.zeros(n))
+    return np.concatenate(out).astype(np.float32)
