@@ -36,7 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # matching summary under profiles/); valid while the sources it was taken on
 # are unchanged
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
-TRAFFIC_SOURCES = ("fem_kernels.cu", "fem_internal.h", "fem_plan.cpp", "fem_plan.h", "fem_api.cpp")
+TRAFFIC_SOURCES = ("fem_kernels.cu", "fem_device.cuh", "fem_internal.h", "fem_plan.cpp",
+                   "fem_plan.h")
 
 
 def sources_digest() -> str:
@@ -48,10 +49,12 @@ def sources_digest() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(kernel: str, precision: str, variant: str, n_units: int):
+def measured_traffic(kernel: str, precision: str, variant: str, n_units: int,
+                     scope: str = "single"):
     """ncu DRAM bytes (read + write) per launch of `kernel`, scaled from the
     captured workload to n_units by the units processed; None when no
-    capture matches or the sources changed since it was taken."""
+    capture matches or the sources changed since it was taken.  scope is
+    "single" (one mesh) or "batch" (a batch of instances)."""
     try:
         with open(TRAFFIC_FILE) as fh:
             entries = json.load(fh)["entries"]
@@ -60,7 +63,7 @@ def measured_traffic(kernel: str, precision: str, variant: str, n_units: int):
     digest = sources_digest()
     for e in entries:
         if (e["kernel"], e["precision"], e["variant"]) == (kernel, precision, variant) \
-                and e["sources_sha256"] == digest:
+                and e.get("scope", "single") == scope and e["sources_sha256"] == digest:
             per_unit = (e["dram_read_bytes"] + e["dram_write_bytes"]) / e["units"]
             return int(round(per_unit * n_units))
     return None
@@ -183,7 +186,13 @@ def hbm_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms.  The
+    sampler starts before the warm-up steps; when the timed region is short,
+    the caller keeps stepping (untimed) after it until the sampler has seen
+    `min_s` seconds, so that the record holds several samples under the
+    same load."""
+
+    min_s = 1.0
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -198,12 +207,19 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            self.t0 = time.perf_counter()
         except Exception:
             self.proc = None
+
+    def remaining(self) -> float:
+        """Seconds the sampler still wants under load (0 when enough)."""
+        if self.proc is None:
+            return 0.0
+        return max(0.0, self.min_s - (time.perf_counter() - self.t0))
 
     def _read(self):
         for line in self.proc.stdout:
@@ -235,7 +251,9 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 50,
+                "window": "warm-up, timed region and untimed steps after it (at least "
+                          f"{self.min_s:.1f} s under the same step loop)"}
 
 
 def cpu_baseline(workload: str, seconds: float):
@@ -319,6 +337,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def cpu_baseline_batch(probs, seconds: float):
+    """The FP64 oracle as it stands, single thread, on a bounded subset of
+    a batch's instances (the first ones, up to 1.5M tets), each stepped at
+    0.9 of its own stable step in turn; returns the cpu_baseline record."""
+    import oracle
+    sub, tot = [], 0
+    for p in probs:
+        if sub and tot + p.n_tets > 1.5e6:
+            break
+        sub.append(p)
+        tot += p.n_tets
+    os_, dts = [], []
+    for p in sub:
+        o = oracle.OracleProblem(p)
+        o.set_temperature(p.T0)
+        os_.append(o)
+        dts.append(0.9 * o.stable_dt())
+    upd, rounds, t0 = 0.0, 0, time.perf_counter()
+    while True:
+        for o, d, p in zip(os_, dts, sub):
+            o.step(1, d)
+            upd += p.n_tets
+        rounds += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or rounds >= 1000:
+            break
+    return {"value": upd / el, "unit": "tet-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {len(sub)} instances of the batch ({tot} tets), {rounds} FP64 "
+                      f"steps each at its own dt, {el:.1f} s single-thread"}
+
+
 def run_batched(args):
     """Batched castings (256 instances, 20k-500k tets each, FP32): one
     fem_advance to a common end time, every instance at 0.9 x its own
@@ -363,7 +412,15 @@ def run_batched(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    post = 0
+    while clocks.remaining() > 0.0:    # untimed advances so the clock record has samples
+        t_now += span
+        b.advance(t_now)
+        torch.cuda.synchronize()
+        post += 1
     clk = clocks.stop()
+    if clk is not None:
+        clk["untimed_advances_after"] = post
     value = updates / (ms / 1e3)
     info = b.info()
     # kernels in the timed advance: per step, two per run of consecutive
@@ -373,6 +430,59 @@ def run_batched(args):
     for st in range(int(n.max())):
         act = nk > st
         launches += 2 * int(act[0] + np.count_nonzero(act[1:] & ~act[:-1]))
+
+    # per-kernel device times of a step of every instance (each at the
+    # smallest instance step, stable for all): events around each kernel
+    kms = b.step_profile(args.profile_steps, float(dt.min())) / max(1, args.profile_steps)
+    s = 4 if args.precision == "fp32" else 8
+    peak, peak_kind = hbm_peak()
+    E_all, N_all, n_int = int(tets.sum()), info["n_nodes"], info["n_interior_nodes"]
+    alg = [E_all * (16 + 6 * s) + n_int * 4 * s, (N_all - n_int) * 4 * s]
+    names = ["k_block_step", "k_shared_update"]
+    k_dom = int(np.argmax(kms))
+    achieved = alg[k_dom] / (kms[k_dom] / 1e3) / 1e9
+    adv_alg = (16 + 6 * s + (N_all / E_all) * 4 * s) * value / 1e9
+    roofline = {"bound": "hbm", "kernel": names[k_dom], "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": measured_traffic(names[k_dom], args.precision, "block",
+                                            E_all if k_dom == 0 else N_all, scope="batch"),
+                "peak_source": peak_kind, "alg_bytes_per_launch": int(alg[k_dom]),
+                "kernel_ms": {nm: round(float(v), 4) for nm, v in zip(names, kms)},
+                "launch": "all instances stepping",
+                "advance": {"achieved": round(adv_alg, 1), "frac": round(adv_alg / peak, 4),
+                            "note": "whole timed advance at 42.7 B per tet-update (FP32)"}}
+
+    # end to end through the C ABI: every advance uploads the whole batch's
+    # state from pinned host memory, advances every instance by the same
+    # span and reads all temperatures back (pipelined calls, one sync)
+    e2e = None
+    if not args.no_e2e:
+        ke = max(2, min(args.e2e_steps, 10))
+        io_dt = torch.float32 if args.precision == "fp32" else torch.float64
+        E64 = torch.empty(N_all, dtype=torch.float64)
+        b.state(E64.numpy())
+        E_io = E64.to(io_dt).pin_memory()
+        T_io = [torch.empty(N_all, dtype=io_dt, pin_memory=True) for _ in range(2)]
+
+        def loop(k, t):
+            for i in range(k):
+                b.set_state_async(E_io, 0, 0.0)
+                t += span
+                b.advance(t)
+                b.temperature_async(T_io[i % 2])
+            b.sync()
+            return t
+
+        t_now = loop(1, t_now)
+        t0 = time.perf_counter()
+        t_now = loop(ke, t_now)
+        el = time.perf_counter() - t0
+        isz = E_io.element_size()
+        e2e = {"value": updates * ke / el, "unit": "tet-updates/s",
+               "h2d_bytes_per_step": N_all * isz, "d2h_bytes_per_step": N_all * isz,
+               "steps": ke, "step": "one fem_advance of every instance",
+               "api": f"fem_set_state_async{'_f32' if isz == 4 else ''} + fem_advance + "
+                      f"fem_get_temperature_async{'_f32' if isz == 4 else ''}, fem_sync at the end"}
     b.close()
     seq = None
     if not args.no_sequential:
@@ -392,10 +502,9 @@ def run_batched(args):
                 torch.cuda.synchronize()
                 tot += e0.elapsed_time(e1)
         seq = updates / (tot / 1e3)
-    s = 4 if args.precision == "fp32" else 8
-    peak, peak_kind = hbm_peak()
-    alg = 16 + 6 * s + (info["n_nodes"] / info["n_tets"]) * 4 * s
-    achieved = alg * value / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline_batch(probs, args.cpu_seconds)
     line = {
         "metric": "tet-element updates/s", "value": value, "unit": "tet-updates/s",
         "n_gpus": 1, "steps": int(n.max()), "warmup": args.warmup, "ms_per_step": ms / n.max(),
@@ -409,10 +518,7 @@ def run_batched(args):
                    "threads": info["threads"], "precision": args.precision,
                    "sequential_value": seq, "autotune": tuned,
                    "l2": "inputs larger than L2 (no flush)", "setup_s": round(t_setup, 1)},
-        "roofline": {"bound": "hbm", "kernel": "whole advance (block + shared-node kernels)",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind},
-        "cpu_baseline": None, "e2e": None, "clocks": clk,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
@@ -457,10 +563,10 @@ def main():
     E, N = p.n_tets, p.n_nodes
 
     # warm-up, then K timed steps between barriers, CUDA events on the stream
-    mesh.step(args.warmup, dt)
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    mesh.step(args.warmup, dt)
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -472,7 +578,14 @@ def main():
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
+    post = 0
+    while clocks.remaining() > 0.0:    # untimed steps so the clock record has samples
+        mesh.step(32, dt)
+        torch.cuda.synchronize()
+        post += 32
     clk = clocks.stop()
+    if clk is not None:
+        clk["untimed_steps_after"] = post
     ms = max_over_ranks(ms, world, "cuda")
     value = job_throughput(E, args.steps, world, ms / 1e3)
     kernels_per_step = 2 if info["n_shared_nodes"] > 0 or args.variant != "block" else 1

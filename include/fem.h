@@ -55,7 +55,9 @@ typedef enum {
     FEM_ENOMEM = 2,    /* host or device allocation failed (nothing leaked) */
     FEM_ECUDA = 3,     /* a CUDA runtime call failed, or no usable GPU */
     FEM_ESTATE = 4,    /* call out of order (e.g. fem_step before materials) */
-    FEM_EUNSTABLE = 5, /* non-finite temperatures/energy: dt above the stable limit */
+    FEM_EUNSTABLE = 5, /* non-finite temperatures/energy, or an energy balance
+                          residual beyond its rounding bound (fem_get_energy):
+                          dt above the stable limit */
     FEM_ETIMEOUT = 6   /* a bounded device wait gave up (reported by the next
                           fem_get_* call; the state is then not valid) */
 } fem_status;
@@ -289,7 +291,16 @@ fem_status fem_get_enthalpy(fem_mesh *m, double *h_out);
  * yet released sum_i Lc_i f_l(T_i).  Without Dirichlet nodes U - U0 -
  * out[2] is zero up to rounding in the enthalpy formulation (only
  * approximately in the apparent-capacity one).  Synchronises.
- * FEM_EUNSTABLE if U is non-finite. */
+ * FEM_EUNSTABLE if U is non-finite, or if the balance residual
+ * |U - U0 - out[2]| exceeds 2 u (n + 16) S, the most that rounding can
+ * give: u the unit roundoff of the mesh's precision (2^-24 FP32, 2^-53
+ * FP64), n the steps since fem_set_temperature, S the larger of |U0| and
+ * |U| with |U| capped at sum_i C_i T_hi + Lc_i (T_hi the highest initial
+ * or effective ambient temperature T_inf - q/h of the data).  A run past
+ * the stability limit crosses that bound while every value is still
+ * finite.  The check is made in the enthalpy formulation without Dirichlet
+ * nodes, from fem_set_temperature (or fem_batch_create) until a state is
+ * uploaded with fem_set_state*; out[] is written either way. */
 fem_status fem_get_energy(fem_mesh *m, double out[4]);
 
 /* Use the given cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)

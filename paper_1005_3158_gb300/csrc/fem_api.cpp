@@ -159,6 +159,13 @@ struct fem_mesh {
     double time = 0.0;
     double U0 = 0.0;
     double q_carry = 0.0;             // boundary heat of device buffers already released
+    // energy balance check (fem_get_energy): the account is exact from
+    // fem_set_temperature on, until a state is uploaded (fem_set_state*);
+    // acct_steps counts the steps taken since the account began
+    bool acct_exact = false;
+    int64_t acct_steps = 0;
+    double acct_T0max = 0.0;          // highest initial temperature
+    double env_U = -1.0;              // cached enthalpy_envelope, < 0 when stale
     // ---- batch of independent instances (fem_batch_create); n_inst == 0
     // for a plain mesh.  Ranges are in caller order, [n_inst + 1] each.
     int32_t n_inst = 0;
@@ -302,11 +309,32 @@ int default_block_elems(const fem_mesh *m)
 
 bool is_block(const fem_mesh *m) { return m->opt.variant == FEM_VARIANT_BLOCK; }
 bool is_lm(const fem_mesh *m) { return m->opt.formulation == FEM_APPARENT_CAPACITY; }
+bool has_dirichlet(const fem_mesh *m) { return !m->is_dir.empty(); }
+
+// Largest total enthalpy content a stable run of the current data can
+// reach: sum_i C_i T_hi + Lc_i, with T_hi the highest temperature the data
+// allow (the initial temperatures and the effective ambient T_inf - q/h of
+// every Robin face; interface faces take their sisters' temperatures).
+// +inf when a face with h = 0 heats by a flux alone (no such bound).
+double enthalpy_envelope(fem_mesh *m)
+{
+    if (m->env_U >= 0.0) return m->env_U;
+    double Th = m->acct_T0max;
+    for (size_t f = 0; f < m->fa.size(); f++) {
+        // fa = h A / 12, fg = A/3 (h T_inf - q): T_inf - q/h = fg / (4 fa)
+        if (m->fa[f] > 0.0) Th = std::max(Th, m->fg[f] / (4.0 * m->fa[f]));
+        else if (m->fg[f] > 0.0) return m->env_U = HUGE_VAL;
+    }
+    double U = 0.0;
+    for (int64_t i = 0; i < m->N; i++) U += m->Cn[(size_t)i] * Th + m->Lcn[(size_t)i];
+    return m->env_U = U;
+}
 
 // faces/fa/fg = Robin faces, then interface faces (whose load term the
 // interface kernel rewrites every step)
 void combine_faces(fem_mesh *m)
 {
+    m->env_U = -1.0;
     m->faces = m->rb_faces;
     m->faces.insert(m->faces.end(), m->if_faces.begin(), m->if_faces.end());
     m->fa = m->rb_fa;
@@ -1154,6 +1182,7 @@ fem_status step_impl(fem_mesh *m, int64_t n, double dt)
             if (st) return st;
         }
     m->step += n;
+    m->acct_steps += n;
     m->time += dt * (double)n;
     return FEM_OK;
 }
@@ -1184,6 +1213,7 @@ fem_status step_profile_impl(fem_mesh *m, int64_t n, double dt, double *ms)
             ms[k] += t;
         }
         m->step += 1;
+        m->acct_steps += 1;
         m->time += dt;
     }
     for (int k = 0; k <= nk; k++) cudaEventDestroy(ev[k]);
@@ -1455,6 +1485,7 @@ fem_status fem_set_materials(fem_mesh *m, const fem_material *mats, int32_t n_ma
         if (st) return st;
         m->w.swap(w);
         m->Cn.swap(C);
+        m->env_U = -1.0;
         m->mn.swap(mn);
         m->Lcn.swap(Lc);
         m->rng_id.swap(rid);
@@ -1632,6 +1663,10 @@ fem_status fem_set_temperature(fem_mesh *m, const double *T0)
     m->step = 0;
     m->time = 0.0;
     m->q_carry = 0.0;
+    m->acct_exact = true;
+    m->acct_steps = 0;
+    m->acct_T0max = *std::max_element(T0, T0 + m->N);
+    m->env_U = -1.0;
     if (m->n_inst > 0) {
         m->inst_t.assign((size_t)m->n_inst, 0.0);
         m->inst_steps.assign((size_t)m->n_inst, 0);
@@ -1672,6 +1707,7 @@ fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
     }
     m->step = step;
     m->time = t;
+    m->acct_exact = false;   // the uploaded state need not balance the account
     return ok();
 }
 
@@ -1745,7 +1781,12 @@ fem_status fem_step_profile(fem_mesh *m, int64_t n_steps, double dt, double *ms_
     *n_used = nk;
     st = m->prec == FEM_FP32 ? step_profile_impl<float>(m, n_steps, dt, ms_out)
                              : step_profile_impl<double>(m, n_steps, dt, ms_out);
-    return st ? st : ok();
+    if (st) return st;
+    for (int32_t i = 0; i < m->n_inst; i++) {   // as fem_step: every instance took them
+        m->inst_t[(size_t)i] += dt * (double)n_steps;
+        m->inst_steps[(size_t)i] += n_steps;
+    }
+    return ok();
 }
 
 fem_status fem_autotune(fem_mesh *m, const int32_t *block_elems, const int32_t *threads, int32_t n,
@@ -1771,7 +1812,7 @@ fem_status fem_autotune(fem_mesh *m, const int32_t *block_elems, const int32_t *
     if ((st = stash_state(m))) return st;
     // what the timed steps change, put back afterwards
     const std::vector<double> E0 = m->pending;
-    const int64_t step0 = m->step;
+    const int64_t step0 = m->step, acct0 = m->acct_steps;
     const double time0 = m->time, q0 = m->q_carry;
     const fem_options opt0 = m->opt;
     const std::vector<double> it0 = m->inst_t, iq0 = m->inst_q;
@@ -1780,6 +1821,7 @@ fem_status fem_autotune(fem_mesh *m, const int32_t *block_elems, const int32_t *
         m->opt = o;
         reset_partition(m, E0);
         m->step = step0;
+        m->acct_steps = acct0;
         m->time = time0;
         m->q_carry = q0;
         m->inst_t = it0;
@@ -1861,6 +1903,7 @@ fem_status set_state_async_impl(fem_mesh *m, const io *E, int64_t step, double t
     m->in_idx = 1 - i;
     m->step = step;
     m->time = t;
+    m->acct_exact = false;   // the uploaded state need not balance the account
     return ok();
 }
 
@@ -2006,6 +2049,34 @@ fem_status fem_get_energy(fem_mesh *m, double out[4])
     out[3] = r[1];
     if (!std::isfinite(r[0]))
         return fail(FEM_EUNSTABLE, "non-finite total enthalpy: dt above the stable limit?");
+    // Energy balance: in the enthalpy formulation every step conserves
+    // U - Q_b exactly (zero column sums of K^e), so without Dirichlet nodes
+    // U - U0 - Q_b only collects rounding.  Each step rounds every E_i once,
+    // by at most half an ulp (2^-24 |E_i| in FP32, 2^-53 in FP64), and the
+    // E_i of a stable run are positive (E = 0 at 0 K), so rounding alone
+    // stays below 2 u (steps + 16) U_max with u the unit roundoff and U_max
+    // the largest total enthalpy of the run.  A run past the stability
+    // limit grows an oscillating mode whose rounding errors scale with
+    // sum |E_i| >> U: it crosses that bound while every value is still
+    // finite.
+    // The scale is the larger of |U0| and |U|, with |U| capped by the
+    // envelope a stable run cannot leave (the boundary heat of a blown-up
+    // run grows with it and would otherwise move the bound along).
+    if (m->acct_exact && !is_lm(m) && !has_dirichlet(m)) {
+        const double u = m->prec == FEM_FP32 ? 0x1p-24 : 0x1p-53;
+        const double scale =
+            std::max(std::fabs(out[1]), std::min(std::fabs(out[0]), enthalpy_envelope(m)));
+        const double bound = 2.0 * u * (double)(m->acct_steps + 16) * scale;
+        const double resid = out[0] - out[1] - out[2];
+        if (!(std::fabs(resid) <= bound)) {
+            char msg[256];
+            snprintf(msg, sizeof msg,
+                     "energy balance residual U - U0 - Q_b = %.6g J exceeds the rounding bound "
+                     "%.6g J after %lld steps: dt above the stable limit?",
+                     resid, bound, (long long)m->acct_steps);
+            return fail(FEM_EUNSTABLE, msg);
+        }
+    }
     return ok();
 }
 
@@ -2242,6 +2313,9 @@ fem_status fem_batch_create(fem_mesh *const *parts, int32_t n_parts, fem_mesh **
         build_node_elems(m->N, m->E, m->tets.data(), m->adj);
         m->have_mat = true;
         m->state = fem_mesh::ST_PENDING_T;
+        m->acct_exact = true;
+        m->acct_steps = 0;
+        m->acct_T0max = *std::max_element(m->pending.begin(), m->pending.end());
         m->inst_dt.resize((size_t)n_parts);
         for (int32_t i = 0; i < n_parts; i++) m->inst_dt[(size_t)i] = 0.9 * m->inst_stable[(size_t)i];
         m->inst_t.assign((size_t)n_parts, 0.0);
@@ -2405,6 +2479,7 @@ fem_status advance_impl(fem_mesh *m, double t_end)
         max_n = std::max(max_n, n[(size_t)i]);
     }
     m->step += max_n;
+    m->acct_steps += max_n;
     m->time = std::max(m->time, t_end);
     return FEM_OK;
 }

@@ -1,10 +1,13 @@
-// Nodal phase-change relations of the enthalpy formulation, shared by the
-// CUDA translation units of libfem (device code only).  Eqs. 5 and 11 with a
-// linear liquid fraction between the solidus Ts and the liquidus Tl:
-// E(T) = C T + Lc f_l(T) and its exact piecewise-linear inverse T(E).
+// Device helpers shared by the CUDA translation units of libfem (device
+// code only): the nodal phase-change relations of the enthalpy formulation
+// (Eqs. 5 and 11 with a linear liquid fraction between the solidus Ts and
+// the liquidus Tl: E(T) = C T + Lc f_l(T) and its exact piecewise-linear
+// inverse T(E)), and PTX wrappers for mbarriers and bulk copies.
 #pragma once
 
 #include <cstdint>
+
+#include "fem_internal.h"
 
 namespace fem {
 
@@ -48,6 +51,68 @@ __device__ __forceinline__ double latent_of(real E, real C, real Lc, uint8_t ph,
     const real T = temperature_of(E, C, Lc, ph, ranges);
     double l = (double)E - (double)C * (double)T;
     return l < 0.0 ? 0.0 : (l > (double)Lc ? (double)Lc : l);
+}
+
+// PTX wrappers: mbarrier + 1-D bulk copy (TMA) global -> shared.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned address and
+// size; nothing to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for phase `parity` of the barrier; gives up after kWaitNs of device
+// time or kWaitPolls polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t i = 1; i < kWaitPolls; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
 }
 
 }  // namespace fem

@@ -5,6 +5,8 @@
   cleared and a valid state steps normally again.
 * A step far above the stable limit blows the state up; fem_get_temperature
   reports FEM_EUNSTABLE (the output is still written).
+* A step a little above the true limit is caught earlier, by the energy
+  balance check of fem_get_energy, while every value is still finite.
 * Device allocation failure, injected on the host (FEM_FAULT_ALLOC_AFTER=k
   fails every device allocation after the k-th of a mesh upload), returns
   FEM_ENOMEM from the first call that needs the device, releases the partial
@@ -74,6 +76,56 @@ def test_unstable_step_reported(fem, prec):
         # is still non-finite
         with pytest.raises(fem.FemError):
             m.temperature()
+
+
+def _lambda_max(p):
+    """Largest eigenvalue of C^-1 (K + H) of a sensible-only problem, from
+    the oracle's residual map applied to unit vectors."""
+    o = oracle.OracleProblem(p)
+    C, _, _ = o.lumped()
+    n = p.n_nodes
+    R0, _ = o.residual(np.zeros(n))
+    M = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        M[:, j] = -(o.residual(e)[0] - R0)
+    s = 1.0 / np.sqrt(C)
+    return np.linalg.eigvalsh(s[:, None] * M * s[None, :]).max()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_energy_residual_reported_before_overflow(fem, prec):
+    """At 1.2 x the true stability limit 2 / lambda_max an oscillating mode
+    grows by |1 - 2.4| = 1.4 per step.  The scheme still conserves energy
+    exactly, but the rounding of ever larger nodal values pushes the balance
+    residual U - U0 - Q_b past its rounding bound: fem_get_energy reports
+    FEM_EUNSTABLE while every temperature is still finite."""
+    p = mg.unit_cube(5)
+    mats = p.materials.copy()
+    mats[:, 3] = 0.0
+    p.materials = mats
+    dt = 1.2 * 2.0 / _lambda_max(p)
+    with fem.Mesh(p, prec, reorder=1, block_elems=128) as m:
+        # below the limit the balance holds over many steps
+        m.step(2000, 0.95 * 2.0 / _lambda_max(p))
+        m.energy()
+        m.set_temperature(p.T0)
+        for k in range(1, 600):
+            m.step(2, dt)
+            try:
+                m.energy()
+            except fem.FemError as e:
+                assert e.status == fem.FEM_EUNSTABLE
+                assert "balance" in str(e)
+                break
+        else:
+            pytest.fail("no FEM_EUNSTABLE from the energy balance")
+        T = m.temperature()        # raises FEM_EUNSTABLE if anything is non-finite
+        assert np.isfinite(T).all()
+        assert np.abs(T - 300.0).max() > 1e3    # the state has clearly blown up
+        print(f"{prec}: balance check tripped after {2 * k} steps, max |T| = "
+              f"{np.abs(T).max():.3g} K")
 
 
 _CHILD = r"""
