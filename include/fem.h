@@ -499,6 +499,103 @@ typedef void *(*fem_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*fem_free_fn)(void *ptr, void *ctx);
 fem_status fem_set_allocator(fem_mesh *m, fem_alloc_fn alloc, fem_free_fn free_fn, void *ctx);
 
+/* ---- Learned surrogate: 16 explicit steps per network evaluation -------
+ * The explicit step is bounded by the stability limit of Eq. 13; a small
+ * message-passing network on the node graph of the mesh advances the
+ * nodal enthalpy by 16 steps of the mesh's dt in one evaluation.  The
+ * paper has no surrogate: this is the library's addition, trained on
+ * trajectories of the library's own explicit solver, which stays the
+ * fallback and the judge of the surrogate's error.
+ *
+ * Graph: nodes are the mesh nodes; an edge joins two nodes of one tet, with
+ * weight W_ij = -sum_e K^e_ab over the tets that hold it (Eq. 9), so that
+ * sum_j W_ij (T_j - T_i) is the conduction part of the explicit residual.
+ * s_i = dt_i / C_i; hA_i = sum h A / 3 and g_i = sum A (h T_inf - q) / 3 over
+ * the node's Robin faces (Eq. 4 lumped to its row sums).
+ * Features x_i (16; T = T(E) of Eqs. 5 and 11, f = (E - C T) / Lc the liquid
+ * fraction, 0 without latent heat):
+ *   (T - 600)/300, f, Lc/(300 C), 16 s hA, 16 s (g - hA T)/300,
+ *   16 s sum_j W_ij (T_j - T_i)/300, 16 s sum_j W_ij (f_j - f_i), 1,
+ *   (T - Ts)/300 and (T - Tl)/300 (phase-change nodes, else 0),
+ *   16 s sum_j W_ij, 0 x 5.
+ * Network (BF16 operands on the tensor cores, FP32 accumulation):
+ *   h0 = relu(W_in x + b_in)                                16 -> 64
+ *   l = 1..3: phi = relu(P_l h + p_l)                       64 -> 32
+ *             m_i = s_i sum_j W_ij (phi_j - phi_i)          (FP32 sums)
+ *             h  += relu(U_l [h; m] + u_l)                  96 -> 64
+ *   z = relu(D1 h + d1), y = d2 . z + d2b,  E'_i = E_i + 10 K * C_i y_i.
+ * Parameters: one FP32 vector of FEM_SG_N_PARAMS values, in this order:
+ *   W_in [64][16], b_in [64], then for l = 1..3: P_l [32][64], p_l [32],
+ *   U_l [64][96], u_l [64]; then D1 [64][64], d1 [64], d2 [64], d2b [1]
+ *   (matrices row-major, out x in).
+ * Training: loss = mean_i (y_i - y*_i)^2, y*_i = (E*_i - E_i) / (10 K C_i)
+ * with E* the state 16 explicit steps later; Adam (b1 0.9, b2 0.999,
+ * eps 1e-8) on the FP32 vector.
+ * Scope: FP32 block-variant meshes in the enthalpy formulation with
+ * constant conductivity, Robin faces, no Dirichlet nodes and no interface
+ * faces (FEM_EINVAL otherwise).  Device arrays named E_* below are FP32
+ * [n_nodes] in the surrogate's own node order (fem_surrogate_order); work
+ * runs on the mesh's stream, asynchronously unless stated.  The surrogate
+ * belongs to its mesh: destroy it first. */
+#define FEM_SG_N_PARAMS 30177
+typedef struct fem_surrogate fem_surrogate;
+
+/* Build the graph of a mesh that has materials, boundary and a state (its
+ * device data are uploaded if needed).  dt: the explicit step of a plain
+ * mesh (> 0); a batch uses each instance's current step (fem_set_instance_dt)
+ * and ignores dt.  Errors: FEM_EINVAL (scope above, bad dt), FEM_ESTATE,
+ * FEM_ENOMEM, FEM_ECUDA. */
+fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate **out);
+
+/* Sizes: nodes, directed edges (non-zeros of the graph), parameters. */
+fem_status fem_surrogate_info(fem_surrogate *s, int64_t *n_nodes, int64_t *n_edges,
+                              int64_t *n_params);
+
+/* caller_of [n_nodes]: the caller's node id at each surrogate position. */
+fem_status fem_surrogate_order(fem_surrogate *s, int32_t *caller_of);
+
+/* Parameters from / to a host array of n == FEM_SG_N_PARAMS floats.
+ * Setting them resets the Adam moments and step count.  Synchronises. */
+fem_status fem_surrogate_set_params(fem_surrogate *s, const float *theta, int64_t n);
+fem_status fem_surrogate_get_params(fem_surrogate *s, float *theta, int64_t n);
+
+/* The mesh's current state into E_dev (device), or E_dev into the mesh
+ * (the step count and time are kept; the energy account stops balancing). */
+fem_status fem_surrogate_read_state(fem_surrogate *s, float *E_dev);
+fem_status fem_surrogate_write_state(fem_surrogate *s, const float *E_dev);
+
+/* E_out = the network's state 16 steps after E_in (device arrays). */
+fem_status fem_surrogate_predict(fem_surrogate *s, const float *E_in, float *E_out);
+
+/* One training step on the pair (E_in, E_star) (device arrays): forward,
+ * loss, backward, then an Adam step of size lr (lr == 0: gradient only,
+ * parameters unchanged).  loss_out (host, may be NULL) receives the loss
+ * of the parameters before the step; a non-NULL loss_out synchronises.
+ * FEM_ETIMEOUT if a bounded device wait gave up. */
+fem_status fem_surrogate_train_step(fem_surrogate *s, const float *E_in, const float *E_star,
+                                    float lr, double *loss_out);
+
+/* Advance the mesh by 16 * n_macro explicit steps through the network:
+ * its state is read, stepped n_macro times and written back; the step
+ * count and time (each batch instance's with its own dt) advance, and the
+ * energy account no longer balances (the boundary heat of those steps is
+ * not accumulated). */
+fem_status fem_surrogate_advance(fem_surrogate *s, int64_t n_macro);
+
+/* Test hook: a host copy of an internal buffer after the last forward or
+ * training step (surrogate order).  which: 0 x (bf16 [n][16]), 1 h_layer
+ * (bf16 [n][64], layer 0..3), 2 phi (bf16 [n][32], layer 0..2), 3 m (bf16
+ * [n][32]), 4 relu output r (bf16 [n][64]), 5 z (f32 [n][64]), 6 y (f32
+ * [n]), 7 gradient (f32 [FEM_SG_N_PARAMS]), 8 node data (f32 [n][5]: C, Lc,
+ * s, hA, g), 9 graph (int32 rowptr [n+1], int32 col [n_edges], f32 w
+ * [n_edges], concatenated).  bf16 values are raw 16-bit patterns.  The
+ * training-only buffers (x, m, r, z, y) hold the last training step's
+ * values.  Synchronises. */
+fem_status fem_surrogate_debug(fem_surrogate *s, int32_t which, int32_t layer, void *out);
+
+/* Release the surrogate's device memory (NULL is a no-op). */
+void fem_surrogate_destroy(fem_surrogate *s);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fem_last_error(void);
 

@@ -2548,3 +2548,72 @@ fem_status fem_get_instance_energy(fem_mesh *m, int32_t inst, double out[4])
 }
 
 }  // extern "C"
+
+// ---- accessors of the learned surrogate (fem_surrogate.cu) ----------------
+
+int fem::surrogate_mesh_view(::fem_mesh *m, SurrogateMeshView *v)
+{
+    if (!m || !v) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_mat) return fail(FEM_ESTATE, "fem_set_materials has not been called");
+    fem_status st = ensure_plan(m);
+    if (st) return st;
+    *v = SurrogateMeshView{};
+    v->N = m->N;
+    v->E = m->E;
+    v->xyz = m->xyz.data();
+    v->tets = m->tets.data();
+    v->w = m->w.data();
+    v->C = m->Cn.data();
+    v->Lc = m->Lcn.data();
+    v->rng_id = m->rng_id.data();
+    v->ranges = m->ranges.data();
+    v->n_ranges = (int32_t)(m->ranges.size() / 2);
+    v->F_rb = m->F_rb;
+    v->rb_faces = m->rb_faces.data();
+    v->rb_fa = m->rb_fa.data();
+    v->rb_fg = m->rb_fg.data();
+    v->n_inst = m->n_inst;
+    v->inst_node = m->n_inst ? m->inst_node.data() : nullptr;
+    v->inst_dt = m->n_inst ? m->inst_dt.data() : nullptr;
+    v->prec = m->prec;
+    v->variant = m->opt.variant;
+    v->formulation = m->opt.formulation;
+    v->has_kt = m->has_kt ? 1 : 0;
+    v->has_dir = has_dirichlet(m) ? 1 : 0;
+    v->F_if = m->F_if;
+    v->node_new = is_block(m) ? m->bp.node_new.data() : nullptr;
+    return FEM_OK;
+}
+
+int fem::surrogate_mesh_device(::fem_mesh *m, StateView<float> *v, void **stream, int *device)
+{
+    if (!m || !v) return fail(FEM_EINVAL, "NULL argument");
+    if (m->prec != FEM_FP32 || !is_block(m) || is_lm(m))
+        return fail(FEM_EINVAL, "the surrogate needs an FP32 block-variant mesh in the enthalpy formulation");
+    fem_status st = ready_for_io(m);
+    if (st) return st;
+    *v = view_of<float>(m);
+    if (stream) *stream = (void *)m->stream;
+    if (device) *device = m->device;
+    return FEM_OK;
+}
+
+int fem::surrogate_mesh_advanced(::fem_mesh *m, int64_t n_steps, double dt)
+{
+    if (!m) return fail(FEM_EINVAL, "NULL argument");
+    KERNEL(refresh_mirror<float>(m), "mirror kernel");
+    m->step += n_steps;
+    m->acct_exact = false;
+    if (m->n_inst > 0) {
+        double t_max = m->time;
+        for (int32_t i = 0; i < m->n_inst; i++) {
+            m->inst_t[(size_t)i] += m->inst_dt[(size_t)i] * (double)n_steps;
+            m->inst_steps[(size_t)i] += n_steps;
+            t_max = std::max(t_max, m->inst_t[(size_t)i]);
+        }
+        m->time = t_max;
+    } else {
+        m->time += dt * (double)n_steps;
+    }
+    return FEM_OK;
+}

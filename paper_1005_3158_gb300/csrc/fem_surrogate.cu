@@ -266,3 +266,1400 @@ __global__ void __launch_bounds__(128) k_sg_encode(Graph g, Acts a, const uint8_
     tc::fence_after();
     if (tid < 32) tc::tmem_free(tbase, 128);
 }
+
+namespace {
+
+// Graph messages of one tile: m_i = s_i sum_j W_ij (phi_j - phi_i) for the
+// 128 nodes of the tile (rows), 32 channels, FP32 sums of bf16 values.  Warp
+// w takes rows 32 w .. 32 w + 31, four at a time: 8 lanes per node, 4
+// channels per lane, one 8-byte gather per neighbour and lane.  The bf16
+// result lands in columns koff .. koff + 31 of row r of the core-matrix
+// operand sA (K columns) and, if msave is set, in msave[i][0..31].
+__device__ __forceinline__ void tile_messages(const Graph &g, const uint16_t *__restrict__ phi,
+                                              int64_t tile0, uint8_t *sA, uint32_t K, uint32_t koff,
+                                              uint16_t *msave)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> 3, sub = lane & 7;
+#pragma unroll 1
+    for (int rr = 0; rr < 8; rr++) {
+        const int r = warp * 32 + rr * 4 + grp;
+        const int64_t i = tile0 + r;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (i < g.n) {
+            const uint2 me = __ldg(reinterpret_cast<const uint2 *>(phi + i * 32) + sub);
+            const float p0 = bf_lo(me.x), p1 = bf_hi(me.x), p2 = bf_lo(me.y), p3 = bf_hi(me.y);
+            const int k1 = __ldg(g.rowptr + i + 1);
+            int k = __ldg(g.rowptr + i);
+            for (; k + 1 < k1; k += 2) {
+                const int j0 = __ldg(g.col + k), j1 = __ldg(g.col + k + 1);
+                const float w0 = __ldg(g.w + k), w1 = __ldg(g.w + k + 1);
+                const uint2 o0 = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j0 * 32) + sub);
+                const uint2 o1 = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j1 * 32) + sub);
+                a0 += w0 * (bf_lo(o0.x) - p0);
+                a1 += w0 * (bf_hi(o0.x) - p1);
+                a2 += w0 * (bf_lo(o0.y) - p2);
+                a3 += w0 * (bf_hi(o0.y) - p3);
+                a0 += w1 * (bf_lo(o1.x) - p0);
+                a1 += w1 * (bf_hi(o1.x) - p1);
+                a2 += w1 * (bf_lo(o1.y) - p2);
+                a3 += w1 * (bf_hi(o1.y) - p3);
+            }
+            if (k < k1) {
+                const int j0 = __ldg(g.col + k);
+                const float w0 = __ldg(g.w + k);
+                const uint2 o0 = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j0 * 32) + sub);
+                a0 += w0 * (bf_lo(o0.x) - p0);
+                a1 += w0 * (bf_hi(o0.x) - p1);
+                a2 += w0 * (bf_lo(o0.y) - p2);
+                a3 += w0 * (bf_hi(o0.y) - p3);
+            }
+            const float s = __ldg(g.s + i);
+            a0 *= s;
+            a1 *= s;
+            a2 *= s;
+            a3 *= s;
+        }
+        const uint2 packed = make_uint2(pack_bf2(a0, a1), pack_bf2(a2, a3));
+        *reinterpret_cast<uint2 *>(sA + core_off(r, koff + 4 * sub, K)) = packed;
+        if (msave) reinterpret_cast<uint2 *>(msave + i * 32)[sub] = packed;
+    }
+}
+
+}  // namespace
+
+// Layer l (0-based) of the message passing: h[l] -> h[l+1], then either the
+// next layer's projection phi[l+1] or (LAST) the decoder and the new state.
+template <bool LAST>
+__global__ void __launch_bounds__(128) k_sg_layer(Graph g, Acts a, const uint8_t *__restrict__ img,
+                                                  const float *__restrict__ theta, Layout L, int l,
+                                                  int train, int *err)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sA = sm + kSA, *sB1 = sm + kSB1, *sB2 = sm + kSB2;
+    float *sBias = reinterpret_cast<float *>(sm + kSBias);   // u | p or d1 | d2 (rounded)
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + kSTmem);
+    int *sOk = reinterpret_cast<int *>(sm + kSOk);
+    const uint32_t bar = smem_addr(sm + kSBar);
+    const int tid = threadIdx.x;
+    constexpr uint32_t N2 = LAST ? 64 : 32;
+    if (tid < 32) tc::tmem_alloc(sTmem, 128);
+    if (tid == 0) { mbar_init(bar, 1); mbar_fence_init(); }
+    copy_img(sB1, img + L.img_u[l], 64 * 96 * 2);
+    copy_img(sB2, img + (LAST ? L.img_d1 : L.img_p[l + 1]), N2 * 64 * 2);
+    if (tid < 64) sBias[tid] = theta[L.u[l] + tid];
+    if (tid < (int)N2) sBias[64 + tid] = theta[(LAST ? L.d1 : L.p[l + 1]) + tid];
+    if (LAST && tid < 64) sBias[128 + tid] = round_bf(theta[L.d2 + tid]);
+    const float d2b = LAST ? theta[L.d2b] : 0.f;
+    tc::fence_before();
+    tc::fence_smem_async();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *sTmem;
+    uint32_t phase = 0;
+    const uint32_t sa = smem_addr(sA), sb1 = smem_addr(sB1), sb2 = smem_addr(sB2);
+    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
+        const int64_t i = (int64_t)tile * 128 + tid;
+        const bool valid = i < g.n;
+        uint32_t hp[32];
+        const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[l] + i * 64);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint4 v = hs[q];
+            hp[4 * q] = v.x;
+            hp[4 * q + 1] = v.y;
+            hp[4 * q + 2] = v.z;
+            hp[4 * q + 3] = v.w;
+            st_row8(sA, tid, 8 * q, 96, v);
+        }
+        tile_messages(g, a.phi[l], (int64_t)tile * 128, sA, 96, 64, train ? a.m[l] : nullptr);
+        tc::fence_smem_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            tc::mma_bf16(tbase, sa, sb1, 96, 128, 64, false);
+            tc::commit(bar);
+        }
+        if (!cta_wait(bar, phase, sOk, err)) break;
+        phase ^= 1;
+        tc::fence_after();
+        // r = relu(U [h; m] + u), h' = h + r (rounded to bf16)
+        uint32_t rp[32];
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tc::ld16(tc::lane_addr(tbase, c0), v);
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                const float r0 = fmaxf(v[c] + sBias[c0 + c], 0.f);
+                const float r1 = fmaxf(v[c + 1] + sBias[c0 + c + 1], 0.f);
+                const uint32_t h2 = hp[(c0 + c) / 2];
+                rp[(c0 + c) / 2] = pack_bf2(r0, r1);
+                hp[(c0 + c) / 2] = valid ? pack_bf2(bf_lo(h2) + r0, bf_hi(h2) + r1) : 0u;
+            }
+        }
+        uint4 *hn = reinterpret_cast<uint4 *>(a.h[l + 1] + i * 64);
+        uint4 *rs = reinterpret_cast<uint4 *>(a.r[l] + i * 64);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint4 v = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+            hn[q] = v;
+            if (train)
+                rs[q] = valid ? make_uint4(rp[4 * q], rp[4 * q + 1], rp[4 * q + 2], rp[4 * q + 3])
+                              : make_uint4(0u, 0u, 0u, 0u);
+            st_row8(sA, tid, 8 * q, 64, v);
+        }
+        tc::fence_before();
+        tc::fence_smem_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            tc::mma_bf16(tbase + 64, sa, sb2, 64, 128, N2, false);
+            tc::commit(bar);
+        }
+        if (!cta_wait(bar, phase, sOk, err)) break;
+        phase ^= 1;
+        tc::fence_after();
+        if (!LAST) {
+            uint32_t pp[16];
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                float v[16];
+                tc::ld16(tc::lane_addr(tbase, 64 + c0), v);
+#pragma unroll
+                for (int c = 0; c < 16; c += 2)
+                    pp[(c0 + c) / 2] = valid ? pack_bf2(fmaxf(v[c] + sBias[64 + c0 + c], 0.f),
+                                                        fmaxf(v[c + 1] + sBias[64 + c0 + c + 1], 0.f))
+                                             : 0u;
+            }
+            uint4 *ps = reinterpret_cast<uint4 *>(a.phi[l + 1] + i * 32);
+#pragma unroll
+            for (int q = 0; q < 4; q++) ps[q] = make_uint4(pp[4 * q], pp[4 * q + 1], pp[4 * q + 2], pp[4 * q + 3]);
+        } else {
+            // decoder: z = relu(D1 h3 + d1), y = d2 . z + d2b, E' = E + C Y_S y
+            float y = d2b;
+            float4 *zs = reinterpret_cast<float4 *>(a.z + i * 64);
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float v[16];
+                tc::ld16(tc::lane_addr(tbase, 64 + c0), v);
+#pragma unroll
+                for (int c = 0; c < 16; c++) {
+                    v[c] = valid ? fmaxf(v[c] + sBias[64 + c0 + c], 0.f) : 0.f;
+                    y = fmaf(sBias[128 + c0 + c], v[c], y);
+                }
+                if (train) {
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        zs[c0 / 4 + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+            if (valid) {
+                if (train) a.y[i] = y;
+                a.E_out[i] = fmaf(g.C[i] * kYS, y, a.E_in[i]);
+            }
+        }
+        tc::fence_before();
+        __syncthreads();
+    }
+    __syncthreads();
+    tc::fence_after();
+    if (tid < 32) tc::tmem_free(tbase, 128);
+}
+
+// ---------------------------------------------------------------------------
+// Backward (training)
+// ---------------------------------------------------------------------------
+//
+// Weight gradients are sums over nodes, formed on the tensor cores as
+// transposed products: dW^T (inputs x outputs) = sum_n [in_n; 1]^T dout_n
+// with K = the tile's 128 nodes, the node inputs written transposed into a
+// 128-row operand (input channels, then a row of ones whose product is the
+// bias gradient, then zero rows) and the output gradients transposed into
+// the B operand.  Each persistent CTA accumulates its tiles in TMEM and
+// writes one partial per weight; k_sg_reduce_adam sums the partials in CTA
+// order (deterministic).
+
+namespace {
+
+__device__ __forceinline__ uint16_t bf_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ void st_T(uint8_t *s, uint32_t row, uint32_t col, uint32_t K, uint16_t v)
+{
+    *reinterpret_cast<uint16_t *>(s + core_off(row, col, K)) = v;
+}
+// zero `bytes` (multiple of 16) of shared memory with all threads
+__device__ __forceinline__ void zero_smem(uint8_t *s, uint32_t bytes)
+{
+    for (uint32_t o = threadIdx.x * 16; o < bytes; o += blockDim.x * 16)
+        *reinterpret_cast<uint4 *>(s + o) = make_uint4(0u, 0u, 0u, 0u);
+}
+// rows [r0, r0 + nr) of a TMEM accumulator (this thread's lane = row), ncols
+// columns -> dst[row * ncols + col]
+__device__ __forceinline__ void store_acc(uint32_t tbase, uint32_t col0, uint32_t ncols, int nr,
+                                          float *dst)
+{
+    const int row = threadIdx.x;
+    for (uint32_t c0 = 0; c0 < ncols; c0 += 16) {
+        float v[16];
+        tc::ld16(tc::lane_addr(tbase, col0 + c0), v);
+        if (row < nr)
+#pragma unroll
+            for (int c = 0; c < 16; c++) dst[row * ncols + c0 + c] = v[c];
+    }
+}
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Shared-memory plan of the backward kernels.
+constexpr uint32_t kBA1 = 0;                         // 128 x 64  node-major operand (dz / dpre)
+constexpr uint32_t kBB1 = kBA1 + 128 * 64 * 2;       // <= 96 x 64 weight image
+constexpr uint32_t kBA2 = kBB1 + 96 * 64 * 2;        // 128 x 128 transposed inputs [in; 1]
+constexpr uint32_t kBB2 = kBA2 + 128 * 128 * 2;      // 64 x 128 transposed output gradient
+constexpr uint32_t kBA3 = kBB2 + 64 * 128 * 2;       // 128 x 64  du
+constexpr uint32_t kBB3 = kBA3 + 128 * 64 * 2;       // 96 x 64   U^T image
+constexpr uint32_t kBA4 = kBB3 + 96 * 64 * 2;        // 128 x 128 transposed [h; m; 1]
+constexpr uint32_t kBB4 = kBA4 + 128 * 128 * 2;      // 64 x 128  du^T
+constexpr uint32_t kBVec = kBB4 + 64 * 128 * 2;      // 64 floats (d2 rounded) + reduction space
+constexpr uint32_t kBRed = kBVec + 64 * 4;           // 4 warps x 68 floats
+constexpr uint32_t kBBar = kBRed + 4 * 68 * 4;
+constexpr uint32_t kBTmem = kBBar + 8;
+constexpr uint32_t kBOk = kBTmem + 4;
+constexpr uint32_t kSmemBwd = kBOk + 4 + 16;
+
+// TMEM columns of the backward kernels (512 allocated, one CTA per SM)
+constexpr uint32_t kTdh = 0, kTacc1 = 64, kTdx = 128, kTacc2 = 256;
+
+// Layer lu's node-local backward from dL/dh_{lu+1} (FP32, registers dh[64]):
+// du = dh * (r > 0); dX = du U (tensor cores) -> dhdir = dh + dX[:, :64],
+// gm_out = s dX[:, 64:]; dU^T += [h; m; 1]^T du accumulated in kTacc2.
+// Writes the operands, issues both products, waits and finishes the
+// epilogue.  Returns false if a wait gave up.
+__device__ bool layer_back(const Graph &g, const Acts &a, const Grads &gr, float *gm_out, int lu,
+                           int64_t i, bool valid, const float (&dh)[64], uint8_t *sm, uint32_t tbase,
+                           uint32_t bar, uint32_t &phase, bool first, int *sOk, int *err)
+{
+    const int t = threadIdx.x;
+    uint8_t *sA3 = sm + kBA3, *sA4 = sm + kBA4, *sB4 = sm + kBB4;
+    const uint4 *rs = reinterpret_cast<const uint4 *>(a.r[lu] + i * 64);
+    const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[lu] + i * 64);
+    const uint4 *ms = reinterpret_cast<const uint4 *>(a.m[lu] + i * 32);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const uint4 rv = rs[q], hv = hs[q];
+        const uint32_t rw[4] = {rv.x, rv.y, rv.z, rv.w}, hw[4] = {hv.x, hv.y, hv.z, hv.w};
+        uint32_t du[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int c = 8 * q + 2 * e;
+            const float d0 = (valid && bf_lo(rw[e]) > 0.f) ? dh[c] : 0.f;
+            const float d1 = (valid && bf_hi(rw[e]) > 0.f) ? dh[c + 1] : 0.f;
+            du[e] = pack_bf2(d0, d1);
+            st_T(sB4, c, t, 128, (uint16_t)(du[e] & 0xFFFF));
+            st_T(sB4, c + 1, t, 128, (uint16_t)(du[e] >> 16));
+            st_T(sA4, c, t, 128, (uint16_t)(hw[e] & 0xFFFF));
+            st_T(sA4, c + 1, t, 128, (uint16_t)(hw[e] >> 16));
+        }
+        st_row8(sA3, t, 8 * q, 64, make_uint4(du[0], du[1], du[2], du[3]));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const uint4 mv = ms[q];
+        const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int c = 64 + 8 * q + 2 * e;
+            st_T(sA4, c, t, 128, (uint16_t)(mw[e] & 0xFFFF));
+            st_T(sA4, c + 1, t, 128, (uint16_t)(mw[e] >> 16));
+        }
+    }
+    st_T(sA4, 96, t, 128, valid ? bf_bits(1.f) : (uint16_t)0);
+    tc::fence_before();
+    tc::fence_smem_async();
+    __syncthreads();
+    if (t == 0) {
+        tc::fence_after();
+        tc::mma_bf16(tbase + kTdx, smem_addr(sA3), smem_addr(sm + kBB3), 64, 128, 96, false);
+        tc::mma_bf16(tbase + kTacc2, smem_addr(sA4), smem_addr(sB4), 128, 128, 64, !first);
+        tc::commit(bar);
+    }
+    if (!cta_wait(bar, phase, sOk, err)) return false;
+    phase ^= 1;
+    tc::fence_after();
+    float4 *dd = reinterpret_cast<float4 *>(gr.dhdir + i * 64);
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        tc::ld16(tc::lane_addr(tbase, kTdx + c0), v);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            dd[c0 / 4 + q] = valid ? make_float4(dh[c0 + 4 * q] + v[4 * q], dh[c0 + 4 * q + 1] + v[4 * q + 1],
+                                                 dh[c0 + 4 * q + 2] + v[4 * q + 2],
+                                                 dh[c0 + 4 * q + 3] + v[4 * q + 3])
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float s = valid ? g.s[i] : 0.f;
+    float4 *gs = reinterpret_cast<float4 *>(gm_out + i * 32);
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += 16) {
+        float v[16];
+        tc::ld16(tc::lane_addr(tbase, kTdx + 64 + c0), v);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            gs[c0 / 4 + q] = make_float4(s * v[4 * q], s * v[4 * q + 1], s * v[4 * q + 2], s * v[4 * q + 3]);
+    }
+    tc::fence_before();
+    return true;
+}
+
+}  // namespace
+
+// Loss and the decoder's backward pass, then layer 3's node-local backward.
+//   y* = (E* - E) / (C Y_S), loss = mean (y - y*)^2, dy = 2 (y - y*) / n,
+//   dd2 = sum dy z, dd2b = sum dy, dz = dy d2 (z > 0),
+//   dD1^T += [h3; 1]^T dz, dh3 = dz D1.
+__global__ void __launch_bounds__(128) k_sg_bwd_head(Graph g, Acts a, Grads gr, float *gm_out,
+                                                     const uint8_t *__restrict__ img,
+                                                     const float *__restrict__ theta, Layout L,
+                                                     int *err)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sA1 = sm + kBA1, *sB1 = sm + kBB1, *sA2 = sm + kBA2, *sB2 = sm + kBB2;
+    float *sD2 = reinterpret_cast<float *>(sm + kBVec);
+    float *sRed = reinterpret_cast<float *>(sm + kBRed);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + kBTmem);
+    int *sOk = reinterpret_cast<int *>(sm + kBOk);
+    const uint32_t bar = smem_addr(sm + kBBar);
+    const int t = threadIdx.x;
+    const int lu = kLayers - 1;
+    if (t < 32) tc::tmem_alloc(sTmem, 512);
+    if (t == 0) { mbar_init(bar, 1); mbar_fence_init(); }
+    zero_smem(sA2, 128 * 128 * 2);
+    zero_smem(sm + kBA4, 128 * 128 * 2);
+    copy_img(sB1, img + L.img_d1t, 64 * 64 * 2);
+    copy_img(sm + kBB3, img + L.img_ut[lu], 96 * 64 * 2);
+    if (t < 64) sD2[t] = round_bf(theta[L.d2 + t]);
+    tc::fence_before();
+    tc::fence_smem_async();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *sTmem;
+    uint32_t phase = 0;
+    float acc_d2[64];
+#pragma unroll
+    for (int c = 0; c < 64; c++) acc_d2[c] = 0.f;
+    float acc_d2b = 0.f;
+    double loss = 0.0;
+    bool first = true, ok = true;
+    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
+        const int64_t i = (int64_t)tile * 128 + t;
+        const bool valid = i < g.n;
+        float dy = 0.f;
+        if (valid) {
+            const float ys = (gr.E_star[i] - a.E_in[i]) / (g.C[i] * kYS);
+            const float d = a.y[i] - ys;
+            loss += (double)d * (double)d;
+            dy = 2.f * d * gr.inv_n;
+        }
+        acc_d2b += dy;
+        const float4 *zs = reinterpret_cast<const float4 *>(a.z + i * 64);
+        const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[kLayers] + i * 64);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float4 z0 = zs[2 * q], z1 = zs[2 * q + 1];
+            const float zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+            uint32_t dz[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int c = 8 * q + 2 * e;
+                acc_d2[c] = fmaf(dy, zv[2 * e], acc_d2[c]);
+                acc_d2[c + 1] = fmaf(dy, zv[2 * e + 1], acc_d2[c + 1]);
+                const float d0 = zv[2 * e] > 0.f ? dy * sD2[c] : 0.f;
+                const float d1 = zv[2 * e + 1] > 0.f ? dy * sD2[c + 1] : 0.f;
+                dz[e] = pack_bf2(d0, d1);
+                st_T(sB2, c, t, 128, (uint16_t)(dz[e] & 0xFFFF));
+                st_T(sB2, c + 1, t, 128, (uint16_t)(dz[e] >> 16));
+            }
+            st_row8(sA1, t, 8 * q, 64, make_uint4(dz[0], dz[1], dz[2], dz[3]));
+            const uint4 hv = hs[q];
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                st_T(sA2, 8 * q + 2 * e, t, 128, (uint16_t)(hw[e] & 0xFFFF));
+                st_T(sA2, 8 * q + 2 * e + 1, t, 128, (uint16_t)(hw[e] >> 16));
+            }
+        }
+        st_T(sA2, 64, t, 128, valid ? bf_bits(1.f) : (uint16_t)0);
+        tc::fence_smem_async();
+        __syncthreads();
+        if (t == 0) {
+            tc::fence_after();
+            tc::mma_bf16(tbase + kTdh, smem_addr(sA1), smem_addr(sB1), 64, 128, 64, false);
+            tc::mma_bf16(tbase + kTacc1, smem_addr(sA2), smem_addr(sB2), 128, 128, 64, !first);
+            tc::commit(bar);
+        }
+        if (!cta_wait(bar, phase, sOk, err)) { ok = false; break; }
+        phase ^= 1;
+        tc::fence_after();
+        float dh[64];
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tc::ld16(tc::lane_addr(tbase, kTdh + c0), v);
+#pragma unroll
+            for (int c = 0; c < 16; c++) dh[c0 + c] = v[c];
+        }
+        if (!layer_back(g, a, gr, gm_out, lu, i, valid, dh, sm, tbase, bar, phase, first, sOk, err)) {
+            ok = false;
+            break;
+        }
+        first = false;
+        __syncthreads();
+    }
+    // partials of this CTA
+    float *part = gr.partial + (size_t)blockIdx.x * kPartFloats;
+    __syncthreads();
+    tc::fence_after();
+    if (ok) {
+        if (first) {   // no tile: zero partials
+            for (int q = t; q < kPartD1; q += 128) part[kPartD1Off + q] = 0.f;
+            for (int q = t; q < kPartU; q += 128) part[part_U(lu) + q] = 0.f;
+        } else {
+            store_acc(tbase, kTacc1, 64, 65, part + kPartD1Off);
+            store_acc(tbase, kTacc2, 64, 97, part + part_U(lu));
+        }
+    }
+    const int warp = t >> 5, lane = t & 31;
+#pragma unroll
+    for (int c = 0; c < 64; c++) {
+        const float v = warp_sum_f(acc_d2[c]);
+        if (lane == 0) sRed[warp * 68 + c] = v;
+    }
+    {
+        const float v = warp_sum_f(acc_d2b);
+        if (lane == 0) sRed[warp * 68 + 64] = v;
+    }
+    double lw = loss;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lw += __shfl_xor_sync(0xffffffffu, lw, o);
+    __syncthreads();
+    if (t < 65) part[kPartd2Off + t] = sRed[t] + sRed[68 + t] + sRed[136 + t] + sRed[204 + t];
+    __syncthreads();
+    double *sL = reinterpret_cast<double *>(sRed);
+    if (lane == 0) sL[warp] = lw;
+    __syncthreads();
+    if (t == 0) gr.loss_part[blockIdx.x] = sL[0] + sL[1] + sL[2] + sL[3];
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (t < 32) tc::tmem_free(tbase, 512);
+}
+
+// Backward of layer l's message and projection, then layer l-1's node-local
+// backward (l >= 1) or the encoder's (l == 0):
+//   dphi_j = sum_i W_ji (gm_i - gm_j)      (adjoint of m = s L phi, W symmetric)
+//   dpre = dphi (phi > 0);  dP_l^T += [h_l; 1]^T dpre;  dh_l = dhdir + dpre P_l
+__global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr, const float *gm_in,
+                                                    float *gm_out, const uint8_t *__restrict__ img,
+                                                    Layout L, int l, int *err)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sA1 = sm + kBA1, *sB1 = sm + kBB1, *sA2 = sm + kBA2, *sB2 = sm + kBB2;
+    uint8_t *sA4 = sm + kBA4, *sB4 = sm + kBB4;
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + kBTmem);
+    int *sOk = reinterpret_cast<int *>(sm + kBOk);
+    const uint32_t bar = smem_addr(sm + kBBar);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int grp = lane >> 3, sub = lane & 7;
+    if (t < 32) tc::tmem_alloc(sTmem, 512);
+    if (t == 0) { mbar_init(bar, 1); mbar_fence_init(); }
+    zero_smem(sA2, 128 * 128 * 2);
+    zero_smem(sA4, 128 * 128 * 2);
+    copy_img(sB1, img + L.img_pt[l], 64 * 32 * 2);
+    if (l >= 1) copy_img(sm + kBB3, img + L.img_ut[l - 1], 96 * 64 * 2);
+    tc::fence_before();
+    tc::fence_smem_async();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *sTmem;
+    uint32_t phase = 0;
+    bool first = true, ok = true;
+    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
+        const int64_t tile0 = (int64_t)tile * 128;
+        // adjoint message sums: 8 lanes per node, 4 channels per lane
+#pragma unroll 1
+        for (int rr = 0; rr < 8; rr++) {
+            const int r = warp * 32 + rr * 4 + grp;
+            const int64_t j = tile0 + r;
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            if (j < g.n) {
+                const float4 me = __ldg(reinterpret_cast<const float4 *>(gm_in + j * 32) + sub);
+                const int k1 = __ldg(g.rowptr + j + 1);
+                for (int k = __ldg(g.rowptr + j); k < k1; k++) {
+                    const int ii = __ldg(g.col + k);
+                    const float w = __ldg(g.w + k);
+                    const float4 o = __ldg(reinterpret_cast<const float4 *>(gm_in + (int64_t)ii * 32) + sub);
+                    d[0] += w * (o.x - me.x);
+                    d[1] += w * (o.y - me.y);
+                    d[2] += w * (o.z - me.z);
+                    d[3] += w * (o.w - me.w);
+                }
+                const uint2 ph = __ldg(reinterpret_cast<const uint2 *>(a.phi[l] + j * 32) + sub);
+                if (!(bf_lo(ph.x) > 0.f)) d[0] = 0.f;
+                if (!(bf_hi(ph.x) > 0.f)) d[1] = 0.f;
+                if (!(bf_lo(ph.y) > 0.f)) d[2] = 0.f;
+                if (!(bf_hi(ph.y) > 0.f)) d[3] = 0.f;
+            }
+            const uint32_t q0 = pack_bf2(d[0], d[1]), q1 = pack_bf2(d[2], d[3]);
+            *reinterpret_cast<uint2 *>(sA1 + core_off(r, 4 * sub, 32)) = make_uint2(q0, q1);
+            st_T(sB2, 4 * sub, r, 128, (uint16_t)(q0 & 0xFFFF));
+            st_T(sB2, 4 * sub + 1, r, 128, (uint16_t)(q0 >> 16));
+            st_T(sB2, 4 * sub + 2, r, 128, (uint16_t)(q1 & 0xFFFF));
+            st_T(sB2, 4 * sub + 3, r, 128, (uint16_t)(q1 >> 16));
+        }
+        const int64_t i = tile0 + t;
+        const bool valid = i < g.n;
+        const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[l] + i * 64);
+        uint32_t hw[32];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint4 hv = hs[q];
+            hw[4 * q] = hv.x;
+            hw[4 * q + 1] = hv.y;
+            hw[4 * q + 2] = hv.z;
+            hw[4 * q + 3] = hv.w;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                st_T(sA2, 8 * q + 2 * e, t, 128, (uint16_t)(hw[4 * q + e] & 0xFFFF));
+                st_T(sA2, 8 * q + 2 * e + 1, t, 128, (uint16_t)(hw[4 * q + e] >> 16));
+            }
+        }
+        st_T(sA2, 64, t, 128, valid ? bf_bits(1.f) : (uint16_t)0);
+        tc::fence_smem_async();
+        __syncthreads();
+        if (t == 0) {
+            tc::fence_after();
+            tc::mma_bf16(tbase + kTdh, smem_addr(sA1), smem_addr(sB1), 32, 128, 64, false);
+            tc::mma_bf16(tbase + kTacc1, smem_addr(sA2), smem_addr(sB2), 128, 128, 32, !first);
+            tc::commit(bar);
+        }
+        if (!cta_wait(bar, phase, sOk, err)) { ok = false; break; }
+        phase ^= 1;
+        tc::fence_after();
+        float dh[64];
+        const float4 *dd = reinterpret_cast<const float4 *>(gr.dhdir + i * 64);
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tc::ld16(tc::lane_addr(tbase, kTdh + c0), v);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float4 b = dd[c0 / 4 + q];
+                dh[c0 + 4 * q] = b.x + v[4 * q];
+                dh[c0 + 4 * q + 1] = b.y + v[4 * q + 1];
+                dh[c0 + 4 * q + 2] = b.z + v[4 * q + 2];
+                dh[c0 + 4 * q + 3] = b.w + v[4 * q + 3];
+            }
+        }
+        if (l >= 1) {
+            if (!layer_back(g, a, gr, gm_out, l - 1, i, valid, dh, sm, tbase, bar, phase, first, sOk, err)) {
+                ok = false;
+                break;
+            }
+        } else {
+            // encoder: d0 = dh0 (h0 > 0);  dW_in^T += [x; 1]^T d0
+            const uint4 *xs = reinterpret_cast<const uint4 *>(a.x + i * 16);
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const uint4 xv = xs[q];
+                const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    st_T(sA4, 8 * q + 2 * e, t, 128, (uint16_t)(xw[e] & 0xFFFF));
+                    st_T(sA4, 8 * q + 2 * e + 1, t, 128, (uint16_t)(xw[e] >> 16));
+                }
+            }
+            st_T(sA4, 16, t, 128, valid ? bf_bits(1.f) : (uint16_t)0);
+#pragma unroll
+            for (int c = 0; c < 64; c += 2) {
+                const uint32_t h2 = hw[c / 2];
+                const float d0 = (valid && bf_lo(h2) > 0.f) ? dh[c] : 0.f;
+                const float d1 = (valid && bf_hi(h2) > 0.f) ? dh[c + 1] : 0.f;
+                const uint32_t q = pack_bf2(d0, d1);
+                st_T(sB4, c, t, 128, (uint16_t)(q & 0xFFFF));
+                st_T(sB4, c + 1, t, 128, (uint16_t)(q >> 16));
+            }
+            tc::fence_before();
+            tc::fence_smem_async();
+            __syncthreads();
+            if (t == 0) {
+                tc::fence_after();
+                tc::mma_bf16(tbase + kTacc2, smem_addr(sA4), smem_addr(sB4), 128, 128, 64, !first);
+                tc::commit(bar);
+            }
+            if (!cta_wait(bar, phase, sOk, err)) { ok = false; break; }
+            phase ^= 1;
+            tc::fence_after();
+        }
+        first = false;
+        tc::fence_before();
+        __syncthreads();
+    }
+    float *part = gr.partial + (size_t)blockIdx.x * kPartFloats;
+    __syncthreads();
+    tc::fence_after();
+    if (ok) {
+        float *p1 = part + part_P(l);
+        float *p2 = l >= 1 ? part + part_U(l - 1) : part + kPartWinOff;
+        const int n2 = l >= 1 ? kPartU : kPartWin;
+        if (first) {
+            for (int q = t; q < kPartP; q += 128) p1[q] = 0.f;
+            for (int q = t; q < n2; q += 128) p2[q] = 0.f;
+        } else {
+            store_acc(tbase, kTacc1, 32, 65, p1);
+            store_acc(tbase, kTacc2, 64, l >= 1 ? 97 : 17, p2);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (t < 32) tc::tmem_free(tbase, 512);
+}
+
+namespace {
+
+// Where parameter q's gradient sits in a CTA's partial (see Grads).
+__device__ __forceinline__ int partial_index(int q)
+{
+    if (q < kOffBin) { const int o = q / kNF, in = q % kNF; return kPartWinOff + in * 64 + o; }
+    if (q < kLayerBase) return kPartWinOff + kNF * 64 + (q - kOffBin);
+    if (q < kOffD1) {
+        const int l = (q - kLayerBase) / kLayerSize;
+        const int r = q - layer_P(l);
+        if (r < kMSG * kHID) { const int o = r / kHID, in = r % kHID; return part_P(l) + in * kMSG + o; }
+        if (r < kMSG * kHID + kMSG) return part_P(l) + kHID * kMSG + (r - kMSG * kHID);
+        const int r2 = q - layer_U(l);
+        if (r2 < kHID * (kHID + kMSG)) {
+            const int o = r2 / (kHID + kMSG), in = r2 % (kHID + kMSG);
+            return part_U(l) + in * 64 + o;
+        }
+        return part_U(l) + (kHID + kMSG) * 64 + (q - layer_u(l));
+    }
+    if (q < kOffd1) { const int o = (q - kOffD1) / kHID, in = (q - kOffD1) % kHID; return kPartD1Off + in * 64 + o; }
+    if (q < kOffd2) return kPartD1Off + kHID * 64 + (q - kOffd1);
+    return kPartd2Off + (q - kOffd2);   // d2 [64], then d2b
+}
+
+}  // namespace
+
+// Sum the per-CTA partials in CTA order into the gradient, then one Adam
+// step (Kingma and Ba, 2015) on the FP32 master weights: m = b1 m + (1-b1) g,
+// v = b2 v + (1-b2) g^2, theta -= lr (m / bc1) / (sqrt(v / bc2) + eps) with
+// bc1 = 1 - b1^t, bc2 = 1 - b2^t.  lr == 0 leaves theta, m, v unchanged
+// (gradient only).  The loss (mean squared error) lands in *loss.
+__global__ void k_sg_reduce_adam(const float *__restrict__ partial, const double *__restrict__ loss_part,
+                                 int n_parts, float *__restrict__ grad, float *__restrict__ theta,
+                                 float *__restrict__ mom, float *__restrict__ vel, AdamArgs ad,
+                                 double *loss)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0) {
+        double s = 0.0;
+        for (int b = 0; b < n_parts; b++) s += loss_part[b];
+        *loss = s * (double)ad.inv_n;
+    }
+    if (q >= kNParams) return;
+    const int pi = partial_index(q);
+    float gsum = 0.f;
+    for (int b = 0; b < n_parts; b++) gsum += partial[(size_t)b * kPartFloats + pi];
+    grad[q] = gsum;
+    if (ad.lr == 0.f) return;
+    // every operation rounded on its own (no contraction into FMAs)
+    const float m = __fadd_rn(__fmul_rn(ad.b1, mom[q]), __fmul_rn(ad.omb1, gsum));
+    const float v = __fadd_rn(__fmul_rn(ad.b2, vel[q]), __fmul_rn(__fmul_rn(ad.omb2, gsum), gsum));
+    mom[q] = m;
+    vel[q] = v;
+    const float mh = __fdiv_rn(m, ad.bc1), vh = __fdiv_rn(v, ad.bc2);
+    theta[q] = __fsub_rn(theta[q], __fdiv_rn(__fmul_rn(ad.lr, mh), __fadd_rn(__fsqrt_rn(vh), ad.eps)));
+}
+
+// State transfer between the mesh's block layout and the surrogate order.
+__global__ void k_sg_gather(StateView<float> v, const int32_t *__restrict__ int_id, int32_t n,
+                            float *__restrict__ E)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) E[i] = v.E(int_id[i]);
+}
+__global__ void k_sg_scatter(StateView<float> v, const int32_t *__restrict__ int_id, int32_t n,
+                             const float *__restrict__ E)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v.E(int_id[i]) = E[i];
+}
+
+}  // namespace sg
+}  // namespace fem
+
+// ===========================================================================
+// Host side and C ABI
+// ===========================================================================
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "fem.h"
+
+using namespace fem;
+using namespace fem::sg;
+
+struct fem_surrogate {
+    fem_mesh *mesh = nullptr;
+    int device = -1, n_sm = 0;
+    int32_t n = 0, n_tiles = 0;
+    int64_t nnz = 0;
+    std::vector<int32_t> caller_of;   // surrogate position -> caller node
+    double dt = 0.0;                  // plain mesh: the step the graph was built for
+    std::vector<void *> bufs;
+    Graph g{};
+    Acts a{};
+    Layout L{};
+    ImgTable tab{};
+    uint32_t img_bytes = 0;
+    int32_t *int_id = nullptr;        // internal node of each surrogate position
+    float *E0 = nullptr, *E1 = nullptr;
+    float *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr;
+    uint8_t *img = nullptr;
+    int *err = nullptr;
+    bool train_ok = false;            // training buffers allocated
+    float *dhdir = nullptr, *gm[2] = {nullptr, nullptr}, *partial = nullptr;
+    double *loss_part = nullptr, *loss = nullptr;
+    int64_t adam_t = 0;
+    bool have_params = false;
+};
+
+namespace {
+
+fem_status sfail(fem_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+fem_status sfail(fem_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    fem::set_last_error(buf);
+    return st;
+}
+fem_status sok()
+{
+    fem::set_last_error("");
+    return FEM_OK;
+}
+
+#define SCU(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return sfail(e_ == cudaErrorMemoryAllocation ? FEM_ENOMEM : FEM_ECUDA,          \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+    } while (0)
+
+template <typename T>
+fem_status salloc(fem_surrogate *s, T **p, size_t count)
+{
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16) + 256;
+    SCU(cudaMalloc(&q, bytes));
+    s->bufs.push_back(q);
+    SCU(cudaMemset(q, 0, bytes));
+    *p = (T *)q;
+    return FEM_OK;
+}
+
+template <typename T>
+fem_status supload(fem_surrogate *s, T **p, const std::vector<T> &h, size_t count)
+{
+    fem_status st = salloc(s, p, count);
+    if (st) return st;
+    if (!h.empty()) SCU(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FEM_OK;
+}
+
+void release(fem_surrogate *s)
+{
+    for (void *p : s->bufs) cudaFree(p);
+    s->bufs.clear();
+}
+
+// Recursive coordinate bisection of the nodes idx[lo, hi) into runs whose
+// lengths are multiples of 128 (the last run of the whole order excepted):
+// the left part takes 128 * ceil(n / 256) nodes along the longest axis.
+void rcb_nodes(const double *xyz, std::vector<int32_t> &idx, int64_t lo, int64_t hi)
+{
+    while (hi - lo > kTile) {
+        double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+        for (int64_t k = lo; k < hi; k++)
+            for (int d = 0; d < 3; d++) {
+                mn[d] = std::min(mn[d], xyz[3 * (size_t)idx[(size_t)k] + d]);
+                mx[d] = std::max(mx[d], xyz[3 * (size_t)idx[(size_t)k] + d]);
+            }
+        int ax = 0;
+        for (int d = 1; d < 3; d++)
+            if (mx[d] - mn[d] > mx[ax] - mn[ax]) ax = d;
+        const int64_t left = (int64_t)kTile * ((hi - lo + 2 * kTile - 1) / (2 * kTile));
+        const int64_t mid = lo + std::min(left, hi - lo);
+        std::nth_element(idx.begin() + lo, idx.begin() + mid, idx.begin() + hi, [&](int32_t p, int32_t q) {
+            const double a = xyz[3 * (size_t)p + ax], b = xyz[3 * (size_t)q + ax];
+            return a < b || (a == b && p < q);
+        });
+        if (mid >= hi) return;
+        rcb_nodes(xyz, idx, lo, mid);
+        lo = mid;
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// Image table and vector offsets of the parameter layout.
+void build_layout(fem_surrogate *s)
+{
+    ImgTable &t = s->tab;
+    t.n = 0;
+    uint32_t bytes = 0;
+    auto add = [&](uint32_t off, uint32_t sr, uint32_t sc, uint32_t rows, uint32_t cols, bool tr) {
+        ImgEntry e{off, sr, sc, rows, cols, tr ? 1u : 0u, bytes, 0u};
+        t.e[t.n++] = e;
+        const uint32_t at = bytes;
+        bytes += rows * cols * 2;
+        bytes = (bytes + 127) & ~127u;
+        return at;
+    };
+    Layout &L = s->L;
+    L.img_win = add(kOffWin, kHID, kNF, kHID, kNF, false);
+    for (int l = 0; l < kLayers; l++) {
+        L.img_p[l] = add(layer_P(l), kMSG, kHID, kMSG, kHID, false);
+        L.img_u[l] = add(layer_U(l), kHID, kHID + kMSG, kHID, kHID + kMSG, false);
+        L.img_pt[l] = add(layer_P(l), kMSG, kHID, kHID, kMSG, true);
+        L.img_ut[l] = add(layer_U(l), kHID, kHID + kMSG, kHID + kMSG, kHID, true);
+    }
+    L.img_d1 = add(kOffD1, kHID, kHID, kHID, kHID, false);
+    L.img_d1t = add(kOffD1, kHID, kHID, kHID, kHID, true);
+    s->img_bytes = bytes;
+    L.b_in = kOffBin;
+    for (int l = 0; l < kLayers; l++) {
+        L.p[l] = layer_p(l);
+        L.u[l] = layer_u(l);
+    }
+    L.d1 = kOffd1;
+    L.d2 = kOffd2;
+    L.d2b = kOffd2b;
+}
+
+fem_status build_graph(fem_surrogate *s, const SurrogateMeshView &v, const std::vector<double> &dt_node)
+{
+    const int64_t N = v.N, E = v.E;
+    if (N > INT32_MAX / 2) return sfail(FEM_EINVAL, "too many nodes for the surrogate");
+    // node order: recursive coordinate bisection per instance
+    std::vector<int32_t> &ord = s->caller_of;
+    ord.resize((size_t)N);
+    std::iota(ord.begin(), ord.end(), 0);
+    if (v.n_inst > 0) {
+        for (int32_t k = 0; k < v.n_inst; k++) rcb_nodes(v.xyz, ord, v.inst_node[k], v.inst_node[k + 1]);
+    } else {
+        rcb_nodes(v.xyz, ord, 0, N);
+    }
+    std::vector<int32_t> pos((size_t)N);
+    for (int64_t k = 0; k < N; k++) pos[(size_t)ord[(size_t)k]] = (int32_t)k;
+    // node -> incident tets (caller ids)
+    std::vector<int64_t> nt_ptr((size_t)N + 1, 0);
+    for (int64_t e = 0; e < E; e++)
+        for (int c = 0; c < 4; c++) nt_ptr[(size_t)v.tets[4 * e + c] + 1]++;
+    for (int64_t i = 0; i < N; i++) nt_ptr[(size_t)i + 1] += nt_ptr[(size_t)i];
+    std::vector<int32_t> nt((size_t)nt_ptr[(size_t)N]);
+    {
+        std::vector<int64_t> fill(nt_ptr.begin(), nt_ptr.end() - 1);
+        for (int64_t e = 0; e < E; e++)
+            for (int c = 0; c < 4; c++) nt[(size_t)fill[(size_t)v.tets[4 * e + c]]++] = (int32_t)e;
+    }
+    static const int kPairIdx[4][4] = {{-1, 0, 1, 2}, {0, -1, 3, 4}, {1, 3, -1, 5}, {2, 4, 5, -1}};
+    // assembled W_ij per surrogate row, columns in surrogate order, ascending
+    std::vector<int32_t> rowptr((size_t)N + 1, 0), col;
+    std::vector<float> w, wsum((size_t)N);
+    col.reserve((size_t)N * 15);
+    w.reserve((size_t)N * 15);
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t k = 0; k < N; k++) {
+        const int32_t i = ord[(size_t)k];
+        row.clear();
+        for (int64_t q = nt_ptr[(size_t)i]; q < nt_ptr[(size_t)i + 1]; q++) {
+            const int64_t e = nt[(size_t)q];
+            const int32_t *t = v.tets + 4 * e;
+            int a = 0;
+            while (t[a] != i) a++;
+            for (int b = 0; b < 4; b++) {
+                if (b == a) continue;
+                const double wab = v.w[6 * e + kPairIdx[a][b]];
+                const int32_t j = pos[(size_t)t[b]];
+                bool found = false;
+                for (auto &pr : row)
+                    if (pr.first == j) { pr.second += wab; found = true; break; }
+                if (!found) row.emplace_back(j, wab);
+            }
+        }
+        std::sort(row.begin(), row.end());
+        double ws = 0.0;
+        for (auto &pr : row) {
+            col.push_back(pr.first);
+            const float wf = (float)pr.second;
+            w.push_back(wf);
+            ws += (double)wf;
+        }
+        wsum[(size_t)k] = (float)ws;
+        rowptr[(size_t)k + 1] = (int32_t)col.size();
+    }
+    s->nnz = (int64_t)col.size();
+    // node data in surrogate order
+    const int64_t rows = (int64_t)s->n_tiles * kTile;
+    std::vector<float> C((size_t)rows, 1.f), Lc((size_t)rows, 0.f), sv((size_t)rows, 0.f),
+        hA((size_t)rows, 0.f), gg((size_t)rows, 0.f);
+    std::vector<uint8_t> ph((size_t)rows, 0);
+    std::vector<int32_t> iid((size_t)N);
+    std::vector<double> hA_c((size_t)N, 0.0), g_c((size_t)N, 0.0);
+    for (int64_t f = 0; f < v.F_rb; f++)
+        for (int c = 0; c < 3; c++) {
+            const int32_t nd = v.rb_faces[3 * f + c];
+            hA_c[(size_t)nd] += 4.0 * v.rb_fa[f];   // h A / 3 = 4 (h A / 12)
+            g_c[(size_t)nd] += v.rb_fg[f];
+        }
+    for (int64_t k = 0; k < N; k++) {
+        const int32_t i = ord[(size_t)k];
+        C[(size_t)k] = (float)v.C[i];
+        Lc[(size_t)k] = (float)v.Lc[i];
+        sv[(size_t)k] = (float)(dt_node[(size_t)i] / v.C[i]);
+        hA[(size_t)k] = (float)hA_c[(size_t)i];
+        gg[(size_t)k] = (float)g_c[(size_t)i];
+        ph[(size_t)k] = v.rng_id[i];
+        iid[(size_t)k] = v.node_new[i];
+    }
+    std::vector<float> rg(v.ranges, v.ranges + 2 * v.n_ranges);
+    std::vector<float> rgf(rg.begin(), rg.end());
+    fem_status st;
+    int32_t *d_rowptr, *d_col;
+    float *d_w, *d_wsum, *d_s, *d_C, *d_Lc, *d_hA, *d_g, *d_rg;
+    uint8_t *d_ph;
+    if ((st = supload(s, &d_rowptr, rowptr, rowptr.size()))) return st;
+    if ((st = supload(s, &d_col, col, col.size()))) return st;
+    if ((st = supload(s, &d_w, w, w.size()))) return st;
+    if ((st = supload(s, &d_wsum, wsum, (size_t)rows))) return st;
+    if ((st = supload(s, &d_s, sv, (size_t)rows))) return st;
+    if ((st = supload(s, &d_C, C, (size_t)rows))) return st;
+    if ((st = supload(s, &d_Lc, Lc, (size_t)rows))) return st;
+    if ((st = supload(s, &d_hA, hA, (size_t)rows))) return st;
+    if ((st = supload(s, &d_g, gg, (size_t)rows))) return st;
+    if ((st = supload(s, &d_rg, rgf, rgf.size()))) return st;
+    if ((st = supload(s, &d_ph, ph, (size_t)rows))) return st;
+    if ((st = supload(s, &s->int_id, iid, (size_t)N))) return st;
+    Graph &g = s->g;
+    g.n = (int32_t)N;
+    g.n_tiles = s->n_tiles;
+    g.rowptr = d_rowptr;
+    g.col = d_col;
+    g.w = d_w;
+    g.wsum = d_wsum;
+    g.s = d_s;
+    g.C = d_C;
+    g.Lc = d_Lc;
+    g.ph = d_ph;
+    g.ranges = d_rg;
+    g.hA = d_hA;
+    g.g = d_g;
+    return FEM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+fem_status launch_check(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sfail(FEM_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return FEM_OK;
+}
+
+int fwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, 4 * s->n_sm)); }
+int bwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->n_sm)); }
+
+// Forward pass from E_in (device, surrogate order) into E_out.
+fem_status forward(fem_surrogate *s, const float *E_in, float *E_out, bool train, cudaStream_t st)
+{
+    Acts a = s->a;
+    a.E_in = E_in;
+    a.E_out = E_out;
+    k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(E_in, s->g, a.tf);
+    k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, train ? 1 : 0, s->err);
+    for (int l = 0; l < kLayers - 1; l++)
+        k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l,
+                                                              train ? 1 : 0, s->err);
+    k_sg_layer<true><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, kLayers - 1,
+                                                         train ? 1 : 0, s->err);
+    return launch_check("surrogate forward");
+}
+
+fem_status pack(fem_surrogate *s, cudaStream_t st)
+{
+    k_sg_pack<<<dim3(8, s->tab.n), 256, 0, st>>>(s->theta, s->img, s->tab);
+    return launch_check("parameter packing");
+}
+
+fem_status ensure_train(fem_surrogate *s)
+{
+    if (s->train_ok) return FEM_OK;
+    const size_t rows = (size_t)s->n_tiles * kTile;
+    fem_status st;
+    if ((st = salloc(s, &s->dhdir, rows * 64))) return st;
+    if ((st = salloc(s, &s->gm[0], rows * 32))) return st;
+    if ((st = salloc(s, &s->gm[1], rows * 32))) return st;
+    if ((st = salloc(s, &s->partial, (size_t)s->n_sm * kPartFloats))) return st;
+    if ((st = salloc(s, &s->loss_part, (size_t)s->n_sm))) return st;
+    if ((st = salloc(s, &s->loss, 1))) return st;
+    s->train_ok = true;
+    return FEM_OK;
+}
+
+fem_status check_err(fem_surrogate *s, cudaStream_t st)
+{
+    int flag = 0;
+    SCU(cudaMemcpyAsync(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCU(cudaStreamSynchronize(st));
+    if (flag) {
+        SCU(cudaMemsetAsync(s->err, 0, sizeof(int), st));
+        return sfail(FEM_ETIMEOUT, "a bounded tensor-core wait of the surrogate gave up");
+    }
+    return FEM_OK;
+}
+
+fem_status mesh_stream(fem_surrogate *s, StateView<float> *v, cudaStream_t *st)
+{
+    void *stream = nullptr;
+    int dev = -1;
+    int r = surrogate_mesh_device(s->mesh, v, &stream, &dev);
+    if (r) return (fem_status)r;
+    if (dev != s->device) return sfail(FEM_ESTATE, "the mesh moved to another device");
+    SCU(cudaSetDevice(s->device));
+    *st = (cudaStream_t)stream;
+    return FEM_OK;
+}
+
+}  // namespace
+
+extern "C" fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate **out)
+{
+    if (!m || !out) return sfail(FEM_EINVAL, "NULL argument");
+    *out = nullptr;
+    SurrogateMeshView v{};
+    int r = surrogate_mesh_view(m, &v);
+    if (r) return (fem_status)r;
+    if (v.prec != FEM_FP32 || v.variant != FEM_VARIANT_BLOCK || v.formulation != FEM_ENTHALPY)
+        return sfail(FEM_EINVAL, "the surrogate needs an FP32 block-variant mesh in the enthalpy formulation");
+    if (v.has_kt || v.has_dir || v.F_if > 0)
+        return sfail(FEM_EINVAL, "the surrogate covers constant conductivity, Robin faces only "
+                                 "(no Dirichlet nodes, no interface faces)");
+    if (v.n_inst == 0 && !(dt > 0.0 && std::isfinite(dt)))
+        return sfail(FEM_EINVAL, "dt must be positive and finite");
+    std::vector<double> dt_node((size_t)v.N, dt);
+    if (v.n_inst > 0)
+        for (int32_t k = 0; k < v.n_inst; k++)
+            for (int64_t i = v.inst_node[k]; i < v.inst_node[k + 1]; i++) dt_node[(size_t)i] = v.inst_dt[k];
+    StateView<float> sv{};
+    void *stream = nullptr;
+    int dev = -1;
+    if ((r = surrogate_mesh_device(m, &sv, &stream, &dev))) return (fem_status)r;
+    if ((r = surrogate_mesh_view(m, &v))) return (fem_status)r;   // node_new of the uploaded plan
+    fem_surrogate *s = new (std::nothrow) fem_surrogate();
+    if (!s) return sfail(FEM_ENOMEM, "host allocation failed");
+    s->mesh = m;
+    s->device = dev;
+    s->dt = dt;
+    s->n = (int32_t)v.N;
+    s->n_tiles = (int32_t)((v.N + kTile - 1) / kTile);
+    fem_status st = FEM_OK;
+    try {
+        cudaSetDevice(dev);
+        cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
+        build_layout(s);
+        st = build_graph(s, v, dt_node);
+        const size_t rows = (size_t)s->n_tiles * kTile;
+        if (!st) st = salloc(s, &s->a.tf, rows);
+        if (!st) st = salloc(s, &s->a.x, rows * 16);
+        for (int l = 0; l <= kLayers && !st; l++) st = salloc(s, &s->a.h[l], rows * 64);
+        for (int l = 0; l < kLayers && !st; l++) {
+            st = salloc(s, &s->a.phi[l], rows * 32);
+            if (!st) st = salloc(s, &s->a.m[l], rows * 32);
+            if (!st) st = salloc(s, &s->a.r[l], rows * 64);
+        }
+        if (!st) st = salloc(s, &s->a.z, rows * 64);
+        if (!st) st = salloc(s, &s->a.y, rows);
+        if (!st) st = salloc(s, &s->E0, rows);
+        if (!st) st = salloc(s, &s->E1, rows);
+        if (!st) st = salloc(s, &s->theta, (size_t)kNParams);
+        if (!st) st = salloc(s, &s->mom, (size_t)kNParams);
+        if (!st) st = salloc(s, &s->vel, (size_t)kNParams);
+        if (!st) st = salloc(s, &s->grad, (size_t)kNParams);
+        if (!st) st = salloc(s, &s->img, (size_t)s->img_bytes);
+        if (!st) st = salloc(s, &s->err, 1);
+        if (!st) {
+            cudaFuncSetAttribute(k_sg_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFwd);
+            cudaFuncSetAttribute(k_sg_layer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFwd);
+            cudaFuncSetAttribute(k_sg_layer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFwd);
+            cudaFuncSetAttribute(k_sg_bwd_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
+            cudaFuncSetAttribute(k_sg_bwd_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = sfail(FEM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+        }
+    } catch (const std::bad_alloc &) {
+        st = sfail(FEM_ENOMEM, "host allocation failed");
+    }
+    if (st) {
+        release(s);
+        delete s;
+        return st;
+    }
+    *out = s;
+    return sok();
+}
+
+extern "C" fem_status fem_surrogate_info(fem_surrogate *s, int64_t *n_nodes, int64_t *n_edges,
+                                         int64_t *n_params)
+{
+    if (!s) return sfail(FEM_EINVAL, "NULL surrogate");
+    if (n_nodes) *n_nodes = s->n;
+    if (n_edges) *n_edges = s->nnz;
+    if (n_params) *n_params = kNParams;
+    return sok();
+}
+
+extern "C" fem_status fem_surrogate_order(fem_surrogate *s, int32_t *caller_of)
+{
+    if (!s || !caller_of) return sfail(FEM_EINVAL, "NULL argument");
+    std::memcpy(caller_of, s->caller_of.data(), s->caller_of.size() * sizeof(int32_t));
+    return sok();
+}
+
+extern "C" fem_status fem_surrogate_set_params(fem_surrogate *s, const float *theta, int64_t n)
+{
+    if (!s || !theta) return sfail(FEM_EINVAL, "NULL argument");
+    if (n != kNParams) return sfail(FEM_EINVAL, "n = %lld parameters, expected %d", (long long)n, kNParams);
+    for (int64_t q = 0; q < n; q++)
+        if (!std::isfinite(theta[q])) return sfail(FEM_EINVAL, "non-finite parameter %lld", (long long)q);
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    SCU(cudaMemcpyAsync(s->theta, theta, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st));
+    SCU(cudaMemsetAsync(s->mom, 0, (size_t)n * sizeof(float), st));
+    SCU(cudaMemsetAsync(s->vel, 0, (size_t)n * sizeof(float), st));
+    if ((r = pack(s, st))) return r;
+    SCU(cudaStreamSynchronize(st));
+    s->adam_t = 0;
+    s->have_params = true;
+    return sok();
+}
+
+extern "C" fem_status fem_surrogate_get_params(fem_surrogate *s, float *theta, int64_t n)
+{
+    if (!s || !theta) return sfail(FEM_EINVAL, "NULL argument");
+    if (n != kNParams) return sfail(FEM_EINVAL, "n = %lld parameters, expected %d", (long long)n, kNParams);
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    SCU(cudaMemcpyAsync(theta, s->theta, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    SCU(cudaStreamSynchronize(st));
+    return sok();
+}
+
+extern "C" fem_status fem_surrogate_read_state(fem_surrogate *s, float *E_dev)
+{
+    if (!s || !E_dev) return sfail(FEM_EINVAL, "NULL argument");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, E_dev);
+    return launch_check("state gather") ? FEM_ECUDA : sok();
+}
+
+extern "C" fem_status fem_surrogate_write_state(fem_surrogate *s, const float *E_dev)
+{
+    if (!s || !E_dev) return sfail(FEM_EINVAL, "NULL argument");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    k_sg_scatter<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, E_dev);
+    if ((r = launch_check("state scatter"))) return r;
+    r = (fem_status)surrogate_mesh_advanced(s->mesh, 0, 0.0);
+    return r ? r : sok();
+}
+
+extern "C" fem_status fem_surrogate_predict(fem_surrogate *s, const float *E_in, float *E_out)
+{
+    if (!s || !E_in || !E_out) return sfail(FEM_EINVAL, "NULL argument");
+    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    r = forward(s, E_in, E_out, false, st);
+    return r ? r : sok();
+}
+
+extern "C" fem_status fem_surrogate_train_step(fem_surrogate *s, const float *E_in, const float *E_star,
+                                               float lr, double *loss_out)
+{
+    if (!s || !E_in || !E_star) return sfail(FEM_EINVAL, "NULL argument");
+    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return sfail(FEM_EINVAL, "lr must be >= 0 and finite");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    if ((r = ensure_train(s))) return r;
+    if ((r = forward(s, E_in, s->E1, true, st))) return r;
+    Grads gr{};
+    gr.E_star = E_star;
+    gr.dhdir = s->dhdir;
+    gr.partial = s->partial;
+    gr.loss_part = s->loss_part;
+    gr.inv_n = 1.f / (float)s->n;
+    Acts a = s->a;
+    a.E_in = E_in;
+    a.E_out = s->E1;
+    const int gb = bwd_grid(s);
+    k_sg_bwd_head<<<gb, 128, kSmemBwd, st>>>(s->g, a, gr, s->gm[0], s->img, s->theta, s->L, s->err);
+    for (int l = kLayers - 1; l >= 0; l--) {
+        const float *gin = s->gm[(kLayers - 1 - l) & 1];
+        float *gout = s->gm[(kLayers - l) & 1];
+        k_sg_bwd_mid<<<gb, 128, kSmemBwd, st>>>(s->g, a, gr, gin, gout, s->img, s->L, l, s->err);
+    }
+    if ((r = launch_check("surrogate backward"))) return r;
+    AdamArgs ad{};
+    const double b1 = 0.9, b2 = 0.999;
+    if (lr > 0.f) s->adam_t += 1;
+    const int64_t t = std::max<int64_t>(s->adam_t, 1);
+    ad.lr = lr;
+    ad.b1 = (float)b1;
+    ad.b2 = (float)b2;
+    ad.omb1 = (float)(1.0 - b1);
+    ad.omb2 = (float)(1.0 - b2);
+    ad.eps = 1e-8f;
+    ad.bc1 = (float)(1.0 - std::pow(b1, (double)t));
+    ad.bc2 = (float)(1.0 - std::pow(b2, (double)t));
+    ad.inv_n = 1.f / (float)s->n;
+    k_sg_reduce_adam<<<(kNParams + 255) / 256, 256, 0, st>>>(s->partial, s->loss_part, gb, s->grad, s->theta,
+                                                             s->mom, s->vel, ad, s->loss);
+    if ((r = launch_check("gradient reduction"))) return r;
+    if (lr > 0.f && (r = pack(s, st))) return r;
+    if (loss_out) {
+        SCU(cudaMemcpyAsync(loss_out, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if ((r = check_err(s, st))) return r;
+    }
+    return sok();
+}
+
+extern "C" fem_status fem_surrogate_advance(fem_surrogate *s, int64_t n_macro)
+{
+    if (!s) return sfail(FEM_EINVAL, "NULL surrogate");
+    if (n_macro < 0) return sfail(FEM_EINVAL, "n_macro must be >= 0");
+    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
+    if (n_macro == 0) return sok();
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, s->E0);
+    float *cur = s->E0, *nxt = s->E1;
+    for (int64_t k = 0; k < n_macro; k++) {
+        if ((r = forward(s, cur, nxt, false, st))) return r;
+        std::swap(cur, nxt);
+    }
+    k_sg_scatter<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, cur);
+    if ((r = launch_check("state scatter"))) return r;
+    r = (fem_status)surrogate_mesh_advanced(s->mesh, kMacroSteps * n_macro, s->dt);
+    return r ? r : sok();
+}
+
+// Test hook: host copy of an internal buffer (surrogate order, padded rows
+// excluded).  which: 0 x (bf16 [n][16]), 1 h_l (bf16 [n][64], l = 0..3),
+// 2 phi_l (bf16 [n][32]), 3 m_l (bf16 [n][32]), 4 r_l (bf16 [n][64]),
+// 5 z (f32 [n][64]), 6 y (f32 [n]), 7 gradient (f32 [n_params]),
+// 8 node data (f32 [n][5]: C, Lc, s, hA, g), 9 CSR (int32 rowptr [n+1]
+// then col [nnz], then f32 w [nnz]).  Synchronises.
+extern "C" fem_status fem_surrogate_debug(fem_surrogate *s, int32_t which, int32_t layer, void *out)
+{
+    if (!s || !out) return sfail(FEM_EINVAL, "NULL argument");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    SCU(cudaStreamSynchronize(st));
+    const size_t n = (size_t)s->n;
+    const bool lok = layer >= 0 && layer < kLayers;
+    switch (which) {
+    case 0: SCU(cudaMemcpy(out, s->a.x, n * 16 * 2, cudaMemcpyDeviceToHost)); break;
+    case 1:
+        if (layer < 0 || layer > kLayers) return sfail(FEM_EINVAL, "layer out of range");
+        SCU(cudaMemcpy(out, s->a.h[layer], n * 64 * 2, cudaMemcpyDeviceToHost));
+        break;
+    case 2: case 3: case 4: {
+        if (!lok) return sfail(FEM_EINVAL, "layer out of range");
+        const void *src = which == 2 ? (const void *)s->a.phi[layer]
+                                     : which == 3 ? (const void *)s->a.m[layer] : (const void *)s->a.r[layer];
+        SCU(cudaMemcpy(out, src, n * (which == 4 ? 64 : 32) * 2, cudaMemcpyDeviceToHost));
+        break;
+    }
+    case 5: SCU(cudaMemcpy(out, s->a.z, n * 64 * 4, cudaMemcpyDeviceToHost)); break;
+    case 6: SCU(cudaMemcpy(out, s->a.y, n * 4, cudaMemcpyDeviceToHost)); break;
+    case 7: SCU(cudaMemcpy(out, s->grad, (size_t)kNParams * 4, cudaMemcpyDeviceToHost)); break;
+    case 8: {
+        float *o = (float *)out;
+        const float *src[5] = {s->g.C, s->g.Lc, s->g.s, s->g.hA, s->g.g};
+        std::vector<float> tmp(n);
+        for (int k = 0; k < 5; k++) {
+            SCU(cudaMemcpy(tmp.data(), src[k], n * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < n; i++) o[i * 5 + k] = tmp[i];
+        }
+        break;
+    }
+    case 9: {
+        int32_t *o = (int32_t *)out;
+        SCU(cudaMemcpy(o, s->g.rowptr, (n + 1) * 4, cudaMemcpyDeviceToHost));
+        SCU(cudaMemcpy(o + n + 1, s->g.col, (size_t)s->nnz * 4, cudaMemcpyDeviceToHost));
+        SCU(cudaMemcpy(o + n + 1 + s->nnz, s->g.w, (size_t)s->nnz * 4, cudaMemcpyDeviceToHost));
+        break;
+    }
+    default: return sfail(FEM_EINVAL, "unknown buffer %d", which);
+    }
+    return check_err(s, st) ? FEM_ETIMEOUT : sok();
+}
+
+extern "C" void fem_surrogate_destroy(fem_surrogate *s)
+{
+    if (!s) return;
+    if (s->device >= 0) cudaSetDevice(s->device);
+    cudaDeviceSynchronize();
+    release(s);
+    delete s;
+}

@@ -41,7 +41,12 @@ ABI_SYMBOLS = (
     "fem_get_instance_energy", "fem_set_allocator", "fem_autotune", "fem_set_state_async",
     "fem_get_temperature_async", "fem_sync", "fem_set_state_async_f32",
     "fem_get_temperature_async_f32",
+    "fem_surrogate_create", "fem_surrogate_info", "fem_surrogate_order",
+    "fem_surrogate_set_params", "fem_surrogate_get_params", "fem_surrogate_read_state",
+    "fem_surrogate_write_state", "fem_surrogate_predict", "fem_surrogate_train_step",
+    "fem_surrogate_advance", "fem_surrogate_debug", "fem_surrogate_destroy",
 )
+FEM_SG_N_PARAMS = 30177
 
 
 class FemMaterial(ctypes.Structure):
@@ -122,6 +127,17 @@ def _load():
         "fem_set_state_async_f32": [P, P, i64, ctypes.c_double],
         "fem_get_temperature_async_f32": [P, P],
         "fem_sync": [P],
+        "fem_surrogate_create": [P, ctypes.c_double, ctypes.POINTER(P)],
+        "fem_surrogate_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "fem_surrogate_order": [P, ip],
+        "fem_surrogate_set_params": [P, P, i64],
+        "fem_surrogate_get_params": [P, P, i64],
+        "fem_surrogate_read_state": [P, P],
+        "fem_surrogate_write_state": [P, P],
+        "fem_surrogate_predict": [P, P, P],
+        "fem_surrogate_train_step": [P, P, P, ctypes.c_float, dp],
+        "fem_surrogate_advance": [P, i64],
+        "fem_surrogate_debug": [P, ctypes.c_int32, ctypes.c_int32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -131,6 +147,8 @@ def _load():
     lib.fem_last_error.argtypes = []
     lib.fem_mesh_destroy.restype = None
     lib.fem_mesh_destroy.argtypes = [P]
+    lib.fem_surrogate_destroy.restype = None
+    lib.fem_surrogate_destroy.argtypes = [P]
     return lib
 
 
@@ -612,3 +630,94 @@ class Batch(Mesh):
     def instance_temperature(self, i, T=None):
         T = self.temperature() if T is None else T
         return T[self.node_start[i]:self.node_start[i + 1]]
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate (fem_surrogate_*): device arrays are passed as pointers
+# (e.g. torch.Tensor.data_ptr()), FP32, in the surrogate's node order.
+# ---------------------------------------------------------------------------
+
+def _dptr(buf):
+    return ctypes.c_void_p(buf if isinstance(buf, int) else buf.data_ptr())
+
+
+class Surrogate:
+    """One surrogate on a Mesh or Batch (fem_surrogate_create).  dt: the
+    mesh's explicit step (ignored for a batch)."""
+
+    def __init__(self, mesh, dt=0.0):
+        h = ctypes.c_void_p()
+        _check(_lib.fem_surrogate_create(mesh.h, float(dt), ctypes.byref(h)))
+        self.h = h
+        self.mesh = mesh
+        n, e, q = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.fem_surrogate_info(self.h, ctypes.byref(n), ctypes.byref(e), ctypes.byref(q)))
+        self.n_nodes, self.n_edges, self.n_params = n.value, e.value, q.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.fem_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def order(self):
+        out = np.zeros(self.n_nodes, np.int32)
+        _check(_lib.fem_surrogate_order(self.h, _pi(out)))
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(_lib.fem_surrogate_set_params(self.h, ctypes.c_void_p(th.ctypes.data), th.size))
+
+    def params(self):
+        th = np.zeros(self.n_params, np.float32)
+        _check(_lib.fem_surrogate_get_params(self.h, ctypes.c_void_p(th.ctypes.data), th.size))
+        return th
+
+    def read_state(self, E_dev):
+        _check(_lib.fem_surrogate_read_state(self.h, _dptr(E_dev)))
+
+    def write_state(self, E_dev):
+        _check(_lib.fem_surrogate_write_state(self.h, _dptr(E_dev)))
+
+    def predict(self, E_in, E_out):
+        _check(_lib.fem_surrogate_predict(self.h, _dptr(E_in), _dptr(E_out)))
+
+    def train_step(self, E_in, E_star, lr, want_loss=True):
+        loss = ctypes.c_double(float("nan"))
+        _check(_lib.fem_surrogate_train_step(self.h, _dptr(E_in), _dptr(E_star), float(lr),
+                                             ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def advance(self, n_macro):
+        _check(_lib.fem_surrogate_advance(self.h, int(n_macro)))
+
+    def debug(self, which, layer=0):
+        n = self.n_nodes
+        shapes = {0: (np.uint16, (n, 16)), 1: (np.uint16, (n, 64)), 2: (np.uint16, (n, 32)),
+                  3: (np.uint16, (n, 32)), 4: (np.uint16, (n, 64)), 5: (np.float32, (n, 64)),
+                  6: (np.float32, (n,)), 7: (np.float32, (self.n_params,)),
+                  8: (np.float32, (n, 5))}
+        if which == 9:
+            buf = np.zeros(n + 1 + 2 * self.n_edges, np.int32)
+            _check(_lib.fem_surrogate_debug(self.h, 9, 0, ctypes.c_void_p(buf.ctypes.data)))
+            rowptr, col = buf[:n + 1], buf[n + 1:n + 1 + self.n_edges]
+            w = buf[n + 1 + self.n_edges:].view(np.float32)
+            return rowptr, col, w
+        dt, shape = shapes[which]
+        out = np.zeros(shape, dt)
+        _check(_lib.fem_surrogate_debug(self.h, int(which), int(layer), ctypes.c_void_p(out.ctypes.data)))
+        if dt == np.uint16:
+            out = (out.astype(np.uint32) << 16).view(np.float32)
+        return out

@@ -1,0 +1,222 @@
+"""GPU parity of the learned surrogate (fem_surrogate_*) against the CPU
+oracle of oracle/surrogate.py, on the same seeded inputs.
+
+* Graph and node data: the assembled conductances W_ij, C, Lc, s = dt/C and
+  the lumped Robin terms equal the oracle's (FP32 rounding).
+* Forward: every intermediate (features, h, phi, m, relu outputs, z, y) and
+  the new state equal the oracle's bf16-emulating forward pass.
+* Backward: the gradient of every parameter tensor equals the oracle's.
+* Adam: one step from the GPU's own gradient equals the oracle's Adam.
+* Advance: the mesh state after n macro steps equals n oracle forward passes.
+* Sizes: one tile, several tiles with a ragged tail, and more tiles than
+  SMs (the persistent kernels loop), a batch whose instances have their own
+  time steps.
+
+Tolerances.  Both sides round the same quantities to bf16 at the same
+points and accumulate in FP32 (GPU) or FP64 (oracle).  Where an FP32 value
+sits within its accumulation error of a bf16 rounding boundary the two
+sides round it to neighbouring bf16 values, 2^-8 relative apart, and the
+difference propagates through the later layers; such flips are rare, so the
+bound is on the bulk (mean |difference| <= 2e-3 of mean |reference|) and on
+the worst element (<= 3e-2 of the largest reference value).  Gradients are
+sums over all nodes of such products: per tensor, max |difference| <= 3e-2
+of max |reference| and cosine similarity >= 0.9995.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import surrogate as osg
+from paper_1005_3158_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_3158_gb300 import fem
+    return torch, fem
+
+
+def _close(gpu, ref, what, bulk=2e-3, worst=3e-2):
+    gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
+    assert gpu.shape == ref.shape, what
+    d = np.abs(gpu - ref)
+    scale = np.abs(ref).max()
+    if scale == 0.0:
+        assert d.max() == 0.0, what
+        return
+    assert d.mean() <= bulk * max(np.abs(ref).mean(), 1e-3 * scale), \
+        f"{what}: mean |diff| {d.mean():.3g} vs mean |ref| {np.abs(ref).mean():.3g}"
+    assert d.max() <= worst * scale, f"{what}: max |diff| {d.max():.3g} vs max |ref| {scale:.3g}"
+
+
+def _problem(kind):
+    if kind == "small":
+        return mg.random_small(21, nx=5, ny=4, nz=3)
+    if kind == "cube10":
+        return mg.unit_cube(10, jitter=0.2)
+    if kind == "cube30":
+        return mg.unit_cube(30, jitter=0.1)
+    raise ValueError(kind)
+
+
+def _params(seed):
+    th = mg.surrogate_init(osg.PARAM_SHAPES, seed=seed)
+    th = th + mg.rng_of(seed + 1).normal(0, 0.05, size=th.shape).astype(np.float32)
+    return th.astype(np.float32)
+
+
+def _setup(env, p, steps=30):
+    torch, fem = env
+    m = fem.Mesh(p, "fp32", reorder=1)
+    dt = 0.9 * m.stable_dt()
+    m.step(steps, dt)
+    s = fem.Surrogate(m, dt)
+    order = s.order()
+    E_dev = torch.empty(s.n_nodes, dtype=torch.float32, device="cuda")
+    s.read_state(E_dev)
+    torch.cuda.synchronize()
+    E_sg = E_dev.cpu().numpy()
+    E_caller = np.empty_like(E_sg)
+    E_caller[order] = E_sg
+    return m, s, dt, order, E_dev, E_caller
+
+
+@pytest.mark.parametrize("kind", ["small", "cube10"])
+def test_graph_and_node_data(env, kind):
+    p = _problem(kind)
+    m, s, dt, order, _, _ = _setup(env, p, steps=1)
+    g = osg.SurrogateGraph(p, dt)
+    rowptr, col, w = s.debug(9)
+    n = s.n_nodes
+    pos = np.empty(n, np.int64)
+    pos[order] = np.arange(n)
+    # oracle edges mapped into surrogate order, sorted like the GPU rows
+    gi, gj = pos[g.ei], pos[g.ej]
+    key = np.lexsort((gj, gi))
+    assert np.array_equal(np.repeat(np.arange(n), np.diff(rowptr)), gi[key])
+    assert np.array_equal(col, gj[key])
+    assert np.allclose(w, g.W[key], rtol=1e-6, atol=1e-6 * np.abs(g.W).max())
+    nd = s.debug(8)
+    for k, ref in enumerate((g.C, g.Lc, g.s, g.hA, g.g)):
+        r = ref[order]
+        assert np.allclose(nd[:, k], r, rtol=2e-6, atol=1e-6 * max(np.abs(r).max(), 1e-30)), k
+    s.close()
+    m.close()
+
+
+def _oracle_target(p, E_caller, dt):
+    o = oracle.OracleProblem(p)
+    o.set_enthalpy(E_caller.astype(np.float64))
+    o.step(16, dt)
+    return o.enthalpy().astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["small", "cube10", "cube30"])
+def test_forward_backward_adam(env, kind):
+    torch, fem = env
+    p = _problem(kind)
+    m, s, dt, order, E_dev, E_caller = _setup(env, p)
+    g = osg.SurrogateGraph(p, dt)
+    th = _params(7)
+    s.set_params(th)
+    E_star = _oracle_target(p, E_caller, dt)
+    Es_dev = torch.tensor(E_star[order], device="cuda")
+    loss = s.train_step(E_dev, Es_dev, 0.0)          # gradient only
+    E_out_ref, sv = osg.forward(th, g, E_caller, emulate=True)
+    ys = osg.target(g, E_caller, E_star, emulate=True)
+    loss_ref, grad_ref = osg.backward(th, g, sv, ys, emulate=True)
+    _close(s.debug(0), sv["x"][order], "x")
+    for l in range(osg.LAYERS + 1):
+        _close(s.debug(1, l), sv[f"h{l}"][order], f"h{l}")
+    for l in range(osg.LAYERS):
+        _close(s.debug(2, l), sv[f"phi{l + 1}"][order], f"phi{l + 1}")
+        _close(s.debug(3, l), sv[f"m{l + 1}"][order], f"m{l + 1}")
+        _close(s.debug(4, l), sv[f"r{l + 1}"][order], f"r{l + 1}")
+    _close(s.debug(5), sv["z"][order], "z")
+    _close(s.debug(6), sv["y"][order], "y")
+    assert loss == pytest.approx(loss_ref, rel=2e-2)
+    grad = s.debug(7)
+    k = 0
+    for name, shape in osg.PARAM_SHAPES:
+        nn = int(np.prod(shape))
+        a, b = grad[k:k + nn].astype(np.float64), grad_ref[k:k + nn].astype(np.float64)
+        k += nn
+        if np.abs(b).max() == 0:
+            assert np.abs(a).max() <= 1e-12, name
+            continue
+        assert np.abs(a - b).max() <= 3e-2 * np.abs(b).max(), name
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert cos >= 0.9995, (name, cos)
+    # the new state of the forward pass (predict, inference kernels)
+    out = torch.empty_like(E_dev)
+    s.predict(E_dev, out)
+    torch.cuda.synchronize()
+    dE = out.cpu().numpy().astype(np.float64) - E_caller[order]
+    _close(dE, (E_out_ref.astype(np.float64) - E_caller)[order], "E_out - E")
+    # one Adam step from the GPU's own gradient
+    s.train_step(E_dev, Es_dev, 1e-3)
+    th1, _, _ = osg.adam(th, grad, np.zeros_like(th), np.zeros_like(th), 1, 1e-3)
+    assert np.allclose(s.params(), th1, rtol=0, atol=1e-6)
+    s.close()
+    m.close()
+
+
+def test_advance_updates_the_mesh(env):
+    torch, fem = env
+    p = _problem("small")
+    m, s, dt, order, E_dev, E_caller = _setup(env, p)
+    g = osg.SurrogateGraph(p, dt)
+    th = _params(11)
+    s.set_params(th)
+    step0 = m.state()[1]
+    s.advance(2)
+    E1, step1, t1 = m.state()
+    assert step1 == step0 + 32
+    E_ref = E_caller
+    for _ in range(2):
+        E_ref, _ = osg.forward(th, g, E_ref, emulate=True)
+    _close(E1 - E_caller, E_ref.astype(np.float64) - E_caller, "advanced state")
+    s.close()
+    m.close()
+
+
+def test_batch_instances_keep_their_steps(env):
+    torch, fem = env
+    probs = [mg.random_small(31, nx=4, ny=3, nz=3), mg.random_small(32, nx=6, ny=4, nz=2)]
+    b = fem.Batch(probs, "fp32", block_elems=128)
+    dts = 0.9 * b.instance_stable_dt()
+    b.advance(5 * float(dts.max()))
+    s = fem.Surrogate(b)
+    order = s.order()
+    nd = s.debug(8)
+    start = b.node_start
+    th = _params(13)
+    s.set_params(th)
+    E_dev = torch.empty(s.n_nodes, dtype=torch.float32, device="cuda")
+    s.read_state(E_dev)
+    out = torch.empty_like(E_dev)
+    s.predict(E_dev, out)
+    torch.cuda.synchronize()
+    E_sg, O_sg = E_dev.cpu().numpy(), out.cpu().numpy()
+    E_all = np.empty_like(E_sg)
+    E_all[order] = E_sg
+    O_all = np.empty_like(O_sg)
+    O_all[order] = O_sg
+    s_all = np.empty(s.n_nodes, np.float32)
+    s_all[order] = nd[:, 2]
+    for i, q in enumerate(probs):
+        sl = slice(start[i], start[i + 1])
+        g = osg.SurrogateGraph(q, dts[i])
+        assert np.allclose(s_all[sl], g.s, rtol=2e-6)
+        ref, _ = osg.forward(th, g, E_all[sl], emulate=True)
+        _close(O_all[sl].astype(np.float64) - E_all[sl], ref.astype(np.float64) - E_all[sl],
+               f"instance {i}")
+    s.close()
+    b.close()
