@@ -513,3 +513,53 @@ def surrogate_init(shapes, seed: int = 2024) -> np.ndarray:
         else:
             out.append(np.zeros(n))
     return np.concatenate(out).astype(np.float32)
+
+
+def flanged_variant(seed: int, scale: float = 1.0, nx: int = 70, ny: int = 70,
+                    nz: int = 68) -> Problem:
+    """A seeded member of the flanged-casting family of ``flanged_casting``:
+    body radius 0.07-0.12 m, height 0.22-0.34 m, flange radius 1.2-1.6 x the
+    body radius (at most 0.17 m), flange thickness 0.02-0.05 m, axis moved
+    by up to 0.02 m in x and y, inside the 0.40 x 0.40 x 0.50 m steel box.
+    ``scale`` shrinks the box and every length of the cavity by the same
+    factor and the grid to round(scale * (nx, ny, nz)) hexes, so that the
+    hex spacing (5.7 x 5.7 x 7.4 mm at the default grid) stays the same;
+    scale = 1 gives the 1,999,200-tet meshes of the casting workload."""
+    rng = rng_of(seed)
+    body_r = rng.uniform(0.07, 0.12)
+    body_h = rng.uniform(0.22, 0.34)
+    flange_r = min(0.17, body_r * rng.uniform(1.2, 1.6))
+    flange_t = rng.uniform(0.02, 0.05)
+    off = rng.uniform(-0.02, 0.02, size=2)
+    lx, ly, lz = 0.40 * scale, 0.40 * scale, 0.50 * scale
+    gx, gy, gz = (max(4, int(round(scale * v))) for v in (nx, ny, nz))
+    xyz, tets, _, flags = box_grid(gx, gy, gz, lx, ly, lz, jitter=0.05, seed=seed + 3)
+    c = centroids(xyz, tets)
+    r = np.hypot(c[:, 0] - lx / 2 - off[0] * scale, c[:, 1] - ly / 2 - off[1] * scale)
+    z0 = (lz - body_h * scale) / 2
+    body = (r <= body_r * scale) & (c[:, 2] >= z0) & (c[:, 2] <= z0 + body_h * scale)
+    flange = (r <= flange_r * scale) & (c[:, 2] >= z0) & (c[:, 2] <= z0 + flange_t * scale)
+    alloy = body | flange
+    mat = np.where(alloy, 0, 1).astype(np.int32)
+    faces = box_boundary_faces(tets, flags)
+    hh, ti, q = _robin(faces)
+    T0 = np.where(_node_touches(xyz.shape[0], tets, alloy), T_POUR, T_MOLD)
+    return Problem(xyz=xyz, tets=tets, mat=mat, materials=np.array([ALLOY, STEEL]),
+                   faces=faces, h=hh, t_inf=ti, q=q, T0=T0.astype(np.float64),
+                   name=f"flanged_variant_{seed}_{gx}x{gy}x{gz}")
+
+
+def surrogate_training_set(n: int = 200, seed: int = 3000, lo: float = 0.35,
+                           hi: float = 0.55) -> list:
+    """n training castings of the flanged family at the casting workload's
+    hex spacing, scale uniform in [lo, hi] (about 90k-350k tets each);
+    casting i uses seed + i.  The evaluation geometries (seeds from 4000)
+    are not among them."""
+    rng = rng_of(seed)
+    scales = rng.uniform(lo, hi, size=n)
+    return [flanged_variant(seed + 1 + i, float(sc)) for i, sc in enumerate(scales)]
+
+
+def surrogate_eval_set(n: int = 10, seed: int = 4000) -> list:
+    """n unseen full-size (1,999,200-tet) castings of the flanged family."""
+    return [flanged_variant(seed + i) for i in range(n)]
