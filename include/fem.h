@@ -582,6 +582,20 @@ fem_status fem_surrogate_train_step(fem_surrogate *s, const float *E_in, const f
  * not accumulated). */
 fem_status fem_surrogate_advance(fem_surrogate *s, int64_t n_macro);
 
+/* Surrogate stepping with the explicit solver as judge and fallback (plain
+ * meshes only).  Advances 16 * n_macro steps.  Every judge_every-th macro
+ * step (0: never) the explicit solver takes the 16 steps and the
+ * surrogate's prediction from the same state is compared with its result,
+ * which is kept: d = max_i |E_sg,i - E_i| / C_i, a bound on the
+ * temperature difference (dT/dE <= 1/C).  If d > tol_K (K) the solver
+ * also takes every macro step up to the next judged one.  stats [3] (may be
+ * NULL): macro steps by the surrogate, by the solver (judged ones
+ * included), judged steps that failed; max_err (may be NULL): the largest
+ * d seen.  Synchronises at every judged step.  Errors as fem_step and
+ * fem_surrogate_advance; FEM_EINVAL for a batch or tol_K <= 0. */
+fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int32_t judge_every,
+                               double tol_K, int64_t *stats, double *max_err);
+
 /* Test hook: a host copy of an internal buffer after the last forward or
  * training step (surrogate order).  which: 0 x (bf16 [n][16]), 1 h_layer
  * (bf16 [n][64], layer 0..3), 2 phi (bf16 [n][32], layer 0..2), 3 m (bf16

@@ -1000,6 +1000,20 @@ __global__ void k_sg_scatter(StateView<float> v, const int32_t *__restrict__ int
     if (i < n) v.E(int_id[i]) = E[i];
 }
 
+// Judge: the largest |E_a - E_b| / C_i over the nodes (the bound it puts
+// on the temperature difference: dT/dE <= 1/C), as float bits in *out
+// (non-negative floats order like their bit patterns).
+__global__ void k_sg_judge(const float *__restrict__ Ea, const float *__restrict__ Eb, Graph g,
+                           unsigned int *out)
+{
+    float v = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x)
+        v = fmaxf(v, fabsf(Ea[i] - Eb[i]) / g.C[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+}
+
 }  // namespace sg
 }  // namespace fem
 
@@ -1662,4 +1676,76 @@ extern "C" void fem_surrogate_destroy(fem_surrogate *s)
     cudaDeviceSynchronize();
     release(s);
     delete s;
+}
+
+// Surrogate stepping with the explicit solver as judge and fallback (plain
+// meshes).  Every judge_every-th macro step the explicit solver takes the 16
+// steps itself and the surrogate's prediction from the same state is
+// compared with them; the solver's result is kept.  If the difference,
+// max_i |E_sg - E_plain| / C_i (a bound on the temperature difference),
+// exceeds tol_K the solver also takes the macro steps up to the next judged
+// one.  stats (may be NULL): [0] macro steps by the surrogate, [1] by the
+// solver (judged ones included), [2] judged steps that failed; max_err
+// (may be NULL): the largest judged difference (K).  Synchronises at every
+// judged step.
+extern "C" fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int32_t judge_every,
+                                          double tol_K, int64_t *stats, double *max_err)
+{
+    if (!s) return sfail(FEM_EINVAL, "NULL surrogate");
+    if (n_macro < 0 || judge_every < 0) return sfail(FEM_EINVAL, "n_macro and judge_every must be >= 0");
+    if (!(tol_K > 0.0)) return sfail(FEM_EINVAL, "tol_K must be positive");
+    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
+    SurrogateMeshView mv{};
+    int rr = surrogate_mesh_view(s->mesh, &mv);
+    if (rr) return (fem_status)rr;
+    if (mv.n_inst > 0) return sfail(FEM_EINVAL, "fem_surrogate_solve steps plain meshes only");
+    int64_t n_sg = 0, n_plain = 0, n_fail = 0;
+    double worst = 0.0;
+    int64_t k = 0, plain_until = 0;
+    fem_status r = FEM_OK;
+    while (k < n_macro) {
+        const bool judged = judge_every > 0 && k % judge_every == 0;
+        if (judged || k < plain_until) {
+            StateView<float> v{};
+            cudaStream_t st = nullptr;
+            if ((r = mesh_stream(s, &v, &st))) return r;
+            if (judged) k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, s->E0);
+            if ((r = fem_step(s->mesh, kMacroSteps, s->dt))) return r;
+            n_plain++;
+            if (judged) {
+                if ((r = mesh_stream(s, &v, &st))) return r;
+                float *Epl = s->a.y;   // scratch rows (inference does not use y)
+                k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, Epl);
+                if ((r = forward(s, s->E0, s->E1, false, st))) return r;
+                unsigned int *jb = reinterpret_cast<unsigned int *>(s->E0);   // E0 is free again
+                SCU(cudaMemsetAsync(jb, 0, sizeof(unsigned int), st));
+                k_sg_judge<<<std::min(4 * s->n_sm, (s->n + 255) / 256), 256, 0, st>>>(s->E1, Epl, s->g, jb);
+                if ((r = launch_check("surrogate judge"))) return r;
+                unsigned int bits = 0;
+                SCU(cudaMemcpyAsync(&bits, jb, sizeof(bits), cudaMemcpyDeviceToHost, st));
+                SCU(cudaStreamSynchronize(st));
+                float e;
+                std::memcpy(&e, &bits, sizeof e);
+                worst = std::max(worst, (double)e);
+                if (!((double)e <= tol_K)) {
+                    n_fail++;
+                    plain_until = k + judge_every;
+                }
+            }
+            k++;
+        } else {
+            int64_t run = n_macro - k;
+            if (judge_every > 0) run = std::min(run, judge_every - k % judge_every);
+            if ((r = fem_surrogate_advance(s, run))) return r;
+            n_sg += run;
+            k += run;
+        }
+    }
+    if (stats) {
+        stats[0] = n_sg;
+        stats[1] = n_plain;
+        stats[2] = n_fail;
+    }
+    if (max_err) *max_err = worst;
+    return sok();
 }

@@ -44,7 +44,8 @@ ABI_SYMBOLS = (
     "fem_surrogate_create", "fem_surrogate_info", "fem_surrogate_order",
     "fem_surrogate_set_params", "fem_surrogate_get_params", "fem_surrogate_read_state",
     "fem_surrogate_write_state", "fem_surrogate_predict", "fem_surrogate_train_step",
-    "fem_surrogate_advance", "fem_surrogate_debug", "fem_surrogate_destroy",
+    "fem_surrogate_advance", "fem_surrogate_solve", "fem_surrogate_debug",
+    "fem_surrogate_destroy",
 )
 FEM_SG_N_PARAMS = 30177
 
@@ -137,6 +138,7 @@ def _load():
         "fem_surrogate_predict": [P, P, P],
         "fem_surrogate_train_step": [P, P, P, ctypes.c_float, dp],
         "fem_surrogate_advance": [P, i64],
+        "fem_surrogate_solve": [P, i64, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(i64), dp],
         "fem_surrogate_debug": [P, ctypes.c_int32, ctypes.c_int32, P],
     }
     for name, args in sig.items():
@@ -702,6 +704,16 @@ class Surrogate:
 
     def advance(self, n_macro):
         _check(_lib.fem_surrogate_advance(self.h, int(n_macro)))
+
+    def solve(self, n_macro, judge_every, tol_K):
+        """Hybrid stepping (fem_surrogate_solve): returns (macro steps by the
+        surrogate, by the solver, failed judgements, largest judged
+        difference in K)."""
+        st = (ctypes.c_int64 * 3)()
+        err = ctypes.c_double(0.0)
+        _check(_lib.fem_surrogate_solve(self.h, int(n_macro), int(judge_every), float(tol_K),
+                                        st, ctypes.byref(err)))
+        return int(st[0]), int(st[1]), int(st[2]), float(err.value)
 
     def debug(self, which, layer=0):
         n = self.n_nodes
