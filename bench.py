@@ -94,9 +94,15 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=None,
                     help="default block_with_cores_220 (or the one --config names)")
-    ap.add_argument("--config", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--config", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="1: unit_cube_20 FP64 (parity case), 2: flanged_casting, "
-                         "3: block_with_cores_220 (the default), 4: batched_castings_256")
+                         "3: block_with_cores_220 (the default), 4: batched_castings_256, "
+                         "5: surrogate_flanged (learned 16-step surrogate vs plain FP32)")
+    ap.add_argument("--n-eval", type=int, default=2,
+                    help="surrogate workload: unseen 2M-tet castings evaluated (of 10)")
+    ap.add_argument("--judge-every", type=int, default=8)
+    ap.add_argument("--tol", type=float, default=2.0)
+    ap.add_argument("--params", default="")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", default="block", choices=["block", "atomic", "colored"])
     ap.add_argument("--reorder", type=int, default=1)
@@ -118,7 +124,7 @@ def parse():
                     help="batched workload: skip the instance-by-instance comparison")
     a = ap.parse_args()
     named = {1: "unit_cube_20", 2: "flanged_casting", 3: "block_with_cores_220",
-             4: "batched_castings_256"}
+             4: "batched_castings_256", 5: "surrogate_flanged"}
     if a.workload is None:
         a.workload = named.get(a.config, "block_with_cores_220")
     if a.config == 1 and "--precision" not in sys.argv:
@@ -524,6 +530,141 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_surrogate(args):
+    """The learned surrogate (16 explicit steps per network evaluation) with
+    the plain solver as judge and fallback, against the plain FP32 solver,
+    on unseen full-size castings: both solve from the pour until the casting
+    has solidified (plus 10 %); value = plain time / surrogate time (CUDA
+    events) over those solves, with the max nodal error and the
+    solidification-time error beside it."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_3158_gb300 import fem
+    from paper_1005_3158_gb300 import meshgen as mg
+    from paper_1005_3158_gb300 import surrogate as sgd
+    path = args.params or sgd.PARAMS_FILE
+    if not os.path.exists(path):
+        print(json.dumps({"metric": "surrogate speedup at <=2K max nodal error",
+                          "unavailable": f"no trained parameters at {os.path.basename(path)}"}))
+        return
+    theta = np.load(path).astype(np.float32)
+    geoms = mg.surrogate_eval_set(10)[:max(1, args.n_eval)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = [sgd.evaluate(p, theta, args.judge_every, args.tol, log=lambda *a: None) for p in geoms]
+    clk = clocks.stop()
+    ms_p = sum(r["ms_plain"] for r in res)
+    ms_s = sum(r["ms_surrogate"] for r in res)
+    value = ms_p / ms_s
+    # per-kernel device times of the network on the first geometry
+    p = geoms[0]
+    m = fem.Mesh(p, "fp32", reorder=1)
+    dt = 0.9 * m.stable_dt()
+    sg = fem.Surrogate(m, dt)
+    sg.set_params(theta)
+    sg.profile(3)
+    kms = sg.profile(args.profile_steps) / max(1, args.profile_steps)
+    N, nnz = sg.n_nodes, sg.n_edges
+    names = ["k_sg_tf", "k_sg_encode", "k_sg_layer<false> (layer 1)", "k_sg_layer<false> (layer 2)",
+             "k_sg_layer<true> (layer 3 + decoder)"]
+    # algorithmic bytes of a layer launch: h read + written (bf16 x 64),
+    # phi gathered once per node and written (bf16 x 32), the CSR (column
+    # and weight per edge, row pointer) and s per node
+    alg_layer = N * (128 + 128 + 64 + 64 + 4 + 4) + nnz * 8
+    flops_layer = N * 2 * (96 * 64 + 64 * 32)
+    k_dom = int(np.argmax(kms))
+    peak, peak_kind = hbm_peak()
+    ach = alg_layer / (kms[k_dom] / 1e3) / 1e9
+    tflops = flops_layer / (kms[k_dom] / 1e3) / 1e12
+    roofline = {"bound": "hbm", "kernel": names[k_dom], "achieved": round(ach, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": peak_kind, "alg_bytes_per_launch": int(alg_layer),
+                "kernel_ms": [round(float(v), 4) for v in kms],
+                "tensor": {"flops_per_launch": int(flops_layer), "achieved_tflops": round(tflops, 2),
+                           "note": "dense per-node layers on tcgen05; the message sums gather "
+                                   "on CUDA cores"}}
+    # end to end through the C ABI with host buffers: upload the pour state
+    # (FP32, pinned), solve, read the temperatures back; plain vs surrogate
+    e2e = None
+    if not args.no_e2e:
+        E64 = torch.empty(N, dtype=torch.float64)
+        m.set_temperature(p.T0)
+        m.state(E64.numpy())
+        E_h = E64.to(torch.float32).pin_memory()
+        T_h = torch.empty(N, dtype=torch.float32, pin_memory=True)
+        n_macro = res[0]["macro_steps"]
+        times = {}
+        for name in ("plain", "surrogate"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.set_state_async(E_h, 0, 0.0)
+            if name == "plain":
+                m.step(16 * n_macro, dt)
+            else:
+                sg.solve(n_macro, args.judge_every, args.tol)
+            m.temperature_async(T_h)
+            m.sync()
+            times[name] = time.perf_counter() - t0
+        e2e = {"value": times["plain"] / times["surrogate"], "unit": "x",
+               "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": N * 4,
+               "step": f"one whole solve ({n_macro} macro steps) of {p.name}",
+               "seconds_plain": times["plain"], "seconds_surrogate": times["surrogate"]}
+    sg.close()
+    m.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline_surrogate(theta)
+    line = {
+        "metric": "surrogate speedup at <=2K max nodal error (hybrid surrogate vs plain FP32 "
+                  "solver, same GPU, same simulated time)",
+        "value": value, "unit": "x", "n_gpus": 1, "steps": sum(r["steps"] for r in res),
+        "warmup": 2, "ms_per_step": ms_s / sum(r["steps"] for r in res),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "surrogate_flanged", "geometries": [r["geometry"] for r in res],
+                   "n_tets": res[0]["n_tets"], "n_nodes": res[0]["n_nodes"],
+                   "judge_every": args.judge_every, "tol_K": args.tol,
+                   "params": os.path.basename(path),
+                   "max_err_K": max(r["max_err_K"] for r in res),
+                   "solid_time_rel_err": max((r["solid_time_rel_err"] or 0.0) for r in res),
+                   "macro_by_surrogate": sum(r["macro_by_surrogate"] for r in res),
+                   "macro_by_solver": sum(r["macro_by_solver"] for r in res),
+                   "ms_per_16_steps_plain": ms_p / sum(r["macro_steps"] for r in res),
+                   "ms_per_16_steps_surrogate": ms_s / sum(r["macro_steps"] for r in res),
+                   "ms_per_16_steps_network": float(np.mean([r["ms_per_16_steps_network"] for r in res])),
+                   "per_geometry": [{k: v for k, v in r.items() if k != "err_K_by_macro"} for r in res],
+                   "l2": "inputs larger than L2 (no flush)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_surrogate(theta, seconds: float = 10.0):
+    """The surrogate oracle (numpy forward pass, bf16 emulation) on a small
+    casting of the same family, timed on the host: tet-updates/s it
+    advances (16 steps per pass)."""
+    import numpy as np
+    from oracle import surrogate as osg
+    from paper_1005_3158_gb300 import meshgen as mg
+    p = mg.flanged_variant(4000, 0.2)
+    o = __import__("oracle").OracleProblem(p)
+    dt = 0.9 * o.stable_dt()
+    g = osg.SurrogateGraph(p, dt)
+    o.set_temperature(p.T0)
+    E = o.enthalpy()
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n == 0:
+        E, _ = osg.forward(theta, g, E, emulate=True)
+        n += 1
+    el = time.perf_counter() - t0
+    return {"value": p.n_tets * 16 * n / el, "unit": "tet-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{p.name} ({p.n_tets} tets), {n} surrogate forward passes of the numpy "
+                      f"oracle (16 steps each), {el:.1f} s"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -531,6 +672,9 @@ def main():
         return
     if args.workload.startswith("batched_castings_"):
         run_batched(args)
+        return
+    if args.workload == "surrogate_flanged":
+        run_surrogate(args)
         return
     import numpy as np
     import torch

@@ -596,6 +596,12 @@ fem_status fem_surrogate_advance(fem_surrogate *s, int64_t n_macro);
 fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int32_t judge_every,
                                double tol_K, int64_t *stats, double *max_err);
 
+/* As n_macro forward passes from the mesh's state (left unchanged), with
+ * CUDA events around every kernel on the mesh's stream: ms_out [5] gets the
+ * summed device milliseconds of {T(E) and liquid fraction, encoder, layer
+ * 1, layer 2, layer 3 with the decoder}.  Measurement only. */
+fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, double *ms_out);
+
 /* Test hook: a host copy of an internal buffer after the last forward or
  * training step (surrogate order).  which: 0 x (bf16 [n][16]), 1 h_layer
  * (bf16 [n][64], layer 0..3), 2 phi (bf16 [n][32], layer 0..2), 3 m (bf16

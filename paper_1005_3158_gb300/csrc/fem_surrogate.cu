@@ -135,7 +135,7 @@ constexpr uint32_t kSOk = kSTmem + 4;
 constexpr uint32_t kSmemFwd = kSOk + 4 + 16;
 
 // Encoder: x -> h0 -> phi_1 for every tile.
-__global__ void __launch_bounds__(128) k_sg_encode(Graph g, Acts a, const uint8_t *__restrict__ img,
+__global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uint8_t *__restrict__ img,
                                                    const float *__restrict__ theta, Layout L,
                                                    int train, int *err)
 {
@@ -168,9 +168,26 @@ __global__ void __launch_bounds__(128) k_sg_encode(Graph g, Acts a, const uint8_
             const float2 me = a.tf[i];
             const float T = me.x, f = me.y, C = g.C[i], Lc = g.Lc[i], s = g.s[i];
             float dT = 0.f, df = 0.f;
-            for (int k = g.rowptr[i]; k < g.rowptr[i + 1]; k++) {
-                const float w = g.w[k];
-                const float2 o = a.tf[g.col[k]];
+            const int k1 = g.rowptr[i + 1];
+            int k = g.rowptr[i];
+            for (; k + 3 < k1; k += 4) {   // four independent gathers in flight
+                const int j0 = __ldg(g.col + k), j1 = __ldg(g.col + k + 1), j2 = __ldg(g.col + k + 2),
+                          j3 = __ldg(g.col + k + 3);
+                const float2 o0 = a.tf[j0], o1 = a.tf[j1], o2 = a.tf[j2], o3 = a.tf[j3];
+                const float w0 = __ldg(g.w + k), w1 = __ldg(g.w + k + 1), w2 = __ldg(g.w + k + 2),
+                            w3 = __ldg(g.w + k + 3);
+                dT += w0 * (o0.x - T);
+                df += w0 * (o0.y - f);
+                dT += w1 * (o1.x - T);
+                df += w1 * (o1.y - f);
+                dT += w2 * (o2.x - T);
+                df += w2 * (o2.y - f);
+                dT += w3 * (o3.x - T);
+                df += w3 * (o3.y - f);
+            }
+            for (; k < k1; k++) {
+                const float w = __ldg(g.w + k);
+                const float2 o = a.tf[__ldg(g.col + k)];
                 dT += w * (o.x - T);
                 df += w * (o.y - f);
             }
@@ -286,39 +303,47 @@ __device__ __forceinline__ void tile_messages(const Graph &g, const uint16_t *__
         const int r = warp * 32 + rr * 4 + grp;
         const int64_t i = tile0 + r;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        if (i < g.n) {
+        const bool ok = i < g.n;
+        int k0 = 0, k1 = 0;
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+        if (ok) {
             const uint2 me = __ldg(reinterpret_cast<const uint2 *>(phi + i * 32) + sub);
-            const float p0 = bf_lo(me.x), p1 = bf_hi(me.x), p2 = bf_lo(me.y), p3 = bf_hi(me.y);
-            const int k1 = __ldg(g.rowptr + i + 1);
-            int k = __ldg(g.rowptr + i);
-            for (; k + 1 < k1; k += 2) {
-                const int j0 = __ldg(g.col + k), j1 = __ldg(g.col + k + 1);
-                const float w0 = __ldg(g.w + k), w1 = __ldg(g.w + k + 1);
-                const uint2 o0 = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j0 * 32) + sub);
-                const uint2 o1 = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j1 * 32) + sub);
-                a0 += w0 * (bf_lo(o0.x) - p0);
-                a1 += w0 * (bf_hi(o0.x) - p1);
-                a2 += w0 * (bf_lo(o0.y) - p2);
-                a3 += w0 * (bf_hi(o0.y) - p3);
-                a0 += w1 * (bf_lo(o1.x) - p0);
-                a1 += w1 * (bf_hi(o1.x) - p1);
-                a2 += w1 * (bf_lo(o1.y) - p2);
-                a3 += w1 * (bf_hi(o1.y) - p3);
+            p0 = bf_lo(me.x); p1 = bf_hi(me.x); p2 = bf_lo(me.y); p3 = bf_hi(me.y);
+            k0 = __ldg(g.rowptr + i);
+            k1 = __ldg(g.rowptr + i + 1);
+        }
+        // neighbours in chunks of 8: lane sub of the node's 8-lane group
+        // loads the chunk's sub-th column and weight, the group shares them
+        // by shuffles and issues the 8 gathers back to back
+        const int nch = (k1 - k0 + 7) >> 3;
+        const int m1 = max(nch, __shfl_xor_sync(0xffffffffu, nch, 8));
+        const int nmax = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));   // over the warp's 4 nodes
+        for (int c = 0; c < nmax; c++) {
+            const int kk = k0 + 8 * c + sub;
+            const bool has = kk < k1;
+            const int jj = has ? __ldg(g.col + kk) : (ok ? (int)i : 0);
+            const float ww = has ? __ldg(g.w + kk) : 0.f;
+            uint2 o[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int j = __shfl_sync(0xffffffffu, jj, (lane & ~7) | u);
+                o[u] = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j * 32) + sub);
             }
-            if (k < k1) {
-                const int j0 = __ldg(g.col + k);
-                const float w0 = __ldg(g.w + k);
-                const uint2 o0 = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j0 * 32) + sub);
-                a0 += w0 * (bf_lo(o0.x) - p0);
-                a1 += w0 * (bf_hi(o0.x) - p1);
-                a2 += w0 * (bf_lo(o0.y) - p2);
-                a3 += w0 * (bf_hi(o0.y) - p3);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const float w = __shfl_sync(0xffffffffu, ww, (lane & ~7) | u);
+                a0 += w * (bf_lo(o[u].x) - p0);
+                a1 += w * (bf_hi(o[u].x) - p1);
+                a2 += w * (bf_lo(o[u].y) - p2);
+                a3 += w * (bf_hi(o[u].y) - p3);
             }
-            const float s = __ldg(g.s + i);
-            a0 *= s;
-            a1 *= s;
-            a2 *= s;
-            a3 *= s;
+        }
+        if (ok) {
+            const float sc = __ldg(g.s + i);
+            a0 *= sc;
+            a1 *= sc;
+            a2 *= sc;
+            a3 *= sc;
         }
         const uint2 packed = make_uint2(pack_bf2(a0, a1), pack_bf2(a2, a3));
         *reinterpret_cast<uint2 *>(sA + core_off(r, koff + 4 * sub, K)) = packed;
@@ -331,7 +356,7 @@ __device__ __forceinline__ void tile_messages(const Graph &g, const uint16_t *__
 // Layer l (0-based) of the message passing: h[l] -> h[l+1], then either the
 // next layer's projection phi[l+1] or (LAST) the decoder and the new state.
 template <bool LAST>
-__global__ void __launch_bounds__(128) k_sg_layer(Graph g, Acts a, const uint8_t *__restrict__ img,
+__global__ void __launch_bounds__(128, 4) k_sg_layer(Graph g, Acts a, const uint8_t *__restrict__ img,
                                                   const float *__restrict__ theta, Layout L, int l,
                                                   int train, int *err)
 {
@@ -795,18 +820,39 @@ __global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr, c
             const int r = warp * 32 + rr * 4 + grp;
             const int64_t j = tile0 + r;
             float d[4] = {0.f, 0.f, 0.f, 0.f};
-            if (j < g.n) {
-                const float4 me = __ldg(reinterpret_cast<const float4 *>(gm_in + j * 32) + sub);
-                const int k1 = __ldg(g.rowptr + j + 1);
-                for (int k = __ldg(g.rowptr + j); k < k1; k++) {
-                    const int ii = __ldg(g.col + k);
-                    const float w = __ldg(g.w + k);
-                    const float4 o = __ldg(reinterpret_cast<const float4 *>(gm_in + (int64_t)ii * 32) + sub);
-                    d[0] += w * (o.x - me.x);
-                    d[1] += w * (o.y - me.y);
-                    d[2] += w * (o.z - me.z);
-                    d[3] += w * (o.w - me.w);
+            const bool okj = j < g.n;
+            float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
+            int k0 = 0, k1 = 0;
+            if (okj) {
+                me = __ldg(reinterpret_cast<const float4 *>(gm_in + j * 32) + sub);
+                k0 = __ldg(g.rowptr + j);
+                k1 = __ldg(g.rowptr + j + 1);
+            }
+            // neighbours in chunks of 8 shared by the node's 8-lane group
+            const int nch = (k1 - k0 + 7) >> 3;
+            const int m1 = max(nch, __shfl_xor_sync(0xffffffffu, nch, 8));
+            const int nmax = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));
+            for (int c = 0; c < nmax; c++) {
+                const int kk = k0 + 8 * c + sub;
+                const bool has = kk < k1;
+                const int jj = has ? __ldg(g.col + kk) : (okj ? (int)j : 0);
+                const float ww = has ? __ldg(g.w + kk) : 0.f;
+                float4 o[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int q = __shfl_sync(0xffffffffu, jj, (lane & ~7) | u);
+                    o[u] = __ldg(reinterpret_cast<const float4 *>(gm_in + (int64_t)q * 32) + sub);
                 }
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float w = __shfl_sync(0xffffffffu, ww, (lane & ~7) | u);
+                    d[0] += w * (o[u].x - me.x);
+                    d[1] += w * (o[u].y - me.y);
+                    d[2] += w * (o[u].z - me.z);
+                    d[3] += w * (o[u].w - me.w);
+                }
+            }
+            if (okj) {
                 const uint2 ph = __ldg(reinterpret_cast<const uint2 *>(a.phi[l] + j * 32) + sub);
                 if (!(bf_lo(ph.x) > 0.f)) d[0] = 0.f;
                 if (!(bf_hi(ph.x) > 0.f)) d[1] = 0.f;
@@ -1038,6 +1084,7 @@ using namespace fem::sg;
 struct fem_surrogate {
     fem_mesh *mesh = nullptr;
     int device = -1, n_sm = 0;
+    int fwd_per_sm = 1;               // resident forward CTAs per SM (persistent grid)
     int32_t n = 0, n_tiles = 0;
     int64_t nnz = 0;
     std::vector<int32_t> caller_of;   // surrogate position -> caller node
@@ -1312,7 +1359,9 @@ fem_status launch_check(const char *what)
     return FEM_OK;
 }
 
-int fwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, 4 * s->n_sm)); }
+// Persistent grids: exactly the CTAs that are resident at once (a CTA
+// that waits for a second wave would start its tiles after the others end).
+int fwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->fwd_per_sm * s->n_sm)); }
 int bwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->n_sm)); }
 
 // Forward pass from E_in (device, surrogate order) into E_out.
@@ -1439,6 +1488,16 @@ extern "C" fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate
             cudaFuncSetAttribute(k_sg_layer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFwd);
             cudaFuncSetAttribute(k_sg_bwd_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
             cudaFuncSetAttribute(k_sg_bwd_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
+            // resident forward CTAs per SM: registers and shared memory
+            // (occupancy), and at most four 128-column TMEM allocations
+            int occ = 4, o = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sg_encode, 128, kSmemFwd);
+            occ = std::min(occ, o);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sg_layer<false>, 128, kSmemFwd);
+            occ = std::min(occ, o);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sg_layer<true>, 128, kSmemFwd);
+            occ = std::min(occ, o);
+            s->fwd_per_sm = std::max(1, occ);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) st = sfail(FEM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
         }
@@ -1748,4 +1807,51 @@ extern "C" fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int
     }
     if (max_err) *max_err = worst;
     return sok();
+}
+
+// As n_macro forward passes from the mesh's state (the state is not
+// changed), timing every kernel with CUDA events on the mesh's stream:
+// ms_out [5] receives the summed device milliseconds of {0: T(E) and
+// liquid fraction, 1: encoder, 2: layer 1, 3: layer 2, 4: layer 3 and
+// decoder}.  Measurement only (one synchronisation per pass).
+extern "C" fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, double *ms_out)
+{
+    if (!s || !ms_out) return sfail(FEM_EINVAL, "NULL argument");
+    if (n_macro < 0) return sfail(FEM_EINVAL, "n_macro must be >= 0");
+    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    for (int k = 0; k < 5; k++) ms_out[k] = 0.0;
+    cudaEvent_t ev[6];
+    for (int k = 0; k < 6; k++) SCU(cudaEventCreate(&ev[k]));
+    k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, s->E0);
+    Acts a = s->a;
+    a.E_in = s->E0;
+    a.E_out = s->E1;
+    for (int64_t it = 0; it < n_macro && !r; it++) {
+        cudaEventRecord(ev[0], st);
+        k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(s->E0, s->g, a.tf);
+        cudaEventRecord(ev[1], st);
+        k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, 0, s->err);
+        cudaEventRecord(ev[2], st);
+        for (int l = 0; l < kLayers - 1; l++) {
+            k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l, 0, s->err);
+            cudaEventRecord(ev[3 + l], st);
+        }
+        k_sg_layer<true><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, kLayers - 1, 0,
+                                                             s->err);
+        cudaEventRecord(ev[5], st);
+        r = launch_check("surrogate profile");
+        if (cudaEventSynchronize(ev[5]) != cudaSuccess) r = sfail(FEM_ECUDA, "event synchronisation failed");
+        for (int k = 0; k < 5 && !r; k++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            ms_out[k] += t;
+        }
+    }
+    for (int k = 0; k < 6; k++) cudaEventDestroy(ev[k]);
+    if (r) return r;
+    return check_err(s, st) ? FEM_ETIMEOUT : sok();
 }

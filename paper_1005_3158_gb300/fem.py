@@ -44,7 +44,7 @@ ABI_SYMBOLS = (
     "fem_surrogate_create", "fem_surrogate_info", "fem_surrogate_order",
     "fem_surrogate_set_params", "fem_surrogate_get_params", "fem_surrogate_read_state",
     "fem_surrogate_write_state", "fem_surrogate_predict", "fem_surrogate_train_step",
-    "fem_surrogate_advance", "fem_surrogate_solve", "fem_surrogate_debug",
+    "fem_surrogate_advance", "fem_surrogate_solve", "fem_surrogate_profile", "fem_surrogate_debug",
     "fem_surrogate_destroy",
 )
 FEM_SG_N_PARAMS = 30177
@@ -139,6 +139,7 @@ def _load():
         "fem_surrogate_train_step": [P, P, P, ctypes.c_float, dp],
         "fem_surrogate_advance": [P, i64],
         "fem_surrogate_solve": [P, i64, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(i64), dp],
+        "fem_surrogate_profile": [P, i64, dp],
         "fem_surrogate_debug": [P, ctypes.c_int32, ctypes.c_int32, P],
     }
     for name, args in sig.items():
@@ -714,6 +715,13 @@ class Surrogate:
         _check(_lib.fem_surrogate_solve(self.h, int(n_macro), int(judge_every), float(tol_K),
                                         st, ctypes.byref(err)))
         return int(st[0]), int(st[1]), int(st[2]), float(err.value)
+
+    def profile(self, n_macro):
+        """Summed device ms of each forward kernel over n_macro passes
+        (fem_surrogate_profile)."""
+        out = np.zeros(5)
+        _check(_lib.fem_surrogate_profile(self.h, int(n_macro), _pd(out)))
+        return out
 
     def debug(self, which, layer=0):
         n = self.n_nodes

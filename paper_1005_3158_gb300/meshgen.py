@@ -549,10 +549,10 @@ def flanged_variant(seed: int, scale: float = 1.0, nx: int = 70, ny: int = 70,
                    name=f"flanged_variant_{seed}_{gx}x{gy}x{gz}")
 
 
-def surrogate_training_set(n: int = 200, seed: int = 3000, lo: float = 0.35,
-                           hi: float = 0.55) -> list:
+def surrogate_training_set(n: int = 200, seed: int = 3000, lo: float = 0.40,
+                           hi: float = 0.60) -> list:
     """n training castings of the flanged family at the casting workload's
-    hex spacing, scale uniform in [lo, hi] (about 90k-350k tets each);
+    hex spacing, scale uniform in [lo, hi] (about 130k-430k tets each);
     casting i uses seed + i.  The evaluation geometries (seeds from 4000)
     are not among them."""
     rng = rng_of(seed)

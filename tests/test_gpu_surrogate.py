@@ -220,3 +220,44 @@ def test_batch_instances_keep_their_steps(env):
                f"instance {i}")
     s.close()
     b.close()
+
+
+def test_hybrid_solve_judge_and_fallback(env):
+    """fem_surrogate_solve: with a tolerance no prediction meets, every judged
+    macro step fails and the explicit solver takes every step, so the state
+    is bitwise the plain solver's; with a tolerance every prediction meets,
+    the solver takes only the judged steps, and the state equals the same
+    sequence run by hand (advance between the judged steps)."""
+    torch, fem = env
+    p = _problem("small")
+    th = _params(17)
+    n_macro, J = 6, 3
+    with fem.Mesh(p, "fp32", reorder=1) as ref:
+        dt = 0.9 * ref.stable_dt()
+        ref.step(n_macro * 16, dt)
+        E_plain = ref.state()[0]
+    with fem.Mesh(p, "fp32", reorder=1) as m:
+        s = fem.Surrogate(m, dt)
+        s.set_params(th)
+        n_sg, n_pl, n_fail, worst = s.solve(n_macro, J, 1e-30)
+        assert (n_sg, n_pl, n_fail) == (0, n_macro, n_macro // J)
+        assert worst > 0.0
+        E, step, _ = m.state()
+        assert step == n_macro * 16
+        assert np.array_equal(E, E_plain)
+        s.close()
+    with fem.Mesh(p, "fp32", reorder=1) as m, fem.Mesh(p, "fp32", reorder=1) as m2:
+        s = fem.Surrogate(m, dt)
+        s.set_params(th)
+        n_sg, n_pl, n_fail, worst = s.solve(n_macro, J, 1e30)
+        assert (n_sg, n_pl, n_fail) == (n_macro - n_macro // J, n_macro // J, 0)
+        s2 = fem.Surrogate(m2, dt)
+        s2.set_params(th)
+        for k in range(n_macro):
+            if k % J == 0:
+                m2.step(16, dt)
+            else:
+                s2.advance(1)
+        assert np.array_equal(m.state()[0], m2.state()[0])
+        s.close()
+        s2.close()
