@@ -87,12 +87,15 @@ def generate_pairs(probs, every=16, max_steps=4800, log=print):
     return b, s, pairs, dt
 
 
-def train(s, pairs, iters=3000, lr0=1e-3, lr1=1e-5, seed=5, init=None, log=print):
+def train(s, pairs, iters=3000, lr0=1e-3, lr1=1e-5, seed=5, init=None, skip_first=0, log=print):
     """Adam on random pairs (one whole batch snapshot per step), cosine
-    learning-rate decay from lr0 to lr1.  Returns the loss history."""
+    learning-rate decay from lr0 to lr1; the first skip_first pairs (the
+    steep transient right after the pour, which the hybrid solve leaves to
+    the explicit solver) are not used.  Returns the loss history."""
     theta = mg.surrogate_init(param_shapes(), seed=seed) if init is None else init
     s.set_params(theta)
     rng = np.random.default_rng(seed)
+    pairs = pairs[skip_first:]
     hist = []
     t0 = time.time()
     for it in range(iters):
@@ -245,6 +248,8 @@ def main(argv=None):
     ap.add_argument("--every", type=int, default=16)
     ap.add_argument("--iters", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--skip-first", type=int, default=0)
+    ap.add_argument("--init", default="", help="start from these parameters")
     ap.add_argument("--n-eval", type=int, default=10)
     ap.add_argument("--judge-every", type=int, default=8)
     ap.add_argument("--tol", type=float, default=2.0)
@@ -256,7 +261,8 @@ def main(argv=None):
         print(f"training set: {len(probs)} castings, {sum(p.n_tets for p in probs)} tets", flush=True)
         b, s, pairs, dt = generate_pairs(probs, every=a.every)
         print(f"pairs: {len(pairs)} (dt {dt:.4g} s), {time.time() - t0:.1f} s", flush=True)
-        hist = train(s, pairs, iters=a.iters, lr0=a.lr)
+        init = np.load(a.init).astype(np.float32) if a.init else None
+        hist = train(s, pairs, iters=a.iters, lr0=a.lr, init=init, skip_first=a.skip_first)
         np.save(a.out, s.params())
         if a.json:
             with open(a.json, "w") as f:
