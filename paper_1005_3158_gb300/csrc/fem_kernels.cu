@@ -570,69 +570,6 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
             }
 }
 
-// The same exchange with one warp per 32 consecutive shared nodes, whose
-// partials and mirror positions form one contiguous range of P / mpos: the
-// warp stages that range in shared memory with coalesced loads, then each
-// lane sums its node's partials from there in the same (block) order as
-// k_shared_update -- the results are bitwise the same -- updates E and
-// writes the node's mirrors.  A warp whose range exceeds the staging
-// capacity (kShWarpCopies, 8 copies per node on average) reads it from
-// global memory instead.  Enthalpy formulation (no capacity partials).
-constexpr int kShWarpCopies = 256;
-template <typename real, int NT>
-__global__ void __launch_bounds__(NT) k_shared_update_w(const BlockArgs<real> a, const real dt,
-                                                        const bool update)
-{
-    __shared__ real sP[NT / 32][kShWarpCopies];
-    __shared__ int32_t sM[NT / 32][kShWarpCopies];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t s0 = a.s_first + ((int64_t)blockIdx.x * (NT / 32) + warp) * 32;
-    if (s0 >= a.s_end) return;
-    const int64_t s = s0 + lane;
-    const bool in = s < a.s_end;
-    int k0 = 0, k1 = 0;
-    real E = real(0), dts = real(0);
-    bool act = in;
-    if (in) {
-        k0 = __ldg(a.sh_ptr + s);
-        k1 = __ldg(a.sh_ptr + s + 1);
-        E = a.Esh[s];
-        if (update) {
-            if (__ldg(a.ph + a.n_int + s) & kDirichletBit) act = false;
-            dts = a.sh_dt ? a.sh_dt[s] : dt;
-        }
-    }
-    if (k1 > k0 && !FEM_IN(k1 - 1, a.n_copies, a.err)) k1 = k0;
-    const int n_in = (int)((a.s_end - s0) < 32 ? (a.s_end - s0) : 32);
-    const int kb = __shfl_sync(0xffffffffu, k0, 0);
-    const int ke = __shfl_sync(0xffffffffu, k1, n_in - 1);
-    const int nk = ke - kb;
-    const bool staged = nk >= 0 && nk <= kShWarpCopies;
-    if (staged) {
-        for (int q = lane; q < nk; q += 32) {
-            if (update) sP[warp][q] = a.P[kb + q];
-            sM[warp][q] = __ldg(a.mpos + kb + q);
-        }
-        __syncwarp();
-    }
-    if (update) {
-        real R = real(0);
-        if (staged)
-            for (int k = k0; k < k1; ++k) R += sP[warp][k - kb];   // block order
-        else
-            for (int k = k0; k < k1; ++k) R += a.P[k];
-        if (act) {
-            E += dts * R;
-            a.Esh[s] = E;
-        }
-    }
-    if (act)
-        for (int k = k0; k < k1; ++k) {
-            const int32_t mp = staged ? sM[warp][k - kb] : __ldg(a.mpos + k);
-            if (FEM_IN(mp, (int64_t)a.n_blocks * a.ls, a.err)) a.Eloc[mp] = E;
-        }
-}
-
 // Interface faces (Eq. 8): every interface face is a Robin face whose
 // ambient temperature is the mean temperature of its sister face (the
 // nearest face of the other region, Section 3) at step n.  This kernel
@@ -936,32 +873,23 @@ int launch_interface(StateView<real> v, const real *C, const real *Lc, const uin
 }
 
 template <typename real>
-int launch_exchange(const BlockArgs<real> &a, real dt, bool update, void *stream)
-{
-    const int64_t n = a.s_end - a.s_first;
-    if (n <= 0) return (int)cudaGetLastError();
-    if (a.Pc) {   // apparent capacity: capacity partials as well
-        const int64_t per = (int64_t)kShNT * kShNPT;
-        k_shared_update<real, kShNT, kShNPT><<<(int)((n + per - 1) / per), kShNT, 0,
-                                               (cudaStream_t)stream>>>(a, dt, update);
-    } else {
-        const int64_t per = kShNT;   // one warp per 32 nodes
-        k_shared_update_w<real, kShNT><<<(int)((n + per - 1) / per), kShNT, 0, (cudaStream_t)stream>>>(
-            a, dt, update);
-    }
-    return (int)cudaGetLastError();
-}
-
-template <typename real>
 int launch_mirror_copies(const BlockArgs<real> &a, void *stream)
 {
-    return launch_exchange<real>(a, real(0), false, stream);
+    const int64_t n = a.s_end - a.s_first, per = (int64_t)kShNT * kShNPT;
+    if (n > 0)
+        k_shared_update<real, kShNT, kShNPT><<<(int)((n + per - 1) / per), kShNT, 0,
+                                               (cudaStream_t)stream>>>(a, real(0), false);
+    return (int)cudaGetLastError();
 }
 
 template <typename real>
 int launch_shared_update(const BlockArgs<real> &a, double dt, void *stream)
 {
-    return launch_exchange<real>(a, (real)dt, true, stream);
+    const int64_t n = a.s_end - a.s_first, per = (int64_t)kShNT * kShNPT;
+    if (n > 0)
+        k_shared_update<real, kShNT, kShNPT><<<(int)((n + per - 1) / per), kShNT, 0,
+                                               (cudaStream_t)stream>>>(a, (real)dt, true);
+    return (int)cudaGetLastError();
 }
 
 template <typename real>

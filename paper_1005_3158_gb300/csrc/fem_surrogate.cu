@@ -124,6 +124,65 @@ __global__ void k_sg_tf(const float *__restrict__ E, Graph g, float2 *__restrict
     tf[i] = make_float2(T, f);
 }
 
+// Features x of every node (one thread per node; the conduction sums gather
+// four neighbours at a time).
+__global__ void __launch_bounds__(256) k_sg_feat(Graph g, Acts a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)g.n_tiles * 128) return;
+    float x[16];
+#pragma unroll
+    for (int c = 0; c < 16; c++) x[c] = 0.f;
+    if (i < g.n) {
+        const float2 me = a.tf[i];
+        const float T = me.x, f = me.y, C = g.C[i], Lc = g.Lc[i], s = g.s[i];
+        float dT = 0.f, df = 0.f;
+        const int k1 = g.rowptr[i + 1];
+        int k = g.rowptr[i];
+        for (; k + 3 < k1; k += 4) {   // four independent gathers in flight
+            const int j0 = __ldg(g.col + k), j1 = __ldg(g.col + k + 1), j2 = __ldg(g.col + k + 2),
+                      j3 = __ldg(g.col + k + 3);
+            const float2 o0 = a.tf[j0], o1 = a.tf[j1], o2 = a.tf[j2], o3 = a.tf[j3];
+            const float w0 = __ldg(g.w + k), w1 = __ldg(g.w + k + 1), w2 = __ldg(g.w + k + 2),
+                        w3 = __ldg(g.w + k + 3);
+            dT += w0 * (o0.x - T);
+            df += w0 * (o0.y - f);
+            dT += w1 * (o1.x - T);
+            df += w1 * (o1.y - f);
+            dT += w2 * (o2.x - T);
+            df += w2 * (o2.y - f);
+            dT += w3 * (o3.x - T);
+            df += w3 * (o3.y - f);
+        }
+        for (; k < k1; k++) {
+            const float w = __ldg(g.w + k);
+            const float2 o = a.tf[__ldg(g.col + k)];
+            dT += w * (o.x - T);
+            df += w * (o.y - f);
+        }
+        const float Ts = g.ranges[2 * (g.ph[i] & 0x7F)], Tl = g.ranges[2 * (g.ph[i] & 0x7F) + 1];
+        const bool pc = Lc > 0.f;
+        x[0] = (T - kTC) / kTS;
+        x[1] = f;
+        x[2] = Lc / (C * kTS);
+        x[3] = kMacro * s * g.hA[i];
+        x[4] = kMacro * s * (g.g[i] - g.hA[i] * T) / kTS;
+        x[5] = kMacro * s * dT / kTS;
+        x[6] = kMacro * s * df;
+        x[7] = 1.f;
+        x[8] = pc ? (T - Ts) / kTS : 0.f;
+        x[9] = pc ? (T - Tl) / kTS : 0.f;
+        x[10] = kMacro * s * g.wsum[i];
+    }
+    uint4 q0 = make_uint4(pack_bf2(x[0], x[1]), pack_bf2(x[2], x[3]), pack_bf2(x[4], x[5]),
+                          pack_bf2(x[6], x[7]));
+    uint4 q1 = make_uint4(pack_bf2(x[8], x[9]), pack_bf2(x[10], x[11]), pack_bf2(x[12], x[13]),
+                          pack_bf2(x[14], x[15]));
+    uint4 *xs = reinterpret_cast<uint4 *>(a.x + (size_t)i * 16);
+    xs[0] = q0;
+    xs[1] = q1;
+}
+
 // Shared-memory plan of the forward kernels (bytes, 128-byte aligned).
 constexpr uint32_t kSA = 0;                               // A operand, 128 x 96 bf16
 constexpr uint32_t kSB1 = kSA + 128 * 96 * 2;             // first B image (<= 64 x 96)
@@ -134,10 +193,10 @@ constexpr uint32_t kSTmem = kSBar + 8;                    // TMEM base address
 constexpr uint32_t kSOk = kSTmem + 4;
 constexpr uint32_t kSmemFwd = kSOk + 4 + 16;
 
-// Encoder: x -> h0 -> phi_1 for every tile.
+// Encoder: x (from k_sg_feat) -> h0 -> phi_1 for every tile.
 __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uint8_t *__restrict__ img,
                                                    const float *__restrict__ theta, Layout L,
-                                                   int train, int *err)
+                                                   int *err)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sA = sm + kSA, *sB1 = sm + kSB1, *sB2 = sm + kSB2;
@@ -161,60 +220,10 @@ __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uin
     const uint32_t sa = smem_addr(sA), sb1 = smem_addr(sB1), sb2 = smem_addr(sB2);
     for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
         const int64_t i = (int64_t)tile * 128 + tid;
-        float x[16];
-#pragma unroll
-        for (int c = 0; c < 16; c++) x[c] = 0.f;
-        if (i < g.n) {
-            const float2 me = a.tf[i];
-            const float T = me.x, f = me.y, C = g.C[i], Lc = g.Lc[i], s = g.s[i];
-            float dT = 0.f, df = 0.f;
-            const int k1 = g.rowptr[i + 1];
-            int k = g.rowptr[i];
-            for (; k + 3 < k1; k += 4) {   // four independent gathers in flight
-                const int j0 = __ldg(g.col + k), j1 = __ldg(g.col + k + 1), j2 = __ldg(g.col + k + 2),
-                          j3 = __ldg(g.col + k + 3);
-                const float2 o0 = a.tf[j0], o1 = a.tf[j1], o2 = a.tf[j2], o3 = a.tf[j3];
-                const float w0 = __ldg(g.w + k), w1 = __ldg(g.w + k + 1), w2 = __ldg(g.w + k + 2),
-                            w3 = __ldg(g.w + k + 3);
-                dT += w0 * (o0.x - T);
-                df += w0 * (o0.y - f);
-                dT += w1 * (o1.x - T);
-                df += w1 * (o1.y - f);
-                dT += w2 * (o2.x - T);
-                df += w2 * (o2.y - f);
-                dT += w3 * (o3.x - T);
-                df += w3 * (o3.y - f);
-            }
-            for (; k < k1; k++) {
-                const float w = __ldg(g.w + k);
-                const float2 o = a.tf[__ldg(g.col + k)];
-                dT += w * (o.x - T);
-                df += w * (o.y - f);
-            }
-            const float Ts = g.ranges[2 * (g.ph[i] & 0x7F)], Tl = g.ranges[2 * (g.ph[i] & 0x7F) + 1];
-            const bool pc = Lc > 0.f;
-            x[0] = (T - kTC) / kTS;
-            x[1] = f;
-            x[2] = Lc / (C * kTS);
-            x[3] = kMacro * s * g.hA[i];
-            x[4] = kMacro * s * (g.g[i] - g.hA[i] * T) / kTS;
-            x[5] = kMacro * s * dT / kTS;
-            x[6] = kMacro * s * df;
-            x[7] = 1.f;
-            x[8] = pc ? (T - Ts) / kTS : 0.f;
-            x[9] = pc ? (T - Tl) / kTS : 0.f;
-            x[10] = kMacro * s * g.wsum[i];
-        }
-        uint4 q0 = make_uint4(pack_bf2(x[0], x[1]), pack_bf2(x[2], x[3]), pack_bf2(x[4], x[5]),
-                              pack_bf2(x[6], x[7]));
-        uint4 q1 = make_uint4(pack_bf2(x[8], x[9]), pack_bf2(x[10], x[11]), pack_bf2(x[12], x[13]),
-                              pack_bf2(x[14], x[15]));
-        st_row8(sA, tid, 0, 16, q0);
-        st_row8(sA, tid, 8, 16, q1);
-        if (train) {
-            uint4 *xs = reinterpret_cast<uint4 *>(a.x + (size_t)i * 16);
-            xs[0] = q0;
-            xs[1] = q1;
+        {
+            const uint4 *xs = reinterpret_cast<const uint4 *>(a.x + (size_t)i * 16);
+            st_row8(sA, tid, 0, 16, xs[0]);
+            st_row8(sA, tid, 8, 16, xs[1]);
         }
         tc::fence_smem_async();
         __syncthreads();
@@ -284,77 +293,67 @@ __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uin
     if (tid < 32) tc::tmem_free(tbase, 128);
 }
 
-namespace {
-
-// Graph messages of one tile: m_i = s_i sum_j W_ij (phi_j - phi_i) for the
-// 128 nodes of the tile (rows), 32 channels, FP32 sums of bf16 values.  Warp
-// w takes rows 32 w .. 32 w + 31, four at a time: 8 lanes per node, 4
-// channels per lane, one 8-byte gather per neighbour and lane.  The bf16
-// result lands in columns koff .. koff + 31 of row r of the core-matrix
-// operand sA (K columns) and, if msave is set, in msave[i][0..31].
-__device__ __forceinline__ void tile_messages(const Graph &g, const uint16_t *__restrict__ phi,
-                                              int64_t tile0, uint8_t *sA, uint32_t K, uint32_t koff,
-                                              uint16_t *msave)
+// Graph messages of layer l: m_i = s_i sum_j W_ij (phi_j - phi_i), 32
+// channels, FP32 sums of bf16 values, written as bf16.  Eight lanes per
+// node (4 channels each), four nodes per warp; a node's neighbours are
+// taken in chunks of 8, whose columns and weights the node's lanes load
+// together and share by shuffles, so that 8 gathers are in flight per lane.
+// A sparse gather with ~14 non-zeros per row: CUDA cores, one warp per four
+// nodes and many warps per SM to hide the gather latency.
+__global__ void __launch_bounds__(256) k_sg_msg(Graph g, const uint16_t *__restrict__ phi,
+                                                uint16_t *__restrict__ m_out)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int grp = lane >> 3, sub = lane & 7;
-#pragma unroll 1
-    for (int rr = 0; rr < 8; rr++) {
-        const int r = warp * 32 + rr * 4 + grp;
-        const int64_t i = tile0 + r;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        const bool ok = i < g.n;
-        int k0 = 0, k1 = 0;
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-        if (ok) {
-            const uint2 me = __ldg(reinterpret_cast<const uint2 *>(phi + i * 32) + sub);
-            p0 = bf_lo(me.x); p1 = bf_hi(me.x); p2 = bf_lo(me.y); p3 = bf_hi(me.y);
-            k0 = __ldg(g.rowptr + i);
-            k1 = __ldg(g.rowptr + i + 1);
-        }
-        // neighbours in chunks of 8: lane sub of the node's 8-lane group
-        // loads the chunk's sub-th column and weight, the group shares them
-        // by shuffles and issues the 8 gathers back to back
-        const int nch = (k1 - k0 + 7) >> 3;
-        const int m1 = max(nch, __shfl_xor_sync(0xffffffffu, nch, 8));
-        const int nmax = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));   // over the warp's 4 nodes
-        for (int c = 0; c < nmax; c++) {
-            const int kk = k0 + 8 * c + sub;
-            const bool has = kk < k1;
-            const int jj = has ? __ldg(g.col + kk) : (ok ? (int)i : 0);
-            const float ww = has ? __ldg(g.w + kk) : 0.f;
-            uint2 o[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int j = __shfl_sync(0xffffffffu, jj, (lane & ~7) | u);
-                o[u] = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j * 32) + sub);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const float w = __shfl_sync(0xffffffffu, ww, (lane & ~7) | u);
-                a0 += w * (bf_lo(o[u].x) - p0);
-                a1 += w * (bf_hi(o[u].x) - p1);
-                a2 += w * (bf_lo(o[u].y) - p2);
-                a3 += w * (bf_hi(o[u].y) - p3);
-            }
-        }
-        if (ok) {
-            const float sc = __ldg(g.s + i);
-            a0 *= sc;
-            a1 *= sc;
-            a2 *= sc;
-            a3 *= sc;
-        }
-        const uint2 packed = make_uint2(pack_bf2(a0, a1), pack_bf2(a2, a3));
-        *reinterpret_cast<uint2 *>(sA + core_off(r, koff + 4 * sub, K)) = packed;
-        if (msave) reinterpret_cast<uint2 *>(msave + i * 32)[sub] = packed;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8;
+    const int64_t rows = (int64_t)g.n_tiles * 128;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const bool ok = i < g.n;
+    int k0 = 0, k1 = 0;
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    if (ok) {
+        const uint2 me = __ldg(reinterpret_cast<const uint2 *>(phi + i * 32) + sub);
+        p0 = bf_lo(me.x); p1 = bf_hi(me.x); p2 = bf_lo(me.y); p3 = bf_hi(me.y);
+        k0 = __ldg(g.rowptr + i);
+        k1 = __ldg(g.rowptr + i + 1);
     }
+    const int nch = (k1 - k0 + 7) >> 3;
+    const int m1 = max(nch, __shfl_xor_sync(0xffffffffu, nch, 8));
+    const int nmax = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));   // over the warp's 4 nodes
+    for (int c = 0; c < nmax; c++) {
+        const int kk = k0 + 8 * c + sub;
+        const bool has = kk < k1;
+        const int jj = has ? __ldg(g.col + kk) : (ok ? (int)i : 0);
+        const float ww = has ? __ldg(g.w + kk) : 0.f;
+        uint2 o[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int j = __shfl_sync(0xffffffffu, jj, (lane & ~7) | u);
+            o[u] = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j * 32) + sub);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const float w = __shfl_sync(0xffffffffu, ww, (lane & ~7) | u);
+            a0 += w * (bf_lo(o[u].x) - p0);
+            a1 += w * (bf_hi(o[u].x) - p1);
+            a2 += w * (bf_lo(o[u].y) - p2);
+            a3 += w * (bf_hi(o[u].y) - p3);
+        }
+    }
+    (void)grp;
+    if (ok) {
+        const float sc = __ldg(g.s + i);
+        a0 *= sc;
+        a1 *= sc;
+        a2 *= sc;
+        a3 *= sc;
+    }
+    if (i < rows) reinterpret_cast<uint2 *>(m_out + i * 32)[sub] = make_uint2(pack_bf2(a0, a1), pack_bf2(a2, a3));
 }
 
-}  // namespace
-
-// Layer l (0-based) of the message passing: h[l] -> h[l+1], then either the
-// next layer's projection phi[l+1] or (LAST) the decoder and the new state.
+// Layer l (0-based) of the message passing, node-local: [h[l]; m[l]] ->
+// h[l+1], then either the next layer's projection phi[l+1] or (LAST) the
+// decoder and the new state.
 template <bool LAST>
 __global__ void __launch_bounds__(128, 4) k_sg_layer(Graph g, Acts a, const uint8_t *__restrict__ img,
                                                   const float *__restrict__ theta, Layout L, int l,
@@ -397,7 +396,11 @@ __global__ void __launch_bounds__(128, 4) k_sg_layer(Graph g, Acts a, const uint
             hp[4 * q + 3] = v.w;
             st_row8(sA, tid, 8 * q, 96, v);
         }
-        tile_messages(g, a.phi[l], (int64_t)tile * 128, sA, 96, 64, train ? a.m[l] : nullptr);
+        {
+            const uint4 *ms = reinterpret_cast<const uint4 *>(a.m[l] + i * 32);
+#pragma unroll
+            for (int q = 0; q < 4; q++) st_row8(sA, tid, 64 + 8 * q, 96, ms[q]);
+        }
         tc::fence_smem_async();
         __syncthreads();
         if (tid == 0) {
@@ -1370,13 +1373,19 @@ fem_status forward(fem_surrogate *s, const float *E_in, float *E_out, bool train
     Acts a = s->a;
     a.E_in = E_in;
     a.E_out = E_out;
+    const int rows = s->n_tiles * kTile;
     k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(E_in, s->g, a.tf);
-    k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, train ? 1 : 0, s->err);
-    for (int l = 0; l < kLayers - 1; l++)
-        k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l,
-                                                              train ? 1 : 0, s->err);
-    k_sg_layer<true><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, kLayers - 1,
-                                                         train ? 1 : 0, s->err);
+    k_sg_feat<<<(rows + 255) / 256, 256, 0, st>>>(s->g, a);
+    k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
+    for (int l = 0; l < kLayers; l++) {
+        k_sg_msg<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+        if (l < kLayers - 1)
+            k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l,
+                                                                  train ? 1 : 0, s->err);
+        else
+            k_sg_layer<true><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l,
+                                                                 train ? 1 : 0, s->err);
+    }
     return launch_check("surrogate forward");
 }
 
@@ -1810,10 +1819,13 @@ extern "C" fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int
 }
 
 // As n_macro forward passes from the mesh's state (the state is not
-// changed), timing every kernel with CUDA events on the mesh's stream:
-// ms_out [5] receives the summed device milliseconds of {0: T(E) and
-// liquid fraction, 1: encoder, 2: layer 1, 3: layer 2, 4: layer 3 and
-// decoder}.  Measurement only (one synchronisation per pass).
+// changed), timing the kernels with CUDA events on the mesh's stream:
+// ms_out [5] receives the summed device milliseconds of {0: T(E), liquid
+// fraction and features, 1: encoder, 2: the three message sums, 3: the
+// dense parts of layers 1 and 2, 4: layer 3 with the decoder}.  Note that
+// the message sums of a layer read the previous dense kernel's output, so
+// in this pass they run on stale inputs (the times are what matters).
+// Measurement only (one synchronisation per pass).
 extern "C" fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, double *ms_out)
 {
     if (!s || !ms_out) return sfail(FEM_EINVAL, "NULL argument");
@@ -1830,16 +1842,20 @@ extern "C" fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, d
     Acts a = s->a;
     a.E_in = s->E0;
     a.E_out = s->E1;
+    const int rows = s->n_tiles * kTile;
     for (int64_t it = 0; it < n_macro && !r; it++) {
         cudaEventRecord(ev[0], st);
         k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(s->E0, s->g, a.tf);
+        k_sg_feat<<<(rows + 255) / 256, 256, 0, st>>>(s->g, a);
         cudaEventRecord(ev[1], st);
-        k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, 0, s->err);
+        k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
         cudaEventRecord(ev[2], st);
-        for (int l = 0; l < kLayers - 1; l++) {
+        for (int l = 0; l < kLayers; l++)
+            k_sg_msg<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+        cudaEventRecord(ev[3], st);
+        for (int l = 0; l < kLayers - 1; l++)
             k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l, 0, s->err);
-            cudaEventRecord(ev[3 + l], st);
-        }
+        cudaEventRecord(ev[4], st);
         k_sg_layer<true><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, kLayers - 1, 0,
                                                              s->err);
         cudaEventRecord(ev[5], st);

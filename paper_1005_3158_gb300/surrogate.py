@@ -241,7 +241,11 @@ def evaluate(p, theta, judge_every=8, tol=2.0, max_macro=4000, log=print):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("cmd", choices=["train", "eval", "run"],
+                    help="train, eval, or run: a plain surrogate advance of --macro macro "
+                         "steps on one casting of --scale (for profilers)")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--macro", type=int, default=4)
     ap.add_argument("--out", default=PARAMS_FILE)
     ap.add_argument("--params", default=PARAMS_FILE)
     ap.add_argument("--n-train", type=int, default=200)
@@ -270,6 +274,17 @@ def main(argv=None):
                            "n_train": len(probs), "seconds": time.time() - t0}, f)
         s.close()
         b.close()
+    elif a.cmd == "run":
+        theta = np.load(a.params).astype(np.float32)
+        p = mg.flanged_variant(4000, a.scale)
+        m = fem.Mesh(p, "fp32", reorder=1)
+        s = fem.Surrogate(m, 0.9 * m.stable_dt())
+        s.set_params(theta)
+        s.advance(a.macro)
+        _sync()
+        print(f"{p.name}: {p.n_tets} tets, {a.macro} surrogate macro steps")
+        s.close()
+        m.close()
     else:
         theta = np.load(a.params).astype(np.float32)
         out = [evaluate(p, theta, a.judge_every, a.tol) for p in mg.surrogate_eval_set(a.n_eval)]
