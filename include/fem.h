@@ -575,6 +575,16 @@ fem_status fem_surrogate_predict(fem_surrogate *s, const float *E_in, float *E_o
 fem_status fem_surrogate_train_step(fem_surrogate *s, const float *E_in, const float *E_star,
                                     float lr, double *loss_out);
 
+/* Training over several pairs per step: fem_surrogate_accumulate runs the
+ * forward and backward pass of one pair (as fem_surrogate_train_step) and
+ * adds its gradient to an accumulator (loss_out as there);
+ * fem_surrogate_apply takes one Adam step of size lr > 0 with the mean of
+ * the accumulated gradients and clears them (FEM_ESTATE if none).
+ * fem_surrogate_train_step refuses to run while gradients are pending. */
+fem_status fem_surrogate_accumulate(fem_surrogate *s, const float *E_in, const float *E_star,
+                                    double *loss_out);
+fem_status fem_surrogate_apply(fem_surrogate *s, float lr);
+
 /* Advance the mesh by 16 * n_macro explicit steps through the network:
  * its state is read, stepped n_macro times and written back; the step
  * count and time (each batch instance's with its own dt) advance, and the

@@ -124,42 +124,38 @@ __global__ void k_sg_tf(const float *__restrict__ E, Graph g, float2 *__restrict
     tf[i] = make_float2(T, f);
 }
 
-// Features x of every node (one thread per node; the conduction sums gather
-// four neighbours at a time).
+// Features x of every node.  Eight lanes per node: the conduction sums over
+// the node's edges are split over the lanes (one neighbour each per round)
+// and reduced by shuffles; lanes 0 and 1 write the 16 bf16 channels.
 __global__ void __launch_bounds__(256) k_sg_feat(Graph g, Acts a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)g.n_tiles * 128) return;
-    float x[16];
-#pragma unroll
-    for (int c = 0; c < 16; c++) x[c] = 0.f;
-    if (i < g.n) {
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8;
+    const bool ok = i < g.n;
+    float T = 0.f, f = 0.f, dT = 0.f, df = 0.f;
+    if (ok) {
         const float2 me = a.tf[i];
-        const float T = me.x, f = me.y, C = g.C[i], Lc = g.Lc[i], s = g.s[i];
-        float dT = 0.f, df = 0.f;
-        const int k1 = g.rowptr[i + 1];
-        int k = g.rowptr[i];
-        for (; k + 3 < k1; k += 4) {   // four independent gathers in flight
-            const int j0 = __ldg(g.col + k), j1 = __ldg(g.col + k + 1), j2 = __ldg(g.col + k + 2),
-                      j3 = __ldg(g.col + k + 3);
-            const float2 o0 = a.tf[j0], o1 = a.tf[j1], o2 = a.tf[j2], o3 = a.tf[j3];
-            const float w0 = __ldg(g.w + k), w1 = __ldg(g.w + k + 1), w2 = __ldg(g.w + k + 2),
-                        w3 = __ldg(g.w + k + 3);
-            dT += w0 * (o0.x - T);
-            df += w0 * (o0.y - f);
-            dT += w1 * (o1.x - T);
-            df += w1 * (o1.y - f);
-            dT += w2 * (o2.x - T);
-            df += w2 * (o2.y - f);
-            dT += w3 * (o3.x - T);
-            df += w3 * (o3.y - f);
-        }
-        for (; k < k1; k++) {
+        T = me.x;
+        f = me.y;
+        const int k1 = __ldg(g.rowptr + i + 1);
+        for (int k = __ldg(g.rowptr + i) + sub; k < k1; k += 8) {
             const float w = __ldg(g.w + k);
             const float2 o = a.tf[__ldg(g.col + k)];
             dT += w * (o.x - T);
             df += w * (o.y - f);
         }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        dT += __shfl_xor_sync(0xffffffffu, dT, o);
+        df += __shfl_xor_sync(0xffffffffu, df, o);
+    }
+    if (sub >= 2 || i >= (int64_t)g.n_tiles * 128) return;
+    float x[16];
+#pragma unroll
+    for (int c = 0; c < 16; c++) x[c] = 0.f;
+    if (ok) {
+        const float C = g.C[i], Lc = g.Lc[i], s = g.s[i];
         const float Ts = g.ranges[2 * (g.ph[i] & 0x7F)], Tl = g.ranges[2 * (g.ph[i] & 0x7F) + 1];
         const bool pc = Lc > 0.f;
         x[0] = (T - kTC) / kTS;
@@ -174,13 +170,11 @@ __global__ void __launch_bounds__(256) k_sg_feat(Graph g, Acts a)
         x[9] = pc ? (T - Tl) / kTS : 0.f;
         x[10] = kMacro * s * g.wsum[i];
     }
-    uint4 q0 = make_uint4(pack_bf2(x[0], x[1]), pack_bf2(x[2], x[3]), pack_bf2(x[4], x[5]),
-                          pack_bf2(x[6], x[7]));
-    uint4 q1 = make_uint4(pack_bf2(x[8], x[9]), pack_bf2(x[10], x[11]), pack_bf2(x[12], x[13]),
-                          pack_bf2(x[14], x[15]));
-    uint4 *xs = reinterpret_cast<uint4 *>(a.x + (size_t)i * 16);
-    xs[0] = q0;
-    xs[1] = q1;
+    const uint4 q0 = make_uint4(pack_bf2(x[0], x[1]), pack_bf2(x[2], x[3]), pack_bf2(x[4], x[5]),
+                                pack_bf2(x[6], x[7]));
+    const uint4 q1 = make_uint4(pack_bf2(x[8], x[9]), pack_bf2(x[10], x[11]), pack_bf2(x[12], x[13]),
+                                pack_bf2(x[14], x[15]));
+    reinterpret_cast<uint4 *>(a.x + (size_t)i * 16)[sub] = sub == 0 ? q0 : q1;
 }
 
 // Shared-memory plan of the forward kernels (bytes, 128-byte aligned).
@@ -294,61 +288,63 @@ __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uin
 }
 
 // Graph messages of layer l: m_i = s_i sum_j W_ij (phi_j - phi_i), 32
-// channels, FP32 sums of bf16 values, written as bf16.  Eight lanes per
-// node (4 channels each), four nodes per warp; a node's neighbours are
-// taken in chunks of 8, whose columns and weights the node's lanes load
-// together and share by shuffles, so that 8 gathers are in flight per lane.
-// A sparse gather with ~14 non-zeros per row: CUDA cores, one warp per four
-// nodes and many warps per SM to hide the gather latency.
+// channels, FP32 sums of bf16 values, written as bf16; evaluated as
+// s_i (sum_j W_ij phi_j - (sum_j W_ij) phi_i).  Four lanes per node (8
+// channels each, one 16-byte gather per neighbour and lane), eight nodes per
+// warp; a node's neighbours are taken in chunks of 4 whose columns and
+// weights the node's lanes load together and share by shuffles.  A sparse
+// gather with ~14 non-zeros per row: CUDA cores, many warps per SM to hide
+// the gather latency.
 __global__ void __launch_bounds__(256) k_sg_msg(Graph g, const uint16_t *__restrict__ phi,
                                                 uint16_t *__restrict__ m_out)
 {
-    const int lane = threadIdx.x & 31;
-    const int grp = lane >> 3, sub = lane & 7;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8;
+    const int lane = threadIdx.x & 31, sub = lane & 3;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 4;
     const int64_t rows = (int64_t)g.n_tiles * 128;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const bool ok = i < g.n;
     int k0 = 0, k1 = 0;
-    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
     if (ok) {
-        const uint2 me = __ldg(reinterpret_cast<const uint2 *>(phi + i * 32) + sub);
-        p0 = bf_lo(me.x); p1 = bf_hi(me.x); p2 = bf_lo(me.y); p3 = bf_hi(me.y);
         k0 = __ldg(g.rowptr + i);
         k1 = __ldg(g.rowptr + i + 1);
     }
-    const int nch = (k1 - k0 + 7) >> 3;
-    const int m1 = max(nch, __shfl_xor_sync(0xffffffffu, nch, 8));
-    const int nmax = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));   // over the warp's 4 nodes
-    for (int c = 0; c < nmax; c++) {
-        const int kk = k0 + 8 * c + sub;
+    int nch = (k1 - k0 + 3) >> 2;
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) nch = max(nch, __shfl_xor_sync(0xffffffffu, nch, o));
+    for (int c = 0; c < nch; c++) {
+        const int kk = k0 + 4 * c + sub;
         const bool has = kk < k1;
-        const int jj = has ? __ldg(g.col + kk) : (ok ? (int)i : 0);
+        const int jj = has ? __ldg(g.col + kk) : 0;
         const float ww = has ? __ldg(g.w + kk) : 0.f;
-        uint2 o[8];
+        uint4 o[4];
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int j = __shfl_sync(0xffffffffu, jj, (lane & ~7) | u);
-            o[u] = __ldg(reinterpret_cast<const uint2 *>(phi + (int64_t)j * 32) + sub);
+        for (int u = 0; u < 4; u++) {
+            const int j = __shfl_sync(0xffffffffu, jj, (lane & ~3) | u);
+            o[u] = __ldg(reinterpret_cast<const uint4 *>(phi + (int64_t)j * 32) + sub);
         }
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const float w = __shfl_sync(0xffffffffu, ww, (lane & ~7) | u);
-            a0 += w * (bf_lo(o[u].x) - p0);
-            a1 += w * (bf_hi(o[u].x) - p1);
-            a2 += w * (bf_lo(o[u].y) - p2);
-            a3 += w * (bf_hi(o[u].y) - p3);
+        for (int u = 0; u < 4; u++) {
+            const float w = __shfl_sync(0xffffffffu, ww, (lane & ~3) | u);
+            acc[0] = fmaf(w, bf_lo(o[u].x), acc[0]);
+            acc[1] = fmaf(w, bf_hi(o[u].x), acc[1]);
+            acc[2] = fmaf(w, bf_lo(o[u].y), acc[2]);
+            acc[3] = fmaf(w, bf_hi(o[u].y), acc[3]);
+            acc[4] = fmaf(w, bf_lo(o[u].z), acc[4]);
+            acc[5] = fmaf(w, bf_hi(o[u].z), acc[5]);
+            acc[6] = fmaf(w, bf_lo(o[u].w), acc[6]);
+            acc[7] = fmaf(w, bf_hi(o[u].w), acc[7]);
         }
     }
-    (void)grp;
+    uint4 out = make_uint4(0u, 0u, 0u, 0u);
     if (ok) {
-        const float sc = __ldg(g.s + i);
-        a0 *= sc;
-        a1 *= sc;
-        a2 *= sc;
-        a3 *= sc;
+        const uint4 me = __ldg(reinterpret_cast<const uint4 *>(phi + i * 32) + sub);
+        const float ws = __ldg(g.wsum + i), sc = __ldg(g.s + i);
+        out.x = pack_bf2(sc * fmaf(-ws, bf_lo(me.x), acc[0]), sc * fmaf(-ws, bf_hi(me.x), acc[1]));
+        out.y = pack_bf2(sc * fmaf(-ws, bf_lo(me.y), acc[2]), sc * fmaf(-ws, bf_hi(me.y), acc[3]));
+        out.z = pack_bf2(sc * fmaf(-ws, bf_lo(me.z), acc[4]), sc * fmaf(-ws, bf_hi(me.z), acc[5]));
+        out.w = pack_bf2(sc * fmaf(-ws, bf_lo(me.w), acc[6]), sc * fmaf(-ws, bf_hi(me.w), acc[7]));
     }
-    if (i < rows) reinterpret_cast<uint2 *>(m_out + i * 32)[sub] = make_uint2(pack_bf2(a0, a1), pack_bf2(a2, a3));
+    if (i < rows) reinterpret_cast<uint4 *>(m_out + i * 32)[sub] = out;
 }
 
 // Layer l (0-based) of the message passing, node-local: [h[l]; m[l]] ->
@@ -505,7 +501,7 @@ __global__ void __launch_bounds__(128, 4) k_sg_layer(Graph g, Acts a, const uint
 // 128-row operand (input channels, then a row of ones whose product is the
 // bias gradient, then zero rows) and the output gradients transposed into
 // the B operand.  Each persistent CTA accumulates its tiles in TMEM and
-// writes one partial per weight; k_sg_reduce_adam sums the partials in CTA
+// writes one partial per weight; k_sg_reduce sums the partials in CTA
 // order (deterministic).
 
 namespace {
@@ -1004,31 +1000,42 @@ __device__ __forceinline__ int partial_index(int q)
 
 }  // namespace
 
-// Sum the per-CTA partials in CTA order into the gradient, then one Adam
-// step (Kingma and Ba, 2015) on the FP32 master weights: m = b1 m + (1-b1) g,
-// v = b2 v + (1-b2) g^2, theta -= lr (m / bc1) / (sqrt(v / bc2) + eps) with
-// bc1 = 1 - b1^t, bc2 = 1 - b2^t.  lr == 0 leaves theta, m, v unchanged
-// (gradient only).  The loss (mean squared error) lands in *loss.
-__global__ void k_sg_reduce_adam(const float *__restrict__ partial, const double *__restrict__ loss_part,
-                                 int n_parts, float *__restrict__ grad, float *__restrict__ theta,
-                                 float *__restrict__ mom, float *__restrict__ vel, AdamArgs ad,
-                                 double *loss)
+// Sum the per-CTA partials in CTA order into the gradient of this pair
+// (grad) and add it to the accumulated gradient (acc); the pair's loss (mean
+// squared error) lands in *loss and is added to *loss_acc.
+__global__ void k_sg_reduce(const float *__restrict__ partial, const double *__restrict__ loss_part,
+                            int n_parts, float inv_n, float *__restrict__ grad, float *__restrict__ acc,
+                            double *loss, double *loss_acc)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q == 0) {
         double s = 0.0;
         for (int b = 0; b < n_parts; b++) s += loss_part[b];
-        *loss = s * (double)ad.inv_n;
+        *loss = s * (double)inv_n;
+        *loss_acc += s * (double)inv_n;
     }
     if (q >= kNParams) return;
     const int pi = partial_index(q);
     float gsum = 0.f;
     for (int b = 0; b < n_parts; b++) gsum += partial[(size_t)b * kPartFloats + pi];
     grad[q] = gsum;
-    if (ad.lr == 0.f) return;
+    acc[q] += gsum;
+}
+
+// One Adam step (Kingma and Ba, 2015) on the FP32 master weights with the
+// mean of the accumulated gradients, g = acc / count: m = b1 m + (1-b1) g,
+// v = b2 v + (1-b2) g^2, theta -= lr (m / bc1) / (sqrt(v / bc2) + eps) with
+// bc1 = 1 - b1^t, bc2 = 1 - b2^t; the accumulator is cleared.
+__global__ void k_sg_adam(float *__restrict__ acc, float count, float *__restrict__ theta,
+                          float *__restrict__ mom, float *__restrict__ vel, AdamArgs ad)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kNParams) return;
+    const float g = __fdiv_rn(acc[q], count);
+    acc[q] = 0.f;
     // every operation rounded on its own (no contraction into FMAs)
-    const float m = __fadd_rn(__fmul_rn(ad.b1, mom[q]), __fmul_rn(ad.omb1, gsum));
-    const float v = __fadd_rn(__fmul_rn(ad.b2, vel[q]), __fmul_rn(__fmul_rn(ad.omb2, gsum), gsum));
+    const float m = __fadd_rn(__fmul_rn(ad.b1, mom[q]), __fmul_rn(ad.omb1, g));
+    const float v = __fadd_rn(__fmul_rn(ad.b2, vel[q]), __fmul_rn(__fmul_rn(ad.omb2, g), g));
     mom[q] = m;
     vel[q] = v;
     const float mh = __fdiv_rn(m, ad.bc1), vh = __fdiv_rn(v, ad.bc2);
@@ -1100,12 +1107,13 @@ struct fem_surrogate {
     uint32_t img_bytes = 0;
     int32_t *int_id = nullptr;        // internal node of each surrogate position
     float *E0 = nullptr, *E1 = nullptr;
-    float *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr;
+    float *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr, *acc = nullptr;
+    int64_t n_acc = 0;                // pairs in the accumulated gradient
     uint8_t *img = nullptr;
     int *err = nullptr;
     bool train_ok = false;            // training buffers allocated
     float *dhdir = nullptr, *gm[2] = {nullptr, nullptr}, *partial = nullptr;
-    double *loss_part = nullptr, *loss = nullptr;
+    double *loss_part = nullptr, *loss = nullptr;   // loss[0]: last pair, loss[1]: accumulated
     int64_t adam_t = 0;
     bool have_params = false;
 };
@@ -1375,10 +1383,10 @@ fem_status forward(fem_surrogate *s, const float *E_in, float *E_out, bool train
     a.E_out = E_out;
     const int rows = s->n_tiles * kTile;
     k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(E_in, s->g, a.tf);
-    k_sg_feat<<<(rows + 255) / 256, 256, 0, st>>>(s->g, a);
+    k_sg_feat<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a);
     k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
     for (int l = 0; l < kLayers; l++) {
-        k_sg_msg<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+        k_sg_msg<<<(rows * 4 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
         if (l < kLayers - 1)
             k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l,
                                                                   train ? 1 : 0, s->err);
@@ -1405,7 +1413,7 @@ fem_status ensure_train(fem_surrogate *s)
     if ((st = salloc(s, &s->gm[1], rows * 32))) return st;
     if ((st = salloc(s, &s->partial, (size_t)s->n_sm * kPartFloats))) return st;
     if ((st = salloc(s, &s->loss_part, (size_t)s->n_sm))) return st;
-    if ((st = salloc(s, &s->loss, 1))) return st;
+    if ((st = salloc(s, &s->loss, 2))) return st;
     s->train_ok = true;
     return FEM_OK;
 }
@@ -1489,6 +1497,7 @@ extern "C" fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate
         if (!st) st = salloc(s, &s->mom, (size_t)kNParams);
         if (!st) st = salloc(s, &s->vel, (size_t)kNParams);
         if (!st) st = salloc(s, &s->grad, (size_t)kNParams);
+        if (!st) st = salloc(s, &s->acc, (size_t)kNParams);
         if (!st) st = salloc(s, &s->img, (size_t)s->img_bytes);
         if (!st) st = salloc(s, &s->err, 1);
         if (!st) {
@@ -1499,13 +1508,21 @@ extern "C" fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate
             cudaFuncSetAttribute(k_sg_bwd_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
             // resident forward CTAs per SM: registers and shared memory
             // (occupancy), and at most four 128-column TMEM allocations
-            int occ = 4, o = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sg_encode, 128, kSmemFwd);
-            occ = std::min(occ, o);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sg_layer<false>, 128, kSmemFwd);
-            occ = std::min(occ, o);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sg_layer<true>, 128, kSmemFwd);
-            occ = std::min(occ, o);
+            int regs_sm = 65536, smem_sm = 0;
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            int occ = 4;
+            const void *fns[3] = {(const void *)k_sg_encode, (const void *)k_sg_layer<false>,
+                                  (const void *)k_sg_layer<true>};
+            for (const void *fn : fns) {
+                cudaFuncAttributes fa{};
+                if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) continue;
+                // registers are allocated per warp in units of 256
+                const int regs_cta = 4 * (((fa.numRegs * 32 + 255) / 256) * 256);
+                const int smem_cta = (int)(kSmemFwd + fa.sharedSizeBytes) + 1024;
+                if (regs_cta > 0) occ = std::min(occ, regs_sm / regs_cta);
+                if (smem_sm > 0) occ = std::min(occ, smem_sm / smem_cta);
+            }
             s->fwd_per_sm = std::max(1, occ);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) st = sfail(FEM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
@@ -1552,6 +1569,8 @@ extern "C" fem_status fem_surrogate_set_params(fem_surrogate *s, const float *th
     SCU(cudaMemcpyAsync(s->theta, theta, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st));
     SCU(cudaMemsetAsync(s->mom, 0, (size_t)n * sizeof(float), st));
     SCU(cudaMemsetAsync(s->vel, 0, (size_t)n * sizeof(float), st));
+    SCU(cudaMemsetAsync(s->acc, 0, (size_t)n * sizeof(float), st));
+    s->n_acc = 0;
     if ((r = pack(s, st))) return r;
     SCU(cudaStreamSynchronize(st));
     s->adam_t = 0;
@@ -1608,16 +1627,14 @@ extern "C" fem_status fem_surrogate_predict(fem_surrogate *s, const float *E_in,
     return r ? r : sok();
 }
 
-extern "C" fem_status fem_surrogate_train_step(fem_surrogate *s, const float *E_in, const float *E_star,
-                                               float lr, double *loss_out)
+namespace {
+
+// Forward (saving activations), loss, backward and the gradient reduction
+// of one pair; the gradient is added to the accumulator.
+fem_status accumulate_pair(fem_surrogate *s, const float *E_in, const float *E_star, double *loss_out,
+                           cudaStream_t st)
 {
-    if (!s || !E_in || !E_star) return sfail(FEM_EINVAL, "NULL argument");
-    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
-    if (!(lr >= 0.f) || !std::isfinite(lr)) return sfail(FEM_EINVAL, "lr must be >= 0 and finite");
-    StateView<float> v{};
-    cudaStream_t st = nullptr;
-    fem_status r = mesh_stream(s, &v, &st);
-    if (r) return r;
+    fem_status r;
     if ((r = ensure_train(s))) return r;
     if ((r = forward(s, E_in, s->E1, true, st))) return r;
     Grads gr{};
@@ -1637,26 +1654,86 @@ extern "C" fem_status fem_surrogate_train_step(fem_surrogate *s, const float *E_
         k_sg_bwd_mid<<<gb, 128, kSmemBwd, st>>>(s->g, a, gr, gin, gout, s->img, s->L, l, s->err);
     }
     if ((r = launch_check("surrogate backward"))) return r;
+    k_sg_reduce<<<(kNParams + 255) / 256, 256, 0, st>>>(s->partial, s->loss_part, gb, 1.f / (float)s->n,
+                                                        s->grad, s->acc, s->loss, s->loss + 1);
+    if ((r = launch_check("gradient reduction"))) return r;
+    s->n_acc += 1;
+    if (loss_out) {
+        SCU(cudaMemcpyAsync(loss_out, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if ((r = check_err(s, st))) return r;
+    }
+    return FEM_OK;
+}
+
+// One Adam step of size lr with the mean of the accumulated gradients.
+fem_status apply_adam(fem_surrogate *s, float lr, cudaStream_t st)
+{
     AdamArgs ad{};
     const double b1 = 0.9, b2 = 0.999;
-    if (lr > 0.f) s->adam_t += 1;
-    const int64_t t = std::max<int64_t>(s->adam_t, 1);
+    s->adam_t += 1;
+    const double t = (double)s->adam_t;
     ad.lr = lr;
     ad.b1 = (float)b1;
     ad.b2 = (float)b2;
     ad.omb1 = (float)(1.0 - b1);
     ad.omb2 = (float)(1.0 - b2);
     ad.eps = 1e-8f;
-    ad.bc1 = (float)(1.0 - std::pow(b1, (double)t));
-    ad.bc2 = (float)(1.0 - std::pow(b2, (double)t));
-    ad.inv_n = 1.f / (float)s->n;
-    k_sg_reduce_adam<<<(kNParams + 255) / 256, 256, 0, st>>>(s->partial, s->loss_part, gb, s->grad, s->theta,
-                                                             s->mom, s->vel, ad, s->loss);
-    if ((r = launch_check("gradient reduction"))) return r;
-    if (lr > 0.f && (r = pack(s, st))) return r;
-    if (loss_out) {
-        SCU(cudaMemcpyAsync(loss_out, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
-        if ((r = check_err(s, st))) return r;
+    ad.bc1 = (float)(1.0 - std::pow(b1, t));
+    ad.bc2 = (float)(1.0 - std::pow(b2, t));
+    k_sg_adam<<<(kNParams + 255) / 256, 256, 0, st>>>(s->acc, (float)s->n_acc, s->theta, s->mom, s->vel, ad);
+    fem_status r = launch_check("Adam step");
+    if (r) return r;
+    s->n_acc = 0;
+    SCU(cudaMemsetAsync(s->loss + 1, 0, sizeof(double), st));
+    return pack(s, st);
+}
+
+}  // namespace
+
+extern "C" fem_status fem_surrogate_accumulate(fem_surrogate *s, const float *E_in, const float *E_star,
+                                               double *loss_out)
+{
+    if (!s || !E_in || !E_star) return sfail(FEM_EINVAL, "NULL argument");
+    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    r = accumulate_pair(s, E_in, E_star, loss_out, st);
+    return r ? r : sok();
+}
+
+extern "C" fem_status fem_surrogate_apply(fem_surrogate *s, float lr)
+{
+    if (!s) return sfail(FEM_EINVAL, "NULL surrogate");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return sfail(FEM_EINVAL, "lr must be positive and finite");
+    if (s->n_acc == 0) return sfail(FEM_ESTATE, "no accumulated gradient (fem_surrogate_accumulate)");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    r = apply_adam(s, lr, st);
+    return r ? r : sok();
+}
+
+extern "C" fem_status fem_surrogate_train_step(fem_surrogate *s, const float *E_in, const float *E_star,
+                                               float lr, double *loss_out)
+{
+    if (!s || !E_in || !E_star) return sfail(FEM_EINVAL, "NULL argument");
+    if (!s->have_params) return sfail(FEM_ESTATE, "no parameters (fem_surrogate_set_params)");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return sfail(FEM_EINVAL, "lr must be >= 0 and finite");
+    if (s->n_acc != 0) return sfail(FEM_ESTATE, "an accumulated gradient is pending (fem_surrogate_apply)");
+    StateView<float> v{};
+    cudaStream_t st = nullptr;
+    fem_status r = mesh_stream(s, &v, &st);
+    if (r) return r;
+    if ((r = accumulate_pair(s, E_in, E_star, loss_out, st))) return r;
+    if (lr > 0.f) {
+        if ((r = apply_adam(s, lr, st))) return r;
+    } else {   // gradient only: drop the accumulation
+        SCU(cudaMemsetAsync(s->acc, 0, (size_t)kNParams * sizeof(float), st));
+        SCU(cudaMemsetAsync(s->loss + 1, 0, sizeof(double), st));
+        s->n_acc = 0;
     }
     return sok();
 }
@@ -1846,12 +1923,12 @@ extern "C" fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, d
     for (int64_t it = 0; it < n_macro && !r; it++) {
         cudaEventRecord(ev[0], st);
         k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(s->E0, s->g, a.tf);
-        k_sg_feat<<<(rows + 255) / 256, 256, 0, st>>>(s->g, a);
+        k_sg_feat<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a);
         cudaEventRecord(ev[1], st);
         k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
         cudaEventRecord(ev[2], st);
         for (int l = 0; l < kLayers; l++)
-            k_sg_msg<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+            k_sg_msg<<<(rows * 4 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
         cudaEventRecord(ev[3], st);
         for (int l = 0; l < kLayers - 1; l++)
             k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l, 0, s->err);

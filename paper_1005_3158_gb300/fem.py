@@ -43,6 +43,7 @@ ABI_SYMBOLS = (
     "fem_get_temperature_async_f32",
     "fem_surrogate_create", "fem_surrogate_info", "fem_surrogate_order",
     "fem_surrogate_set_params", "fem_surrogate_get_params", "fem_surrogate_read_state",
+    "fem_surrogate_accumulate", "fem_surrogate_apply",
     "fem_surrogate_write_state", "fem_surrogate_predict", "fem_surrogate_train_step",
     "fem_surrogate_advance", "fem_surrogate_solve", "fem_surrogate_profile", "fem_surrogate_debug",
     "fem_surrogate_destroy",
@@ -137,6 +138,8 @@ def _load():
         "fem_surrogate_write_state": [P, P],
         "fem_surrogate_predict": [P, P, P],
         "fem_surrogate_train_step": [P, P, P, ctypes.c_float, dp],
+        "fem_surrogate_accumulate": [P, P, P, dp],
+        "fem_surrogate_apply": [P, ctypes.c_float],
         "fem_surrogate_advance": [P, i64],
         "fem_surrogate_solve": [P, i64, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(i64), dp],
         "fem_surrogate_profile": [P, i64, dp],
@@ -702,6 +705,15 @@ class Surrogate:
         _check(_lib.fem_surrogate_train_step(self.h, _dptr(E_in), _dptr(E_star), float(lr),
                                              ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+    def accumulate(self, E_in, E_star, want_loss=False):
+        loss = ctypes.c_double(float("nan"))
+        _check(_lib.fem_surrogate_accumulate(self.h, _dptr(E_in), _dptr(E_star),
+                                             ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def apply(self, lr):
+        _check(_lib.fem_surrogate_apply(self.h, float(lr)))
 
     def advance(self, n_macro):
         _check(_lib.fem_surrogate_advance(self.h, int(n_macro)))

@@ -87,11 +87,13 @@ def generate_pairs(probs, every=16, max_steps=4800, log=print):
     return b, s, pairs, dt
 
 
-def train(s, pairs, iters=3000, lr0=1e-3, lr1=1e-5, seed=5, init=None, skip_first=0, log=print):
-    """Adam on random pairs (one whole batch snapshot per step), cosine
-    learning-rate decay from lr0 to lr1; the first skip_first pairs (the
-    steep transient right after the pour, which the hybrid solve leaves to
-    the explicit solver) are not used.  Returns the loss history."""
+def train(s, pairs, iters=3000, lr0=1e-3, lr1=1e-5, seed=5, init=None, skip_first=0,
+          per_step=1, log=print):
+    """Adam on random pairs (each a whole batch snapshot), per_step pairs
+    accumulated per step, cosine learning-rate decay from lr0 to lr1; the
+    first skip_first pairs (the steep transient right after the pour, which
+    the hybrid solve leaves to the explicit solver) are not used.  Returns
+    the loss history."""
     theta = mg.surrogate_init(param_shapes(), seed=seed) if init is None else init
     s.set_params(theta)
     rng = np.random.default_rng(seed)
@@ -100,10 +102,14 @@ def train(s, pairs, iters=3000, lr0=1e-3, lr1=1e-5, seed=5, init=None, skip_firs
     t0 = time.time()
     for it in range(iters):
         lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * it / max(1, iters - 1)))
-        Ea, Eb = pairs[int(rng.integers(len(pairs)))]
         want = it % 50 == 0 or it == iters - 1
-        loss = s.train_step(Ea, Eb, lr, want_loss=want)
+        losses = []
+        for q in range(per_step):
+            Ea, Eb = pairs[int(rng.integers(len(pairs)))]
+            losses.append(s.accumulate(Ea, Eb, want_loss=want))
+        s.apply(lr)
         if want:
+            loss = float(np.mean(losses))
             hist.append((it, loss))
             if it % 500 == 0 or it == iters - 1:
                 log(f"  iter {it}: loss {loss:.4g}, lr {lr:.2e}, {time.time() - t0:.1f} s")
@@ -253,6 +259,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--skip-first", type=int, default=0)
+    ap.add_argument("--per-step", type=int, default=1, help="pairs accumulated per Adam step")
     ap.add_argument("--init", default="", help="start from these parameters")
     ap.add_argument("--n-eval", type=int, default=10)
     ap.add_argument("--judge-every", type=int, default=8)
@@ -266,7 +273,8 @@ def main(argv=None):
         b, s, pairs, dt = generate_pairs(probs, every=a.every)
         print(f"pairs: {len(pairs)} (dt {dt:.4g} s), {time.time() - t0:.1f} s", flush=True)
         init = np.load(a.init).astype(np.float32) if a.init else None
-        hist = train(s, pairs, iters=a.iters, lr0=a.lr, init=init, skip_first=a.skip_first)
+        hist = train(s, pairs, iters=a.iters, lr0=a.lr, init=init, skip_first=a.skip_first,
+                     per_step=a.per_step)
         np.save(a.out, s.params())
         if a.json:
             with open(a.json, "w") as f:
