@@ -553,7 +553,7 @@ def run_surrogate(args):
     geoms = mg.surrogate_eval_set(10)[:max(1, args.n_eval)]
     clocks = ClockSampler(0)
     clocks.start()
-    res = [sgd.evaluate(p, theta, args.judge_every, args.tol, log=lambda *a: None) for p in geoms]
+    res = [sgd.evaluate(p, theta, args.judge_every, (args.tol,), log=lambda *a: None) for p in geoms]
     clk = clocks.stop()
     ms_p = sum(r["ms_plain"] for r in res)
     ms_s = sum(r["ms_surrogate"] for r in res)
@@ -634,7 +634,8 @@ def run_surrogate(args):
                    "ms_per_16_steps_plain": ms_p / sum(r["macro_steps"] for r in res),
                    "ms_per_16_steps_surrogate": ms_s / sum(r["macro_steps"] for r in res),
                    "ms_per_16_steps_network": float(np.mean([r["ms_per_16_steps_network"] for r in res])),
-                   "per_geometry": [{k: v for k, v in r.items() if k != "err_K_by_macro"} for r in res],
+                   "per_geometry": [{k: v for k, v in r.items() if k not in ("err_K_by_macro", "by_tol")}
+                                    for r in res],
                    "l2": "inputs larger than L2 (no flush)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": None,

@@ -550,15 +550,7 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
         for (int j = 0; j < NPT; j++) {
             R[j] = Cp[j] = real(0);
             if (k1[j] > k0[j] && !FEM_IN(k1[j] - 1, a.n_copies, a.err)) k1[j] = k0[j];
-            int k = k0[j];
-            for (; k + 3 < k1[j]; k += 4) {   // loads first, then the adds in block order
-                const real p0 = a.P[k], p1 = a.P[k + 1], p2 = a.P[k + 2], p3 = a.P[k + 3];
-                R[j] += p0;
-                R[j] += p1;
-                R[j] += p2;
-                R[j] += p3;
-            }
-            for (; k < k1[j]; ++k) R[j] += a.P[k];   // block order
+            for (int k = k0[j]; k < k1[j]; ++k) R[j] += a.P[k];   // block order
             if (a.Pc)   // apparent capacity: T += dt R / C_app
                 for (int k = k0[j]; k < k1[j]; ++k) Cp[j] += a.Pc[k];
         }
@@ -571,21 +563,11 @@ __global__ void __launch_bounds__(NT) k_shared_update(const BlockArgs<real> a, c
     }
 #pragma unroll
     for (int j = 0; j < NPT; j++)
-        if (act[j]) {
-            int k = k0[j];
-            for (; k + 3 < k1[j]; k += 4) {   // the four positions first, then the stores
-                const int32_t m0 = __ldg(a.mpos + k), m1 = __ldg(a.mpos + k + 1),
-                              m2 = __ldg(a.mpos + k + 2), m3 = __ldg(a.mpos + k + 3);
-                if (FEM_IN(m0, (int64_t)a.n_blocks * a.ls, a.err)) a.Eloc[m0] = E[j];
-                if (FEM_IN(m1, (int64_t)a.n_blocks * a.ls, a.err)) a.Eloc[m1] = E[j];
-                if (FEM_IN(m2, (int64_t)a.n_blocks * a.ls, a.err)) a.Eloc[m2] = E[j];
-                if (FEM_IN(m3, (int64_t)a.n_blocks * a.ls, a.err)) a.Eloc[m3] = E[j];
-            }
-            for (; k < k1[j]; ++k) {
+        if (act[j])
+            for (int k = k0[j]; k < k1[j]; ++k) {
                 const int32_t mp = __ldg(a.mpos + k);
                 if (FEM_IN(mp, (int64_t)a.n_blocks * a.ls, a.err)) a.Eloc[mp] = E[j];
             }
-        }
 }
 
 // Interface faces (Eq. 8): every interface face is a Robin face whose

@@ -131,17 +131,30 @@ def _solid_times(T_hist, times, alloy, Ts):
     return out
 
 
-def evaluate(p, theta, judge_every=8, tol=2.0, max_macro=4000, log=print):
-    """One geometry: plain FP32 solve from the pour until the casting has
-    solidified (plus 10 %), then the surrogate's hybrid solve over the same
-    macro steps, both read back every macro step for the errors, then both
-    timed again without read-backs."""
+def _timed(fn):
     import torch
+    stream = torch.cuda.current_stream()
+    _sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    _sync()
+    return e0.elapsed_time(e1)
+
+
+def evaluate(p, theta, judge_every=8, tols=(2.0,), max_macro=4000, log=print):
+    """One geometry: plain FP32 solve from the pour until the casting has
+    solidified (plus 10 %); then, for every tolerance, the surrogate's
+    hybrid solve over the same macro steps read back every macro step (max
+    nodal difference, solidification time) and timed again without
+    read-backs; the plain solve and the network alone are timed too.  The
+    result's top-level figures are those of the first tolerance; all are in
+    res["by_tol"]."""
     Ts = float(p.materials[0][4])
     alloy = np.zeros(p.n_nodes, bool)
     alloy[p.tets[p.mat == 0].ravel()] = True
     res = {"geometry": p.name, "n_tets": p.n_tets, "n_nodes": p.n_nodes}
-    # plain solve with read-backs: temperatures at every macro step
     m = fem.Mesh(p, "fp32", reorder=1)
     dt = 0.9 * m.stable_dt()
     T_plain = [m.temperature().astype(np.float32)]
@@ -152,96 +165,79 @@ def evaluate(p, theta, judge_every=8, tol=2.0, max_macro=4000, log=print):
         T_plain.append(m.temperature().astype(np.float32))
         if T_plain[-1][alloy].max() <= Ts:
             break
-    n_solid = k
-    n_macro = min(max_macro, int(math.ceil(1.1 * n_solid)))
+    n_macro = min(max_macro, int(math.ceil(1.1 * k)))
     while k < n_macro:
         m.step(MACRO, dt)
         k += 1
         T_plain.append(m.temperature().astype(np.float32))
+    m.close()
     times = np.arange(n_macro + 1) * MACRO * dt
-    res.update({"dt": dt, "macro_steps": n_macro, "steps": n_macro * MACRO,
-                "simulated_s": float(times[-1])})
-    # surrogate (hybrid) solve with read-backs
-    m2 = fem.Mesh(p, "fp32", reorder=1)
-    s = fem.Surrogate(m2, dt)
-    s.set_params(theta)
-    T_sg = [m2.temperature().astype(np.float32)]
-    err_t = [0.0]
-    n_sg = n_pl = n_fail = 0
-    worst_judge = 0.0
-    plain_until = 0
-    # the policy of fem_surrogate_solve, one macro step at a time so that
-    # every macro step can be read back
-    for k in range(n_macro):
-        if judge_every > 0 and k % judge_every == 0:
-            a, b_, c, e = s.solve(1, 1, tol)
-            n_pl += b_
-            n_fail += c
-            worst_judge = max(worst_judge, e)
-            if c:
-                plain_until = k + judge_every
-        elif k < plain_until:
-            m2.step(MACRO, dt)
-            n_pl += 1
-        else:
-            s.advance(1)
-            n_sg += 1
-        T_sg.append(m2.temperature().astype(np.float32))
-        err_t.append(float(np.abs(T_sg[-1] - T_plain[k + 1]).max()))
     st_plain = _solid_times(T_plain, times, alloy, Ts)
-    st_sg = _solid_times(T_sg, times, alloy, Ts)
-    ts_p, ts_s = float(st_plain.max()), float(st_sg.max())
-    res.update({"max_err_K": float(max(err_t)), "err_K_by_macro": err_t[::max(1, n_macro // 20)],
-                "solid_time_plain_s": ts_p, "solid_time_surrogate_s": ts_s,
-                "solid_time_rel_err": abs(ts_s - ts_p) / ts_p if math.isfinite(ts_p) else None,
-                "macro_by_surrogate": n_sg, "macro_by_solver": n_pl, "judge_failures": n_fail,
-                "max_judged_K": worst_judge})
-    s.close()
-    m2.close()
-    # timing without read-backs, CUDA events on the default stream
-    stream = torch.cuda.current_stream()
-    for name in ("plain", "surrogate"):
-        mm = fem.Mesh(p, "fp32", reorder=1)
-        ss = None
-        if name == "surrogate":
-            ss = fem.Surrogate(mm, dt)
-            ss.set_params(theta)
-            ss.solve(2, judge_every, tol)       # warm-up
-        else:
-            mm.step(2 * MACRO, dt)
-        mm.set_temperature(p.T0)
-        _sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        if name == "plain":
-            mm.step(n_macro * MACRO, dt)
-        else:
-            ss.solve(n_macro, judge_every, tol)
-        e1.record(stream)
-        _sync()
-        res[f"ms_{name}"] = e0.elapsed_time(e1)
-        if ss is not None:
-            ss.close()
-        mm.close()
-    # the network alone: n_macro macro steps, no judge
+    ts_p = float(st_plain.max())
+    res.update({"dt": dt, "macro_steps": n_macro, "steps": n_macro * MACRO,
+                "simulated_s": float(times[-1]), "solid_time_plain_s": ts_p})
+    # timings: plain solver, network alone
     mm = fem.Mesh(p, "fp32", reorder=1)
+    mm.step(2 * MACRO, dt)
+    mm.set_temperature(p.T0)
+    res["ms_plain"] = _timed(lambda: mm.step(n_macro * MACRO, dt))
     ss = fem.Surrogate(mm, dt)
     ss.set_params(theta)
+    mm.set_temperature(p.T0)
     ss.advance(2)
-    _sync()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ss.advance(n_macro)
-    e1.record(stream)
-    _sync()
-    res["ms_per_16_steps_network"] = e0.elapsed_time(e1) / n_macro
+    mm.set_temperature(p.T0)
+    res["ms_per_16_steps_network"] = _timed(lambda: ss.advance(n_macro)) / n_macro
+    res["ms_per_16_steps_plain"] = res["ms_plain"] / n_macro
+    by_tol = {}
+    for tol in tols:
+        r = {"tol_K": tol}
+        m2 = fem.Mesh(p, "fp32", reorder=1)
+        s = fem.Surrogate(m2, dt)
+        s.set_params(theta)
+        T_sg = [m2.temperature().astype(np.float32)]
+        err_t = [0.0]
+        n_sg = n_pl = n_fail = 0
+        worst_judge = 0.0
+        plain_until = 0
+        # the policy of fem_surrogate_solve, one macro step at a time so that
+        # every macro step can be read back
+        for k in range(n_macro):
+            if judge_every > 0 and k % judge_every == 0:
+                _, b_, c, e = s.solve(1, 1, tol)
+                n_pl += b_
+                n_fail += c
+                worst_judge = max(worst_judge, e)
+                if c:
+                    plain_until = k + judge_every
+            elif k < plain_until:
+                m2.step(MACRO, dt)
+                n_pl += 1
+            else:
+                s.advance(1)
+                n_sg += 1
+            T_sg.append(m2.temperature().astype(np.float32))
+            err_t.append(float(np.abs(T_sg[-1] - T_plain[k + 1]).max()))
+        s.close()
+        m2.close()
+        ts_s = float(_solid_times(T_sg, times, alloy, Ts).max())
+        r.update({"max_err_K": float(max(err_t)), "err_K_by_macro": err_t[::max(1, n_macro // 20)],
+                  "solid_time_surrogate_s": ts_s,
+                  "solid_time_rel_err": abs(ts_s - ts_p) / ts_p if math.isfinite(ts_p) else None,
+                  "macro_by_surrogate": n_sg, "macro_by_solver": n_pl, "judge_failures": n_fail,
+                  "max_judged_K": worst_judge})
+        mm.set_temperature(p.T0)
+        ss.solve(2, judge_every, tol)       # warm-up
+        mm.set_temperature(p.T0)
+        r["ms_surrogate"] = _timed(lambda: ss.solve(n_macro, judge_every, tol))
+        r["ms_per_16_steps_surrogate"] = r["ms_surrogate"] / n_macro
+        r["speedup"] = res["ms_plain"] / r["ms_surrogate"]
+        by_tol[str(tol)] = r
+        log(json.dumps({"geometry": p.name, **{k: v for k, v in r.items() if k != "err_K_by_macro"}}))
     ss.close()
     mm.close()
-    res["ms_per_16_steps_plain"] = res["ms_plain"] / n_macro
-    res["ms_per_16_steps_surrogate"] = res["ms_surrogate"] / n_macro
-    res["speedup"] = res["ms_plain"] / res["ms_surrogate"]
-    m.close()
-    log(json.dumps({k: v for k, v in res.items() if k != "err_K_by_macro"}))
+    res.update({k: v for k, v in by_tol[str(tols[0])].items()})
+    res["by_tol"] = by_tol
+    log(json.dumps({k: v for k, v in res.items() if k not in ("err_K_by_macro", "by_tol")}))
     return res
 
 
@@ -263,7 +259,7 @@ def main(argv=None):
     ap.add_argument("--init", default="", help="start from these parameters")
     ap.add_argument("--n-eval", type=int, default=10)
     ap.add_argument("--judge-every", type=int, default=8)
-    ap.add_argument("--tol", type=float, default=2.0)
+    ap.add_argument("--tol", type=float, nargs="+", default=[2.0])
     ap.add_argument("--json", default="")
     a = ap.parse_args(argv)
     if a.cmd == "train":
@@ -295,7 +291,7 @@ def main(argv=None):
         m.close()
     else:
         theta = np.load(a.params).astype(np.float32)
-        out = [evaluate(p, theta, a.judge_every, a.tol) for p in mg.surrogate_eval_set(a.n_eval)]
+        out = [evaluate(p, theta, a.judge_every, tuple(a.tol)) for p in mg.surrogate_eval_set(a.n_eval)]
         if a.json:
             with open(a.json, "w") as f:
                 json.dump(out, f)
