@@ -17,6 +17,7 @@
 
 #include "fem.h"
 #include "fem_internal.h"
+#include "fem_mesh_access.h"
 #include "fem_plan.h"
 
 using namespace fem;

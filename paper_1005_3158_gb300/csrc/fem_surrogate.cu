@@ -34,6 +34,7 @@
 
 #include "fem_device.cuh"
 #include "fem_internal.h"
+#include "fem_mesh_access.h"
 #include "fem_surrogate.h"
 #include "fem_tc.cuh"
 
