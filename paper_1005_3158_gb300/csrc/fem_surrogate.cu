@@ -783,13 +783,80 @@ __global__ void __launch_bounds__(128) k_sg_bwd_head(Graph g, Acts a, Grads gr, 
     if (t < 32) tc::tmem_free(tbase, 512);
 }
 
-// Backward of layer l's message and projection, then layer l-1's node-local
-// backward (l >= 1) or the encoder's (l == 0):
-//   dphi_j = sum_i W_ji (gm_i - gm_j)      (adjoint of m = s L phi, W symmetric)
-//   dpre = dphi (phi > 0);  dP_l^T += [h_l; 1]^T dpre;  dh_l = dhdir + dpre P_l
-__global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr, const float *gm_in,
-                                                    float *gm_out, const uint8_t *__restrict__ img,
-                                                    Layout L, int l, int *err)
+// Adjoint of layer l's messages: dpre_j = (phi_j > 0) sum_i W_ji (gm_i -
+// gm_j) (the adjoint of m = s L phi for symmetric W, gm = s dL/dm), as bf16;
+// evaluated as sum_i W_ji gm_i - (sum_i W_ji) gm_j.  Four lanes per node, 8
+// channels each, neighbours in chunks of 4 shared by shuffles.
+__global__ void __launch_bounds__(256) k_sg_msg_bwd(Graph g, const float *__restrict__ gm,
+                                                    const uint16_t *__restrict__ phi,
+                                                    uint16_t *__restrict__ dpre)
+{
+    const int lane = threadIdx.x & 31, sub = lane & 3;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 4;
+    const int64_t rows = (int64_t)g.n_tiles * 128;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool ok = j < g.n;
+    int k0 = 0, k1 = 0;
+    if (ok) {
+        k0 = __ldg(g.rowptr + j);
+        k1 = __ldg(g.rowptr + j + 1);
+    }
+    int nch = (k1 - k0 + 3) >> 2;
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) nch = max(nch, __shfl_xor_sync(0xffffffffu, nch, o));
+    for (int c = 0; c < nch; c++) {
+        const int kk = k0 + 4 * c + sub;
+        const bool has = kk < k1;
+        const int ii = has ? __ldg(g.col + kk) : 0;
+        const float ww = has ? __ldg(g.w + kk) : 0.f;
+        float4 o0[4], o1[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int q = __shfl_sync(0xffffffffu, ii, (lane & ~3) | u);
+            o0[u] = __ldg(reinterpret_cast<const float4 *>(gm + (int64_t)q * 32) + 2 * sub);
+            o1[u] = __ldg(reinterpret_cast<const float4 *>(gm + (int64_t)q * 32) + 2 * sub + 1);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const float w = __shfl_sync(0xffffffffu, ww, (lane & ~3) | u);
+            acc[0] = fmaf(w, o0[u].x, acc[0]);
+            acc[1] = fmaf(w, o0[u].y, acc[1]);
+            acc[2] = fmaf(w, o0[u].z, acc[2]);
+            acc[3] = fmaf(w, o0[u].w, acc[3]);
+            acc[4] = fmaf(w, o1[u].x, acc[4]);
+            acc[5] = fmaf(w, o1[u].y, acc[5]);
+            acc[6] = fmaf(w, o1[u].z, acc[6]);
+            acc[7] = fmaf(w, o1[u].w, acc[7]);
+        }
+    }
+    uint4 out = make_uint4(0u, 0u, 0u, 0u);
+    if (ok) {
+        const float4 m0 = __ldg(reinterpret_cast<const float4 *>(gm + j * 32) + 2 * sub);
+        const float4 m1 = __ldg(reinterpret_cast<const float4 *>(gm + j * 32) + 2 * sub + 1);
+        const float me[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        const uint4 ph = __ldg(reinterpret_cast<const uint4 *>(phi + j * 32) + sub);
+        const uint32_t pw[4] = {ph.x, ph.y, ph.z, ph.w};
+        const float ws = __ldg(g.wsum + j);
+        uint32_t q[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            float d0 = fmaf(-ws, me[2 * e], acc[2 * e]), d1 = fmaf(-ws, me[2 * e + 1], acc[2 * e + 1]);
+            if (!(bf_lo(pw[e]) > 0.f)) d0 = 0.f;
+            if (!(bf_hi(pw[e]) > 0.f)) d1 = 0.f;
+            q[e] = pack_bf2(d0, d1);
+        }
+        out = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+    if (j < rows) reinterpret_cast<uint4 *>(dpre + j * 32)[sub] = out;
+}
+
+// Backward of layer l's projection, then layer l-1's node-local backward
+// (l >= 1) or the encoder's (l == 0), from dpre (k_sg_msg_bwd):
+//   dP_l^T += [h_l; 1]^T dpre;  dh_l = dhdir + dpre P_l
+__global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr,
+                                                    const uint16_t *__restrict__ dpre, float *gm_out,
+                                                    const uint8_t *__restrict__ img, Layout L, int l,
+                                                    int *err)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sA1 = sm + kBA1, *sB1 = sm + kBB1, *sA2 = sm + kBA2, *sB2 = sm + kBB2;
@@ -797,8 +864,7 @@ __global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr, c
     uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + kBTmem);
     int *sOk = reinterpret_cast<int *>(sm + kBOk);
     const uint32_t bar = smem_addr(sm + kBBar);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int grp = lane >> 3, sub = lane & 7;
+    const int t = threadIdx.x;
     if (t < 32) tc::tmem_alloc(sTmem, 512);
     if (t == 0) { mbar_init(bar, 1); mbar_fence_init(); }
     zero_smem(sA2, 128 * 128 * 2);
@@ -814,57 +880,21 @@ __global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr, c
     bool first = true, ok = true;
     for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
         const int64_t tile0 = (int64_t)tile * 128;
-        // adjoint message sums: 8 lanes per node, 4 channels per lane
-#pragma unroll 1
-        for (int rr = 0; rr < 8; rr++) {
-            const int r = warp * 32 + rr * 4 + grp;
-            const int64_t j = tile0 + r;
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            const bool okj = j < g.n;
-            float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
-            int k0 = 0, k1 = 0;
-            if (okj) {
-                me = __ldg(reinterpret_cast<const float4 *>(gm_in + j * 32) + sub);
-                k0 = __ldg(g.rowptr + j);
-                k1 = __ldg(g.rowptr + j + 1);
-            }
-            // neighbours in chunks of 8 shared by the node's 8-lane group
-            const int nch = (k1 - k0 + 7) >> 3;
-            const int m1 = max(nch, __shfl_xor_sync(0xffffffffu, nch, 8));
-            const int nmax = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));
-            for (int c = 0; c < nmax; c++) {
-                const int kk = k0 + 8 * c + sub;
-                const bool has = kk < k1;
-                const int jj = has ? __ldg(g.col + kk) : (okj ? (int)j : 0);
-                const float ww = has ? __ldg(g.w + kk) : 0.f;
-                float4 o[8];
+        // dpre (from k_sg_msg_bwd): A operand (node rows) and transposed B
+        {
+            const int64_t r64 = tile0 + t;
+            const uint4 *ds = reinterpret_cast<const uint4 *>(dpre + r64 * 32);
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const int q = __shfl_sync(0xffffffffu, jj, (lane & ~7) | u);
-                    o[u] = __ldg(reinterpret_cast<const float4 *>(gm_in + (int64_t)q * 32) + sub);
-                }
+            for (int q = 0; q < 4; q++) {
+                const uint4 v = ds[q];
+                st_row8(sA1, t, 8 * q, 32, v);
+                const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const float w = __shfl_sync(0xffffffffu, ww, (lane & ~7) | u);
-                    d[0] += w * (o[u].x - me.x);
-                    d[1] += w * (o[u].y - me.y);
-                    d[2] += w * (o[u].z - me.z);
-                    d[3] += w * (o[u].w - me.w);
+                for (int e = 0; e < 4; e++) {
+                    st_T(sB2, 8 * q + 2 * e, t, 128, (uint16_t)(w4[e] & 0xFFFF));
+                    st_T(sB2, 8 * q + 2 * e + 1, t, 128, (uint16_t)(w4[e] >> 16));
                 }
             }
-            if (okj) {
-                const uint2 ph = __ldg(reinterpret_cast<const uint2 *>(a.phi[l] + j * 32) + sub);
-                if (!(bf_lo(ph.x) > 0.f)) d[0] = 0.f;
-                if (!(bf_hi(ph.x) > 0.f)) d[1] = 0.f;
-                if (!(bf_lo(ph.y) > 0.f)) d[2] = 0.f;
-                if (!(bf_hi(ph.y) > 0.f)) d[3] = 0.f;
-            }
-            const uint32_t q0 = pack_bf2(d[0], d[1]), q1 = pack_bf2(d[2], d[3]);
-            *reinterpret_cast<uint2 *>(sA1 + core_off(r, 4 * sub, 32)) = make_uint2(q0, q1);
-            st_T(sB2, 4 * sub, r, 128, (uint16_t)(q0 & 0xFFFF));
-            st_T(sB2, 4 * sub + 1, r, 128, (uint16_t)(q0 >> 16));
-            st_T(sB2, 4 * sub + 2, r, 128, (uint16_t)(q1 & 0xFFFF));
-            st_T(sB2, 4 * sub + 3, r, 128, (uint16_t)(q1 >> 16));
         }
         const int64_t i = tile0 + t;
         const bool valid = i < g.n;
@@ -1114,6 +1144,7 @@ struct fem_surrogate {
     int *err = nullptr;
     bool train_ok = false;            // training buffers allocated
     float *dhdir = nullptr, *gm[2] = {nullptr, nullptr}, *partial = nullptr;
+    uint16_t *dpre = nullptr;         // [rows][32] bf16, adjoint messages of one layer
     double *loss_part = nullptr, *loss = nullptr;   // loss[0]: last pair, loss[1]: accumulated
     int64_t adam_t = 0;
     bool have_params = false;
@@ -1412,6 +1443,7 @@ fem_status ensure_train(fem_surrogate *s)
     if ((st = salloc(s, &s->dhdir, rows * 64))) return st;
     if ((st = salloc(s, &s->gm[0], rows * 32))) return st;
     if ((st = salloc(s, &s->gm[1], rows * 32))) return st;
+    if ((st = salloc(s, &s->dpre, rows * 32))) return st;
     if ((st = salloc(s, &s->partial, (size_t)s->n_sm * kPartFloats))) return st;
     if ((st = salloc(s, &s->loss_part, (size_t)s->n_sm))) return st;
     if ((st = salloc(s, &s->loss, 2))) return st;
@@ -1652,7 +1684,8 @@ fem_status accumulate_pair(fem_surrogate *s, const float *E_in, const float *E_s
     for (int l = kLayers - 1; l >= 0; l--) {
         const float *gin = s->gm[(kLayers - 1 - l) & 1];
         float *gout = s->gm[(kLayers - l) & 1];
-        k_sg_bwd_mid<<<gb, 128, kSmemBwd, st>>>(s->g, a, gr, gin, gout, s->img, s->L, l, s->err);
+        k_sg_msg_bwd<<<(s->n_tiles * kTile * 4 + 255) / 256, 256, 0, st>>>(s->g, gin, a.phi[l], s->dpre);
+        k_sg_bwd_mid<<<gb, 128, kSmemBwd, st>>>(s->g, a, gr, s->dpre, gout, s->img, s->L, l, s->err);
     }
     if ((r = launch_check("surrogate backward"))) return r;
     k_sg_reduce<<<(kNParams + 255) / 256, 256, 0, st>>>(s->partial, s->loss_part, gb, 1.f / (float)s->n,
