@@ -88,16 +88,22 @@ def generate_pairs(probs, every=16, max_steps=4800, log=print):
 
 
 def train(s, pairs, iters=3000, lr0=1e-3, lr1=1e-5, seed=5, init=None, skip_first=0,
-          per_step=1, log=print):
+          per_step=1, push=0.0, log=print):
     """Adam on random pairs (each a whole batch snapshot), per_step pairs
     accumulated per step, cosine learning-rate decay from lr0 to lr1; the
     first skip_first pairs (the steep transient right after the pour, which
-    the hybrid solve leaves to the explicit solver) are not used.  Returns
-    the loss history."""
+    the hybrid solve leaves to the explicit solver) are not used.  With
+    probability `push` a sample is a pushforward pair instead: the network's
+    own prediction from pair k's input, trained towards the solver's state
+    one macro step later (pair k + 1's target), so that the network learns
+    to correct the errors its own steps make (the pairs are consecutive
+    macro steps).  Returns the loss history."""
+    import torch
     theta = mg.surrogate_init(param_shapes(), seed=seed) if init is None else init
     s.set_params(theta)
     rng = np.random.default_rng(seed)
     pairs = pairs[skip_first:]
+    scratch = torch.empty_like(pairs[0][0])
     hist = []
     t0 = time.time()
     for it in range(iters):
@@ -105,8 +111,13 @@ def train(s, pairs, iters=3000, lr0=1e-3, lr1=1e-5, seed=5, init=None, skip_firs
         want = it % 50 == 0 or it == iters - 1
         losses = []
         for q in range(per_step):
-            Ea, Eb = pairs[int(rng.integers(len(pairs)))]
-            losses.append(s.accumulate(Ea, Eb, want_loss=want))
+            if push > 0.0 and rng.random() < push and len(pairs) > 1:
+                k = int(rng.integers(len(pairs) - 1))
+                s.predict(pairs[k][0], scratch)
+                losses.append(s.accumulate(scratch, pairs[k + 1][1], want_loss=want))
+            else:
+                Ea, Eb = pairs[int(rng.integers(len(pairs)))]
+                losses.append(s.accumulate(Ea, Eb, want_loss=want))
         s.apply(lr)
         if want:
             loss = float(np.mean(losses))
@@ -256,6 +267,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--skip-first", type=int, default=0)
     ap.add_argument("--per-step", type=int, default=1, help="pairs accumulated per Adam step")
+    ap.add_argument("--push", type=float, default=0.0, help="fraction of pushforward pairs")
     ap.add_argument("--init", default="", help="start from these parameters")
     ap.add_argument("--n-eval", type=int, default=10)
     ap.add_argument("--judge-every", type=int, default=8)
@@ -270,7 +282,7 @@ def main(argv=None):
         print(f"pairs: {len(pairs)} (dt {dt:.4g} s), {time.time() - t0:.1f} s", flush=True)
         init = np.load(a.init).astype(np.float32) if a.init else None
         hist = train(s, pairs, iters=a.iters, lr0=a.lr, init=init, skip_first=a.skip_first,
-                     per_step=a.per_step)
+                     per_step=a.per_step, push=a.push)
         np.save(a.out, s.params())
         if a.json:
             with open(a.json, "w") as f:
