@@ -82,6 +82,30 @@ __device__ __forceinline__ void st_row8(uint8_t *s, uint32_t r, uint32_t k0, uin
     *reinterpret_cast<uint4 *>(s + core_off(r, k0, K)) = v;
 }
 
+// Activations with K channels stored tile by tile in the tensor-core
+// operand layout: tile t (nodes 128 t .. 128 t + 127) is one contiguous
+// block of 256 K bytes laid out as the core-matrix operand of fem_tc.cuh,
+// so one bulk copy brings a tile into shared memory ready for the MMA.
+// Pointer to the 8 channels c0..c0+7 of node i.
+__device__ __forceinline__ uint16_t *tile_chunk(uint16_t *base, int64_t i, uint32_t c0, uint32_t K)
+{
+    return base + (i >> 7) * (128 * (int64_t)K) + (core_off((uint32_t)(i & 127), c0, K) >> 1);
+}
+__device__ __forceinline__ const uint16_t *tile_chunk(const uint16_t *base, int64_t i, uint32_t c0, uint32_t K)
+{
+    return base + (i >> 7) * (128 * (int64_t)K) + (core_off((uint32_t)(i & 127), c0, K) >> 1);
+}
+// Node i's row of a tile-layout activation, 8 channels per element.
+struct TileRow {
+    const uint16_t *base;
+    int64_t i;
+    uint32_t K;
+    __device__ __forceinline__ uint4 operator[](int q) const
+    {
+        return *reinterpret_cast<const uint4 *>(tile_chunk(base, i, 8 * q, K));
+    }
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -175,7 +199,7 @@ __global__ void __launch_bounds__(256) k_sg_feat(Graph g, Acts a)
                                 pack_bf2(x[6], x[7]));
     const uint4 q1 = make_uint4(pack_bf2(x[8], x[9]), pack_bf2(x[10], x[11]), pack_bf2(x[12], x[13]),
                                 pack_bf2(x[14], x[15]));
-    reinterpret_cast<uint4 *>(a.x + (size_t)i * 16)[sub] = sub == 0 ? q0 : q1;
+    *reinterpret_cast<uint4 *>(tile_chunk(a.x, i, 8 * sub, 16)) = sub == 0 ? q0 : q1;
 }
 
 // Shared-memory plan of the forward kernels (bytes, 128-byte aligned).
@@ -215,11 +239,8 @@ __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uin
     const uint32_t sa = smem_addr(sA), sb1 = smem_addr(sB1), sb2 = smem_addr(sB2);
     for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
         const int64_t i = (int64_t)tile * 128 + tid;
-        {
-            const uint4 *xs = reinterpret_cast<const uint4 *>(a.x + (size_t)i * 16);
-            st_row8(sA, tid, 0, 16, xs[0]);
-            st_row8(sA, tid, 8, 16, xs[1]);
-        }
+        st_row8(sA, tid, 0, 16, *reinterpret_cast<const uint4 *>(tile_chunk(a.x, i, 0, 16)));
+        st_row8(sA, tid, 8, 16, *reinterpret_cast<const uint4 *>(tile_chunk(a.x, i, 8, 16)));
         tc::fence_smem_async();
         __syncthreads();
         if (tid == 0) {
@@ -245,11 +266,10 @@ __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uin
 #pragma unroll
             for (int c = 0; c < 32; c++) hp[c] = 0u;
         }
-        uint4 *hs = reinterpret_cast<uint4 *>(a.h[0] + (size_t)i * 64);
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const uint4 v = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-            hs[q] = v;
+            *reinterpret_cast<uint4 *>(tile_chunk(a.h[0], i, 8 * q, 64)) = v;
             st_row8(sA, tid, 8 * q, 64, v);
         }
         tc::fence_before();
@@ -290,82 +310,144 @@ __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uin
 
 // Graph messages of layer l: m_i = s_i sum_j W_ij (phi_j - phi_i), 32
 // channels, FP32 sums of bf16 values, written as bf16; evaluated as
-// s_i (sum_j W_ij phi_j - (sum_j W_ij) phi_i).  Four lanes per node (8
-// channels each, one 16-byte gather per neighbour and lane), eight nodes per
-// warp; a node's neighbours are taken in chunks of 4 whose columns and
-// weights the node's lanes load together and share by shuffles.  A sparse
-// gather with ~14 non-zeros per row: CUDA cores, many warps per SM to hide
-// the gather latency.
+// s_i (sum_j W_ij phi_j - (sum_j W_ij) phi_i).  Two lanes per node (16
+// channels each: two 16-byte gathers per neighbour and lane), sixteen nodes
+// per warp; a node's neighbours are taken in pairs whose columns and
+// weights the node's two lanes load together and share by shuffles.  A
+// sparse gather with ~14 non-zeros per row: CUDA cores, many warps per SM to
+// hide the gather latency.
 __global__ void __launch_bounds__(256) k_sg_msg(Graph g, const uint16_t *__restrict__ phi,
                                                 uint16_t *__restrict__ m_out)
 {
-    const int lane = threadIdx.x & 31, sub = lane & 3;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 4;
+    const int lane = threadIdx.x & 31, sub = lane & 1;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;
     const int64_t rows = (int64_t)g.n_tiles * 128;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; c++) acc[c] = 0.f;
     const bool ok = i < g.n;
     int k0 = 0, k1 = 0;
     if (ok) {
         k0 = __ldg(g.rowptr + i);
         k1 = __ldg(g.rowptr + i + 1);
     }
-    int nch = (k1 - k0 + 3) >> 2;
+    int nch = (k1 - k0 + 1) >> 1;
 #pragma unroll
-    for (int o = 4; o < 32; o <<= 1) nch = max(nch, __shfl_xor_sync(0xffffffffu, nch, o));
+    for (int o = 2; o < 32; o <<= 1) nch = max(nch, __shfl_xor_sync(0xffffffffu, nch, o));
     for (int c = 0; c < nch; c++) {
-        const int kk = k0 + 4 * c + sub;
+        const int kk = k0 + 2 * c + sub;
         const bool has = kk < k1;
         const int jj = has ? __ldg(g.col + kk) : 0;
         const float ww = has ? __ldg(g.w + kk) : 0.f;
-        uint4 o[4];
+        uint4 o[2][2];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int j = __shfl_sync(0xffffffffu, jj, (lane & ~3) | u);
-            o[u] = __ldg(reinterpret_cast<const uint4 *>(phi + (int64_t)j * 32) + sub);
+        for (int u = 0; u < 2; u++) {
+            const int j = __shfl_sync(0xffffffffu, jj, (lane & ~1) | u);
+            const uint4 *src = reinterpret_cast<const uint4 *>(phi + (int64_t)j * 32) + 2 * sub;
+            o[u][0] = __ldg(src);
+            o[u][1] = __ldg(src + 1);
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const float w = __shfl_sync(0xffffffffu, ww, (lane & ~3) | u);
-            acc[0] = fmaf(w, bf_lo(o[u].x), acc[0]);
-            acc[1] = fmaf(w, bf_hi(o[u].x), acc[1]);
-            acc[2] = fmaf(w, bf_lo(o[u].y), acc[2]);
-            acc[3] = fmaf(w, bf_hi(o[u].y), acc[3]);
-            acc[4] = fmaf(w, bf_lo(o[u].z), acc[4]);
-            acc[5] = fmaf(w, bf_hi(o[u].z), acc[5]);
-            acc[6] = fmaf(w, bf_lo(o[u].w), acc[6]);
-            acc[7] = fmaf(w, bf_hi(o[u].w), acc[7]);
+        for (int u = 0; u < 2; u++) {
+            const float w = __shfl_sync(0xffffffffu, ww, (lane & ~1) | u);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t v4[4] = {o[u][h].x, o[u][h].y, o[u][h].z, o[u][h].w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    acc[8 * h + 2 * e] = fmaf(w, bf_lo(v4[e]), acc[8 * h + 2 * e]);
+                    acc[8 * h + 2 * e + 1] = fmaf(w, bf_hi(v4[e]), acc[8 * h + 2 * e + 1]);
+                }
+            }
         }
     }
-    uint4 out = make_uint4(0u, 0u, 0u, 0u);
+    uint4 out[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
     if (ok) {
-        const uint4 me = __ldg(reinterpret_cast<const uint4 *>(phi + i * 32) + sub);
+        const uint4 *me = reinterpret_cast<const uint4 *>(phi + i * 32) + 2 * sub;
         const float ws = __ldg(g.wsum + i), sc = __ldg(g.s + i);
-        out.x = pack_bf2(sc * fmaf(-ws, bf_lo(me.x), acc[0]), sc * fmaf(-ws, bf_hi(me.x), acc[1]));
-        out.y = pack_bf2(sc * fmaf(-ws, bf_lo(me.y), acc[2]), sc * fmaf(-ws, bf_hi(me.y), acc[3]));
-        out.z = pack_bf2(sc * fmaf(-ws, bf_lo(me.z), acc[4]), sc * fmaf(-ws, bf_hi(me.z), acc[5]));
-        out.w = pack_bf2(sc * fmaf(-ws, bf_lo(me.w), acc[6]), sc * fmaf(-ws, bf_hi(me.w), acc[7]));
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint4 mv = __ldg(me + h);
+            const uint32_t v4[4] = {mv.x, mv.y, mv.z, mv.w};
+            uint32_t q[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                q[e] = pack_bf2(sc * fmaf(-ws, bf_lo(v4[e]), acc[8 * h + 2 * e]),
+                                sc * fmaf(-ws, bf_hi(v4[e]), acc[8 * h + 2 * e + 1]));
+            out[h] = make_uint4(q[0], q[1], q[2], q[3]);
+        }
     }
-    if (i < rows) reinterpret_cast<uint4 *>(m_out + i * 32)[sub] = out;
+    if (i < rows) {
+        *reinterpret_cast<uint4 *>(tile_chunk(m_out, i, 16 * sub, 32)) = out[0];
+        *reinterpret_cast<uint4 *>(tile_chunk(m_out, i, 16 * sub + 8, 32)) = out[1];
+    }
+}
+
+// Shared-memory plan of the layer kernel: two stages of [h tile | m tile]
+// (the A operand, filled by bulk copies), the U image and the second image.
+constexpr uint32_t kLStage = 128 * 64 * 2 + 128 * 32 * 2;     // 24 KB
+constexpr uint32_t kLA = 0;                                  // stage s at kLA + s * kLStage
+constexpr uint32_t kLB1 = 2 * kLStage;                       // U_l image, 64 x 96
+constexpr uint32_t kLB2 = kLB1 + 64 * 96 * 2;                // P_{l+1} or D1 image (<= 64 x 64)
+constexpr uint32_t kLBias = kLB2 + 64 * 64 * 2;              // u | p or d1 | d2 (rounded)
+constexpr uint32_t kLBar = kLBias + 192 * 4;                 // full[0], full[1], mma
+constexpr uint32_t kLTmem = kLBar + 24;
+constexpr uint32_t kLOk = kLTmem + 4;
+constexpr uint32_t kSmemLayer = kLOk + 4 + 16;
+
+// Thread 0 of a layer CTA: the bulk copies of one tile's h and m blocks into
+// stage st, completing on that stage's barrier.
+__device__ __forceinline__ void layer_issue(uint8_t *sm, uint32_t bar_full0, int st, int tile,
+                                            const uint8_t *hsrc, const uint8_t *msrc)
+{
+    constexpr uint32_t kHB = 128 * 64 * 2, kMB = 128 * 32 * 2;
+    uint8_t *dst = sm + kLA + st * kLStage;
+    const uint32_t bf = bar_full0 + 8 * st;
+    mbar_arrive_expect_tx(bf, kHB + kMB);
+    bulk_load(smem_addr(dst), hsrc + (size_t)tile * kHB, kHB, bf);
+    bulk_load(smem_addr(dst + kHB), msrc + (size_t)tile * kMB, kMB, bf);
+}
+
+// Bounded wait by thread 0 on barrier `bar`, outcome for every thread.
+__device__ __forceinline__ bool cta_wait_bar(uint32_t bar, uint32_t parity, int *s_ok, int *err)
+{
+    return cta_wait(bar, parity, s_ok, err);
 }
 
 // Layer l (0-based) of the message passing, node-local: [h[l]; m[l]] ->
 // h[l+1], then either the next layer's projection phi[l+1] or (LAST) the
-// decoder and the new state.
+// decoder and the new state.  Persistent over tiles with two stages: the
+// bulk copies of tile n + 2 are in flight while tile n + 1 waits and tile
+// n computes.  The new h is written in place over the stage's h tile (each
+// thread rewrites only its own row) and feeds the second product.
 template <bool LAST>
-__global__ void __launch_bounds__(128, 4) k_sg_layer(Graph g, Acts a, const uint8_t *__restrict__ img,
+__global__ void __launch_bounds__(128, 3) k_sg_layer(Graph g, Acts a, const uint8_t *__restrict__ img,
                                                   const float *__restrict__ theta, Layout L, int l,
                                                   int train, int *err)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *sA = sm + kSA, *sB1 = sm + kSB1, *sB2 = sm + kSB2;
-    float *sBias = reinterpret_cast<float *>(sm + kSBias);   // u | p or d1 | d2 (rounded)
-    uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + kSTmem);
-    int *sOk = reinterpret_cast<int *>(sm + kSOk);
-    const uint32_t bar = smem_addr(sm + kSBar);
+    uint8_t *sB1 = sm + kLB1, *sB2 = sm + kLB2;
+    float *sBias = reinterpret_cast<float *>(sm + kLBias);
+    uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + kLTmem);
+    int *sOk = reinterpret_cast<int *>(sm + kLOk);
+    const uint32_t bar_full0 = smem_addr(sm + kLBar);   // stage st: bar_full0 + 8 st
+    const uint32_t bar_mma = smem_addr(sm + kLBar + 16);
     const int tid = threadIdx.x;
     constexpr uint32_t N2 = LAST ? 64 : 32;
+    constexpr uint32_t kHB = 128 * 64 * 2, kMB = 128 * 32 * 2;   // bytes of an h / m tile
+    const uint8_t *hsrc = reinterpret_cast<const uint8_t *>(a.h[l]);
+    const uint8_t *msrc = reinterpret_cast<const uint8_t *>(a.m[l]);
     if (tid < 32) tc::tmem_alloc(sTmem, 128);
-    if (tid == 0) { mbar_init(bar, 1); mbar_fence_init(); }
+    if (tid == 0) {
+        mbar_init(bar_full0, 1);
+        mbar_init(bar_full0 + 8, 1);
+        mbar_init(bar_mma, 1);
+        mbar_fence_init();
+        for (int st = 0; st < 2; st++) {
+            const int tile = blockIdx.x + st * gridDim.x;
+            if (tile < g.n_tiles) layer_issue(sm, bar_full0, st, tile, hsrc, msrc);
+        }
+    }
     copy_img(sB1, img + L.img_u[l], 64 * 96 * 2);
     copy_img(sB2, img + (LAST ? L.img_d1 : L.img_p[l + 1]), N2 * 64 * 2);
     if (tid < 64) sBias[tid] = theta[L.u[l] + tid];
@@ -377,73 +459,67 @@ __global__ void __launch_bounds__(128, 4) k_sg_layer(Graph g, Acts a, const uint
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = *sTmem;
-    uint32_t phase = 0;
-    const uint32_t sa = smem_addr(sA), sb1 = smem_addr(sB1), sb2 = smem_addr(sB2);
-    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x) {
+    uint32_t mma_phase = 0;
+    const uint32_t sb1 = smem_addr(sB1), sb2 = smem_addr(sB2);
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, it++) {
+        const int st = it & 1;
+        uint8_t *sAh = sm + kLA + st * kLStage, *sAm = sAh + kHB;
+        if (!cta_wait_bar(bar_full0 + 8 * st, (uint32_t)((it >> 1) & 1), sOk, err)) { ok = false; break; }
         const int64_t i = (int64_t)tile * 128 + tid;
         const bool valid = i < g.n;
-        uint32_t hp[32];
-        const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[l] + i * 64);
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const uint4 v = hs[q];
-            hp[4 * q] = v.x;
-            hp[4 * q + 1] = v.y;
-            hp[4 * q + 2] = v.z;
-            hp[4 * q + 3] = v.w;
-            st_row8(sA, tid, 8 * q, 96, v);
-        }
-        {
-            const uint4 *ms = reinterpret_cast<const uint4 *>(a.m[l] + i * 32);
-#pragma unroll
-            for (int q = 0; q < 4; q++) st_row8(sA, tid, 64 + 8 * q, 96, ms[q]);
-        }
-        tc::fence_smem_async();
-        __syncthreads();
         if (tid == 0) {
             tc::fence_after();
-            tc::mma_bf16(tbase, sa, sb1, 96, 128, 64, false);
-            tc::commit(bar);
+            tc::mma_bf16_2seg(tbase, smem_addr(sAh), 64, smem_addr(sAm), 32, sb1, 96, 128, 64);
+            tc::commit(bar_mma);
         }
-        if (!cta_wait(bar, phase, sOk, err)) break;
-        phase ^= 1;
+        if (!cta_wait(bar_mma, mma_phase, sOk, err)) { ok = false; break; }
+        mma_phase ^= 1;
         tc::fence_after();
-        // r = relu(U [h; m] + u), h' = h + r (rounded to bf16)
-        uint32_t rp[32];
+        // r = relu(U [h; m] + u), h' = h + r (rounded to bf16), 16 columns at a time
+        uint16_t *hdst = a.h[l + 1] + (int64_t)tile * (128 * 64);
 #pragma unroll
         for (int c0 = 0; c0 < 64; c0 += 16) {
             float v[16];
             tc::ld16(tc::lane_addr(tbase, c0), v);
+            uint4 hv[2] = {*reinterpret_cast<const uint4 *>(sAh + core_off(tid, c0, 64)),
+                           *reinterpret_cast<const uint4 *>(sAh + core_off(tid, c0 + 8, 64))};
+            uint32_t rq[8], hq[8];
 #pragma unroll
-            for (int c = 0; c < 16; c += 2) {
-                const float r0 = fmaxf(v[c] + sBias[c0 + c], 0.f);
-                const float r1 = fmaxf(v[c + 1] + sBias[c0 + c + 1], 0.f);
-                const uint32_t h2 = hp[(c0 + c) / 2];
-                rp[(c0 + c) / 2] = pack_bf2(r0, r1);
-                hp[(c0 + c) / 2] = valid ? pack_bf2(bf_lo(h2) + r0, bf_hi(h2) + r1) : 0u;
+            for (int h = 0; h < 2; h++) {
+                const uint32_t hw[4] = {hv[h].x, hv[h].y, hv[h].z, hv[h].w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int c = c0 + 8 * h + 2 * e;
+                    const float r0 = fmaxf(v[8 * h + 2 * e] + sBias[c], 0.f);
+                    const float r1 = fmaxf(v[8 * h + 2 * e + 1] + sBias[c + 1], 0.f);
+                    rq[4 * h + e] = pack_bf2(r0, r1);
+                    hq[4 * h + e] = valid ? pack_bf2(bf_lo(hw[e]) + r0, bf_hi(hw[e]) + r1) : 0u;
+                }
             }
-        }
-        uint4 *hn = reinterpret_cast<uint4 *>(a.h[l + 1] + i * 64);
-        uint4 *rs = reinterpret_cast<uint4 *>(a.r[l] + i * 64);
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const uint4 v = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-            hn[q] = v;
-            if (train)
-                rs[q] = valid ? make_uint4(rp[4 * q], rp[4 * q + 1], rp[4 * q + 2], rp[4 * q + 3])
+            for (int h = 0; h < 2; h++) {
+                const uint4 nv = make_uint4(hq[4 * h], hq[4 * h + 1], hq[4 * h + 2], hq[4 * h + 3]);
+                const uint32_t off = core_off(tid, c0 + 8 * h, 64);
+                *reinterpret_cast<uint4 *>(sAh + off) = nv;
+                *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(hdst) + off) = nv;
+                if (train)
+                    reinterpret_cast<uint4 *>(a.r[l] + i * 64)[c0 / 8 + h] =
+                        valid ? make_uint4(rq[4 * h], rq[4 * h + 1], rq[4 * h + 2], rq[4 * h + 3])
                               : make_uint4(0u, 0u, 0u, 0u);
-            st_row8(sA, tid, 8 * q, 64, v);
+            }
         }
         tc::fence_before();
         tc::fence_smem_async();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after();
-            tc::mma_bf16(tbase + 64, sa, sb2, 64, 128, N2, false);
-            tc::commit(bar);
+            tc::mma_bf16(tbase + 64, smem_addr(sAh), sb2, 64, 128, N2, false);
+            tc::commit(bar_mma);
         }
-        if (!cta_wait(bar, phase, sOk, err)) break;
-        phase ^= 1;
+        if (!cta_wait(bar_mma, mma_phase, sOk, err)) { ok = false; break; }
+        mma_phase ^= 1;
         tc::fence_after();
         if (!LAST) {
             uint32_t pp[16];
@@ -486,6 +562,22 @@ __global__ void __launch_bounds__(128, 4) k_sg_layer(Graph g, Acts a, const uint
         }
         tc::fence_before();
         __syncthreads();
+        // the stage is free again: the copies of the tile two steps ahead
+        if (tid == 0) {
+            const int next = tile + 2 * gridDim.x;
+            if (next < g.n_tiles) {
+                tc::fence_smem_async();
+                layer_issue(sm, bar_full0, st, next, hsrc, msrc);
+            }
+        }
+    }
+    if (!ok && tid == 0) {
+        // give the copies in flight a bounded chance to land before exit
+        for (int q = 0; q < 2; q++) {
+            const int k = it + q;
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile < g.n_tiles) mbar_wait(bar_full0 + 8 * (k & 1), (uint32_t)((k >> 1) & 1));
+        }
     }
     __syncthreads();
     tc::fence_after();
@@ -570,8 +662,8 @@ __device__ bool layer_back(const Graph &g, const Acts &a, const Grads &gr, float
     const int t = threadIdx.x;
     uint8_t *sA3 = sm + kBA3, *sA4 = sm + kBA4, *sB4 = sm + kBB4;
     const uint4 *rs = reinterpret_cast<const uint4 *>(a.r[lu] + i * 64);
-    const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[lu] + i * 64);
-    const uint4 *ms = reinterpret_cast<const uint4 *>(a.m[lu] + i * 32);
+    const TileRow hs{a.h[lu], i, 64};
+    const TileRow ms{a.m[lu], i, 32};
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const uint4 rv = rs[q], hv = hs[q];
@@ -691,7 +783,7 @@ __global__ void __launch_bounds__(128) k_sg_bwd_head(Graph g, Acts a, Grads gr, 
         }
         acc_d2b += dy;
         const float4 *zs = reinterpret_cast<const float4 *>(a.z + i * 64);
-        const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[kLayers] + i * 64);
+        const TileRow hs{a.h[kLayers], i, 64};
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const float4 z0 = zs[2 * q], z1 = zs[2 * q + 1];
@@ -898,7 +990,7 @@ __global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr,
         }
         const int64_t i = tile0 + t;
         const bool valid = i < g.n;
-        const uint4 *hs = reinterpret_cast<const uint4 *>(a.h[l] + i * 64);
+        const TileRow hs{a.h[l], i, 64};
         uint32_t hw[32];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
@@ -947,7 +1039,7 @@ __global__ void __launch_bounds__(128) k_sg_bwd_mid(Graph g, Acts a, Grads gr,
             }
         } else {
             // encoder: d0 = dh0 (h0 > 0);  dW_in^T += [x; 1]^T d0
-            const uint4 *xs = reinterpret_cast<const uint4 *>(a.x + i * 16);
+            const TileRow xs{a.x, i, 16};
 #pragma unroll
             for (int q = 0; q < 2; q++) {
                 const uint4 xv = xs[q];
@@ -1125,7 +1217,8 @@ using namespace fem::sg;
 struct fem_surrogate {
     fem_mesh *mesh = nullptr;
     int device = -1, n_sm = 0;
-    int fwd_per_sm = 1;               // resident forward CTAs per SM (persistent grid)
+    int fwd_per_sm = 1;               // resident encoder CTAs per SM (persistent grid)
+    int layer_per_sm = 1;             // resident layer CTAs per SM
     int32_t n = 0, n_tiles = 0;
     int64_t nnz = 0;
     std::vector<int32_t> caller_of;   // surrogate position -> caller node
@@ -1405,6 +1498,7 @@ fem_status launch_check(const char *what)
 // Persistent grids: exactly the CTAs that are resident at once (a CTA
 // that waits for a second wave would start its tiles after the others end).
 int fwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->fwd_per_sm * s->n_sm)); }
+int layer_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->layer_per_sm * s->n_sm)); }
 int bwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->n_sm)); }
 
 // Forward pass from E_in (device, surrogate order) into E_out.
@@ -1418,12 +1512,12 @@ fem_status forward(fem_surrogate *s, const float *E_in, float *E_out, bool train
     k_sg_feat<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a);
     k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
     for (int l = 0; l < kLayers; l++) {
-        k_sg_msg<<<(rows * 4 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+        k_sg_msg<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
         if (l < kLayers - 1)
-            k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l,
+            k_sg_layer<false><<<layer_grid(s), 128, kSmemLayer, st>>>(s->g, a, s->img, s->theta, s->L, l,
                                                                   train ? 1 : 0, s->err);
         else
-            k_sg_layer<true><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l,
+            k_sg_layer<true><<<layer_grid(s), 128, kSmemLayer, st>>>(s->g, a, s->img, s->theta, s->L, l,
                                                                  train ? 1 : 0, s->err);
     }
     return launch_check("surrogate forward");
@@ -1535,8 +1629,8 @@ extern "C" fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate
         if (!st) st = salloc(s, &s->err, 1);
         if (!st) {
             cudaFuncSetAttribute(k_sg_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFwd);
-            cudaFuncSetAttribute(k_sg_layer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFwd);
-            cudaFuncSetAttribute(k_sg_layer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFwd);
+            cudaFuncSetAttribute(k_sg_layer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLayer);
+            cudaFuncSetAttribute(k_sg_layer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLayer);
             cudaFuncSetAttribute(k_sg_bwd_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
             cudaFuncSetAttribute(k_sg_bwd_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
             // resident forward CTAs per SM: registers and shared memory
@@ -1544,18 +1638,22 @@ extern "C" fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate
             int regs_sm = 65536, smem_sm = 0;
             cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
             cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-            int occ = 4;
-            const void *fns[3] = {(const void *)k_sg_encode, (const void *)k_sg_layer<false>,
-                                  (const void *)k_sg_layer<true>};
-            for (const void *fn : fns) {
+            // at most four 128-column TMEM allocations per SM
+            auto resident = [&](const void *fn, uint32_t dyn) {
+                int occ = 4;
                 cudaFuncAttributes fa{};
-                if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) continue;
-                // registers are allocated per warp in units of 256
-                const int regs_cta = 4 * (((fa.numRegs * 32 + 255) / 256) * 256);
-                const int smem_cta = (int)(kSmemFwd + fa.sharedSizeBytes) + 1024;
-                if (regs_cta > 0) occ = std::min(occ, regs_sm / regs_cta);
-                if (smem_sm > 0) occ = std::min(occ, smem_sm / smem_cta);
-            }
+                if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) {
+                    // registers are allocated per warp in units of 256
+                    const int regs_cta = 4 * (((fa.numRegs * 32 + 255) / 256) * 256);
+                    const int smem_cta = (int)(dyn + fa.sharedSizeBytes) + 1024;
+                    if (regs_cta > 0) occ = std::min(occ, regs_sm / regs_cta);
+                    if (smem_sm > 0) occ = std::min(occ, smem_sm / smem_cta);
+                }
+                return std::max(1, occ);
+            };
+            const int occ = resident((const void *)k_sg_encode, kSmemFwd);
+            s->layer_per_sm = std::min(resident((const void *)k_sg_layer<false>, kSmemLayer),
+                                       resident((const void *)k_sg_layer<true>, kSmemLayer));
             s->fwd_per_sm = std::max(1, occ);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) st = sfail(FEM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
@@ -1794,6 +1892,22 @@ extern "C" fem_status fem_surrogate_advance(fem_surrogate *s, int64_t n_macro)
     return r ? r : sok();
 }
 
+namespace {
+
+// Host copy of a tile-layout activation with K channels as rows [n][K].
+fem_status untile(fem_surrogate *s, const uint16_t *dev, uint32_t K, uint16_t *out)
+{
+    const size_t rows = (size_t)s->n_tiles * kTile;
+    std::vector<uint16_t> raw(rows * K);
+    SCU(cudaMemcpy(raw.data(), dev, raw.size() * 2, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < (size_t)s->n; i++)
+        for (uint32_t c = 0; c < K; c++)
+            out[i * K + c] = raw[(i >> 7) * 128 * K + (core_off((uint32_t)(i & 127), c, K) >> 1)];
+    return FEM_OK;
+}
+
+}  // namespace
+
 // Test hook: host copy of an internal buffer (surrogate order, padded rows
 // excluded).  which: 0 x (bf16 [n][16]), 1 h_l (bf16 [n][64], l = 0..3),
 // 2 phi_l (bf16 [n][32]), 3 m_l (bf16 [n][32]), 4 r_l (bf16 [n][64]),
@@ -1811,15 +1925,18 @@ extern "C" fem_status fem_surrogate_debug(fem_surrogate *s, int32_t which, int32
     const size_t n = (size_t)s->n;
     const bool lok = layer >= 0 && layer < kLayers;
     switch (which) {
-    case 0: SCU(cudaMemcpy(out, s->a.x, n * 16 * 2, cudaMemcpyDeviceToHost)); break;
+    case 0: if ((r = untile(s, s->a.x, 16, (uint16_t *)out))) return r; break;
     case 1:
         if (layer < 0 || layer > kLayers) return sfail(FEM_EINVAL, "layer out of range");
-        SCU(cudaMemcpy(out, s->a.h[layer], n * 64 * 2, cudaMemcpyDeviceToHost));
+        if ((r = untile(s, s->a.h[layer], 64, (uint16_t *)out))) return r;
         break;
-    case 2: case 3: case 4: {
+    case 3:
         if (!lok) return sfail(FEM_EINVAL, "layer out of range");
-        const void *src = which == 2 ? (const void *)s->a.phi[layer]
-                                     : which == 3 ? (const void *)s->a.m[layer] : (const void *)s->a.r[layer];
+        if ((r = untile(s, s->a.m[layer], 32, (uint16_t *)out))) return r;
+        break;
+    case 2: case 4: {
+        if (!lok) return sfail(FEM_EINVAL, "layer out of range");
+        const void *src = which == 2 ? (const void *)s->a.phi[layer] : (const void *)s->a.r[layer];
         SCU(cudaMemcpy(out, src, n * (which == 4 ? 64 : 32) * 2, cudaMemcpyDeviceToHost));
         break;
     }
@@ -1962,12 +2079,12 @@ extern "C" fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, d
         k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
         cudaEventRecord(ev[2], st);
         for (int l = 0; l < kLayers; l++)
-            k_sg_msg<<<(rows * 4 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+            k_sg_msg<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
         cudaEventRecord(ev[3], st);
         for (int l = 0; l < kLayers - 1; l++)
-            k_sg_layer<false><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, l, 0, s->err);
+            k_sg_layer<false><<<layer_grid(s), 128, kSmemLayer, st>>>(s->g, a, s->img, s->theta, s->L, l, 0, s->err);
         cudaEventRecord(ev[4], st);
-        k_sg_layer<true><<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, kLayers - 1, 0,
+        k_sg_layer<true><<<layer_grid(s), 128, kSmemLayer, st>>>(s->g, a, s->img, s->theta, s->L, kLayers - 1, 0,
                                                              s->err);
         cudaEventRecord(ev[5], st);
         r = launch_check("surrogate profile");

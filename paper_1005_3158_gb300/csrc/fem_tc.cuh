@@ -82,6 +82,27 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint32_t sa, uint32_t 
             : "memory");
     }
 }
+// The same with A in two segments along K: K1 columns at sa1 (an operand of
+// K1 columns) followed by K2 columns at sa2 (an operand of K2 columns); B
+// is one operand of K1 + K2 columns.
+__device__ __forceinline__ void mma_bf16_2seg(uint32_t tmem_d, uint32_t sa1, uint32_t K1, uint32_t sa2,
+                                              uint32_t K2, uint32_t sb, uint32_t KB, uint32_t M,
+                                              uint32_t N)
+{
+    const uint32_t id = idesc_bf16(M, N);
+    for (uint32_t k = 0; k < (K1 + K2) / 16; k++) {
+        const bool first = k < K1 / 16;
+        const uint64_t da = first ? sdesc(sa1 + 256 * k, K1) : sdesc(sa2 + 256 * (k - K1 / 16), K2);
+        const uint64_t db = sdesc(sb + 256 * k, KB);
+        const uint32_t acc = k > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+            "l"(da), "l"(db), "r"(id), "r"(acc)
+            : "memory");
+    }
+}
 // Arrive once on the mbarrier when every MMA issued so far by this thread
 // has completed.
 __device__ __forceinline__ void commit(uint32_t bar)
