@@ -149,13 +149,13 @@ __global__ void k_sg_tf(const float *__restrict__ E, Graph g, float2 *__restrict
     tf[i] = make_float2(T, f);
 }
 
-// Features x of every node.  Eight lanes per node: the conduction sums over
-// the node's edges are split over the lanes (one neighbour each per round)
-// and reduced by shuffles; lanes 0 and 1 write the 16 bf16 channels.
+// Features x of every node.  Two lanes per node (sixteen nodes per warp):
+// the conduction sums over the node's edges are split over the two lanes
+// and combined by one shuffle; each lane writes 8 of the 16 bf16 channels.
 __global__ void __launch_bounds__(256) k_sg_feat(Graph g, Acts a)
 {
-    const int lane = threadIdx.x & 31, sub = lane & 7;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8;
+    const int lane = threadIdx.x & 31, sub = lane & 1;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 2;
     const bool ok = i < g.n;
     float T = 0.f, f = 0.f, dT = 0.f, df = 0.f;
     if (ok) {
@@ -163,43 +163,53 @@ __global__ void __launch_bounds__(256) k_sg_feat(Graph g, Acts a)
         T = me.x;
         f = me.y;
         const int k1 = __ldg(g.rowptr + i + 1);
-        for (int k = __ldg(g.rowptr + i) + sub; k < k1; k += 8) {
-            const float w = __ldg(g.w + k);
-            const float2 o = a.tf[__ldg(g.col + k)];
-            dT += w * (o.x - T);
-            df += w * (o.y - f);
+        int k = __ldg(g.rowptr + i) + sub;
+        for (; k + 2 < k1; k += 4) {   // two neighbours per lane in flight
+            const int j0 = __ldg(g.col + k), j1 = __ldg(g.col + k + 2);
+            const float w0 = __ldg(g.w + k), w1 = __ldg(g.w + k + 2);
+            const float2 o0 = a.tf[j0], o1 = a.tf[j1];
+            dT += w0 * (o0.x - T);
+            df += w0 * (o0.y - f);
+            dT += w1 * (o1.x - T);
+            df += w1 * (o1.y - f);
+        }
+        if (k < k1) {
+            const float w0 = __ldg(g.w + k);
+            const float2 o0 = a.tf[__ldg(g.col + k)];
+            dT += w0 * (o0.x - T);
+            df += w0 * (o0.y - f);
         }
     }
+    dT += __shfl_xor_sync(0xffffffffu, dT, 1);
+    df += __shfl_xor_sync(0xffffffffu, df, 1);
+    if (i >= (int64_t)g.n_tiles * 128) return;
+    constexpr float kInvTS = 1.f / kTS;
+    float x[8];
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        dT += __shfl_xor_sync(0xffffffffu, dT, o);
-        df += __shfl_xor_sync(0xffffffffu, df, o);
-    }
-    if (sub >= 2 || i >= (int64_t)g.n_tiles * 128) return;
-    float x[16];
-#pragma unroll
-    for (int c = 0; c < 16; c++) x[c] = 0.f;
+    for (int c = 0; c < 8; c++) x[c] = 0.f;
     if (ok) {
-        const float C = g.C[i], Lc = g.Lc[i], s = g.s[i];
-        const float Ts = g.ranges[2 * (g.ph[i] & 0x7F)], Tl = g.ranges[2 * (g.ph[i] & 0x7F) + 1];
-        const bool pc = Lc > 0.f;
-        x[0] = (T - kTC) / kTS;
-        x[1] = f;
-        x[2] = Lc / (C * kTS);
-        x[3] = kMacro * s * g.hA[i];
-        x[4] = kMacro * s * (g.g[i] - g.hA[i] * T) / kTS;
-        x[5] = kMacro * s * dT / kTS;
-        x[6] = kMacro * s * df;
-        x[7] = 1.f;
-        x[8] = pc ? (T - Ts) / kTS : 0.f;
-        x[9] = pc ? (T - Tl) / kTS : 0.f;
-        x[10] = kMacro * s * g.wsum[i];
+        const float s = g.s[i];
+        if (sub == 0) {
+            const float C = g.C[i], Lc = g.Lc[i];
+            x[0] = (T - kTC) * kInvTS;
+            x[1] = f;
+            x[2] = Lc / C * kInvTS;
+            x[3] = kMacro * s * g.hA[i];
+            x[4] = kMacro * s * (g.g[i] - g.hA[i] * T) * kInvTS;
+            x[5] = kMacro * s * dT * kInvTS;
+            x[6] = kMacro * s * df;
+            x[7] = 1.f;
+        } else if (g.Lc[i] > 0.f) {
+            const int r = g.ph[i] & 0x7F;
+            x[0] = (T - g.ranges[2 * r]) * kInvTS;
+            x[1] = (T - g.ranges[2 * r + 1]) * kInvTS;
+            x[2] = kMacro * s * g.wsum[i];
+        } else {
+            x[2] = kMacro * s * g.wsum[i];
+        }
     }
-    const uint4 q0 = make_uint4(pack_bf2(x[0], x[1]), pack_bf2(x[2], x[3]), pack_bf2(x[4], x[5]),
-                                pack_bf2(x[6], x[7]));
-    const uint4 q1 = make_uint4(pack_bf2(x[8], x[9]), pack_bf2(x[10], x[11]), pack_bf2(x[12], x[13]),
-                                pack_bf2(x[14], x[15]));
-    *reinterpret_cast<uint4 *>(tile_chunk(a.x, i, 8 * sub, 16)) = sub == 0 ? q0 : q1;
+    *reinterpret_cast<uint4 *>(tile_chunk(a.x, i, 8 * sub, 16)) =
+        make_uint4(pack_bf2(x[0], x[1]), pack_bf2(x[2], x[3]), pack_bf2(x[4], x[5]), pack_bf2(x[6], x[7]));
 }
 
 // Shared-memory plan of the forward kernels (bytes, 128-byte aligned).
@@ -1509,7 +1519,7 @@ fem_status forward(fem_surrogate *s, const float *E_in, float *E_out, bool train
     a.E_out = E_out;
     const int rows = s->n_tiles * kTile;
     k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(E_in, s->g, a.tf);
-    k_sg_feat<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a);
+    k_sg_feat<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a);
     k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
     for (int l = 0; l < kLayers; l++) {
         k_sg_msg<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
@@ -2074,7 +2084,7 @@ extern "C" fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, d
     for (int64_t it = 0; it < n_macro && !r; it++) {
         cudaEventRecord(ev[0], st);
         k_sg_tf<<<(s->n + 255) / 256, 256, 0, st>>>(s->E0, s->g, a.tf);
-        k_sg_feat<<<(rows * 8 + 255) / 256, 256, 0, st>>>(s->g, a);
+        k_sg_feat<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a);
         cudaEventRecord(ev[1], st);
         k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
         cudaEventRecord(ev[2], st);
