@@ -318,6 +318,68 @@ __global__ void __launch_bounds__(128, 4) k_sg_encode(Graph g, Acts a, const uin
     if (tid < 32) tc::tmem_free(tbase, 128);
 }
 
+// The same messages tile by tile (the cache blocking of the paper's Section
+// 4.2, applied to the graph): one CTA stages the phi rows of its 128-node
+// tile and of the tile's halo (the neighbours outside it) in shared memory
+// with coalesced 16-byte loads, then sums every node's messages from there
+// through the edges' local columns (two lanes per node, 16 channels each).
+constexpr int kMsgTileThreads = 256;
+__global__ void __launch_bounds__(kMsgTileThreads) k_sg_msg_tile(Graph g, const uint16_t *__restrict__ phi,
+                                                                 uint16_t *__restrict__ m_out)
+{
+    extern __shared__ __align__(16) uint4 sphi[];   // (128 + halo) rows x 4 chunks of 8 channels
+    const int tile = blockIdx.x, tid = threadIdx.x;
+    const int64_t r0 = (int64_t)tile * 128;
+    const int h0 = __ldg(g.halo_ptr + tile), nh = __ldg(g.halo_ptr + tile + 1) - h0;
+    const int nstage = (128 + nh) * 4;
+    for (int q = tid; q < nstage; q += kMsgTileThreads) {
+        const int row = q >> 2, part = q & 3;
+        int64_t gr;
+        if (row < 128) gr = r0 + row;
+        else gr = __ldg(g.halo_idx + h0 + row - 128);
+        sphi[q] = (gr < g.n) ? __ldg(reinterpret_cast<const uint4 *>(phi + gr * 32) + part)
+                             : make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    const int r = tid >> 1, sub = tid & 1;
+    const int64_t i = r0 + r;
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; c++) acc[c] = 0.f;
+    uint4 out[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+    if (i < g.n) {
+        const int k1 = __ldg(g.rowptr + i + 1);
+        for (int k = __ldg(g.rowptr + i); k < k1; k++) {
+            const int lj = __ldg(g.lcol + k);
+            const float w = __ldg(g.w + k);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint4 o = sphi[lj * 4 + 2 * sub + h];
+                const uint32_t v4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    acc[8 * h + 2 * e] = fmaf(w, bf_lo(v4[e]), acc[8 * h + 2 * e]);
+                    acc[8 * h + 2 * e + 1] = fmaf(w, bf_hi(v4[e]), acc[8 * h + 2 * e + 1]);
+                }
+            }
+        }
+        const float ws = __ldg(g.wsum + i), sc = __ldg(g.s + i);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint4 mv = sphi[r * 4 + 2 * sub + h];
+            const uint32_t v4[4] = {mv.x, mv.y, mv.z, mv.w};
+            uint32_t q[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                q[e] = pack_bf2(sc * fmaf(-ws, bf_lo(v4[e]), acc[8 * h + 2 * e]),
+                                sc * fmaf(-ws, bf_hi(v4[e]), acc[8 * h + 2 * e + 1]));
+            out[h] = make_uint4(q[0], q[1], q[2], q[3]);
+        }
+    }
+    *reinterpret_cast<uint4 *>(tile_chunk(m_out, i, 16 * sub, 32)) = out[0];
+    *reinterpret_cast<uint4 *>(tile_chunk(m_out, i, 16 * sub + 8, 32)) = out[1];
+}
+
 // Graph messages of layer l: m_i = s_i sum_j W_ij (phi_j - phi_i), 32
 // channels, FP32 sums of bf16 values, written as bf16; evaluated as
 // s_i (sum_j W_ij phi_j - (sum_j W_ij) phi_i).  Two lanes per node (16
@@ -1436,6 +1498,37 @@ fem_status build_graph(fem_surrogate *s, const SurrogateMeshView &v, const std::
         rowptr[(size_t)k + 1] = (int32_t)col.size();
     }
     s->nnz = (int64_t)col.size();
+    // tile blocking: each tile's neighbour rows outside the tile, and every
+    // edge's column as a row of the staged block
+    std::vector<int32_t> halo_ptr((size_t)s->n_tiles + 1, 0), halo_idx;
+    std::vector<uint16_t> lcol(col.size());
+    int32_t max_halo = 0;
+    {
+        std::vector<int32_t> slot((size_t)N, -1);
+        for (int32_t t = 0; t < s->n_tiles; t++) {
+            const int64_t r0 = (int64_t)t * kTile, r1 = std::min<int64_t>(N, r0 + kTile);
+            const size_t h0 = halo_idx.size();
+            for (int64_t r = r0; r < r1; r++)
+                for (int32_t k = rowptr[(size_t)r]; k < rowptr[(size_t)r + 1]; k++) {
+                    const int32_t j = col[(size_t)k];
+                    int32_t l;
+                    if (j >= r0 && j < r1) {
+                        l = (int32_t)(j - r0);
+                    } else {
+                        if (slot[(size_t)j] < 0) {
+                            slot[(size_t)j] = (int32_t)(halo_idx.size() - h0);
+                            halo_idx.push_back(j);
+                        }
+                        l = kTile + slot[(size_t)j];
+                    }
+                    if (l > 65535) return sfail(FEM_EINVAL, "a tile's neighbourhood exceeds 65535 rows");
+                    lcol[(size_t)k] = (uint16_t)l;
+                }
+            for (size_t q = h0; q < halo_idx.size(); q++) slot[(size_t)halo_idx[q]] = -1;
+            halo_ptr[(size_t)t + 1] = (int32_t)halo_idx.size();
+            max_halo = std::max<int32_t>(max_halo, (int32_t)(halo_idx.size() - h0));
+        }
+    }
     // node data in surrogate order
     const int64_t rows = (int64_t)s->n_tiles * kTile;
     std::vector<float> C((size_t)rows, 1.f), Lc((size_t)rows, 0.f), sv((size_t)rows, 0.f),
@@ -1477,6 +1570,11 @@ fem_status build_graph(fem_surrogate *s, const SurrogateMeshView &v, const std::
     if ((st = supload(s, &d_rg, rgf, rgf.size()))) return st;
     if ((st = supload(s, &d_ph, ph, (size_t)rows))) return st;
     if ((st = supload(s, &s->int_id, iid, (size_t)N))) return st;
+    int32_t *d_hptr, *d_hidx;
+    uint16_t *d_lcol;
+    if ((st = supload(s, &d_hptr, halo_ptr, halo_ptr.size()))) return st;
+    if ((st = supload(s, &d_hidx, halo_idx, halo_idx.size()))) return st;
+    if ((st = supload(s, &d_lcol, lcol, lcol.size()))) return st;
     Graph &g = s->g;
     g.n = (int32_t)N;
     g.n_tiles = s->n_tiles;
@@ -1491,6 +1589,10 @@ fem_status build_graph(fem_surrogate *s, const SurrogateMeshView &v, const std::
     g.ranges = d_rg;
     g.hA = d_hA;
     g.g = d_g;
+    g.halo_ptr = d_hptr;
+    g.halo_idx = d_hidx;
+    g.lcol = d_lcol;
+    g.max_halo = max_halo;
     return FEM_OK;
 }
 
@@ -1509,6 +1611,17 @@ fem_status launch_check(const char *what)
 // that waits for a second wave would start its tiles after the others end).
 int fwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->fwd_per_sm * s->n_sm)); }
 int layer_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->layer_per_sm * s->n_sm)); }
+
+// Message sums of one layer: tile-staged when a tile and its halo fit in
+// shared memory, else the gather kernel.
+constexpr int kMsgTileMaxRows = 3200;   // 200 KB of staged rows
+void launch_msg(const fem_surrogate *s, const uint16_t *phi, uint16_t *m, cudaStream_t st)
+{
+    if (128 + s->g.max_halo <= kMsgTileMaxRows)
+        k_sg_msg_tile<<<s->n_tiles, kMsgTileThreads, (size_t)(128 + s->g.max_halo) * 64, st>>>(s->g, phi, m);
+    else
+        k_sg_msg<<<(s->n_tiles * kTile * 2 + 255) / 256, 256, 0, st>>>(s->g, phi, m);
+}
 int bwd_grid(const fem_surrogate *s) { return std::max(1, std::min(s->n_tiles, s->n_sm)); }
 
 // Forward pass from E_in (device, surrogate order) into E_out.
@@ -1522,7 +1635,7 @@ fem_status forward(fem_surrogate *s, const float *E_in, float *E_out, bool train
     k_sg_feat<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a);
     k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
     for (int l = 0; l < kLayers; l++) {
-        k_sg_msg<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+        launch_msg(s, a.phi[l], a.m[l], st);
         if (l < kLayers - 1)
             k_sg_layer<false><<<layer_grid(s), 128, kSmemLayer, st>>>(s->g, a, s->img, s->theta, s->L, l,
                                                                   train ? 1 : 0, s->err);
@@ -1642,6 +1755,8 @@ extern "C" fem_status fem_surrogate_create(fem_mesh *m, double dt, fem_surrogate
             cudaFuncSetAttribute(k_sg_layer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLayer);
             cudaFuncSetAttribute(k_sg_layer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLayer);
             cudaFuncSetAttribute(k_sg_bwd_head, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
+            cudaFuncSetAttribute(k_sg_msg_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMsgTileMaxRows * 64);
             cudaFuncSetAttribute(k_sg_bwd_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBwd);
             // resident forward CTAs per SM: registers and shared memory
             // (occupancy), and at most four 128-column TMEM allocations
@@ -2089,7 +2204,7 @@ extern "C" fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, d
         k_sg_encode<<<fwd_grid(s), 128, kSmemFwd, st>>>(s->g, a, s->img, s->theta, s->L, s->err);
         cudaEventRecord(ev[2], st);
         for (int l = 0; l < kLayers; l++)
-            k_sg_msg<<<(rows * 2 + 255) / 256, 256, 0, st>>>(s->g, a.phi[l], a.m[l]);
+            launch_msg(s, a.phi[l], a.m[l], st);
         cudaEventRecord(ev[3], st);
         for (int l = 0; l < kLayers - 1; l++)
             k_sg_layer<false><<<layer_grid(s), 128, kSmemLayer, st>>>(s->g, a, s->img, s->theta, s->L, l, 0, s->err);

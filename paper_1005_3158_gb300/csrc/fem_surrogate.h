@@ -72,6 +72,13 @@ struct Graph {
     const uint8_t *ph;  // phase-change range index (low 7 bits)
     const float *ranges;
     const float *hA, *g;  // lumped Robin terms sum h A / 3, sum A (h T_inf - q) / 3
+    // tile blocking of the message sums: the rows of tile t's neighbours
+    // outside the tile are halo_idx[halo_ptr[t] .. halo_ptr[t + 1]); lcol[k]
+    // is edge k's column as a row of the staged block (tile rows 0..127,
+    // then the halo rows)
+    const int32_t *halo_ptr, *halo_idx;
+    const uint16_t *lcol;
+    int32_t max_halo;
 };
 
 // Activations (surrogate order, n_tiles * 128 rows each, bf16 as uint16).
