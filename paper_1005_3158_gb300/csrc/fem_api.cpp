@@ -311,6 +311,11 @@ int default_block_elems(const fem_mesh *m)
 bool is_block(const fem_mesh *m) { return m->opt.variant == FEM_VARIANT_BLOCK; }
 bool is_lm(const fem_mesh *m) { return m->opt.formulation == FEM_APPARENT_CAPACITY; }
 bool has_dirichlet(const fem_mesh *m) { return !m->is_dir.empty(); }
+// Shared-node copies and their mirror positions (block variant; null for
+// the flat variants): the set-state kernels write the mirrors themselves.
+const int32_t *mirror_ptr(const fem_mesh *m) { return is_block(m) ? m->dShPtr : nullptr; }
+const int32_t *mirror_pos(const fem_mesh *m) { return is_block(m) ? m->dMpos : nullptr; }
+int64_t mirror_len(const fem_mesh *m) { return is_block(m) ? (int64_t)m->bp.blocks.size() * m->ls : 0; }
 
 // Largest total enthalpy content a stable run of the current data can
 // reach: sum_i C_i T_hi + Lc_i, with T_hi the highest temperature the data
@@ -999,9 +1004,10 @@ fem_status apply_pending(fem_mesh *m)
                                             m->dDirT, m->N, m->stream),
                "initial-state kernel");
     else
-        KERNEL(launch_set_state<real>(view_of<real>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream),
+        KERNEL(launch_set_state<real>(view_of<real>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream,
+                                      mirror_ptr(m), mirror_pos(m), mirror_len(m)),
                "state kernel");
-    KERNEL(refresh_mirror<real>(m), "mirror kernel");
+    if (initial) KERNEL(refresh_mirror<real>(m), "mirror kernel");
     CU(cudaMemsetAsync(m->dQcum, 0, (size_t)n_qcum(m) * sizeof(double), m->stream));
     if (initial) {
         // a new energy account: U0 = sum E of the initial state, no boundary heat
@@ -1691,11 +1697,11 @@ fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
         cudaSetDevice(m->device);
         CU(cudaMemcpyAsync(m->dIo, E, (size_t)m->N * sizeof(double), cudaMemcpyHostToDevice, m->stream));
         KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream)
-                   : launch_set_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream),
+                   ? launch_set_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream,
+                                             mirror_ptr(m), mirror_pos(m), mirror_len(m))
+                   : launch_set_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream,
+                                              mirror_ptr(m), mirror_pos(m), mirror_len(m)),
                "state kernel");
-        KERNEL(m->prec == FEM_FP32 ? refresh_mirror<float>(m) : refresh_mirror<double>(m),
-               "mirror kernel");
     } else {
         if (!finite_all(E, m->N)) return fail(FEM_EINVAL, "non-finite enthalpy");
         m->pending.assign(E, E + m->N);
@@ -1890,16 +1896,19 @@ fem_status set_state_async_impl(fem_mesh *m, const io *E, int64_t step, double t
     if (sizeof(io) == 4) {
         const float *src = reinterpret_cast<const float *>(m->dIn[i]);
         KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state_f32<float>(view_of<float>(m), src, m->dNodeOld, m->N, m->dErr, m->stream)
-                   : launch_set_state_f32<double>(view_of<double>(m), src, m->dNodeOld, m->N, m->dErr, m->stream),
+                   ? launch_set_state_f32<float>(view_of<float>(m), src, m->dNodeOld, m->N, m->dErr, m->stream,
+                                                 mirror_ptr(m), mirror_pos(m), mirror_len(m))
+                   : launch_set_state_f32<double>(view_of<double>(m), src, m->dNodeOld, m->N, m->dErr, m->stream,
+                                                  mirror_ptr(m), mirror_pos(m), mirror_len(m)),
                "state kernel");
     } else {
         KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state<float>(view_of<float>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream)
-                   : launch_set_state<double>(view_of<double>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream),
+                   ? launch_set_state<float>(view_of<float>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream,
+                                             mirror_ptr(m), mirror_pos(m), mirror_len(m))
+                   : launch_set_state<double>(view_of<double>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream,
+                                              mirror_ptr(m), mirror_pos(m), mirror_len(m)),
                "state kernel");
     }
-    KERNEL(m->prec == FEM_FP32 ? refresh_mirror<float>(m) : refresh_mirror<double>(m), "mirror kernel");
     CU(cudaEventRecord(m->ev_in_free[i], m->stream));
     m->in_idx = 1 - i;
     m->step = step;

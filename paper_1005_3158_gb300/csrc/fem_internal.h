@@ -244,10 +244,14 @@ int launch_set_temperature(StateView<real> v, const real *C, const real *Lc, con
                            const real *ranges, const double *T_in, const int32_t *node_old,
                            const double *dirT_int, int64_t n, void *stream);
 // launch_set_state / launch_get_temperature set kErrBadInput / kErrNonFinite
-// in *err for non-finite values (err may be null).
+// in *err for non-finite values (err may be null).  With sh_ptr and mpos
+// (block variant: shared node -> copies, copy -> mirror position, n_loc
+// entries of the local arrays) the set-state kernels also write the shared
+// nodes' mirrors.
 template <typename real>
 int launch_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
-                     int *err, void *stream);
+                     int *err, void *stream, const int32_t *sh_ptr = nullptr,
+                     const int32_t *mpos = nullptr, int64_t n_loc = 0);
 template <typename real>
 int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
@@ -256,7 +260,8 @@ int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, con
 // fem_get_temperature_async_f32).
 template <typename real>
 int launch_set_state_f32(StateView<real> v, const float *E_in, const int32_t *node_old, int64_t n,
-                         int *err, void *stream);
+                         int *err, void *stream, const int32_t *sh_ptr = nullptr,
+                         const int32_t *mpos = nullptr, int64_t n_loc = 0);
 template <typename real>
 int launch_get_temperature_f32(StateView<real> v, const real *ranges, float *T_out,
                                const int32_t *node_old, int64_t n, int *err, void *stream);

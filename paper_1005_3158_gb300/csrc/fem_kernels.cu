@@ -692,9 +692,12 @@ __global__ void k_set_temperature(StateView<real> v, const real *C, const real *
 // running one after another.
 constexpr int kIoBatch = 4;
 
+// With sh_ptr / mpos (block variant), a shared node's mirrors in the
+// blocks' local arrays are written too, so that no separate mirror refresh
+// has to follow.
 template <typename real, typename io = double>
 __global__ void k_set_state(StateView<real> v, const io *E_in, const int32_t *node_old, int64_t n,
-                            int *err)
+                            int *err, const int32_t *sh_ptr, const int32_t *mpos, int64_t n_loc)
 {
     bool bad = false;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -711,6 +714,15 @@ __global__ void k_set_state(StateView<real> v, const io *E_in, const int32_t *no
             if (i < n) {
                 bad |= !isfinite(E[u]);
                 state_set_E(v, i, (real)E[u]);
+                if (sh_ptr && i >= v.n_int) {
+                    const int64_t sn = i - v.n_int;
+                    const real stored = v.Esh[sn];
+                    const int k1 = __ldg(sh_ptr + sn + 1);
+                    for (int k = __ldg(sh_ptr + sn); k < k1; ++k) {
+                        const int32_t mp = __ldg(mpos + k);
+                        if (FEM_IN(mp, n_loc, err)) v.Eloc[mp] = stored;
+                    }
+                }
             }
         }
     }
@@ -944,9 +956,11 @@ int launch_set_temperature(StateView<real> v, const real *C, const real *Lc, con
 
 template <typename real>
 int launch_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
-                     int *err, void *stream)
+                     int *err, void *stream, const int32_t *sh_ptr, const int32_t *mpos,
+                     int64_t n_loc)
 {
-    k_set_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n, err);
+    k_set_state<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n, err, sh_ptr,
+                                                                       mpos, n_loc);
     return (int)cudaGetLastError();
 }
 
@@ -962,9 +976,11 @@ int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, con
 
 template <typename real>
 int launch_set_state_f32(StateView<real> v, const float *E_in, const int32_t *node_old, int64_t n,
-                         int *err, void *stream)
+                         int *err, void *stream, const int32_t *sh_ptr, const int32_t *mpos,
+                         int64_t n_loc)
 {
-    k_set_state<real, float><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n, err);
+    k_set_state<real, float><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, E_in, node_old, n, err,
+                                                                              sh_ptr, mpos, n_loc);
     return (int)cudaGetLastError();
 }
 
@@ -1019,12 +1035,12 @@ int launch_energy_reduce(const double *pa, int64_t na, const double *pb, int64_t
                                               const uint8_t *, const real *, const double *,      \
                                               const int32_t *, const double *, int64_t, void *);  \
     template int launch_set_state<real>(StateView<real>, const double *, const int32_t *, int64_t, \
-                                        int *, void *);                                           \
+                                        int *, void *, const int32_t *, const int32_t *, int64_t); \
     template int launch_get_temperature<real>(StateView<real>, const real *, const real *,        \
                                               const uint8_t *, const real *, double *,            \
                                               const int32_t *, int64_t, int *, void *);           \
     template int launch_set_state_f32<real>(StateView<real>, const float *, const int32_t *, int64_t, \
-                                            int *, void *);                                           \
+                                            int *, void *, const int32_t *, const int32_t *, int64_t); \
     template int launch_get_temperature_f32<real>(StateView<real>, const real *, float *,             \
                                                   const int32_t *, int64_t, int *, void *);            \
     template int launch_get_state<real>(StateView<real>, double *, const int32_t *, int64_t,      \

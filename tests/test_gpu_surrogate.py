@@ -261,3 +261,57 @@ def test_hybrid_solve_judge_and_fallback(env):
         assert np.array_equal(m.state()[0], m2.state()[0])
         s.close()
         s2.close()
+
+
+def test_precision_of_the_trained_surrogate(env):
+    """Precision pattern (1) for the BF16 surrogate, stated against the FP64
+    oracle on the 2.0M-tet casting family at a size the oracle steps in
+    seconds (a 0.2-scale flanged casting, ~16k tets): from oracle states
+    along the solidification, (a) the GPU's BF16 network against the same
+    network evaluated in FP64 by the oracle (the cost of BF16 arithmetic),
+    (b) the GPU's 16-step prediction against 16 FP64 explicit steps of the
+    oracle (model and precision together).  Printed under -s; the test
+    checks only that both are finite and that (a) is far below (b)."""
+    torch, fem = env
+    from paper_1005_3158_gb300 import surrogate as sgd
+    import os
+    if not os.path.exists(sgd.PARAMS_FILE):
+        pytest.skip("no trained parameters")
+    th = np.load(sgd.PARAMS_FILE).astype(np.float32)
+    p = mg.flanged_variant(4000, 0.2)
+    o = oracle.OracleProblem(p)
+    o.set_temperature(p.T0)
+    dt = 0.9 * o.stable_dt()
+    g = osg.SurrogateGraph(p, dt)
+    with fem.Mesh(p, "fp32", reorder=1) as m:
+        s = fem.Surrogate(m, dt)
+        s.set_params(th)
+        order = s.order()
+        rows = []
+        for k in range(0, 60):
+            E = o.enthalpy()
+            if k in (2, 10, 30, 59):
+                E_dev = torch.tensor(E.astype(np.float32)[order], device="cuda")
+                out = torch.empty_like(E_dev)
+                s.predict(E_dev, out)
+                torch.cuda.synchronize()
+                E_gpu = np.empty(p.n_nodes)
+                E_gpu[order] = out.cpu().numpy()
+                E64, _ = osg.forward(th.astype(np.float64), g, E, emulate=False)
+                o2 = oracle.OracleProblem(p)
+                o2.set_enthalpy(E)
+                o2.step(16, dt)
+                T_ref = o2.temperature()
+                o2.set_enthalpy(E_gpu)
+                T_gpu = o2.temperature()
+                o2.set_enthalpy(E64)
+                T_64 = o2.temperature()
+                rows.append((k, float(np.abs(T_gpu - T_64).max()), float(np.abs(T_gpu - T_ref).max()),
+                             float(np.abs(T_gpu - T_ref).mean())))
+            o.step(16, dt)
+        s.close()
+    for k, a, b, c in rows:
+        print(f"macro step {k}: |BF16 net - FP64 net| max {a:.3g} K; "
+              f"|net - 16 FP64 steps| max {b:.3g} K, mean {c:.3g} K")
+    assert all(np.isfinite([a, b, c]).all() for _, a, b, c in rows)
+    assert max(r[1] for r in rows) < max(r[2] for r in rows)
