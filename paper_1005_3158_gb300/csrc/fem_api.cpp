@@ -692,7 +692,8 @@ fem_status upload_block(fem_mesh *m)
     if ((st = upload<int32_t>(m, &m->dShPtr, bp.sh_ptr.data(), bp.sh_ptr.size()))) return st;
     {
         // per-block local node arrays at stride ls: interior nodes, then the
-        // block's shared copies, then padding (C = 1, Lc = 0)
+        // block's shared copies, then padding; (1/C, Lc) per node, padding
+        // (1, 0)
         const int32_t ls = (int32_t)(((int64_t)bp.max_nloc + 31) / 32 * 32);
         m->ls = ls;
         const size_t nl = bp.blocks.size() * (size_t)ls;
@@ -710,7 +711,7 @@ fem_status upload_block(fem_mesh *m)
             const size_t base = bi * (size_t)ls;
             for (int32_t l = 0; l < b.nint; l++) {
                 const int32_t o = old[(size_t)b.n0 + l];
-                cl[2 * (base + l)] = (real)m->Cn[o];
+                cl[2 * (base + l)] = (real)(1.0 / m->Cn[o]);
                 cl[2 * (base + l) + 1] = (real)m->Lcn[o];
                 ph[base + l] = node_ph(o);
                 home[(size_t)b.n0 + l] = (int32_t)(base + l);
@@ -718,7 +719,7 @@ fem_status upload_block(fem_mesh *m)
             for (int32_t k = 0; k < b.nsh; k++) {
                 const size_t c = (size_t)b.c0 + k, at = base + (size_t)b.nint + k;
                 const int32_t o = old[bp.copy_node[c]];
-                cl[2 * at] = (real)m->Cn[o];
+                cl[2 * at] = (real)(1.0 / m->Cn[o]);
                 cl[2 * at + 1] = (real)m->Lcn[o];
                 ph[at] = node_ph(o);
                 pos[at] = bp.copy_pos[c];

@@ -28,6 +28,26 @@ __device__ __forceinline__ real temperature_of(real E, real C, real Lc, uint8_t 
     return Ts + (E - E_sol) / (C + Lc / (Tl - Ts));
 }
 
+// The same from the reciprocal capacity rC = 1/C (rounded once): the solid
+// and liquid branches become products, and only the mushy branch divides.
+// Ta = E / C is the temperature if no latent heat were stored, Tb the
+// temperature if all of it were; T(E) is Ta below the solidus, Tb above the
+// liquidus and, in between, the point where E = C T + Lc (T - Ts)/(Tl - Ts).
+template <typename real>
+__device__ __forceinline__ real temperature_of_rc(real E, real rC, real Lc, uint8_t ph,
+                                                  const real *__restrict__ ranges)
+{
+    const real Ta = E * rC;
+    if (!(Lc > real(0))) return Ta;
+    const int r = ph & 0x7F;
+    const real Ts = __ldg(ranges + 2 * r), Tl = __ldg(ranges + 2 * r + 1);
+    if (Ta <= Ts) return Ta;
+    const real Tb = (E - Lc) * rC;
+    if (Tb >= Tl) return Tb;
+    if (Tl <= Ts) return Ts;   // isothermal plateau
+    return Ts + (Ta - Ts) / (real(1) + Lc * rC / (Tl - Ts));
+}
+
 // Enthalpy content of a node at temperature T.
 template <typename real>
 __device__ __forceinline__ real enthalpy_of(real T, real C, real Lc, uint8_t ph,

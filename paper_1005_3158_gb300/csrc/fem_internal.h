@@ -121,7 +121,7 @@ struct BlockArgs {
     // shared node's copy (E mirrored by the exchange), the rest padding.
     int32_t ls;                // local-array stride (multiple of 32)
     real *Eloc;                // [n_blocks*ls]
-    const real *CLloc;         // [n_blocks*ls][2] (C, Lc)
+    const real *CLloc;         // [n_blocks*ls][2] (1/C, Lc)
     const uint8_t *phloc;      // [n_blocks*ls] phase-range index | kDirichletBit
     const int32_t *posloc;     // [n_blocks*ls] shared copy: its position in P
     const real *ranges;        // [n_ranges][2] (Ts, Tl)

@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     if (threadIdx.x == 0 && bi.nf > 0) qprev = a.qcum[b];
 
     // local nodes: enthalpy -> temperature (Eqs. 5, 11); padding entries
-    // hold C = 1, Lc = 0 and give a harmless T
+    // hold 1/C = 1, Lc = 0 and give a harmless T
     real Tl[MAXJ];
 #pragma unroll
     for (int j = 0; j < MAXJ; j++) {
@@ -366,12 +366,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
             if (LM) {   // the state is T
                 Tl[j] = sE[l];
             } else {
-                const V2 cl = reinterpret_cast<const V2 *>(sv)[l];
-                Tl[j] = temperature_of(sE[l], cl.x, cl.y, sPh[l], a.ranges);
+                const V2 cl = reinterpret_cast<const V2 *>(sv)[l];   // (1/C, Lc)
+                Tl[j] = temperature_of_rc(sE[l], cl.x, cl.y, sPh[l], a.ranges);
             }
         }
     }
-    // the vote below is also the barrier that ends the reads of (C, Lc)
+    // the vote below is also the barrier that ends the reads of (1/C, Lc)
     // from the slot area before pass 1 overwrites it
     if (threadIdx.x == 0) failed = !mbar_wait(bar_s, 0);
     if (__syncthreads_or(failed)) {

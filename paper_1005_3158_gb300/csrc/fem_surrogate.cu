@@ -17,16 +17,22 @@
 // fraction, the lumped Robin terms of Eq. 4 and the conduction change of
 // one explicit step (see fem.h for the 16 channels).
 //
-// Kernels (one CTA of 128 threads per 128-node tile, persistent over tiles):
+// Kernels of one evaluation (nodes in 128-node tiles; x, h and m stored
+// tile by tile in the tensor cores' operand layout, phi row by row):
 //   k_sg_tf        T(E) and liquid fraction per node
-//   k_sg_encode    features, h0 = encoder (tcgen05), phi_1 (tcgen05)
-//   k_sg_layer     message sums on CUDA cores (8 lanes per node, 4 channels
-//                  per lane, FP32), the layer's update and the next layer's
-//                  projection (or the decoder) on tcgen05 tensor cores
+//   k_sg_feat      the 16 input channels (two lanes per node)
+//   k_sg_encode    h0 = encoder and phi_1 = P_1 h0 on tcgen05 tensor cores
+//   k_sg_msg_tile  graph messages m_l on CUDA cores (FP32 sums), one CTA per
+//                  tile with the phi rows of the tile and of its halo staged
+//                  in shared memory (k_sg_msg: the gather form, for graphs
+//                  whose tiles do not fit)
+//   k_sg_layer     h_l = h_{l-1} + relu(U_l [h_{l-1}; m_l] + u_l) and the
+//                  next projection (or the decoder) on tcgen05, persistent
+//                  over tiles with two stages of bulk copies in flight
 //   backward, loss, weight-gradient and Adam kernels for training (below).
-// The message sums gather 14 neighbours per node on average from a graph
-// with ~14 non-zeros per row: a sparse gather, kept on CUDA cores; the
-// dense per-node layers are the contractions that go to the tensor cores.
+// The message sums gather 14 neighbours per node on average: sparse work,
+// kept on CUDA cores; the dense per-node layers are the contractions that go
+// to the tensor cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -506,7 +512,7 @@ __global__ void __launch_bounds__(128, 3) k_sg_layer(Graph g, Acts a, const uint
     const uint32_t bar_mma = smem_addr(sm + kLBar + 16);
     const int tid = threadIdx.x;
     constexpr uint32_t N2 = LAST ? 64 : 32;
-    constexpr uint32_t kHB = 128 * 64 * 2, kMB = 128 * 32 * 2;   // bytes of an h / m tile
+    constexpr uint32_t kHB = 128 * 64 * 2;   // bytes of an h tile
     const uint8_t *hsrc = reinterpret_cast<const uint8_t *>(a.h[l]);
     const uint8_t *msrc = reinterpret_cast<const uint8_t *>(a.m[l]);
     if (tid < 32) tc::tmem_alloc(sTmem, 128);
@@ -2126,32 +2132,38 @@ extern "C" fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int
     fem_status r = FEM_OK;
     while (k < n_macro) {
         const bool judged = judge_every > 0 && k % judge_every == 0;
-        if (judged || k < plain_until) {
+        if (!judged && k < plain_until) {
+            // the solver's macro steps up to the next judged one, in one call
+            // (its step graphs then cover them)
+            int64_t run = std::min(plain_until, n_macro) - k;
+            if (judge_every > 0) run = std::min(run, judge_every - k % judge_every);
+            if ((r = fem_step(s->mesh, run * kMacroSteps, s->dt))) return r;
+            n_plain += run;
+            k += run;
+        } else if (judged) {
             StateView<float> v{};
             cudaStream_t st = nullptr;
             if ((r = mesh_stream(s, &v, &st))) return r;
-            if (judged) k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, s->E0);
+            k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, s->E0);
             if ((r = fem_step(s->mesh, kMacroSteps, s->dt))) return r;
             n_plain++;
-            if (judged) {
-                if ((r = mesh_stream(s, &v, &st))) return r;
-                float *Epl = s->a.y;   // scratch rows (inference does not use y)
-                k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, Epl);
-                if ((r = forward(s, s->E0, s->E1, false, st))) return r;
-                unsigned int *jb = reinterpret_cast<unsigned int *>(s->E0);   // E0 is free again
-                SCU(cudaMemsetAsync(jb, 0, sizeof(unsigned int), st));
-                k_sg_judge<<<std::min(4 * s->n_sm, (s->n + 255) / 256), 256, 0, st>>>(s->E1, Epl, s->g, jb);
-                if ((r = launch_check("surrogate judge"))) return r;
-                unsigned int bits = 0;
-                SCU(cudaMemcpyAsync(&bits, jb, sizeof(bits), cudaMemcpyDeviceToHost, st));
-                SCU(cudaStreamSynchronize(st));
-                float e;
-                std::memcpy(&e, &bits, sizeof e);
-                worst = std::max(worst, (double)e);
-                if (!((double)e <= tol_K)) {
-                    n_fail++;
-                    plain_until = k + judge_every;
-                }
+            if ((r = mesh_stream(s, &v, &st))) return r;
+            float *Epl = s->a.y;   // scratch rows (inference does not use y)
+            k_sg_gather<<<(s->n + 255) / 256, 256, 0, st>>>(v, s->int_id, s->n, Epl);
+            if ((r = forward(s, s->E0, s->E1, false, st))) return r;
+            unsigned int *jb = reinterpret_cast<unsigned int *>(s->E0);   // E0 is free again
+            SCU(cudaMemsetAsync(jb, 0, sizeof(unsigned int), st));
+            k_sg_judge<<<std::min(4 * s->n_sm, (s->n + 255) / 256), 256, 0, st>>>(s->E1, Epl, s->g, jb);
+            if ((r = launch_check("surrogate judge"))) return r;
+            unsigned int bits = 0;
+            SCU(cudaMemcpyAsync(&bits, jb, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            SCU(cudaStreamSynchronize(st));
+            float e;
+            std::memcpy(&e, &bits, sizeof e);
+            worst = std::max(worst, (double)e);
+            if (!((double)e <= tol_K)) {
+                n_fail++;
+                plain_until = k + judge_every;
             }
             k++;
         } else {
