@@ -567,24 +567,43 @@ def run_surrogate(args):
     sg.profile(3)
     kms = sg.profile(args.profile_steps) / max(1, args.profile_steps)
     N, nnz = sg.n_nodes, sg.n_edges
-    names = ["k_sg_tf", "k_sg_encode", "k_sg_layer<false> (layer 1)", "k_sg_layer<false> (layer 2)",
-             "k_sg_layer<true> (layer 3 + decoder)"]
-    # algorithmic bytes of a layer launch: h read + written (bf16 x 64),
-    # phi gathered once per node and written (bf16 x 32), the CSR (column
-    # and weight per edge, row pointer) and s per node
-    alg_layer = N * (128 + 128 + 64 + 64 + 4 + 4) + nnz * 8
-    flops_layer = N * 2 * (96 * 64 + 64 * 32)
+    rows = (N + 127) // 128 * 128
+    # fem_surrogate_profile's groups: kernel, launches per evaluation and
+    # algorithmic bytes per launch (bf16 activations, FP32 graph data)
+    groups = [
+        # T(E) + features: E, C, Lc, phase byte and the Robin terms per node,
+        # T and f read again through the CSR (column + weight per edge), x
+        # written (16 bf16)
+        ("k_sg_tf + k_sg_feat", 2, N * (4 + 4 + 4 + 1 + 8 + 8 + 8 + 32) + nnz * 8),
+        # x read, h0 (64 bf16) and phi_1 (32 bf16) written
+        ("k_sg_encode", 1, rows * (32 + 128 + 64)),
+        # phi read once per node, m written (32 bf16 each), the CSR (int32
+        # column + FP32 weight per edge, row pointer) and wsum, s per node
+        ("k_sg_msg_tile", 3, N * (64 + 64 + 4 + 8) + nnz * 8),
+        # [h; m] read, h and the next phi written
+        ("k_sg_layer<false>", 2, rows * (128 + 64 + 128 + 64)),
+        # [h; m], E and C read, E' written
+        ("k_sg_layer<true>", 1, rows * (128 + 64) + N * (4 + 4 + 4)),
+    ]
+    per_launch = [kms[i] / groups[i][1] for i in range(5)]
     k_dom = int(np.argmax(kms))
     peak, peak_kind = hbm_peak()
-    ach = alg_layer / (kms[k_dom] / 1e3) / 1e9
-    tflops = flops_layer / (kms[k_dom] / 1e3) / 1e12
-    roofline = {"bound": "hbm", "kernel": names[k_dom], "achieved": round(ach, 1),
+    name, nl, alg = groups[k_dom]
+    ach = alg / (per_launch[k_dom] / 1e3) / 1e9
+    # the dense layers' contraction on tcgen05 (U_l [h; m] and P_{l+1} h)
+    flops_layer = rows * 2 * (96 * 64 + 64 * 32)
+    roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
-                "peak_source": peak_kind, "alg_bytes_per_launch": int(alg_layer),
-                "kernel_ms": [round(float(v), 4) for v in kms],
-                "tensor": {"flops_per_launch": int(flops_layer), "achieved_tflops": round(tflops, 2),
-                           "note": "dense per-node layers on tcgen05; the message sums gather "
-                                   "on CUDA cores"}}
+                "peak_source": peak_kind, "alg_bytes_per_launch": int(alg),
+                "launches_per_evaluation": nl,
+                "kernel_ms_per_launch": {g[0]: round(float(v), 4) for g, v in zip(groups, per_launch)},
+                "k_sg_layer<false>": {
+                    "alg_bytes_per_launch": int(groups[3][2]),
+                    "frac_hbm": round(groups[3][2] / (per_launch[3] / 1e3) / 1e9 / peak, 4),
+                    "flops_per_launch": int(flops_layer),
+                    "achieved_tflops": round(flops_layer / (per_launch[3] / 1e3) / 1e12, 2),
+                    "note": "dense per-node layers on tcgen05 (BF16, FP32 accumulation in TMEM); "
+                            "the message sums gather on CUDA cores"}}
     # end to end through the C ABI with host buffers: upload the pour state
     # (FP32, pinned), solve, read the temperatures back; plain vs surrogate
     e2e = None
