@@ -686,10 +686,10 @@ __global__ void k_set_temperature(StateView<real> v, const real *C, const real *
 }
 
 // io: the element type of the caller's array (double, or float for the
-// FP32 host I/O of fem_set_state_async_f32 / fem_get_temperature_async_f32)
-// The permuting I/O loops take kIoBatch nodes per thread per round, all
-// loads first: their index -> value -> store chains then overlap instead of
-// running one after another.
+// FP32 host I/O of fem_set_state_async_f32 / fem_get_temperature_async_f32).
+// The upload takes kIoBatch nodes per thread per round, grid-stride apart,
+// all loads first: their index -> value -> store chains then overlap
+// instead of running one after another.
 constexpr int kIoBatch = 4;
 
 // With sh_ptr / mpos (block variant), a shared node's mirrors in the
@@ -729,27 +729,67 @@ __global__ void k_set_state(StateView<real> v, const io *E_in, const int32_t *no
     if (bad && err) atomicOr(err, kErrBadInput);
 }
 
+// Four consecutive entries of a node array from index i (a multiple of 4).
+// Every device array is a 256-byte-aligned allocation with 256 bytes of
+// tail padding, so the load stays inside it when some of the four indices
+// are past the end (those values are not used).
+__device__ __forceinline__ void load4(const int32_t *p, int32_t (&o)[4])
+{
+    const int4 q = __ldg(reinterpret_cast<const int4 *>(p));
+    o[0] = q.x, o[1] = q.y, o[2] = q.z, o[3] = q.w;
+}
+__device__ __forceinline__ void load4(const float *p, float (&o)[4])
+{
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = q.x, o[1] = q.y, o[2] = q.z, o[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&o)[4])
+{
+    const double2 q0 = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 q1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = q0.x, o[1] = q0.y, o[2] = q1.x, o[3] = q1.y;
+}
+__device__ __forceinline__ void load4(const uint8_t *p, uint8_t (&o)[4])
+{
+    const uint32_t q = __ldg(reinterpret_cast<const unsigned int *>(p));
+    o[0] = (uint8_t)q, o[1] = (uint8_t)(q >> 8), o[2] = (uint8_t)(q >> 16), o[3] = (uint8_t)(q >> 24);
+}
+
+// The state -> the caller's T, in the caller's node order.  Four
+// consecutive nodes per thread: the internal-side arrays (permutation, home
+// slot, C, Lc, phase) come in one 16-byte load each, and the four E
+// gathers and T scatters are independent.
+constexpr int kReadNodes = 4;
 template <typename real, typename io = double>
-__global__ void k_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
-                                  const real *ranges, io *T_out, const int32_t *node_old,
-                                  int64_t n, int *err)
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 6 : 4)
+    k_get_temperature(StateView<real> v, io *T_out, const int32_t *node_old, int64_t n, int *err)
 {
     bool bad = false;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kIoBatch * stride) {
-        double T[kIoBatch];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kReadNodes;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kReadNodes; i0 < n; i0 += stride) {
+        int32_t no[4], hm[4] = {0, 0, 0, 0};
+        real C[4] = {}, Lc[4] = {};
+        uint8_t ph[4] = {0, 0, 0, 0};
+        load4(node_old + i0, no);
+        if (v.home && i0 < v.n_int) load4(v.home + i0, hm);
+        if (!v.is_T) {
+            load4(v.C + i0, C);
+            load4(v.Lc + i0, Lc);
+            load4(v.ph + i0, ph);
+        }
+        real E[4];
 #pragma unroll
-        for (int u = 0; u < kIoBatch; u++) {
-            const int64_t i = i0 + u * stride;
-            T[u] = i < n ? (double)state_T(v, i) : 0.0;
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + u;
+            E[u] = i >= n ? real(0)
+                          : (i < v.n_int ? __ldg(v.Eloc + (v.home ? hm[u] : i)) : __ldg(v.Esh + (i - v.n_int)));
         }
 #pragma unroll
-        for (int u = 0; u < kIoBatch; u++) {
-            const int64_t i = i0 + u * stride;
-            if (i < n) {
-                bad |= !isfinite(T[u]);
-                T_out[node_old[i]] = (io)T[u];
-            }
+        for (int u = 0; u < 4; u++) {
+            if (i0 + u >= n) break;
+            const real T = v.is_T ? E[u] : temperature_of(E[u], C[u], Lc[u], ph[u], v.ranges);
+            bad |= !isfinite((double)T);
+            T_out[no[u]] = (io)T;
         }
     }
     if (bad && err) atomicOr(err, kErrNonFinite);
@@ -969,8 +1009,8 @@ int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, con
                            const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
                            int *err, void *stream)
 {
-    k_get_temperature<real><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
-        v, C, Lc, ph, ranges, T_out, node_old, n, err);
+    k_get_temperature<real><<<grid_for((n + kReadNodes - 1) / kReadNodes, 256), 256, 0,
+                                (cudaStream_t)stream>>>(v, T_out, node_old, n, err);
     return (int)cudaGetLastError();
 }
 
@@ -988,8 +1028,8 @@ template <typename real>
 int launch_get_temperature_f32(StateView<real> v, const real *ranges, float *T_out,
                                const int32_t *node_old, int64_t n, int *err, void *stream)
 {
-    k_get_temperature<real, float><<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
-        v, nullptr, nullptr, nullptr, ranges, T_out, node_old, n, err);
+    k_get_temperature<real, float><<<grid_for((n + kReadNodes - 1) / kReadNodes, 256), 256, 0,
+                                       (cudaStream_t)stream>>>(v, T_out, node_old, n, err);
     return (int)cudaGetLastError();
 }
 
