@@ -593,23 +593,29 @@ fem_status fem_surrogate_apply(fem_surrogate *s, float lr);
 fem_status fem_surrogate_advance(fem_surrogate *s, int64_t n_macro);
 
 /* Surrogate stepping with the explicit solver as judge and fallback (plain
- * meshes only).  Advances 16 * n_macro steps.  Every judge_every-th macro
- * step (0: never) the explicit solver takes the 16 steps and the
- * surrogate's prediction from the same state is compared with its result,
- * which is kept: d = max_i |E_sg,i - E_i| / C_i, a bound on the
- * temperature difference (dT/dE <= 1/C).  If d > tol_K (K) the solver
- * also takes every macro step up to the next judged one.  stats [3] (may be
- * NULL): macro steps by the surrogate, by the solver (judged ones
- * included), judged steps that failed; max_err (may be NULL): the largest
- * d seen.  Synchronises at every judged step.  Errors as fem_step and
- * fem_surrogate_advance; FEM_EINVAL for a batch or tol_K <= 0. */
+ * meshes only).  Advances 16 * n_macro steps.  Macro step 0 is judged (if
+ * judge_every > 0; 0: never judge, the surrogate takes every step): the
+ * explicit solver takes the 16 steps and the surrogate's prediction from
+ * the same state is compared with its result, which is kept: d = max_i
+ * |E_sg,i - E_i| / C_i, a bound on the temperature difference (dT/dE <=
+ * 1/C).  If d <= tol_K (K) the surrogate takes the next judge_every - 1
+ * macro steps and the one after them is judged.  If d > tol_K the solver
+ * takes the next span - 1 macro steps and the one after them is judged,
+ * with span = judge_every * 2^min(f - 1, 6) after the f-th consecutive
+ * failure (a surrogate that keeps failing is tried less and less often).
+ * stats [3] (may be NULL): macro steps by the surrogate, by the solver
+ * (judged ones included), judged steps that failed; max_err (may be
+ * NULL): the largest d seen.  Synchronises at every judged step.  Errors
+ * as fem_step and fem_surrogate_advance; FEM_EINVAL for a batch or tol_K
+ * <= 0. */
 fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int32_t judge_every,
                                double tol_K, int64_t *stats, double *max_err);
 
 /* As n_macro forward passes from the mesh's state (left unchanged), with
- * CUDA events around every kernel on the mesh's stream: ms_out [5] gets the
- * summed device milliseconds of {T(E) and liquid fraction, encoder, layer
- * 1, layer 2, layer 3 with the decoder}.  Measurement only. */
+ * CUDA events around the kernels on the mesh's stream: ms_out [5] gets the
+ * summed device milliseconds of {T(E), liquid fraction and features,
+ * encoder, the three message sums, the dense parts of layers 1 and 2,
+ * layer 3 with the decoder}.  Measurement only. */
 fem_status fem_surrogate_profile(fem_surrogate *s, int64_t n_macro, double *ms_out);
 
 /* Test hook: a host copy of an internal buffer after the last forward or

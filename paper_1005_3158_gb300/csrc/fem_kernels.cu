@@ -319,9 +319,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : (NT <= 512 ? 2 : 1)))
     // load's latency is hidden behind the passes)
     const real dtb = a.blk_dt ? a.blk_dt[b] : dt;
 
-    // the mbarriers were initialised by thread 0 before any other thread
-    // polls them: the barrier below orders the two
-    __syncthreads();
+    // thread 0 initialised the mbarriers before it waits on bar_n; the other
+    // threads touch them only after the vote below, which orders the two
     int failed = 0;
     if (threadIdx.x == 0) failed = !mbar_wait(bar_n, 0);
     if (__syncthreads_or(failed)) {

@@ -2128,15 +2128,17 @@ extern "C" fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int
     if (mv.n_inst > 0) return sfail(FEM_EINVAL, "fem_surrogate_solve steps plain meshes only");
     int64_t n_sg = 0, n_plain = 0, n_fail = 0;
     double worst = 0.0;
-    int64_t k = 0, plain_until = 0;
+    // k: the next macro step; the solver takes every step before plain_until
+    // and judges step next_judge; fails: consecutive failed judgements
+    int64_t k = 0, plain_until = 0, next_judge = 0;
+    int fails = 0;
     fem_status r = FEM_OK;
     while (k < n_macro) {
-        const bool judged = judge_every > 0 && k % judge_every == 0;
+        const bool judged = judge_every > 0 && k == next_judge;
         if (!judged && k < plain_until) {
             // the solver's macro steps up to the next judged one, in one call
             // (its step graphs then cover them)
-            int64_t run = std::min(plain_until, n_macro) - k;
-            if (judge_every > 0) run = std::min(run, judge_every - k % judge_every);
+            const int64_t run = std::min(std::min(plain_until, next_judge), n_macro) - k;
             if ((r = fem_step(s->mesh, run * kMacroSteps, s->dt))) return r;
             n_plain += run;
             k += run;
@@ -2161,14 +2163,22 @@ extern "C" fem_status fem_surrogate_solve(fem_surrogate *s, int64_t n_macro, int
             float e;
             std::memcpy(&e, &bits, sizeof e);
             worst = std::max(worst, (double)e);
+            // a failed judgement hands the steps up to the next one to the
+            // solver; each further consecutive failure doubles that span
+            int64_t span = judge_every;
             if (!((double)e <= tol_K)) {
                 n_fail++;
-                plain_until = k + judge_every;
+                span = (int64_t)judge_every << std::min(fails, kMaxJudgeBackoff);
+                fails++;
+                plain_until = k + span;
+            } else {
+                fails = 0;
             }
+            next_judge = k + span;
             k++;
         } else {
             int64_t run = n_macro - k;
-            if (judge_every > 0) run = std::min(run, judge_every - k % judge_every);
+            if (judge_every > 0) run = std::min(run, next_judge - k);
             if ((r = fem_surrogate_advance(s, run))) return r;
             n_sg += run;
             k += run;

@@ -16,6 +16,9 @@ namespace sg {
 constexpr int kNF = 16, kHID = 64, kMSG = 32, kLayers = 3, kTile = 128;
 constexpr float kTC = 600.f, kTS = 300.f, kYS = 10.f, kMacro = 16.f;
 constexpr int kMacroSteps = 16;
+// Hybrid solve: after f consecutive failed judgements the solver takes the
+// next judge_every * 2^min(f - 1, kMaxJudgeBackoff) macro steps.
+constexpr int kMaxJudgeBackoff = 6;
 
 // Flat FP32 parameter vector (the Linear convention y = W x + b):
 //   W_in [64][16], b_in [64],

@@ -36,6 +36,7 @@ from . import meshgen as mg
 
 PARAMS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "surrogate_params.npy")
 MACRO = 16
+MAX_BACKOFF = 6   # fem_surrogate_solve: largest doubling of the span after failed judgements
 
 
 def param_shapes():
@@ -209,17 +210,25 @@ def evaluate(p, theta, judge_every=8, tols=(2.0,), max_macro=4000, log=print):
         err_t = [0.0]
         n_sg = n_pl = n_fail = 0
         worst_judge = 0.0
-        plain_until = 0
-        # the policy of fem_surrogate_solve, one macro step at a time so that
+        plain_until = next_judge = fails = 0
+        # the policy of fem_surrogate_solve (a failed judgement hands the
+        # span up to the next one to the solver, the span doubling with each
+        # further consecutive failure), one macro step at a time so that
         # every macro step can be read back
         for k in range(n_macro):
-            if judge_every > 0 and k % judge_every == 0:
+            if judge_every > 0 and k == next_judge:
                 _, b_, c, e = s.solve(1, 1, tol)
                 n_pl += b_
                 n_fail += c
                 worst_judge = max(worst_judge, e)
+                span = judge_every
                 if c:
-                    plain_until = k + judge_every
+                    span = judge_every << min(fails, MAX_BACKOFF)
+                    fails += 1
+                    plain_until = k + span
+                else:
+                    fails = 0
+                next_judge = k + span
             elif k < plain_until:
                 m2.step(MACRO, dt)
                 n_pl += 1

@@ -263,6 +263,28 @@ def test_hybrid_solve_judge_and_fallback(env):
         s2.close()
 
 
+def test_hybrid_solve_backs_off_after_failures(env):
+    """A surrogate that keeps failing is judged less and less often: after
+    the f-th consecutive failed judgement the solver takes judge_every *
+    2^(f-1) macro steps before the next judgement (judged at 0, 2, 6, 14
+    for judge_every 2), and the state is still bitwise the plain solver's."""
+    torch, fem = env
+    p = _problem("small")
+    th = _params(17)
+    n_macro, J = 20, 2
+    with fem.Mesh(p, "fp32", reorder=1) as ref:
+        dt = 0.9 * ref.stable_dt()
+        ref.step(n_macro * 16, dt)
+        E_plain = ref.state()[0]
+    with fem.Mesh(p, "fp32", reorder=1) as m:
+        s = fem.Surrogate(m, dt)
+        s.set_params(th)
+        n_sg, n_pl, n_fail, _ = s.solve(n_macro, J, 1e-30)
+        assert (n_sg, n_pl, n_fail) == (0, n_macro, 4)
+        assert np.array_equal(m.state()[0], E_plain)
+        s.close()
+
+
 def test_precision_of_the_trained_surrogate(env):
     """Precision pattern (1) for the BF16 surrogate, stated against the FP64
     oracle on the 2.0M-tet casting family at a size the oracle steps in
