@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # matching summary under profiles/); valid while the sources it was taken on
 # are unchanged
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
-TRAFFIC_SOURCES = ("fem_kernels.cu", "fem_device.cuh", "fem_internal.h", "fem_plan.cpp",
-                   "fem_plan.h")
+TRAFFIC_SOURCES = ("fem_kernels.cu", "fem_state.cuh", "fem_device.cuh", "fem_internal.h",
+                   "fem_plan.cpp", "fem_plan.h")
 
 
 def sources_digest() -> str:
@@ -105,6 +105,9 @@ def parse():
     ap.add_argument("--params", default="")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", default="block", choices=["block", "atomic", "colored"])
+    ap.add_argument("--physics", default="const", choices=["const", "kt", "apparent"],
+                    help="const: constant k, enthalpy (default); kt: temperature-dependent "
+                         "conductivity tables; apparent: the apparent-capacity formulation")
     ap.add_argument("--reorder", type=int, default=1)
     ap.add_argument("--block-elems", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
@@ -714,9 +717,15 @@ def main():
     from paper_1005_3158_gb300 import fem
 
     p = make_problem(args.workload)
+    if args.physics == "kt":
+        # k(T) of the alloy (material 0) and the steel (1): piecewise linear
+        # between the table points, constant beyond them
+        p.k_tables = ((0, [300.0, 600.0, 821.0, 913.0], [150.0, 160.0, 140.0, 90.0]),
+                      (1, [300.0, 900.0], [30.0, 26.0]))
     t_setup = time.perf_counter()
     mesh = fem.Mesh(p, args.precision, reorder=args.reorder, variant=args.variant,
-                    block_elems=args.block_elems, threads=args.threads)
+                    block_elems=args.block_elems, threads=args.threads,
+                    formulation="apparent" if args.physics == "apparent" else "enthalpy")
     dt = 0.9 * mesh.stable_dt()
     stream = torch.cuda.Stream()
     mesh.set_stream(stream.cuda_stream)
@@ -870,7 +879,7 @@ def main():
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n_tets": E, "n_nodes": N,
-                       "n_faces": p.n_faces, "variant": args.variant,
+                       "n_faces": p.n_faces, "variant": args.variant, "physics": args.physics,
                        "precision": args.precision, "reorder": args.reorder,
                        "n_blocks": info["n_blocks"], "threads": info["threads"],
                        "ctas_per_sm": info["ctas_per_sm"], "smem_per_cta": info["smem_per_cta"],

@@ -24,6 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = {
     "fem_kernels.cu": "nvcc",
+    "fem_io.cu": "nvcc",
     "fem_noalloc.cu": "nvcc",
     "fem_surrogate.cu": "nvcc",
     "fem_api.cpp": "g++",

@@ -17,6 +17,7 @@
 
 #include "fem.h"
 #include "fem_internal.h"
+#include "fem_io.h"
 #include "fem_mesh_access.h"
 #include "fem_plan.h"
 
@@ -277,7 +278,7 @@ bool is_lm(const fem_mesh *m);
 // stage the conductances.
 bool weights_from_l2(const fem_mesh *m)
 {
-    return is_block(m) && !m->has_kt && !is_lm(m) && (m->opt.threads == 0 || m->opt.threads == 256);
+    return is_block(m) && !is_lm(m) && (m->opt.threads == 0 || m->opt.threads == 256);
 }
 
 // Dynamic shared memory of a block-kernel CTA for plan bp (largest block;
@@ -991,6 +992,20 @@ fem_status instance_sums(fem_mesh *m, std::vector<double> &U)
     return FEM_OK;
 }
 
+// Upload of a caller-order E array already on the device (src, io = double
+// or float); the block variant's kernel also writes the shared nodes'
+// mirrors.
+template <typename real, typename io>
+int launch_upload(fem_mesh *m, const io *src)
+{
+    if constexpr (sizeof(io) == 8)
+        return launch_set_state<real>(view_of<real>(m), (const double *)src, m->dNodeOld, m->N, m->dErr,
+                                      m->stream, mirror_ptr(m), mirror_pos(m), mirror_len(m));
+    else
+        return launch_set_state_f32<real>(view_of<real>(m), (const float *)src, m->dNodeOld, m->N, m->dErr,
+                                          m->stream, mirror_ptr(m), mirror_pos(m), mirror_len(m));
+}
+
 // Apply a pending initial condition or checkpoint on the device.
 template <typename real>
 fem_status apply_pending(fem_mesh *m)
@@ -1005,8 +1020,7 @@ fem_status apply_pending(fem_mesh *m)
                                             m->dDirT, m->N, m->stream),
                "initial-state kernel");
     else
-        KERNEL(launch_set_state<real>(view_of<real>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream,
-                                      mirror_ptr(m), mirror_pos(m), mirror_len(m)),
+        KERNEL((launch_upload<real, double>(m, m->dIo)),
                "state kernel");
     if (initial) KERNEL(refresh_mirror<real>(m), "mirror kernel");
     CU(cudaMemsetAsync(m->dQcum, 0, (size_t)n_qcum(m) * sizeof(double), m->stream));
@@ -1697,11 +1711,8 @@ fem_status fem_set_state(fem_mesh *m, const double *E, int64_t step, double t)
         // stage through the device buffer on the mesh's stream, no synchronisation
         cudaSetDevice(m->device);
         CU(cudaMemcpyAsync(m->dIo, E, (size_t)m->N * sizeof(double), cudaMemcpyHostToDevice, m->stream));
-        KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state<float>(view_of<float>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream,
-                                             mirror_ptr(m), mirror_pos(m), mirror_len(m))
-                   : launch_set_state<double>(view_of<double>(m), m->dIo, m->dNodeOld, m->N, m->dErr, m->stream,
-                                              mirror_ptr(m), mirror_pos(m), mirror_len(m)),
+        KERNEL((m->prec == FEM_FP32 ? launch_upload<float, double>(m, m->dIo)
+                                    : launch_upload<double, double>(m, m->dIo)),
                "state kernel");
     } else {
         if (!finite_all(E, m->N)) return fail(FEM_EINVAL, "non-finite enthalpy");
@@ -1896,18 +1907,11 @@ fem_status set_state_async_impl(fem_mesh *m, const io *E, int64_t step, double t
     CU(cudaStreamWaitEvent(m->stream, m->ev_in_ready[i], 0));
     if (sizeof(io) == 4) {
         const float *src = reinterpret_cast<const float *>(m->dIn[i]);
-        KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state_f32<float>(view_of<float>(m), src, m->dNodeOld, m->N, m->dErr, m->stream,
-                                                 mirror_ptr(m), mirror_pos(m), mirror_len(m))
-                   : launch_set_state_f32<double>(view_of<double>(m), src, m->dNodeOld, m->N, m->dErr, m->stream,
-                                                  mirror_ptr(m), mirror_pos(m), mirror_len(m)),
+        KERNEL((m->prec == FEM_FP32 ? launch_upload<float, float>(m, src) : launch_upload<double, float>(m, src)),
                "state kernel");
     } else {
-        KERNEL(m->prec == FEM_FP32
-                   ? launch_set_state<float>(view_of<float>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream,
-                                             mirror_ptr(m), mirror_pos(m), mirror_len(m))
-                   : launch_set_state<double>(view_of<double>(m), m->dIn[i], m->dNodeOld, m->N, m->dErr, m->stream,
-                                              mirror_ptr(m), mirror_pos(m), mirror_len(m)),
+        KERNEL((m->prec == FEM_FP32 ? launch_upload<float, double>(m, m->dIn[i])
+                                    : launch_upload<double, double>(m, m->dIn[i])),
                "state kernel");
     }
     CU(cudaEventRecord(m->ev_in_free[i], m->stream));
