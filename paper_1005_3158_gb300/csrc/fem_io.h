@@ -23,6 +23,8 @@ template <typename real>
 int launch_set_state(StateView<real> v, const double *E_in, const int32_t *node_old, int64_t n,
                      int *err, void *stream, const int32_t *sh_ptr = nullptr,
                      const int32_t *mpos = nullptr, int64_t n_loc = 0);
+// (The read-back takes C, Lc, the phase bytes and the ranges from the view;
+// the C, Lc, ph and ranges arguments are not used.)
 template <typename real>
 int launch_get_temperature(StateView<real> v, const real *C, const real *Lc, const uint8_t *ph,
                            const real *ranges, double *T_out, const int32_t *node_old, int64_t n,
