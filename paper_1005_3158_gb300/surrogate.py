@@ -155,6 +155,37 @@ def _timed(fn):
     return e0.elapsed_time(e1)
 
 
+class HybridPolicy:
+    """The macro-step policy of fem_surrogate_solve, step by step: macro
+    step 0 is judged (if judge_every > 0); after a passed judgement the
+    network takes the next judge_every - 1 macro steps, after a failed one
+    the solver does, the span doubling with each further consecutive
+    failure (up to 2^MAX_BACKOFF judge_every); the step after the span is
+    judged again.  action(k) -> "judge" | "solver" | "network"; report
+    every judged step's outcome with judged(k, passed)."""
+
+    def __init__(self, judge_every):
+        self.J = int(judge_every)
+        self.next_judge = 0
+        self.plain_until = 0
+        self.fails = 0
+
+    def action(self, k):
+        if self.J > 0 and k == self.next_judge:
+            return "judge"
+        return "solver" if k < self.plain_until else "network"
+
+    def judged(self, k, passed):
+        span = self.J
+        if passed:
+            self.fails = 0
+        else:
+            span = self.J << min(self.fails, MAX_BACKOFF)
+            self.fails += 1
+            self.plain_until = k + span
+        self.next_judge = k + span
+
+
 def evaluate(p, theta, judge_every=8, tols=(2.0,), max_macro=4000, log=print):
     """One geometry: plain FP32 solve from the pour until the casting has
     solidified (plus 10 %); then, for every tolerance, the surrogate's
@@ -210,26 +241,18 @@ def evaluate(p, theta, judge_every=8, tols=(2.0,), max_macro=4000, log=print):
         err_t = [0.0]
         n_sg = n_pl = n_fail = 0
         worst_judge = 0.0
-        plain_until = next_judge = fails = 0
-        # the policy of fem_surrogate_solve (a failed judgement hands the
-        # span up to the next one to the solver, the span doubling with each
-        # further consecutive failure), one macro step at a time so that
+        # the policy of fem_surrogate_solve, one macro step at a time so that
         # every macro step can be read back
+        pol = HybridPolicy(judge_every)
         for k in range(n_macro):
-            if judge_every > 0 and k == next_judge:
+            act = pol.action(k)
+            if act == "judge":
                 _, b_, c, e = s.solve(1, 1, tol)
                 n_pl += b_
                 n_fail += c
                 worst_judge = max(worst_judge, e)
-                span = judge_every
-                if c:
-                    span = judge_every << min(fails, MAX_BACKOFF)
-                    fails += 1
-                    plain_until = k + span
-                else:
-                    fails = 0
-                next_judge = k + span
-            elif k < plain_until:
+                pol.judged(k, passed=not c)
+            elif act == "solver":
                 m2.step(MACRO, dt)
                 n_pl += 1
             else:
