@@ -36,3 +36,18 @@ def test_rank_helpers_single_process():
     assert bench.max_over_ranks(1.25, 1) == 1.25
     # whole-job throughput: units of all ranks over the slowest rank's time
     assert bench.job_throughput(1000, 10, 4, 2.0) == pytest.approx(1000 * 10 * 4 / 2.0)
+
+
+def test_traffic_record_names_the_digest_sources():
+    """The DRAM-traffic record lists the sources whose digest it carries,
+    the same ones bench.py hashes, and each entry's digest is a SHA-256
+    (bench.py reports the traffic only while the digest matches)."""
+    import bench
+    with open(bench.TRAFFIC_FILE) as fh:
+        rec = json.load(fh)
+    assert tuple(rec["sources"]) == bench.TRAFFIC_SOURCES
+    for f in bench.TRAFFIC_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, "paper_1005_3158_gb300", "csrc", f)), f
+    for e in rec["entries"]:
+        assert len(e["sources_sha256"]) == 64 and e["units"] > 0
+        assert e["dram_read_bytes"] > 0 and e["dram_write_bytes"] > 0
