@@ -49,3 +49,19 @@ def test_explicit_block_size_is_kept():
     with fem.Mesh(p, "fp32", block_elems=2560) as m:   # no automatic shrink
         ne = m.plan("blocks").reshape(-1, 16)[:, 1]
         assert ne.max() > 1792
+
+
+def test_conductivity_tables_keep_the_l2_kernel_size():
+    """k(T) reads the conductances from L2 like constant k, so it gets the
+    same automatic block size (four CTAs per SM); the apparent capacity
+    keeps them in shared memory (its element capacities go over them) and
+    stays at 2,048."""
+    p = mg.block_with_cores(40)
+    p.k_tables = ((0, [300.0, 900.0], [150.0, 120.0]), (1, [300.0, 900.0], [30.0, 26.0]))
+    with fem.Mesh(p, "fp32") as m:
+        ne = m.plan("blocks").reshape(-1, 16)[:, 1]
+        assert 1024 <= ne.max() <= 1792
+        assert _smem_l2(m) <= FOUR_CTA_SMEM
+    with fem.Mesh(mg.block_with_cores(40), "fp32", formulation="apparent") as m:
+        ne = m.plan("blocks").reshape(-1, 16)[:, 1]
+        assert ne.max() > 1792 and ne.max() <= 2048
